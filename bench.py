@@ -1,0 +1,372 @@
+"""Throughput of the out-of-core stencil pipeline with on-the-fly compression.
+
+Workload (default): 3D 7-point heat equation, FP32 compute, 1024^3 grid held
+in pinned host memory, device budget 1 GiB (the plan streams z-slabs),
+temporal blocking k = 4, 64 time steps per bench step, slabs stored and
+transferred as FR4 at 16 bits/value; the same run with uncompressed FP32
+slabs (and BF16, FR4 at 8/12/24) is measured on the same GPU for the
+compressed-vs-uncompressed comparison.  Error is stated against the FP64
+oracle on a sampled central 128^3 sub-box (exact dependency cone).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  N > 1 runs N independent replicas (the
+method works on one GPU; there is no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 1024
+NSTEPS = 64
+K = 4
+BUDGET = 1 << 30
+MAIN = ("fr4", 16)
+COMPARE = [("fp32", 0), ("bf16", 0), ("fr4", 8), ("fr4", 12), ("fr4", 24)]
+METRIC = "Gpts/s out-of-core (compressed vs uncompressed, same GB300) at stated L2 error; % roofline"
+WORKLOAD = "heat7 1024^3 FP32, device budget 1 GiB, k=4, 64 steps/bench step"
+
+
+def fmt_name(fmt, rate):
+    return f"fr4-{rate}" if fmt == "fr4" else fmt
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1", "0x1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl != "reference" else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value, device=None):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- CPU oracle legs
+def oracle_sample(nsample=128, steps=8):
+    """The oracle's version of one bench step on a bounded sample: FP64 heat7
+    with the FR4-16 storage round trip after every pass of k = 4 steps."""
+    import oracle
+    from synth import smooth_random_field
+    u0 = smooth_random_field((nsample,) * 3, 32.0, seed=2)
+    t = time.perf_counter()
+    oracle.heat7_storage_pipeline(u0, steps, K, "fr4", 16)
+    dt = time.perf_counter() - t
+    return nsample ** 3 * steps / dt / 1e9, dt, oracle.threads()
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the CPU oracle as it stands, on the host cores."""
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    ns, steps = 128, 8
+    for _ in range(args.warmup):
+        oracle_sample(ns, steps)
+    vals, total = [], 0.0
+    for _ in range(args.steps):
+        v, dt, cores = oracle_sample(ns, steps)
+        vals.append(v)
+        total += dt
+    value = ns ** 3 * steps * args.steps / total / 1e9
+    sample = f"{ns}^3 smooth field, {steps} steps (2 passes of k=4), FP64 heat7 + FR4-16 round trips, per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "oracle_sample": sample},
+            "cpu_baseline": {"value": value, "unit": "Gpts/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU arm
+def make_plan(ooc, fmt, rate, profile=1):
+    return ooc.Plan(nx=N, ny=N, nz=N, stencil="heat7", k=K, rw_format=fmt, rw_rate=rate or 16,
+                    device_budget_bytes=BUDGET, profile=profile)
+
+
+def timed_steps(torch, plan, nsteps, reps):
+    """reps calls of ooc_step(nsteps), each bracketed by CUDA events on the
+    plan's H2D (first work) and D2H (last work) streams; returns ms list."""
+    out = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(plan.streams[0])
+        plan.step(nsteps)
+        e1.record(plan.streams[2])
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def sampled_error(oracle, u0, got):
+    c0, c1 = N // 2 - 64, N // 2 + 64
+    s = NSTEPS
+    sub = u0[c0 - s:c1 + s, c0 - s:c1 + s, c0 - s:c1 + s].astype(np.float64)
+    exact = oracle.heat7_run(sub, s)[s:-s, s:-s, s:-s]
+    return oracle.error_metrics(got[c0:c1, c0:c1, c0:c1], exact)
+
+
+def run_gpu(args, world, rank, local):
+    import torch
+
+    import paper_2109_05410_gb300 as ooc
+    from synth import smooth_random_field
+
+    torch.cuda.set_device(local)
+    ooc.build()
+    ooc.lib()
+    dev = torch.device("cuda", local)
+    hbm_peak, peak_src = load_peaks()
+    u0 = smooth_random_field((N, N, N), 32.0, seed=2)
+    pts = N ** 3
+
+    # ---- headline: FR4-16 slabs ------------------------------------------------
+    plan = make_plan(ooc, *MAIN)
+    info = plan.info()
+    plan.set_field(0, u0)
+    for _ in range(args.warmup):
+        plan.step(NSTEPS)
+    plan.reset_stats()
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms = timed_steps(torch, plan, NSTEPS, args.steps)
+    torch.cuda.synchronize()
+    barrier(world)
+    st = plan.stats()
+    total_ms = max_over_ranks(world, sum(ms), dev)
+    ms_per_step = total_ms / args.steps
+    value = world * pts * NSTEPS * args.steps / (total_ms / 1e3) / 1e9
+
+    # per-kernel rooflines from the live per-launch events of the timed region
+    nsten = pts * NSTEPS * args.steps
+    rate = MAIN[1]
+    kernels = {
+        "heat7_stencil": {"ms": st["ms_stencil"], "launches": st["n_stencil"], "bytes": 8 * nsten},
+        "fr4_decode": {"ms": st["ms_decode"], "launches": st["n_decode"], "bytes": (4 + rate / 8) * pts * st["passes"]},
+        "fr4_encode": {"ms": st["ms_encode"], "launches": st["n_encode"], "bytes": (4 + rate / 8) * pts * st["passes"]},
+    }
+    for kv in kernels.values():
+        kv["GBs"] = kv["bytes"] / (kv["ms"] / 1e3) / 1e9 if kv["ms"] > 0 else None
+        kv["frac_hbm"] = kv["GBs"] / hbm_peak if kv["GBs"] else None
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    dk = kernels[dom]
+    launches = max(dk["launches"], 1)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": dk["GBs"], "peak": hbm_peak, "unit": "GB/s",
+                "frac": dk["frac_hbm"], "traffic": None,
+                "bytes_per_launch": dk["bytes"] / launches, "ms_per_launch": dk["ms"] / launches,
+                "peak_source": peak_src}
+    h2d_GBs = st["h2d_bytes"] / (st["ms_h2d"] / 1e3) / 1e9 if st["ms_h2d"] > 0 else None
+    d2h_GBs = st["d2h_bytes"] / (st["ms_d2h"] / 1e3) / 1e9 if st["ms_d2h"] > 0 else None
+    plan.close()
+    del plan
+    torch.cuda.empty_cache()
+
+    # ---- end to end through the public API with host FP32 buffers ---------------
+    plan = make_plan(ooc, *MAIN, profile=0)
+    e2e_ms = []
+    host_out = np.empty((N, N, N), dtype=np.float32)
+    for rep in range(1 + min(args.steps, 2)):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(plan.streams[0])
+        plan.set_field(0, u0)
+        plan.step(NSTEPS)
+        plan.get_field(0, out=host_out)
+        e1.record(plan.streams[2])
+        e1.synchronize()
+        if rep > 0:
+            e2e_ms.append(e0.elapsed_time(e1))
+    st_e2e = plan.stats()
+    plan.close()
+    del plan
+    torch.cuda.empty_cache()
+    e2e_ms_max = max_over_ranks(world, statistics.mean(e2e_ms), dev)
+    e2e_value = world * pts * NSTEPS / (e2e_ms_max / 1e3) / 1e9
+    field_bytes = pts * 4
+    nrep = len(e2e_ms) + 1
+    h2d_step = field_bytes + st_e2e["h2d_bytes"] // nrep
+    d2h_step = field_bytes + st_e2e["d2h_bytes"] // nrep
+
+    # ---- compressed vs uncompressed on the same GPU ----------------------------
+    formats = {}
+    for fmt, r in COMPARE:
+        p = make_plan(ooc, fmt, r, profile=0)
+        p.set_field(0, u0)
+        p.step(NSTEPS)  # warm-up
+        m = timed_steps(torch, p, NSTEPS, max(1, min(args.steps, 2)))
+        formats[fmt_name(fmt, r)] = {"Gpts": pts * NSTEPS / (statistics.mean(m) / 1e3) / 1e9,
+                                     "slab_planes": p.info()["slab_planes"], "nslab": p.info()["nslab"]}
+        p.close()
+        del p
+        torch.cuda.empty_cache()
+    formats[fmt_name(*MAIN)] = {"Gpts": value / world, "slab_planes": info["slab_planes"], "nslab": info["nslab"]}
+
+    if rank != 0:
+        return 0
+
+    # ---- stated accuracy and the CPU oracle baseline (rank 0, N = 1 only) --------
+    err = None
+    cpu = None
+    if world == 1:
+        import oracle
+        oracle.build()
+        m = sampled_error(oracle, u0, host_out)  # the e2e run: exactly 64 steps from u0
+        err = {"rel_l2": m["rel_l2"], "max_abs": m["max_abs"], "mean_rel_sampled": m["mean_rel_sampled"],
+               "vs": "FP64 oracle, central 128^3 sub-box after 64 steps"}
+        v, dt, cores = oracle_sample(384, 8)
+        cpu = {"value": v, "unit": "Gpts/s", "cores": cores, "kind": "oracle",
+               "sample": f"384^3 smooth field, 8 steps (2 passes of k=4), FP64 heat7 + FR4-16 round trips, {dt:.1f} s"}
+
+    fp32 = formats["fp32"]["Gpts"]
+    link_dir = 170.0  # GB/s each way with both directions busy (measured H2D/D2H probe)
+    link_roof = {f: link_dir * 1e9 * K / (bits / 8) / 1e9 for f, bits in
+                 (("fp32", 32), ("bf16", 16), ("fr4-8", 8), ("fr4-12", 12), ("fr4-16", 16), ("fr4-24", 24))}
+    hbm_roof = hbm_peak * 1e9 / 8 / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "storage": fmt_name(*MAIN), "grid": [N, N, N], "k": K,
+                   "time_steps_per_bench_step": NSTEPS, "device_budget_bytes": BUDGET,
+                   "slab_planes": info["slab_planes"], "nslab": info["nslab"], "ring_planes": info["ring_planes"],
+                   "device_bytes": info["device_bytes"], "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (4 GiB field streamed from pinned host memory each pass)"},
+        "error": err,
+        "compressed_vs_uncompressed": {"speedup": value / world / fp32 if fp32 else None, "formats": formats},
+        "pipeline_roofline": {"hbm_Gpts": hbm_roof, "link_Gpts": link_roof,
+                              "frac_of_min": (value / world) / min(hbm_roof, link_roof[fmt_name(*MAIN)]),
+                              "link_GBs_each_way_assumed": link_dir,
+                              "h2d_GBs_per_copy": h2d_GBs, "d2h_GBs_per_copy": d2h_GBs},
+        "roofline": roofline,
+        "kernels": kernels,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "Gpts/s", "h2d_bytes_per_step": int(h2d_step),
+                "d2h_bytes_per_step": int(d2h_step),
+                "what": "ooc_set_field(host FP32) + ooc_step(64) + ooc_get_field(host FP32)"},
+        "gpu_launches": int(st["kernel_launches"]),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    world, rank, local = dist_init(args)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, world, rank)
+        return run_gpu(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,183 @@
+/*
+ * ooc.h -- C ABI of the out-of-core stencil library with on-the-fly
+ * fixed-rate compression (libooc.so, CUDA sm_103a).
+ *
+ * The method (Shen, Wu, Okita, Ino, "Accelerating GPU-Based Out-of-Core
+ * Stencil Computation with On-the-Fly Compression"):
+ *   - Section III: a grid larger than device memory is cut into blocks
+ *     (here z-slabs) that stream to and from the GPU with their halo;
+ *     contiguous blocks share the common region on the GPU instead of
+ *     re-sending it (region sharing, Fig. 2), and each block is advanced
+ *     several time steps per transfer (temporal blocking, Section VI setup).
+ *   - Section IV: the fixed-rate lossy codec stores R bits per value, so
+ *     compressed sizes are known and device buffers are preallocated.
+ *   - Section V-A: separate compression -- each slab's output is written
+ *     back as two independently compressed units, the remainder R_i and the
+ *     common region C_{i-1} (Fig. 4).
+ *   - Section V-B: copies and kernels overlap on three CUDA streams (Fig. 5).
+ *
+ * Conventions for every entry point:
+ *   - Grids are [z][y][x], x fastest; nx, ny, nz are multiples of 4.
+ *   - Pointers are plain host or device addresses as stated; the library
+ *     never frees memory it did not allocate, and allocates no device
+ *     memory at all: the caller passes a device arena (its size *is* the
+ *     device budget) and a pinned host arena.
+ *   - Every function returns an ooc_status and never aborts the process.
+ *   - Streams are cudaStream_t passed as void* (0 = legacy default stream).
+ */
+#ifndef OOC_H
+#define OOC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int ooc_status;
+#define OOC_OK 0
+#define OOC_E_INVALID 1  /* bad argument, shape, rate or call order */
+#define OOC_E_BUDGET 2   /* device arena too small for any slab plan */
+#define OOC_E_ALLOC 3    /* host-side bookkeeping allocation failed */
+#define OOC_E_CUDA 4     /* a CUDA runtime call or kernel launch failed */
+#define OOC_E_TIMEOUT 5  /* a bounded wait on the GPU ran past its deadline */
+#define OOC_E_CORRUPT 6  /* inconsistent stored data (e.g. non-finite values) */
+
+/* Stencils (Section III's neighbour average; Section VI's 25-point
+ * acoustic propagator with HALO = 4, Table I). */
+#define OOC_HEAT7 1
+#define OOC_WAVE25 2
+
+/* Storage formats of a field in host memory and on the wire. */
+#define OOC_FMT_FP32 0  /* 4 bytes per value, uncompressed */
+#define OOC_FMT_BF16 1  /* 2 bytes per value, round to nearest even */
+#define OOC_FMT_FR4 2   /* fixed-rate 4^3-block codec, `rate` bits per value */
+
+/* Field indices.  HEAT7: 0 = u.  WAVE25: 0 = p^t, 1 = p^{t-1} (both
+ * read-write, Section VI), 2 = kappa = (v dt / dx)^2 (read-only). */
+#define OOC_FIELD_U 0
+#define OOC_FIELD_P 0
+#define OOC_FIELD_P_PREV 1
+#define OOC_FIELD_KAPPA 2
+
+typedef struct {
+    int64_t nx, ny, nz;          /* grid, multiples of 4 */
+    int32_t stencil;             /* OOC_HEAT7 or OOC_WAVE25 */
+    int32_t k;                   /* temporal block: steps per transfer, >= 1 */
+    double r;                    /* heat7 coefficient (1/6 = neighbour average) */
+    int32_t rw_format, rw_rate;  /* read-write fields: format and bits/value */
+    int32_t ro_format, ro_rate;  /* wave25 kappa: format and bits/value */
+    int64_t device_budget_bytes; /* device arena size the plan must fit in */
+    int32_t slab_planes;         /* slab thickness T (multiple of 4); 0 = largest that fits */
+    int32_t profile;             /* 1 = time every launch and copy with CUDA events */
+    int64_t wait_timeout_ms;     /* deadline for host waits on the GPU; 0 = 600000 */
+} ooc_config;
+
+typedef struct ooc_plan ooc_plan;
+
+typedef struct {
+    int64_t steps_done;        /* time steps completed since bind */
+    int64_t passes;            /* temporal-block passes executed */
+    int64_t slabs;             /* slab visits executed */
+    int64_t h2d_bytes, d2h_bytes;
+    int64_t kernel_launches;   /* launches of this library's kernels in ooc_step */
+    /* Filled only with profile = 1 (summed CUDA-event durations, ms): */
+    double ms_decode, ms_stencil, ms_encode, ms_h2d, ms_d2h;
+    int64_t n_decode, n_stencil, n_encode, n_h2d, n_d2h;
+    double ms_last_step;       /* wall time of the last ooc_step call (host clock) */
+} ooc_stats;
+
+/* Geometry of a plan, for inspection and host-side checks. */
+typedef struct {
+    int64_t slab_planes, nslab, common_planes /* W */, halo /* h */;
+    int64_t ring_planes /* Z */, nrings;
+    int64_t device_bytes, host_bytes;
+    int64_t staging_in_bytes, staging_out_bytes; /* per buffer, per field */
+} ooc_plan_info;
+
+/* Static string for a status code. */
+const char *ooc_status_string(ooc_status s);
+
+/* Bytes of an nx*ny*nz FP32 field stored by the fixed-rate codec at `rate`
+ * bits per value (Section IV: R bits per value, a size fixed in advance):
+ * nx*ny*nz*rate/8.  Returns 0 for invalid arguments. */
+size_t ooc_compressed_bytes(int64_t nx, int64_t ny, int64_t nz, int rate);
+
+/* Compress an FP32 device field d_in[nz][ny][nx] into d_out (device,
+ * ooc_compressed_bytes(...) bytes, 4-byte aligned) on `stream`,
+ * asynchronously.  Rate 1..64 bits/value.  Inputs must be finite.  The
+ * stream layout is 4^3 blocks, bx fastest, each exactly 2*rate 32-bit
+ * words, so any 4-aligned z range is a contiguous byte range (Section V-A's
+ * separately compressed units).  Returns OOC_E_INVALID on bad shapes, rates,
+ * alignment or out_cap < required; OOC_E_CUDA if the launch fails. */
+ooc_status ooc_compress(const float *d_in, int64_t nx, int64_t ny, int64_t nz, int rate,
+                        void *d_out, size_t out_cap, void *stream);
+
+/* Inverse of ooc_compress: d_in holds in_bytes >= ooc_compressed_bytes(...)
+ * bytes of codec stream (device); writes d_out[nz][ny][nx] (device).  Any
+ * word content decodes without faulting. */
+ooc_status ooc_decompress(const void *d_in, size_t in_bytes, int64_t nx, int64_t ny, int64_t nz,
+                          int rate, float *d_out, void *stream);
+
+/* BF16 storage: d_out[i] = bfloat16 of d_in[i], round to nearest even, NaN
+ * kept quiet; and the exact widening back.  Device pointers, n values. */
+ooc_status ooc_bf16_pack(const float *d_in, uint16_t *d_out, int64_t n, void *stream);
+ooc_status ooc_bf16_unpack(const uint16_t *d_in, float *d_out, int64_t n, void *stream);
+
+/* In-core reference runs of the same stencil kernels the pipeline uses
+ * (whole grid as one window), for parity checks.  heat7: nsteps Jacobi steps
+ * of u (device) with scratch d_tmp (device, same size); result in d_u.
+ * wave25: from (d_p, d_pprev) = (p^t, p^{t-1}) to (p^{t+n}, p^{t+n-1}),
+ * adding h_w[t + s] (host array, may be NULL) at (sx, sy, sz) in step s
+ * (0-based); pass sx < 0 for no source. */
+ooc_status ooc_heat7_steps(float *d_u, float *d_tmp, int64_t nx, int64_t ny, int64_t nz, double r,
+                           int64_t nsteps, void *stream);
+ooc_status ooc_wave25_steps(float *d_p, float *d_pprev, const float *d_kappa, int64_t nx, int64_t ny,
+                            int64_t nz, int64_t sx, int64_t sy, int64_t sz, const float *h_w, int64_t t,
+                            int64_t nsteps, void *stream);
+
+/* Plan an out-of-core run (Section III decomposition with Section V-A
+ * units).  Validates `cfg`, chooses the slab thickness T (largest multiple of
+ * 4 that fits device_budget_bytes unless cfg->slab_planes is set) and
+ * reports the device arena and pinned host arena sizes needed.  No CUDA call
+ * is made.  Errors: OOC_E_INVALID (shape not a multiple of 4, k < 1, rate
+ * outside 1..64, unknown format/stencil, T not a multiple of 4),
+ * OOC_E_BUDGET (no T fits), OOC_E_ALLOC. */
+ooc_status ooc_plan_create(const ooc_config *cfg, ooc_plan **out, size_t *device_bytes, size_t *host_bytes);
+
+ooc_status ooc_plan_get_info(const ooc_plan *plan, ooc_plan_info *info);
+
+/* Bind caller-owned memory and streams.  device_arena: >= device_bytes,
+ * 256-byte aligned.  host_arena: >= host_bytes, pinned (cudaHostAlloc or
+ * torch pin_memory), 16-byte aligned; it holds every field in its storage
+ * format and is updated in place by each pass.  streams[0..2] = H2D,
+ * compute, D2H (Fig. 5).  Creates CUDA events; allocates no device memory. */
+ooc_status ooc_plan_bind(ooc_plan *plan, void *device_arena, size_t device_bytes, void *host_arena,
+                         size_t host_bytes, void *const streams[3]);
+
+/* Store / fetch a whole FP32 field (host pointers, nx*ny*nz floats) into /
+ * out of the plan's host storage, encoding / decoding on the GPU.  Blocks
+ * until done.  Must not overlap an ooc_step on the same plan. */
+ooc_status ooc_set_field(ooc_plan *plan, int field, const float *host_src);
+ooc_status ooc_get_field(ooc_plan *plan, int field, float *host_dst);
+
+/* Point source of the wave stencil: p^{n+1}(sx,sy,sz) += w[n] for n < nw
+ * (host array, copied).  nw = 0 removes it. */
+ooc_status ooc_set_source(ooc_plan *plan, int64_t sx, int64_t sy, int64_t sz, const float *w, int64_t nw);
+
+/* Advance nsteps time steps: ceil(nsteps/k) passes of the slab pipeline
+ * (the last pass may be shorter).  Returns after the last D2H has landed,
+ * or OOC_E_TIMEOUT if that takes longer than wait_timeout_ms. */
+ooc_status ooc_step(ooc_plan *plan, int64_t nsteps);
+
+ooc_status ooc_get_stats(const ooc_plan *plan, ooc_stats *stats);
+ooc_status ooc_reset_stats(ooc_plan *plan);
+
+/* Releases the plan's events and host bookkeeping (not the arenas). */
+void ooc_plan_destroy(ooc_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OOC_H */

@@ -1,0 +1,294 @@
+"""Out-of-core stencil computation with on-the-fly fixed-rate compression
+for one GB300 (sm_103a).
+
+This package is a thin ctypes binding over the C ABI of ``libooc.so``
+(declared in ``include/ooc.h``).  Every step of the computation runs in the
+library's CUDA kernels; Python only marshals arguments and uses PyTorch for
+device memory, pinned host memory and streams.  If the library is missing
+the functions raise instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build_mod
+
+__all__ = [
+    "OOC_HEAT7", "OOC_WAVE25", "OOC_FMT_FP32", "OOC_FMT_BF16", "OOC_FMT_FR4",
+    "OocConfig", "OocStats", "OocPlanInfo", "OocError", "lib", "build",
+    "ooc_status_string", "ooc_compressed_bytes", "ooc_compress", "ooc_decompress",
+    "ooc_bf16_pack", "ooc_bf16_unpack", "ooc_heat7_steps", "ooc_wave25_steps", "Plan",
+]
+
+OOC_HEAT7, OOC_WAVE25 = 1, 2
+OOC_FMT_FP32, OOC_FMT_BF16, OOC_FMT_FR4 = 0, 1, 2
+FORMATS = {"fp32": OOC_FMT_FP32, "bf16": OOC_FMT_BF16, "fr4": OOC_FMT_FR4}
+STENCILS = {"heat7": OOC_HEAT7, "wave25": OOC_WAVE25}
+
+
+class OocConfig(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64),
+        ("stencil", ctypes.c_int32), ("k", ctypes.c_int32), ("r", ctypes.c_double),
+        ("rw_format", ctypes.c_int32), ("rw_rate", ctypes.c_int32),
+        ("ro_format", ctypes.c_int32), ("ro_rate", ctypes.c_int32),
+        ("device_budget_bytes", ctypes.c_int64), ("slab_planes", ctypes.c_int32),
+        ("profile", ctypes.c_int32), ("wait_timeout_ms", ctypes.c_int64),
+    ]
+
+
+class OocStats(ctypes.Structure):
+    _fields_ = [
+        ("steps_done", ctypes.c_int64), ("passes", ctypes.c_int64), ("slabs", ctypes.c_int64),
+        ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+        ("ms_decode", ctypes.c_double), ("ms_stencil", ctypes.c_double), ("ms_encode", ctypes.c_double),
+        ("ms_h2d", ctypes.c_double), ("ms_d2h", ctypes.c_double),
+        ("n_decode", ctypes.c_int64), ("n_stencil", ctypes.c_int64), ("n_encode", ctypes.c_int64),
+        ("n_h2d", ctypes.c_int64), ("n_d2h", ctypes.c_int64),
+        ("ms_last_step", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class OocPlanInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "slab_planes", "nslab", "common_planes", "halo", "ring_planes", "nrings",
+        "device_bytes", "host_bytes", "staging_in_bytes", "staging_out_bytes")]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class OocError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__(f"{what}: {ooc_status_string(status)} ({status})")
+        self.status = status
+
+
+_lib = None
+_SIGS = {
+    "ooc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "ooc_compressed_bytes": (ctypes.c_size_t, [ctypes.c_int64] * 3 + [ctypes.c_int]),
+    "ooc_compress": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int64] * 3 + [ctypes.c_int, ctypes.c_void_p,
+                                                                              ctypes.c_size_t, ctypes.c_void_p]),
+    "ooc_decompress": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t] + [ctypes.c_int64] * 3
+                       + [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "ooc_bf16_pack": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "ooc_bf16_unpack": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "ooc_heat7_steps": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p] + [ctypes.c_int64] * 3
+                        + [ctypes.c_double, ctypes.c_int64, ctypes.c_void_p]),
+    "ooc_wave25_steps": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int64] * 6
+                         + [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]),
+    "ooc_plan_create": (ctypes.c_int, [ctypes.POINTER(OocConfig), ctypes.POINTER(ctypes.c_void_p),
+                                       ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+    "ooc_plan_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(OocPlanInfo)]),
+    "ooc_plan_bind": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                     ctypes.c_size_t, ctypes.c_void_p * 3]),
+    "ooc_set_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "ooc_get_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "ooc_set_source": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int64] * 3 + [ctypes.c_void_p, ctypes.c_int64]),
+    "ooc_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "ooc_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(OocStats)]),
+    "ooc_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
+    "ooc_plan_destroy": (None, [ctypes.c_void_p]),
+}
+
+
+def build(force=False):
+    """Compile libooc.so in-tree (nvcc, sm_103a)."""
+    return _build_mod.build(force=force)
+
+
+def lib():
+    """The loaded libooc.so.  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        path = _build_mod.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libooc.so is not built ({path}); call paper_2109_05410_gb300.build()")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status, what):
+    if status != 0:
+        raise OocError(status, what)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def ooc_status_string(s):
+    return lib().ooc_status_string(int(s)).decode()
+
+
+def ooc_compressed_bytes(nx, ny, nz, rate):
+    return int(lib().ooc_compressed_bytes(nx, ny, nz, rate))
+
+
+def ooc_compress(d_in, rate, d_out=None, stream=None):
+    """Encode a float32 CUDA tensor [nz, ny, nx] at ``rate`` bits/value into
+    ``d_out`` (uint8 CUDA tensor, allocated if None); returns d_out."""
+    import torch
+    nz, ny, nx = d_in.shape
+    nbytes = ooc_compressed_bytes(nx, ny, nz, rate)
+    if d_out is None:
+        d_out = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=d_in.device)
+    _check(lib().ooc_compress(_ptr(d_in), nx, ny, nz, rate, _ptr(d_out), d_out.numel() * d_out.element_size(),
+                              _stream(stream)), "ooc_compress")
+    return d_out
+
+
+def ooc_decompress(d_in, shape, rate, d_out=None, stream=None):
+    import torch
+    nz, ny, nx = shape
+    if d_out is None:
+        d_out = torch.empty(shape, dtype=torch.float32, device=d_in.device)
+    _check(lib().ooc_decompress(_ptr(d_in), d_in.numel() * d_in.element_size(), nx, ny, nz, rate, _ptr(d_out),
+                                _stream(stream)), "ooc_decompress")
+    return d_out
+
+
+def ooc_bf16_pack(d_in, d_out=None, stream=None):
+    import torch
+    if d_out is None:
+        d_out = torch.empty(d_in.shape, dtype=torch.int16, device=d_in.device)
+    _check(lib().ooc_bf16_pack(_ptr(d_in), _ptr(d_out), d_in.numel(), _stream(stream)), "ooc_bf16_pack")
+    return d_out
+
+
+def ooc_bf16_unpack(d_in, d_out=None, stream=None):
+    import torch
+    if d_out is None:
+        d_out = torch.empty(d_in.shape, dtype=torch.float32, device=d_in.device)
+    _check(lib().ooc_bf16_unpack(_ptr(d_in), _ptr(d_out), d_in.numel(), _stream(stream)), "ooc_bf16_unpack")
+    return d_out
+
+
+def ooc_heat7_steps(d_u, d_tmp, nsteps, r=1.0 / 6.0, stream=None):
+    nz, ny, nx = d_u.shape
+    _check(lib().ooc_heat7_steps(_ptr(d_u), _ptr(d_tmp), nx, ny, nz, float(r), int(nsteps), _stream(stream)),
+           "ooc_heat7_steps")
+    return d_u
+
+
+def ooc_wave25_steps(d_p, d_pprev, d_kappa, nsteps, src=None, w=None, t=0, stream=None):
+    """Leapfrog in place on (d_p, d_pprev); ``src`` = (sx, sy, sz) and ``w`` a
+    float32 numpy series indexed by absolute step."""
+    nz, ny, nx = d_p.shape
+    if src is None or w is None:
+        sx, sy, sz, wp = -1, -1, -1, None
+    else:
+        sx, sy, sz = src
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        if len(w) < t + nsteps:
+            raise ValueError("source series shorter than t + nsteps")
+        wp = w.ctypes.data_as(ctypes.c_void_p)
+    _check(lib().ooc_wave25_steps(_ptr(d_p), _ptr(d_pprev), _ptr(d_kappa), nx, ny, nz, sx, sy, sz, wp, int(t),
+                                  int(nsteps), _stream(stream)), "ooc_wave25_steps")
+    return d_p, d_pprev
+
+
+def _fmt(v):
+    return FORMATS[v] if isinstance(v, str) else int(v)
+
+
+class Plan:
+    """An out-of-core run bound to torch-allocated arenas and three torch
+    streams (H2D, compute, D2H).  Configuration keys mirror ``ooc_config``:
+    nx, ny, nz, stencil ('heat7'|'wave25'), k, r, rw_format, rw_rate,
+    ro_format, ro_rate, device_budget_bytes, slab_planes, profile,
+    wait_timeout_ms."""
+
+    def __init__(self, device=0, **kw):
+        import torch
+        c = OocConfig()
+        c.nx, c.ny, c.nz = kw["nx"], kw["ny"], kw["nz"]
+        st = kw.get("stencil", "heat7")
+        c.stencil = STENCILS[st] if isinstance(st, str) else int(st)
+        c.k = kw.get("k", 1)
+        c.r = kw.get("r", 1.0 / 6.0)
+        c.rw_format = _fmt(kw.get("rw_format", "fp32"))
+        c.rw_rate = kw.get("rw_rate", 16)
+        c.ro_format = _fmt(kw.get("ro_format", "fp32"))
+        c.ro_rate = kw.get("ro_rate", 16)
+        c.device_budget_bytes = kw.get("device_budget_bytes", 0)
+        c.slab_planes = kw.get("slab_planes", 0)
+        c.profile = int(kw.get("profile", 0))
+        c.wait_timeout_ms = kw.get("wait_timeout_ms", 0)
+        self.config = c
+        self.shape = (c.nz, c.ny, c.nx)
+        self._h = ctypes.c_void_p()
+        dev_b, host_b = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(lib().ooc_plan_create(ctypes.byref(c), ctypes.byref(self._h), ctypes.byref(dev_b),
+                                     ctypes.byref(host_b)), "ooc_plan_create")
+        self.device_bytes, self.host_bytes = dev_b.value, host_b.value
+        self.device = torch.device("cuda", device)
+        self.dev_arena = torch.empty(max(self.device_bytes, 256), dtype=torch.uint8, device=self.device)
+        self.host_arena = torch.empty(max(self.host_bytes, 256), dtype=torch.uint8, pin_memory=True)
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(3)]
+        arr = (ctypes.c_void_p * 3)(*[s.cuda_stream for s in self.streams])
+        _check(lib().ooc_plan_bind(self._h, _ptr(self.dev_arena), self.dev_arena.numel(), _ptr(self.host_arena),
+                                   self.host_arena.numel(), arr), "ooc_plan_bind")
+
+    def info(self):
+        i = OocPlanInfo()
+        _check(lib().ooc_plan_get_info(self._h, ctypes.byref(i)), "ooc_plan_get_info")
+        return i.as_dict()
+
+    def set_field(self, field, host_src):
+        a = np.ascontiguousarray(host_src, dtype=np.float32)
+        if a.shape != self.shape:
+            raise ValueError(f"field shape {a.shape} != {self.shape}")
+        _check(lib().ooc_set_field(self._h, int(field), a.ctypes.data_as(ctypes.c_void_p)), "ooc_set_field")
+
+    def get_field(self, field, out=None):
+        if out is None:
+            out = np.empty(self.shape, dtype=np.float32)
+        _check(lib().ooc_get_field(self._h, int(field), out.ctypes.data_as(ctypes.c_void_p)), "ooc_get_field")
+        return out
+
+    def set_source(self, sx, sy, sz, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        _check(lib().ooc_set_source(self._h, sx, sy, sz, w.ctypes.data_as(ctypes.c_void_p), w.size),
+               "ooc_set_source")
+
+    def step(self, nsteps):
+        _check(lib().ooc_step(self._h, int(nsteps)), "ooc_step")
+
+    def stats(self):
+        s = OocStats()
+        _check(lib().ooc_get_stats(self._h, ctypes.byref(s)), "ooc_get_stats")
+        return s.as_dict()
+
+    def reset_stats(self):
+        _check(lib().ooc_reset_stats(self._h), "ooc_reset_stats")
+
+    def close(self):
+        if self._h:
+            lib().ooc_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,153 @@
+// api.cu -- stand-alone entry points of the C ABI: codec, BF16, in-core
+// stencil runs and status strings.  See include/ooc.h for the contract.
+#include "common.cuh"
+
+using namespace ooc;
+
+namespace {
+
+bool dims_ok(int64_t nx, int64_t ny, int64_t nz)
+{
+    return nx > 0 && ny > 0 && nz > 0 && nx % 4 == 0 && ny % 4 == 0 && nz % 4 == 0 && nx <= (1ll << 30) &&
+           ny <= (1ll << 30) && nz <= (1ll << 30);
+}
+
+bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p % a) == 0; }
+
+ooc_status cuda_status(cudaError_t e) { return e == cudaSuccess ? OOC_OK : OOC_E_CUDA; }
+
+__global__ void bf16_pack_flat(const float *in, uint16_t *out, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t u = __float_as_uint(in[i]);
+        uint32_t h;
+        if ((u & 0x7FFFFFFFu) > 0x7F800000u)
+            h = (u >> 16) | 0x40u;
+        else
+            h = (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+        out[i] = (uint16_t)h;
+    }
+}
+
+__global__ void bf16_unpack_flat(const uint16_t *in, float *out, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __uint_as_float((uint32_t)in[i] << 16);
+}
+
+unsigned flat_grid(int64_t n)
+{
+    int64_t b = (n + 255) / 256;
+    return (unsigned)(b < 1 ? 1 : (b > 152 * 32 ? 152 * 32 : b));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ooc_status_string(ooc_status s)
+{
+    switch (s) {
+    case OOC_OK: return "ok";
+    case OOC_E_INVALID: return "invalid argument";
+    case OOC_E_BUDGET: return "device budget too small";
+    case OOC_E_ALLOC: return "host allocation failed";
+    case OOC_E_CUDA: return "CUDA error";
+    case OOC_E_TIMEOUT: return "timed out waiting for the GPU";
+    case OOC_E_CORRUPT: return "corrupt stored data";
+    default: return "unknown status";
+    }
+}
+
+size_t ooc_compressed_bytes(int64_t nx, int64_t ny, int64_t nz, int rate)
+{
+    if (!dims_ok(nx, ny, nz) || rate < 1 || rate > 64)
+        return 0;
+    return (size_t)nx * (size_t)ny * (size_t)nz * (size_t)rate / 8;
+}
+
+ooc_status ooc_compress(const float *d_in, int64_t nx, int64_t ny, int64_t nz, int rate, void *d_out, size_t out_cap,
+                        void *stream)
+{
+    if (!d_in || !d_out || !dims_ok(nx, ny, nz) || rate < 1 || rate > 64 || !aligned(d_in, 16) ||
+        !aligned(d_out, 4) || out_cap < ooc_compressed_bytes(nx, ny, nz, rate))
+        return OOC_E_INVALID;
+    return cuda_status(launch_fr4_encode(ConstRing{d_in, nz, 0}, nx, ny, 0, nz, rate, (uint32_t *)d_out,
+                                         (cudaStream_t)stream));
+}
+
+ooc_status ooc_decompress(const void *d_in, size_t in_bytes, int64_t nx, int64_t ny, int64_t nz, int rate,
+                          float *d_out, void *stream)
+{
+    if (!d_in || !d_out || !dims_ok(nx, ny, nz) || rate < 1 || rate > 64 || !aligned(d_in, 4) ||
+        !aligned(d_out, 16) || in_bytes < ooc_compressed_bytes(nx, ny, nz, rate))
+        return OOC_E_INVALID;
+    return cuda_status(launch_fr4_decode((const uint32_t *)d_in, nx, ny, 0, nz, rate, Ring{d_out, nz, 0},
+                                         (cudaStream_t)stream));
+}
+
+ooc_status ooc_bf16_pack(const float *d_in, uint16_t *d_out, int64_t n, void *stream)
+{
+    if (n < 0 || (n > 0 && (!d_in || !d_out)))
+        return OOC_E_INVALID;
+    if (n == 0)
+        return OOC_OK;
+    bf16_pack_flat<<<flat_grid(n), 256, 0, (cudaStream_t)stream>>>(d_in, d_out, n);
+    return cuda_status(cudaGetLastError());
+}
+
+ooc_status ooc_bf16_unpack(const uint16_t *d_in, float *d_out, int64_t n, void *stream)
+{
+    if (n < 0 || (n > 0 && (!d_in || !d_out)))
+        return OOC_E_INVALID;
+    if (n == 0)
+        return OOC_OK;
+    bf16_unpack_flat<<<flat_grid(n), 256, 0, (cudaStream_t)stream>>>(d_in, d_out, n);
+    return cuda_status(cudaGetLastError());
+}
+
+ooc_status ooc_heat7_steps(float *d_u, float *d_tmp, int64_t nx, int64_t ny, int64_t nz, double r, int64_t nsteps,
+                           void *stream)
+{
+    if (!d_u || !d_tmp || !dims_ok(nx, ny, nz) || nsteps < 0)
+        return OOC_E_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    float *a = d_u, *b = d_tmp;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        cudaError_t e = launch_heat7(ConstRing{a, nz, 0}, Ring{b, nz, 0}, nx, ny, nz, 0, nz, (float)r, st);
+        if (e != cudaSuccess)
+            return OOC_E_CUDA;
+        float *t = a;
+        a = b;
+        b = t;
+    }
+    if (a != d_u)
+        return cuda_status(cudaMemcpyAsync(d_u, a, sizeof(float) * nx * ny * nz, cudaMemcpyDeviceToDevice, st));
+    return OOC_OK;
+}
+
+ooc_status ooc_wave25_steps(float *d_p, float *d_pprev, const float *d_kappa, int64_t nx, int64_t ny, int64_t nz,
+                            int64_t sx, int64_t sy, int64_t sz, const float *h_w, int64_t t, int64_t nsteps,
+                            void *stream)
+{
+    if (!d_p || !d_pprev || !d_kappa || !dims_ok(nx, ny, nz) || nsteps < 0 || t < 0)
+        return OOC_E_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    float *a = d_p, *b = d_pprev;  // a holds p^n, b holds p^{n-1}
+    for (int64_t s = 0; s < nsteps; ++s) {
+        const bool src = sx >= 0 && h_w != nullptr;
+        const float w = src ? h_w[t + s] : 0.0f;
+        cudaError_t e = launch_wave25(ConstRing{a, nz, 0}, Ring{b, nz, 0}, ConstRing{d_kappa, nz, 0}, nx, ny, nz, 0,
+                                      nz, src ? sx : -1, sy, sz, w, st);
+        if (e != cudaSuccess)
+            return OOC_E_CUDA;
+        float *tmp = a;  // b now holds p^{n+1}
+        a = b;
+        b = tmp;
+    }
+    if (a != d_p)
+        return cuda_status(launch_swap(d_p, d_pprev, nx * ny * nz, st));
+    return OOC_OK;
+}
+
+}  // extern "C"

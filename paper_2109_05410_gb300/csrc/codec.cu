@@ -1,0 +1,559 @@
+// codec.cu -- FR4 fixed-rate 4x4x4 block codec on sm_103a.
+//
+// Section IV of the paper asks for a fixed-rate lossy codec: the user fixes
+// the bits kept per value, so every compressed unit has a known size and the
+// device buffers are preallocated.  FR4 follows the published fixed-rate
+// method (Lindstrom, IEEE TVCG 2014): block floating point on 4^3 blocks,
+// a reversible integer decorrelating transform, sequency ordering,
+// negabinary, and embedded bit-plane coding with group tests.  Its exact
+// definition (header, lifting steps, ordering, plane coder, dequantisation)
+// is stated in the oracle's codec; this file is an independent GPU
+// implementation that must match it bit for bit.
+//
+// GPU design: one thread per 4^3 block.  The 64 values stay in registers
+// (16 coalesced 128-bit loads: neighbouring threads own neighbouring blocks
+// along x).  The bit-plane stage turns the 64 negabinary words into 32
+// 64-bit plane masks with two in-register 32x32 bit transposes; each plane
+// is then written in O(1) chunks per newly significant coefficient
+// (find-first-set over the plane mask) instead of bit by bit.  The
+// compressed words of a CTA are staged in shared memory and written (or
+// read) with coalesced 32-bit accesses.
+#include <utility>
+
+#include "common.cuh"
+
+namespace ooc {
+namespace {
+
+constexpr int kPrec = 26;  // block-floating-point precision (bits)
+constexpr int kThreads = 128;
+
+// ---- sequency order ---------------------------------------------------------
+// r-th coefficient of the coding order: sort by level sum of (i, j, k) with
+// level (0, 1, 2, 2) per axis, ties by linear index (counting order).
+__host__ __device__ constexpr int order_at(int r)
+{
+    int c = 0;
+    for (int s = 0; s <= 6; ++s)
+        for (int l = 0; l < 64; ++l) {
+            const int li = (l & 3) == 0 ? 0 : ((l & 3) == 1 ? 1 : 2);
+            const int lj = ((l >> 2) & 3) == 0 ? 0 : (((l >> 2) & 3) == 1 ? 1 : 2);
+            const int lk = (l >> 4) == 0 ? 0 : ((l >> 4) == 1 ? 1 : 2);
+            if (li + lj + lk == s) {
+                if (c == r)
+                    return l;
+                ++c;
+            }
+        }
+    return -1;
+}
+
+constexpr uint32_t kNB = 0xAAAAAAAAu;
+
+template <int... R>
+__device__ __forceinline__ void to_coding_order(uint32_t (&u)[64], const int32_t (&q)[64],
+                                                std::integer_sequence<int, R...>)
+{
+    ((u[R] = ((uint32_t)q[std::integral_constant<int, order_at(R)>::value] + kNB) ^ kNB), ...);
+}
+
+template <int... R>
+__device__ __forceinline__ void from_coding_order(int32_t (&q)[64], const uint32_t (&u)[64],
+                                                  std::integer_sequence<int, R...>)
+{
+    ((q[std::integral_constant<int, order_at(R)>::value] = (int32_t)((u[R] ^ kNB) - kNB)), ...);
+}
+
+// ---- wrapping int32 lifting ---------------------------------------------------
+__device__ __forceinline__ int32_t wadd(int32_t a, int32_t b) { return (int32_t)((uint32_t)a + (uint32_t)b); }
+__device__ __forceinline__ int32_t wsub(int32_t a, int32_t b) { return (int32_t)((uint32_t)a - (uint32_t)b); }
+
+__device__ __forceinline__ void lift_fwd(int32_t &a0, int32_t &a1, int32_t &a2, int32_t &a3)
+{
+    int32_t d0 = wsub(a0, a1);
+    const int32_t s0 = wadd(a1, d0 >> 1);
+    int32_t d1 = wsub(a2, a3);
+    const int32_t s1 = wadd(a3, d1 >> 1);
+    const int32_t D = wsub(s0, s1);
+    const int32_t S = wadd(s1, D >> 1);
+    d0 = wsub(d0, D >> 1);
+    d1 = wsub(d1, D >> 1);
+    a0 = S;
+    a1 = D;
+    a2 = d0;
+    a3 = d1;
+}
+
+__device__ __forceinline__ void lift_inv(int32_t &a0, int32_t &a1, int32_t &a2, int32_t &a3)
+{
+    const int32_t S = a0, D = a1;
+    const int32_t d0 = wadd(a2, D >> 1);
+    const int32_t d1 = wadd(a3, D >> 1);
+    const int32_t s1 = wsub(S, D >> 1);
+    const int32_t s0 = wadd(s1, D);
+    const int32_t x3 = wsub(s1, d1 >> 1);
+    const int32_t x2 = wadd(x3, d1);
+    const int32_t x1 = wsub(s0, d0 >> 1);
+    const int32_t x0 = wadd(x1, d0);
+    a0 = x0;
+    a1 = x1;
+    a2 = x2;
+    a3 = x3;
+}
+
+__device__ __forceinline__ void transform_fwd(int32_t (&c)[64])
+{
+#pragma unroll
+    for (int z = 0; z < 4; ++z)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            const int b = 4 * y + 16 * z;
+            lift_fwd(c[b], c[b + 1], c[b + 2], c[b + 3]);
+        }
+#pragma unroll
+    for (int z = 0; z < 4; ++z)
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const int b = x + 16 * z;
+            lift_fwd(c[b], c[b + 4], c[b + 8], c[b + 12]);
+        }
+#pragma unroll
+    for (int y = 0; y < 4; ++y)
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const int b = x + 4 * y;
+            lift_fwd(c[b], c[b + 16], c[b + 32], c[b + 48]);
+        }
+}
+
+__device__ __forceinline__ void transform_inv(int32_t (&c)[64])
+{
+#pragma unroll
+    for (int y = 0; y < 4; ++y)
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const int b = x + 4 * y;
+            lift_inv(c[b], c[b + 16], c[b + 32], c[b + 48]);
+        }
+#pragma unroll
+    for (int z = 0; z < 4; ++z)
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const int b = x + 16 * z;
+            lift_inv(c[b], c[b + 4], c[b + 8], c[b + 12]);
+        }
+#pragma unroll
+    for (int z = 0; z < 4; ++z)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            const int b = 4 * y + 16 * z;
+            lift_inv(c[b], c[b + 1], c[b + 2], c[b + 3]);
+        }
+}
+
+// ---- 32x32 bit transpose of a[OFF .. OFF+31] in registers --------------------
+// Afterwards bit i of a[OFF + p] is the former bit p of a[OFF + i].
+template <int OFF, int J, uint32_t M>
+__device__ __forceinline__ void transpose_stage(uint32_t (&a)[64])
+{
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        if (!(k & J)) {
+            const uint32_t t = ((a[OFF + k] >> J) ^ a[OFF + k + J]) & M;
+            a[OFF + k + J] ^= t;
+            a[OFF + k] ^= t << J;
+        }
+    }
+}
+
+// The 16- and 8-bit stages are pure byte moves: one byte permute per word.
+template <int OFF>
+__device__ __forceinline__ void transpose_stage16(uint32_t (&a)[64])
+{
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const uint32_t lo = a[OFF + k], hi = a[OFF + k + 16];
+        a[OFF + k] = __byte_perm(lo, hi, 0x5410);
+        a[OFF + k + 16] = __byte_perm(lo, hi, 0x7632);
+    }
+}
+
+template <int OFF>
+__device__ __forceinline__ void transpose_stage8(uint32_t (&a)[64])
+{
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        if (!(k & 8)) {
+            const uint32_t lo = a[OFF + k], hi = a[OFF + k + 8];
+            a[OFF + k] = __byte_perm(lo, hi, 0x6240);
+            a[OFF + k + 8] = __byte_perm(lo, hi, 0x7351);
+        }
+    }
+}
+
+template <int OFF>
+__device__ __forceinline__ void transpose32(uint32_t (&a)[64])
+{
+    transpose_stage16<OFF>(a);
+    transpose_stage8<OFF>(a);
+    transpose_stage<OFF, 4, 0x0F0F0F0Fu>(a);
+    transpose_stage<OFF, 2, 0x33333333u>(a);
+    transpose_stage<OFF, 1, 0x55555555u>(a);
+}
+
+// ---- bit writer / reader over a thread's shared-memory words ------------------
+struct BitWriter {
+    uint32_t *dst;
+    int widx;
+    int nacc;  // valid bits in acc, < 32 between calls
+    int left;  // budget bits still writable
+    uint64_t acc;
+
+    // Append the low `len` (0..64) bits of v; bits of v above len are zero.
+    __device__ __forceinline__ void raw(uint64_t v, int len)
+    {
+        const uint64_t lo = acc | (v << nacc);
+        const uint64_t hi = nacc ? (v >> (64 - nacc)) : 0ull;
+        const int tot = nacc + len;
+        if (tot >= 64) {
+            dst[widx] = (uint32_t)lo;
+            dst[widx + 1] = (uint32_t)(lo >> 32);
+            widx += 2;
+            acc = hi;
+            nacc = tot - 64;
+        } else if (tot >= 32) {
+            dst[widx++] = (uint32_t)lo;
+            acc = lo >> 32;
+            nacc = tot - 32;
+        } else {
+            acc = lo;
+            nacc = tot;
+        }
+    }
+    // Append min(len, left) low bits of v (bits above len zero).
+    __device__ __forceinline__ void put(uint64_t v, int len)
+    {
+        if (len > left) {
+            len = left;
+            v &= (1ull << len) - 1ull;  // len < 64 here
+        }
+        if (len <= 0)
+            return;
+        left -= len;
+        raw(v, len);
+    }
+    __device__ __forceinline__ void finish(int words)
+    {
+        if (nacc > 0) {
+            dst[widx++] = (uint32_t)acc;
+            nacc = 0;
+        }
+        while (widx < words)
+            dst[widx++] = 0u;
+    }
+};
+
+struct BitReader {
+    const uint32_t *src;  // may be read up to 2 words past the block
+    int pos;
+    int end;
+
+    __device__ __forceinline__ uint64_t peek(int len) const  // 1 <= len <= 64
+    {
+        const int w = pos >> 5, sh = pos & 31;
+        uint64_t v = ((uint64_t)src[w] | ((uint64_t)src[w + 1] << 32)) >> sh;
+        if (sh != 0 && len > 64 - sh)
+            v |= (uint64_t)src[w + 2] << (64 - sh);
+        return len >= 64 ? v : (v & ((1ull << len) - 1ull));
+    }
+    __device__ __forceinline__ uint64_t read(int len)  // bits beyond `end` read as 0
+    {
+        const int av = end - pos;
+        if (len > av)
+            len = av;
+        if (len <= 0)
+            return 0;
+        const uint64_t v = peek(len);
+        pos += len;
+        return v;
+    }
+};
+
+// ---- one block ----------------------------------------------------------------
+__device__ __forceinline__ void encode_block(uint32_t (&v)[64], int rate, uint32_t *dst)
+{
+    const int words = 2 * rate;
+    uint32_t mx = 0;
+#pragma unroll
+    for (int i = 0; i < 64; ++i)
+        mx = max(mx, v[i] & 0x7FFFFFFFu);
+    BitWriter w{dst, 0, 0, 64 * rate, 0ull};
+    if (mx == 0u) {
+        w.finish(words);
+        return;
+    }
+    const int emax = (int)(mx >> 23) - 126;  // largest frexp exponent, >= -126
+    w.put(1u | ((uint32_t)((emax + 127) & 0xFF) << 1), 9);
+
+    // q = trunc(x * 2^(26 - emax)), with the power of two split in two
+    // normal factors; the first product is exact whenever the result can be
+    // nonzero, the second is exact or already below 1.
+    const int kk = kPrec - emax;
+    const int k1 = kk >> 1, k2 = kk - k1;
+    const float s1 = __int_as_float((k1 + 127) << 23);
+    const float s2 = __int_as_float((k2 + 127) << 23);
+    int32_t q[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i)
+        q[i] = __float2int_rz(__fmul_rn(__fmul_rn(__uint_as_float(v[i]), s1), s2));
+
+    transform_fwd(q);
+    to_coding_order(v, q, std::make_integer_sequence<int, 64>{});
+    transpose32<0>(v);   // v[p]      = bits p of coefficients 0..31
+    transpose32<32>(v);  // v[32 + p] = bits p of coefficients 32..63
+
+    // Plane p: the refinement bits of the n significant coefficients, then
+    // the significance part S.  With the new ones of the plane at offsets
+    // t_1 < .. < t_m past n, S holds a group bit 1 at 0, the j-th new one at
+    // D_j = t_j + j, a group bit 1 at D_j + 1 for j < m, and a closing group
+    // bit 0 if coefficients remain; when t_m is the last coefficient its one
+    // is implied and not written.  S is built with one step per new one.
+    int n = 0;
+#pragma unroll
+    for (int p = 31; p >= 0; --p) {
+        if (w.left <= 0)
+            break;
+        const uint64_t X = ((uint64_t)v[32 + p] << 32) | v[p];
+        w.put(n >= 64 ? X : (X & ((1ull << n) - 1ull)), n);
+        if (n < 64) {
+            const uint64_t rest = X >> n;
+            if (rest == 0ull) {
+                w.put(0ull, 1);
+            } else {
+                uint64_t dlo = 0ull, dhi = 0ull, rr = rest;
+                int j = 0, tm = 0;
+                while (rr != 0ull) {
+                    tm = __ffsll((long long)rr) - 1;
+                    ++j;
+                    const int d = tm + j;
+                    if (d < 64)
+                        dlo |= 1ull << d;
+                    else
+                        dhi |= 1ull << (d - 64);
+                    rr &= rr - 1ull;
+                }
+                const int dm = tm + j;  // position of the last new one
+                uint64_t glo = dlo << 1, ghi = (dhi << 1) | (dlo >> 63);
+                if (dm + 1 < 64)
+                    glo &= ~(1ull << (dm + 1));
+                else if (dm + 1 < 128)
+                    ghi &= ~(1ull << (dm + 1 - 64));
+                uint64_t slo = 1ull | dlo | glo, shi = dhi | ghi;
+                int ls;
+                if (n + tm == 63) {  // last coefficient reached: its one is implied
+                    if (dm < 64)
+                        slo &= ~(1ull << dm);
+                    else
+                        shi &= ~(1ull << (dm - 64));
+                    ls = dm;
+                    n = 64;
+                } else {
+                    n += tm + 1;
+                    ls = dm + 1 + (n < 64 ? 1 : 0);
+                }
+                if (ls <= 64) {
+                    w.put(slo, ls);
+                } else {
+                    w.put(slo, 64);
+                    if (ls <= 128) {
+                        w.put(shi, ls - 64);
+                    } else {
+                        w.put(shi, 64);
+                        w.put(0ull, ls - 128);
+                    }
+                }
+            }
+        }
+    }
+    w.finish(words);
+}
+
+__device__ __forceinline__ void decode_block(const uint32_t *src, int rate, float (&out)[64])
+{
+    BitReader r{src, 0, 64 * rate};
+    if ((src[0] & 1u) == 0u) {
+#pragma unroll
+        for (int i = 0; i < 64; ++i)
+            out[i] = 0.0f;
+        return;
+    }
+    const int emax = (int)((src[0] >> 1) & 0xFFu) - 127;
+    r.pos = 9;
+    uint32_t u[64];
+    int n = 0;
+#pragma unroll
+    for (int p = 31; p >= 0; --p) {
+        uint64_t X = 0;
+        if (r.pos < r.end) {
+            if (n > 0)
+                X = r.read(n);
+            if (n < 64) {
+                while (r.pos < r.end) {
+                    if (r.read(1) == 0ull)
+                        break;
+                    const int len = 63 - n;  // explicit scan bits at most
+                    const int av = r.end - r.pos;
+                    const int m = len < av ? len : av;
+                    const uint64_t s = m > 0 ? r.peek(m) : 0ull;
+                    if (s != 0ull) {
+                        const int t = __ffsll((long long)s) - 1;
+                        r.pos += t + 1;
+                        X |= 1ull << (n + t);
+                        n += t + 1;
+                    } else if (av >= len) {
+                        r.pos += len;
+                        X |= 1ull << 63;  // implied one of the last coefficient
+                        n = 64;
+                        break;
+                    } else {
+                        r.pos = r.end;
+                        break;
+                    }
+                }
+            }
+        }
+        u[p] = (uint32_t)X;
+        u[32 + p] = (uint32_t)(X >> 32);
+    }
+    transpose32<0>(u);
+    transpose32<32>(u);
+    int32_t q[64];
+    from_coding_order(q, u, std::make_integer_sequence<int, 64>{});
+    transform_inv(q);
+    // x = RN(RN(q) * 2^(emax - 26)): one exact or correctly rounded scaling.
+    const int k = emax - kPrec;
+    const bool split = k < -126;
+    const float sa = __int_as_float(((split ? k + 64 : k) + 127) << 23);
+    const float sb = __int_as_float((-64 + 127) << 23);
+#pragma unroll
+    for (int i = 0; i < 64; ++i) {
+        float f = __fmul_rn(__int2float_rn(q[i]), sa);
+        if (split)
+            f = __fmul_rn(f, sb);
+        out[i] = f;
+    }
+}
+
+// ---- kernels ------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) fr4_encode_kernel(ConstRing in, int64_t nx, int64_t ny, int64_t z0,
+                                                             int64_t nblk, int rate, uint32_t *__restrict__ out)
+{
+    extern __shared__ uint32_t smem[];
+    const int words = 2 * rate, stride = words + 1;
+    const int64_t first = (int64_t)blockIdx.x * kThreads;
+    const int64_t b = first + threadIdx.x;
+    if (b < nblk) {
+        const int64_t nbx = nx >> 2, nby = ny >> 2;
+        const int64_t bx = b % nbx, t2 = b / nbx, by = t2 % nby, bz = t2 / nby;
+        const int64_t slot = ring_slot(z0 + 4 * bz, in.zbase, in.nslot);
+        const float *p = in.base + (slot * ny + 4 * by) * nx + 4 * bx;
+        uint32_t v[64];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float4 f = __ldg(reinterpret_cast<const float4 *>(p + ((int64_t)k * ny + j) * nx));
+                v[16 * k + 4 * j + 0] = __float_as_uint(f.x);
+                v[16 * k + 4 * j + 1] = __float_as_uint(f.y);
+                v[16 * k + 4 * j + 2] = __float_as_uint(f.z);
+                v[16 * k + 4 * j + 3] = __float_as_uint(f.w);
+            }
+        encode_block(v, rate, smem + threadIdx.x * stride);
+    }
+    __syncthreads();
+    const int64_t left = nblk - first;
+    const int nvalid = left < kThreads ? (int)left : kThreads;
+    uint32_t *dst = out + first * words;
+    for (int o = threadIdx.x; o < nvalid * words; o += kThreads)
+        dst[o] = smem[(o / words) * stride + (o % words)];
+}
+
+__global__ void __launch_bounds__(kThreads) fr4_decode_kernel(const uint32_t *__restrict__ in, int64_t nx, int64_t ny,
+                                                             int64_t z0, int64_t nblk, int rate, Ring out)
+{
+    extern __shared__ uint32_t smem[];
+    const int words = 2 * rate, stride = words + 1;
+    const int64_t first = (int64_t)blockIdx.x * kThreads;
+    const int64_t left = nblk - first;
+    const int nvalid = left < kThreads ? (int)left : kThreads;
+    const uint32_t *src = in + first * words;
+    for (int o = threadIdx.x; o < nvalid * words; o += kThreads)
+        smem[(o / words) * stride + (o % words)] = __ldg(src + o);
+    if (threadIdx.x < 2)
+        smem[kThreads * stride + threadIdx.x] = 0u;  // reader slack past the last block
+    __syncthreads();
+    const int64_t b = first + threadIdx.x;
+    if (b >= nblk)
+        return;
+    float f[64];
+    decode_block(smem + threadIdx.x * stride, rate, f);
+    const int64_t nbx = nx >> 2, nby = ny >> 2;
+    const int64_t bx = b % nbx, t2 = b / nbx, by = t2 % nby, bz = t2 / nby;
+    const int64_t slot = ring_slot(z0 + 4 * bz, out.zbase, out.nslot);
+    float *p = out.base + (slot * ny + 4 * by) * nx + 4 * bx;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            *reinterpret_cast<float4 *>(p + ((int64_t)k * ny + j) * nx) =
+                make_float4(f[16 * k + 4 * j], f[16 * k + 4 * j + 1], f[16 * k + 4 * j + 2], f[16 * k + 4 * j + 3]);
+}
+
+size_t smem_bytes(int rate) { return ((size_t)kThreads * (2 * rate + 1) + 2) * sizeof(uint32_t); }
+
+cudaError_t ensure_smem_attr()
+{
+    static bool done = false;  // per process; the attribute is per function
+    if (done)
+        return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(fr4_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes(64));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fr4_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_bytes(64));
+    if (e == cudaSuccess)
+        done = true;
+    return e;
+}
+
+}  // namespace
+
+cudaError_t launch_fr4_encode(ConstRing in, int64_t nx, int64_t ny, int64_t z0, int64_t z1, int rate,
+                              uint32_t *out, cudaStream_t st)
+{
+    const int64_t nblk = (nx / 4) * (ny / 4) * ((z1 - z0) / 4);
+    if (nblk <= 0)
+        return cudaSuccess;
+    cudaError_t e = ensure_smem_attr();
+    if (e != cudaSuccess)
+        return e;
+    const int64_t grid = (nblk + kThreads - 1) / kThreads;
+    fr4_encode_kernel<<<(unsigned)grid, kThreads, smem_bytes(rate), st>>>(in, nx, ny, z0, nblk, rate, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fr4_decode(const uint32_t *in, int64_t nx, int64_t ny, int64_t z0, int64_t z1, int rate,
+                              Ring out, cudaStream_t st)
+{
+    const int64_t nblk = (nx / 4) * (ny / 4) * ((z1 - z0) / 4);
+    if (nblk <= 0)
+        return cudaSuccess;
+    cudaError_t e = ensure_smem_attr();
+    if (e != cudaSuccess)
+        return e;
+    const int64_t grid = (nblk + kThreads - 1) / kThreads;
+    fr4_decode_kernel<<<(unsigned)grid, kThreads, smem_bytes(rate), st>>>(in, nx, ny, z0, nblk, rate, out);
+    return cudaGetLastError();
+}
+
+}  // namespace ooc

@@ -1,0 +1,58 @@
+// common.cuh -- shared definitions of the CUDA library (product path).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ooc.h"
+
+namespace ooc {
+
+// A "ring" holds a window of z-planes of one field on the device.  Plane z
+// (global index, 0 <= z < nz) lives in slot (z + zbase) mod nslot.  With
+// nslot = nz and zbase = 0 a ring is an ordinary dense field.
+struct Ring {
+    float *base;      // nslot planes of nx*ny floats
+    int64_t nslot;    // Z
+    int64_t zbase;    // in [0, Z)
+};
+
+struct ConstRing {
+    const float *base;
+    int64_t nslot;
+    int64_t zbase;
+};
+
+__host__ __device__ inline int64_t ring_slot(int64_t z, int64_t zbase, int64_t nslot)
+{
+    int64_t s = z + zbase;
+    s %= nslot;
+    return s < 0 ? s + nslot : s;
+}
+
+// Stencil coefficients of the 8th-order central second difference.
+constexpr float kC0 = -205.0f / 72.0f;
+constexpr float kC1 = 8.0f / 5.0f;
+constexpr float kC2 = -1.0f / 5.0f;
+constexpr float kC3 = 8.0f / 315.0f;
+constexpr float kC4 = -1.0f / 560.0f;
+
+// Kernel launchers (stream-ordered, no synchronisation).  All return
+// cudaGetLastError() of the launch.
+cudaError_t launch_heat7(ConstRing in, Ring out, int64_t nx, int64_t ny, int64_t nz, int64_t z0, int64_t z1,
+                         float r, cudaStream_t st);
+cudaError_t launch_wave25(ConstRing p, Ring pprev_out, ConstRing kappa, int64_t nx, int64_t ny, int64_t nz,
+                          int64_t z0, int64_t z1, int64_t sx, int64_t sy, int64_t sz, float w, cudaStream_t st);
+// Codec over the 4-aligned plane range [z0, z1) of a ring; the stream part
+// for those planes is contiguous (2*rate words per block).
+cudaError_t launch_fr4_encode(ConstRing in, int64_t nx, int64_t ny, int64_t z0, int64_t z1, int rate,
+                              uint32_t *out, cudaStream_t st);
+cudaError_t launch_fr4_decode(const uint32_t *in, int64_t nx, int64_t ny, int64_t z0, int64_t z1, int rate,
+                              Ring out, cudaStream_t st);
+// BF16 storage over plane ranges of a ring.
+cudaError_t launch_bf16_pack_ring(ConstRing in, int64_t nx, int64_t ny, int64_t z0, int64_t z1, uint16_t *out,
+                                  cudaStream_t st);
+cudaError_t launch_bf16_unpack_ring(const uint16_t *in, int64_t nx, int64_t ny, int64_t z0, int64_t z1, Ring out,
+                                    cudaStream_t st);
+cudaError_t launch_swap(float *a, float *b, int64_t n, cudaStream_t st);
+
+}  // namespace ooc

@@ -1,0 +1,663 @@
+// pipeline.cu -- the out-of-core slab scheduler (host side) of the C ABI.
+//
+// The grid lives in the pinned host arena, one image per field in its
+// storage format (FP32, BF16 or FR4 codec).  A pass advances the whole grid
+// k time steps (temporal blocking, Section VI setup) by sweeping z-slabs of
+// T planes in increasing z (Section III decomposition):
+//
+//   slab i owns planes [a_i, b_i), a_i = i T.  Its output is the two units
+//   C_{i-1} = [a_i, a_i + W) and R_i = [a_i + W, b_i), compressed separately
+//   (Section V-A, Fig. 4); its input is R_i and C_i = [a_i + W, b_i + W)
+//   (slab 0 also C_{-1} = [0, W)), W = k h rounded up to 4 planes.
+//
+//   Step s = 1..k updates level s on [a_i + (k - s) h, b_i + (k - s) h)
+//   (slab 0 from 0, the last slab to nz): a parallelogram in (z, t).  The
+//   2h planes each level needs below its window were computed by slab i-1
+//   and are still in the level's ring buffer, so nothing is recomputed and
+//   the halo never crosses the host link (region sharing, Fig. 2).
+//
+// Each level parity has one ring of Z planes (plane z in slot
+// (z + zbase) mod Z); p^{s} overwrites p^{s-2} in place.  Passes continue
+// the ring addressing (zbase advances by nz per pass), so the pipeline never
+// drains between passes.  Three streams overlap the copies with the kernels
+// (Section V-B, Fig. 5): H2D(i+1) || decode, k steps, encode (i) || D2H(i-1),
+// ordered by events.  FP32 slabs land directly in the ring (no staging);
+// BF16/FR4 slabs go through double-buffered staging and a decode kernel.
+#include <chrono>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace ooc;
+
+namespace {
+
+constexpr int kEv = 4;  // event ring depth (waits look back at most 2 slabs)
+
+int64_t round4(int64_t v) { return (v + 3) / 4 * 4; }
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+int fmt_bits(int fmt, int rate)
+{
+    if (fmt == OOC_FMT_FP32)
+        return 32;
+    if (fmt == OOC_FMT_BF16)
+        return 16;
+    return rate;
+}
+
+struct ProfPair {
+    cudaEvent_t a, b;
+    int kind;  // 0 decode, 1 stencil, 2 encode, 3 h2d, 4 d2h
+};
+
+}  // namespace
+
+struct ooc_plan {
+    ooc_config cfg{};
+    int64_t T = 0, nslab = 0, W = 0, h = 0, Z = 0;
+    int nrw = 0, nfield = 0, nring = 0;
+    int fmt[3] = {0, 0, 0}, rate[3] = {0, 0, 0};
+    int64_t fplane[3] = {0, 0, 0};  // storage bytes per plane, per field
+    int64_t plane_elems = 0;
+    size_t off_ring[3] = {0, 0, 0};
+    size_t off_in[2][3] = {{0}}, off_out[2][3] = {{0}};
+    size_t in_bytes_field[3] = {0, 0, 0}, out_bytes_field[3] = {0, 0, 0};
+    size_t dev_bytes = 0;
+    size_t off_host[3] = {0, 0, 0};
+    size_t host_bytes = 0;
+    // bound state
+    bool bound = false;
+    char *dev = nullptr;
+    char *host = nullptr;
+    cudaStream_t st[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev_h2d[kEv], ev_dec[kEv], ev_comp[kEv], ev_d2h[kEv];
+    bool events_made = false;
+    std::vector<ProfPair> prof;
+    size_t prof_used = 0;
+    // run state
+    int64_t time = 0;
+    int64_t sx = -1, sy = -1, sz = -1;
+    std::vector<float> w;
+    ooc_stats stats{};
+};
+
+namespace {
+
+bool staged(const ooc_plan *p, int f) { return p->fmt[f] != OOC_FMT_FP32; }
+
+// Layout of the device arena for slab thickness T; returns total bytes.
+size_t layout(ooc_plan *p, int64_t T)
+{
+    const int64_t W = p->W, h = p->h;
+    bool any_staged = false;
+    for (int f = 0; f < p->nfield; ++f)
+        any_staged |= staged(p, f);
+    // FP32 slabs land in the ring while the previous slab computes (2T);
+    // staged slabs land in staging buffers and are decoded in stream order.
+    bool direct = false;
+    for (int f = 0; f < p->nfield; ++f)
+        direct |= !staged(p, f);
+    const int64_t Z = round4((direct ? 2 * T : T) + W + 2 * h);
+    size_t off = 0;
+    const size_t ring_bytes = (size_t)Z * p->plane_elems * sizeof(float);
+    for (int r = 0; r < p->nring; ++r) {
+        p->off_ring[r] = off;
+        off += align256(ring_bytes);
+    }
+    for (int f = 0; f < p->nfield; ++f) {
+        p->in_bytes_field[f] = staged(p, f) ? (size_t)(T + W) * p->fplane[f] : 0;
+        p->out_bytes_field[f] = (staged(p, f) && f < p->nrw) ? (size_t)T * p->fplane[f] : 0;
+    }
+    for (int b = 0; b < 2; ++b)
+        for (int f = 0; f < p->nfield; ++f) {
+            p->off_in[b][f] = off;
+            off += align256(p->in_bytes_field[f]);
+            p->off_out[b][f] = off;
+            off += align256(p->out_bytes_field[f]);
+        }
+    (void)any_staged;
+    p->Z = Z;
+    return off;
+}
+
+Ring ring_view(ooc_plan *p, int r, int64_t zbase)
+{
+    return Ring{(float *)(p->dev + p->off_ring[r]), p->Z, zbase};
+}
+
+ConstRing cring(const Ring &r) { return ConstRing{r.base, r.nslot, r.zbase}; }
+
+// Copy planes [z0, z1) between a ring and contiguous memory (split at wrap).
+cudaError_t copy_ring(ooc_plan *p, int r, int64_t zbase, int64_t z0, int64_t z1, char *hostp, bool to_device,
+                      cudaStream_t st)
+{
+    const size_t pb = (size_t)p->plane_elems * sizeof(float);
+    int64_t z = z0;
+    while (z < z1) {
+        const int64_t slot = ring_slot(z, zbase, p->Z);
+        int64_t n = z1 - z;
+        if (slot + n > p->Z)
+            n = p->Z - slot;
+        char *dptr = p->dev + p->off_ring[r] + (size_t)slot * pb;
+        char *hptr = hostp + (size_t)(z - z0) * pb;
+        cudaError_t e = to_device ? cudaMemcpyAsync(dptr, hptr, (size_t)n * pb, cudaMemcpyHostToDevice, st)
+                                  : cudaMemcpyAsync(hptr, dptr, (size_t)n * pb, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess)
+            return e;
+        z += n;
+    }
+    return cudaSuccess;
+}
+
+ooc_status wait_event(ooc_plan *p, cudaEvent_t ev)
+{
+    const int64_t ms = p->cfg.wait_timeout_ms > 0 ? p->cfg.wait_timeout_ms : 600000;
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(ms);
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess)
+            return OOC_OK;
+        if (e != cudaErrorNotReady)
+            return OOC_E_CUDA;
+        if (std::chrono::steady_clock::now() > deadline)
+            return OOC_E_TIMEOUT;
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+ooc_status prof_begin(ooc_plan *p, cudaStream_t st, int kind, size_t *idx)
+{
+    *idx = (size_t)-1;
+    if (!p->cfg.profile)
+        return OOC_OK;
+    if (p->prof_used == p->prof.size()) {
+        ProfPair pp{};
+        pp.kind = kind;
+        if (cudaEventCreate(&pp.a) != cudaSuccess || cudaEventCreate(&pp.b) != cudaSuccess)
+            return OOC_E_CUDA;
+        try {
+            p->prof.push_back(pp);
+        } catch (...) {
+            return OOC_E_ALLOC;
+        }
+    }
+    *idx = p->prof_used++;
+    p->prof[*idx].kind = kind;
+    return cudaEventRecord(p->prof[*idx].a, st) == cudaSuccess ? OOC_OK : OOC_E_CUDA;
+}
+
+ooc_status prof_end(ooc_plan *p, cudaStream_t st, size_t idx)
+{
+    if (idx == (size_t)-1)
+        return OOC_OK;
+    return cudaEventRecord(p->prof[idx].b, st) == cudaSuccess ? OOC_OK : OOC_E_CUDA;
+}
+
+#define OOC_TRY(x)                   \
+    do {                             \
+        ooc_status _s = (x);         \
+        if (_s != OOC_OK)            \
+            return _s;               \
+    } while (0)
+#define OOC_CUDA(x)                  \
+    do {                             \
+        if ((x) != cudaSuccess)      \
+            return OOC_E_CUDA;       \
+    } while (0)
+
+// Decode planes [z0, z1) of field f from `src` (storage format) into ring r.
+ooc_status decode_into(ooc_plan *p, int f, const char *src, Ring dst, int64_t z0, int64_t z1, cudaStream_t st)
+{
+    const int64_t nx = p->cfg.nx, ny = p->cfg.ny;
+    if (p->fmt[f] == OOC_FMT_FR4)
+        OOC_CUDA(launch_fr4_decode((const uint32_t *)src, nx, ny, z0, z1, p->rate[f], dst, st));
+    else
+        OOC_CUDA(launch_bf16_unpack_ring((const uint16_t *)src, nx, ny, z0, z1, dst, st));
+    return OOC_OK;
+}
+
+ooc_status encode_from(ooc_plan *p, int f, ConstRing srcr, char *dst, int64_t z0, int64_t z1, cudaStream_t st)
+{
+    const int64_t nx = p->cfg.nx, ny = p->cfg.ny;
+    if (p->fmt[f] == OOC_FMT_FR4)
+        OOC_CUDA(launch_fr4_encode(srcr, nx, ny, z0, z1, p->rate[f], (uint32_t *)dst, st));
+    else
+        OOC_CUDA(launch_bf16_pack_ring(srcr, nx, ny, z0, z1, (uint16_t *)dst, st));
+    return OOC_OK;
+}
+
+// Ring holding field f's input level (heat: u -> ring 0; wave: p^t -> 0,
+// p^{t-1} -> 1, kappa -> 2) and its output after a pass of kp steps.
+int input_ring(const ooc_plan *p, int f) { return f; }
+int output_ring(const ooc_plan *p, int f, int64_t kp)
+{
+    if (f == 0)
+        return (int)(kp & 1);
+    return (int)((kp + 1) & 1);  // wave p^{t+kp-1}
+}
+
+struct SlabGeom {
+    int64_t a, b, in_lo, in_hi;
+};
+
+SlabGeom slab_geom(const ooc_plan *p, int64_t i, int64_t Wp)
+{
+    const int64_t nz = p->cfg.nz;
+    SlabGeom g;
+    g.a = i * p->T;
+    g.b = g.a + p->T < nz ? g.a + p->T : nz;
+    g.in_lo = i == 0 ? 0 : (g.a + Wp < nz ? g.a + Wp : nz);
+    g.in_hi = g.b + Wp < nz ? g.b + Wp : nz;
+    if (g.in_hi < g.in_lo)
+        g.in_hi = g.in_lo;
+    return g;
+}
+
+void step_window(const ooc_plan *p, int64_t i, int64_t kp, int64_t s, int64_t *lo, int64_t *hi)
+{
+    const int64_t nz = p->cfg.nz;
+    const SlabGeom g = slab_geom(p, i, 0);
+    int64_t l = i == 0 ? 0 : g.a + (kp - s) * p->h;
+    int64_t u = i == p->nslab - 1 ? nz : g.b + (kp - s) * p->h;
+    if (l > nz)
+        l = nz;
+    if (u > nz)
+        u = nz;
+    *lo = l;
+    *hi = u;
+}
+
+}  // namespace
+
+extern "C" {
+
+ooc_status ooc_plan_create(const ooc_config *cfg, ooc_plan **out, size_t *device_bytes, size_t *host_bytes)
+{
+    if (!cfg || !out)
+        return OOC_E_INVALID;
+    *out = nullptr;
+    const ooc_config c = *cfg;
+    if (c.nx <= 0 || c.ny <= 0 || c.nz <= 0 || c.nx % 4 || c.ny % 4 || c.nz % 4 || c.nx > (1 << 20) ||
+        c.ny > (1 << 20) || c.nz > (1 << 20) || c.k < 1 || c.k > 4096)
+        return OOC_E_INVALID;
+    if (c.stencil != OOC_HEAT7 && c.stencil != OOC_WAVE25)
+        return OOC_E_INVALID;
+    auto fmt_ok = [](int f, int r) {
+        return f == OOC_FMT_FP32 || f == OOC_FMT_BF16 || (f == OOC_FMT_FR4 && r >= 1 && r <= 64);
+    };
+    if (!fmt_ok(c.rw_format, c.rw_rate) || (c.stencil == OOC_WAVE25 && !fmt_ok(c.ro_format, c.ro_rate)))
+        return OOC_E_INVALID;
+    if (c.slab_planes < 0 || c.slab_planes % 4 || c.device_budget_bytes < 0)
+        return OOC_E_INVALID;
+    ooc_plan *p = new (std::nothrow) ooc_plan();
+    if (!p)
+        return OOC_E_ALLOC;
+    p->cfg = c;
+    p->h = c.stencil == OOC_HEAT7 ? 1 : 4;
+    p->W = round4((int64_t)c.k * p->h);
+    p->nrw = c.stencil == OOC_HEAT7 ? 1 : 2;
+    p->nfield = c.stencil == OOC_HEAT7 ? 1 : 3;
+    p->nring = c.stencil == OOC_HEAT7 ? 2 : 3;
+    p->plane_elems = c.nx * c.ny;
+    for (int f = 0; f < p->nfield; ++f) {
+        const bool ro = f >= p->nrw;
+        p->fmt[f] = ro ? c.ro_format : c.rw_format;
+        p->rate[f] = ro ? c.ro_rate : c.rw_rate;
+        p->fplane[f] = p->plane_elems * fmt_bits(p->fmt[f], p->rate[f]) / 8;
+    }
+    size_t off = 0;
+    for (int f = 0; f < p->nfield; ++f) {
+        p->off_host[f] = off;
+        off += align256((size_t)p->fplane[f] * c.nz);
+    }
+    p->host_bytes = off;
+
+    const int64_t nz = c.nz;
+    int64_t T = 0;
+    size_t bytes = 0;
+    if (c.slab_planes > 0) {
+        T = c.slab_planes < nz ? c.slab_planes : nz;
+        bytes = layout(p, T);
+        if (c.device_budget_bytes > 0 && bytes > (size_t)c.device_budget_bytes) {
+            delete p;
+            return OOC_E_BUDGET;
+        }
+    } else {
+        if (c.device_budget_bytes <= 0) {
+            delete p;
+            return OOC_E_INVALID;
+        }
+        for (int64_t t = 4; t <= nz; t += 4) {
+            const size_t b = layout(p, t);
+            if (b > (size_t)c.device_budget_bytes)
+                break;
+            T = t;
+        }
+        if (T == 0) {
+            delete p;
+            return OOC_E_BUDGET;
+        }
+        bytes = layout(p, T);
+    }
+    p->T = T;
+    p->nslab = (nz + T - 1) / T;
+    p->dev_bytes = bytes;
+    *out = p;
+    if (device_bytes)
+        *device_bytes = p->dev_bytes;
+    if (host_bytes)
+        *host_bytes = p->host_bytes;
+    return OOC_OK;
+}
+
+ooc_status ooc_plan_get_info(const ooc_plan *p, ooc_plan_info *info)
+{
+    if (!p || !info)
+        return OOC_E_INVALID;
+    info->slab_planes = p->T;
+    info->nslab = p->nslab;
+    info->common_planes = p->W;
+    info->halo = p->h;
+    info->ring_planes = p->Z;
+    info->nrings = p->nring;
+    info->device_bytes = (int64_t)p->dev_bytes;
+    info->host_bytes = (int64_t)p->host_bytes;
+    info->staging_in_bytes = (int64_t)p->in_bytes_field[0];
+    info->staging_out_bytes = (int64_t)p->out_bytes_field[0];
+    return OOC_OK;
+}
+
+ooc_status ooc_plan_bind(ooc_plan *p, void *device_arena, size_t device_bytes, void *host_arena, size_t host_bytes,
+                         void *const streams[3])
+{
+    if (!p || !device_arena || !host_arena || !streams || device_bytes < p->dev_bytes ||
+        host_bytes < p->host_bytes || ((uintptr_t)device_arena % 256) || ((uintptr_t)host_arena % 16))
+        return OOC_E_INVALID;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, host_arena) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+        cudaGetLastError();
+        return OOC_E_INVALID;  // host arena must be pinned (page-locked) memory
+    }
+    if (cudaPointerGetAttributes(&at, device_arena) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return OOC_E_INVALID;
+    }
+    if (!p->events_made) {
+        for (int i = 0; i < kEv; ++i) {
+            if (cudaEventCreateWithFlags(&p->ev_h2d[i], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&p->ev_dec[i], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&p->ev_comp[i], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&p->ev_d2h[i], cudaEventDisableTiming) != cudaSuccess)
+                return OOC_E_CUDA;
+        }
+        p->events_made = true;
+    }
+    p->dev = (char *)device_arena;
+    p->host = (char *)host_arena;
+    for (int i = 0; i < 3; ++i)
+        p->st[i] = (cudaStream_t)streams[i];
+    p->bound = true;
+    return OOC_OK;
+}
+
+ooc_status ooc_set_source(ooc_plan *p, int64_t sx, int64_t sy, int64_t sz, const float *w, int64_t nw)
+{
+    if (!p || nw < 0 || (nw > 0 && !w))
+        return OOC_E_INVALID;
+    if (nw == 0) {
+        p->sx = p->sy = p->sz = -1;
+        p->w.clear();
+        return OOC_OK;
+    }
+    if (p->cfg.stencil != OOC_WAVE25 || sx < 0 || sy < 0 || sz < 0 || sx >= p->cfg.nx || sy >= p->cfg.ny ||
+        sz >= p->cfg.nz)
+        return OOC_E_INVALID;
+    try {
+        p->w.assign(w, w + nw);
+    } catch (...) {
+        return OOC_E_ALLOC;
+    }
+    p->sx = sx;
+    p->sy = sy;
+    p->sz = sz;
+    return OOC_OK;
+}
+
+ooc_status ooc_set_field(ooc_plan *p, int field, const float *host_src)
+{
+    if (!p || !p->bound || !host_src || field < 0 || field >= p->nfield)
+        return OOC_E_INVALID;
+    const int64_t nz = p->cfg.nz;
+    const size_t pb = (size_t)p->plane_elems * sizeof(float);
+    char *img = p->host + p->off_host[field];
+    if (!staged(p, field)) {
+        std::memcpy(img, host_src, pb * nz);
+        return OOC_OK;
+    }
+    cudaStream_t st = p->st[1];
+    for (int64_t z0 = 0; z0 < nz; z0 += p->T) {
+        const int64_t z1 = z0 + p->T < nz ? z0 + p->T : nz;
+        const int64_t zb = (p->Z - z0 % p->Z) % p->Z;  // plane z0 -> slot 0
+        OOC_CUDA(copy_ring(p, 0, zb, z0, z1, (char *)(host_src + (size_t)z0 * p->plane_elems), true, st));
+        char *stage = p->dev + p->off_in[0][field];
+        OOC_TRY(encode_from(p, field, cring(ring_view(p, 0, zb)), stage, z0, z1, st));
+        OOC_CUDA(cudaMemcpyAsync(img + (size_t)z0 * p->fplane[field], stage, (size_t)(z1 - z0) * p->fplane[field],
+                                 cudaMemcpyDeviceToHost, st));
+        OOC_CUDA(cudaStreamSynchronize(st));
+    }
+    return OOC_OK;
+}
+
+ooc_status ooc_get_field(ooc_plan *p, int field, float *host_dst)
+{
+    if (!p || !p->bound || !host_dst || field < 0 || field >= p->nfield)
+        return OOC_E_INVALID;
+    const int64_t nz = p->cfg.nz;
+    const size_t pb = (size_t)p->plane_elems * sizeof(float);
+    char *img = p->host + p->off_host[field];
+    if (!staged(p, field)) {
+        std::memcpy(host_dst, img, pb * nz);
+        return OOC_OK;
+    }
+    cudaStream_t st = p->st[1];
+    for (int64_t z0 = 0; z0 < nz; z0 += p->T) {
+        const int64_t z1 = z0 + p->T < nz ? z0 + p->T : nz;
+        const int64_t zb = (p->Z - z0 % p->Z) % p->Z;
+        char *stage = p->dev + p->off_in[0][field];
+        OOC_CUDA(cudaMemcpyAsync(stage, img + (size_t)z0 * p->fplane[field], (size_t)(z1 - z0) * p->fplane[field],
+                                 cudaMemcpyHostToDevice, st));
+        OOC_TRY(decode_into(p, field, stage, ring_view(p, 0, zb), z0, z1, st));
+        OOC_CUDA(copy_ring(p, 0, zb, z0, z1, (char *)(host_dst + (size_t)z0 * p->plane_elems), false, st));
+        OOC_CUDA(cudaStreamSynchronize(st));
+    }
+    return OOC_OK;
+}
+
+ooc_status ooc_step(ooc_plan *p, int64_t nsteps)
+{
+    if (!p || !p->bound || nsteps < 0)
+        return OOC_E_INVALID;
+    if (nsteps == 0)
+        return OOC_OK;
+    const auto t_start = std::chrono::steady_clock::now();
+    const int64_t nx = p->cfg.nx, ny = p->cfg.ny, nz = p->cfg.nz, k = p->cfg.k;
+    const bool wave = p->cfg.stencil == OOC_WAVE25;
+    const float r = (float)p->cfg.r;
+    cudaStream_t sH = p->st[0], sC = p->st[1], sD = p->st[2];
+    p->prof_used = 0;
+    const int64_t npass = (nsteps + k - 1) / k;
+    int64_t g = 0;  // slab visits in this call
+    for (int64_t pass = 0; pass < npass; ++pass) {
+        const int64_t kp = (pass + 1) * k <= nsteps ? k : nsteps - pass * k;
+        const int64_t Wp = round4(kp * p->h);
+        const int64_t zb = (pass * nz) % p->Z;
+        const int64_t t0 = p->time + pass * k;
+        for (int64_t i = 0; i < p->nslab; ++i, ++g) {
+            const SlabGeom sg = slab_geom(p, i, Wp);
+            const int e = (int)(g % kEv);
+            // ---- H2D: input units R_i and C_i (slab 0 also C_{-1}) -------------
+            int64_t need = g - 2;  // ring slots / staging of slab g-2 are free
+            if (pass > 0) {
+                // the host units read here were written by slabs i, i+1 of the
+                // previous pass
+                const int64_t gp = g - p->nslab + (i + 1 < p->nslab ? 1 : 0);
+                if (gp > need)
+                    need = gp;
+            }
+            if (need >= 0)
+                OOC_CUDA(cudaStreamWaitEvent(sH, p->ev_d2h[need % kEv], 0));
+            if (g >= 2)
+                OOC_CUDA(cudaStreamWaitEvent(sH, p->ev_dec[(g - 2) % kEv], 0));
+            if (sg.in_hi > sg.in_lo) {
+                size_t pi;
+                OOC_TRY(prof_begin(p, sH, 3, &pi));
+                for (int f = 0; f < p->nfield; ++f) {
+                    char *src = p->host + p->off_host[f] + (size_t)sg.in_lo * p->fplane[f];
+                    const size_t nb = (size_t)(sg.in_hi - sg.in_lo) * p->fplane[f];
+                    if (staged(p, f))
+                        OOC_CUDA(cudaMemcpyAsync(p->dev + p->off_in[g & 1][f], src, nb, cudaMemcpyHostToDevice, sH));
+                    else
+                        OOC_CUDA(copy_ring(p, input_ring(p, f), zb, sg.in_lo, sg.in_hi, src, true, sH));
+                    p->stats.h2d_bytes += (int64_t)nb;
+                }
+                OOC_TRY(prof_end(p, sH, pi));
+            }
+            OOC_CUDA(cudaEventRecord(p->ev_h2d[e], sH));
+
+            // ---- compute: decode, k stencil steps, encode ---------------------
+            OOC_CUDA(cudaStreamWaitEvent(sC, p->ev_h2d[e], 0));
+            if (sg.in_hi > sg.in_lo) {
+                for (int f = 0; f < p->nfield; ++f) {
+                    if (!staged(p, f))
+                        continue;
+                    size_t pi;
+                    OOC_TRY(prof_begin(p, sC, 0, &pi));
+                    OOC_TRY(decode_into(p, f, p->dev + p->off_in[g & 1][f], ring_view(p, input_ring(p, f), zb),
+                                        sg.in_lo, sg.in_hi, sC));
+                    OOC_TRY(prof_end(p, sC, pi));
+                    p->stats.kernel_launches++;
+                }
+            }
+            OOC_CUDA(cudaEventRecord(p->ev_dec[e], sC));
+            for (int64_t s = 1; s <= kp; ++s) {
+                int64_t lo, hi;
+                step_window(p, i, kp, s, &lo, &hi);
+                if (hi <= lo)
+                    continue;
+                size_t pi;
+                OOC_TRY(prof_begin(p, sC, 1, &pi));
+                if (!wave) {
+                    OOC_CUDA(launch_heat7(cring(ring_view(p, (int)((s - 1) & 1), zb)), ring_view(p, (int)(s & 1), zb),
+                                          nx, ny, nz, lo, hi, r, sC));
+                } else {
+                    const int64_t n = t0 + s - 1;  // computing p^{n+1}
+                    const bool src = p->sx >= 0 && n < (int64_t)p->w.size() && p->sz >= lo && p->sz < hi;
+                    OOC_CUDA(launch_wave25(cring(ring_view(p, (int)((s - 1) & 1), zb)), ring_view(p, (int)(s & 1), zb),
+                                           cring(ring_view(p, 2, zb)), nx, ny, nz, lo, hi, src ? p->sx : -1, p->sy,
+                                           p->sz, src ? p->w[n] : 0.0f, sC));
+                }
+                OOC_TRY(prof_end(p, sC, pi));
+                p->stats.kernel_launches++;
+            }
+            bool any_enc = false;
+            for (int f = 0; f < p->nrw; ++f)
+                any_enc |= staged(p, f);
+            if (any_enc && g >= 2)
+                OOC_CUDA(cudaStreamWaitEvent(sC, p->ev_d2h[(g - 2) % kEv], 0));
+            for (int f = 0; f < p->nrw; ++f) {
+                if (!staged(p, f))
+                    continue;
+                size_t pi;
+                OOC_TRY(prof_begin(p, sC, 2, &pi));
+                OOC_TRY(encode_from(p, f, cring(ring_view(p, output_ring(p, f, kp), zb)),
+                                    p->dev + p->off_out[g & 1][f], sg.a, sg.b, sC));
+                OOC_TRY(prof_end(p, sC, pi));
+                p->stats.kernel_launches++;
+            }
+            OOC_CUDA(cudaEventRecord(p->ev_comp[e], sC));
+
+            // ---- D2H: units C_{i-1} and R_i ---------------------------------
+            OOC_CUDA(cudaStreamWaitEvent(sD, p->ev_comp[e], 0));
+            {
+                size_t pi;
+                OOC_TRY(prof_begin(p, sD, 4, &pi));
+                for (int f = 0; f < p->nrw; ++f) {
+                    char *dst = p->host + p->off_host[f] + (size_t)sg.a * p->fplane[f];
+                    const size_t nb = (size_t)(sg.b - sg.a) * p->fplane[f];
+                    if (staged(p, f))
+                        OOC_CUDA(cudaMemcpyAsync(dst, p->dev + p->off_out[g & 1][f], nb, cudaMemcpyDeviceToHost, sD));
+                    else
+                        OOC_CUDA(copy_ring(p, output_ring(p, f, kp), zb, sg.a, sg.b, dst, false, sD));
+                    p->stats.d2h_bytes += (int64_t)nb;
+                }
+                OOC_TRY(prof_end(p, sD, pi));
+            }
+            OOC_CUDA(cudaEventRecord(p->ev_d2h[e], sD));
+            p->stats.slabs++;
+        }
+        p->stats.passes++;
+    }
+    OOC_TRY(wait_event(p, p->ev_d2h[(g - 1) % kEv]));
+    p->time += nsteps;
+    p->stats.steps_done += nsteps;
+    if (p->cfg.profile) {
+        for (size_t j = 0; j < p->prof_used; ++j) {
+            float ms = 0.0f;
+            OOC_CUDA(cudaEventElapsedTime(&ms, p->prof[j].a, p->prof[j].b));
+            switch (p->prof[j].kind) {
+            case 0: p->stats.ms_decode += ms; p->stats.n_decode++; break;
+            case 1: p->stats.ms_stencil += ms; p->stats.n_stencil++; break;
+            case 2: p->stats.ms_encode += ms; p->stats.n_encode++; break;
+            case 3: p->stats.ms_h2d += ms; p->stats.n_h2d++; break;
+            default: p->stats.ms_d2h += ms; p->stats.n_d2h++; break;
+            }
+        }
+    }
+    p->stats.ms_last_step =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    return OOC_OK;
+}
+
+ooc_status ooc_get_stats(const ooc_plan *p, ooc_stats *s)
+{
+    if (!p || !s)
+        return OOC_E_INVALID;
+    *s = p->stats;
+    return OOC_OK;
+}
+
+ooc_status ooc_reset_stats(ooc_plan *p)
+{
+    if (!p)
+        return OOC_E_INVALID;
+    const int64_t steps = p->stats.steps_done;
+    p->stats = ooc_stats{};
+    p->stats.steps_done = steps;
+    return OOC_OK;
+}
+
+void ooc_plan_destroy(ooc_plan *p)
+{
+    if (!p)
+        return;
+    if (p->events_made) {
+        for (int i = 0; i < kEv; ++i) {
+            cudaEventDestroy(p->ev_h2d[i]);
+            cudaEventDestroy(p->ev_dec[i]);
+            cudaEventDestroy(p->ev_comp[i]);
+            cudaEventDestroy(p->ev_d2h[i]);
+        }
+    }
+    for (auto &pp : p->prof) {
+        cudaEventDestroy(pp.a);
+        cudaEventDestroy(pp.b);
+    }
+    delete p;
+}
+
+}  // extern "C"

@@ -1,0 +1,120 @@
+"""GPU codec parity: the FR4 kernels behind ooc_compress / ooc_decompress
+must reproduce the oracle's streams and values bit for bit (Section IV's
+fixed-rate codec, defined in the oracle)."""
+import numpy as np
+import pytest
+
+import oracle
+from synth import random_blocks, smooth_random_field, sine_modes_field
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KINDS = ("normal", "wide", "smooth", "constant", "zero", "denormal", "sparse", "bits")
+
+
+@pytest.fixture(scope="module")
+def ooc():
+    import paper_2109_05410_gb300 as m
+    m.build()
+    m.lib()
+    return m
+
+
+def gpu_encode(ooc, x, rate):
+    d = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+    w = ooc.ooc_compress(d, rate)
+    torch.cuda.synchronize()
+    return w.cpu().numpy().view(np.uint32)
+
+
+def gpu_decode(ooc, words, shape, rate):
+    d = torch.from_numpy(np.ascontiguousarray(words, dtype=np.uint32).view(np.uint8)).cuda()
+    out = ooc.ooc_decompress(d, shape, rate)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("rate", [1, 2, 3, 8, 12, 16, 24, 32, 40, 64])
+@pytest.mark.parametrize("kind", KINDS)
+def test_encode_decode_bit_exact(ooc, kind, rate):
+    x = random_blocks(kind, 700, seed=rate * 31 + len(kind))  # 700 blocks: several CTAs and a ragged tail
+    ref_w = oracle.fr4_encode(x, rate)
+    got_w = gpu_encode(ooc, x, rate)
+    assert np.array_equal(got_w, ref_w)
+    ref_x = oracle.fr4_decode(ref_w, x.shape, rate)
+    got_x = gpu_decode(ooc, ref_w, x.shape, rate)
+    assert np.array_equal(got_x.view(np.uint32), ref_x.view(np.uint32))
+
+
+@pytest.mark.parametrize("shape", [(4, 4, 4), (12, 20, 36), (8, 4, 132), (36, 28, 8)])
+def test_non_cubic_shapes(ooc, shape):
+    x = smooth_random_field(shape, 3.0, seed=sum(shape)).astype(np.float32)
+    for rate in (8, 16):
+        ref_w = oracle.fr4_encode(x, rate)
+        assert np.array_equal(gpu_encode(ooc, x, rate), ref_w)
+        assert np.array_equal(gpu_decode(ooc, ref_w, shape, rate).view(np.uint32),
+                              oracle.fr4_decode(ref_w, shape, rate).view(np.uint32))
+
+
+@pytest.mark.parametrize("rate", [4, 16, 24])
+def test_decode_of_arbitrary_words(ooc, rate):
+    # Any word content must decode without faulting and exactly as the oracle
+    # decodes it (wrapping int32 inverse lifting included).
+    rng = np.random.default_rng(rate)
+    shape = (16, 16, 16)
+    words = rng.integers(0, 1 << 32, size=16 * 16 * 16 * rate // 32, dtype=np.uint64).astype(np.uint32)
+    got = gpu_decode(ooc, words, shape, rate)
+    ref = oracle.fr4_decode(words, shape, rate)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+
+
+def test_bf16_pack_bit_exact(ooc):
+    rng = np.random.default_rng(0)
+    bits = rng.integers(0, 1 << 32, size=1 << 18, dtype=np.uint64).astype(np.uint32)
+    x = bits.view(np.float32)
+    d = torch.from_numpy(x.copy()).cuda()
+    packed = ooc.ooc_bf16_pack(d)
+    back = ooc.ooc_bf16_unpack(packed)
+    torch.cuda.synchronize()
+    assert np.array_equal(packed.cpu().numpy().view(np.uint16), oracle.bf16_bits(x))
+    assert np.array_equal(back.cpu().numpy().view(np.uint32), oracle.bf16_to_f32(oracle.bf16_bits(x)).view(np.uint32))
+
+
+def test_full_size_sampled_blocks(ooc):
+    # The 1024^3 field of the heat benchmark, compressed on the GPU in one
+    # launch; sampled 4^3 blocks are encoded by the oracle one by one and
+    # must equal the matching words of the GPU stream (and decode equally).
+    n = 1024
+    x = smooth_random_field((n, n, n), 32.0, seed=2)
+    rate = 16
+    d = torch.from_numpy(x).cuda()
+    w = ooc.ooc_compress(d, rate)
+    back = ooc.ooc_decompress(w, (n, n, n), rate)
+    torch.cuda.synchronize()
+    wv = w.view(torch.int32)
+    rng = np.random.default_rng(1)
+    nb = n // 4
+    for _ in range(64):
+        bx, by, bz = (int(v) for v in rng.integers(0, nb, size=3))
+        blk = x[4 * bz:4 * bz + 4, 4 * by:4 * by + 4, 4 * bx:4 * bx + 4]
+        ref = oracle.fr4_encode(blk, rate)
+        b = bx + nb * (by + nb * bz)
+        got = wv[b * 2 * rate:(b + 1) * 2 * rate].cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, ref)
+        gb = back[4 * bz:4 * bz + 4, 4 * by:4 * by + 4, 4 * bx:4 * bx + 4].cpu().numpy()
+        assert np.array_equal(gb.view(np.uint32), oracle.fr4_decode(ref, (4, 4, 4), rate).view(np.uint32))
+    # stated accuracy of the whole field at this rate
+    err = (torch.linalg.vector_norm((back - d).double()) / torch.linalg.vector_norm(d.double())).item()
+    assert err < 1e-4, err
+
+
+def test_compress_argument_errors(ooc):
+    d = torch.zeros((8, 8, 8), device="cuda")
+    out = torch.empty(8 * 8 * 8 * 2 - 4, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ooc.OocError):
+        ooc.ooc_compress(d, 16, d_out=out)  # capacity one word short
+    with pytest.raises(ooc.OocError):
+        ooc.ooc_compress(d, 0)
+    with pytest.raises(ooc.OocError):
+        ooc.ooc_compress(torch.zeros((8, 8, 6), device="cuda"), 16)

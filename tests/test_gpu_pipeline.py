@@ -1,0 +1,201 @@
+"""Out-of-core pipeline parity (ooc_plan / ooc_step through the C ABI).
+
+The scheduler must not change arithmetic: a run streamed slab by slab with
+region sharing and temporal blocking is bit-identical to an in-core GPU run
+of the same kernels that applies the same storage round trip (FP32 identity,
+BF16 rounding, FR4 encode+decode) to every stored field at load and after
+every pass.  The in-core kernels and the codec are checked against the
+oracle elsewhere; here the oracle bounds the end-to-end error."""
+import numpy as np
+import pytest
+
+import oracle
+from synth import layered_velocity, ricker, sine_mode, sine_modes_field, smooth_random_field
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ooc():
+    import paper_2109_05410_gb300 as m
+    m.build()
+    m.lib()
+    return m
+
+
+def roundtrip(ooc, d, fmt, rate):
+    if fmt == "fp32":
+        return d.clone()
+    if fmt == "bf16":
+        return ooc.ooc_bf16_unpack(ooc.ooc_bf16_pack(d)).reshape(d.shape)
+    return ooc.ooc_decompress(ooc.ooc_compress(d, rate), tuple(d.shape), rate)
+
+
+def pass_lengths(calls, k):
+    out = []
+    for n in calls:
+        full, rem = divmod(n, k)
+        out += [k] * full + ([rem] if rem else [])
+    return out
+
+
+def incore_heat(ooc, u0, calls, k, fmt, rate):
+    u = roundtrip(ooc, torch.from_numpy(u0).cuda(), fmt, rate)
+    tmp = torch.empty_like(u)
+    for kp in pass_lengths(calls, k):
+        ooc.ooc_heat7_steps(u, tmp, kp)
+        u = roundtrip(ooc, u, fmt, rate)
+    torch.cuda.synchronize()
+    return u.cpu().numpy()
+
+
+def incore_wave(ooc, p0, pm1, kappa, calls, k, fmt, rate, ro_fmt, ro_rate, src, w):
+    kap = roundtrip(ooc, torch.from_numpy(kappa).cuda(), ro_fmt, ro_rate)
+    p = roundtrip(ooc, torch.from_numpy(p0).cuda(), fmt, rate)
+    pp = roundtrip(ooc, torch.from_numpy(pm1).cuda(), fmt, rate)
+    t = 0
+    for kp in pass_lengths(calls, k):
+        ooc.ooc_wave25_steps(p, pp, kap, kp, src=src, w=w, t=t)
+        t += kp
+        p = roundtrip(ooc, p, fmt, rate)
+        pp = roundtrip(ooc, pp, fmt, rate)
+    torch.cuda.synchronize()
+    return p.cpu().numpy(), pp.cpu().numpy()
+
+
+FMTS = [("fp32", 16), ("bf16", 16), ("fr4", 8), ("fr4", 16), ("fr4", 24)]
+
+
+@pytest.mark.parametrize("fmt,rate", FMTS)
+@pytest.mark.parametrize("T,k,calls", [(4, 1, [5]), (8, 2, [7]), (12, 3, [10]), (28, 2, [3, 4]), (64, 4, [9]),
+                                       (32, 5, [11]), (8, 6, [13])])
+def test_heat7_ooc_bit_identical_to_incore(ooc, fmt, rate, T, k, calls):
+    shape = (64, 24, 32)  # nz = 64: thin last slabs for T = 12, 28
+    u0, _ = sine_modes_field(shape, seed=4)
+    plan = ooc.Plan(nx=32, ny=24, nz=64, stencil="heat7", k=k, rw_format=fmt, rw_rate=rate, slab_planes=T)
+    try:
+        plan.set_field(0, u0)
+        for n in calls:
+            plan.step(n)
+        got = plan.get_field(0)
+        st = plan.stats()
+    finally:
+        plan.close()
+    ref = incore_heat(ooc, u0, calls, k, fmt, rate)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+    assert st["steps_done"] == sum(calls)
+    assert st["passes"] == len(pass_lengths(calls, k))
+
+
+def wave_inputs(shape, nsteps, seed=3):
+    v = layered_velocity(shape, seed=seed)
+    dt = 0.4 * 10.0 / v.max()
+    kappa = ((v * dt / 10.0) ** 2).astype(np.float32)
+    nz, ny, nx = shape
+    src = (nx // 2, ny // 2, nz // 2)
+    w = (ricker(nsteps + 8, dt) * float(kappa[src[2], src[1], src[0]])).astype(np.float32)
+    rng = np.random.default_rng(seed)
+    p0 = (1e-3 * rng.normal(size=shape)).astype(np.float32)
+    pm1 = (0.9 * p0).astype(np.float32)
+    return kappa, p0, pm1, src, w
+
+
+@pytest.mark.parametrize("fmt,rate,ro_fmt,ro_rate", [("fp32", 16, "fp32", 16), ("fr4", 16, "fr4", 16),
+                                                     ("fr4", 12, "fp32", 16), ("bf16", 16, "bf16", 16),
+                                                     ("fp32", 16, "fr4", 8)])
+@pytest.mark.parametrize("T,k,calls", [(8, 1, [5]), (16, 2, [7]), (8, 3, [9]), (64, 2, [4]), (24, 3, [2, 5]),
+                                       (40, 10, [12])])
+def test_wave25_ooc_bit_identical_to_incore(ooc, fmt, rate, ro_fmt, ro_rate, T, k, calls):
+    shape = (64, 20, 24)
+    kappa, p0, pm1, src, w = wave_inputs(shape, sum(calls))
+    plan = ooc.Plan(nx=24, ny=20, nz=64, stencil="wave25", k=k, rw_format=fmt, rw_rate=rate, ro_format=ro_fmt,
+                    ro_rate=ro_rate, slab_planes=T)
+    try:
+        plan.set_field(0, p0)
+        plan.set_field(1, pm1)
+        plan.set_field(2, kappa)
+        plan.set_source(*src, w)
+        for n in calls:
+            plan.step(n)
+        got_p, got_pp = plan.get_field(0), plan.get_field(1)
+    finally:
+        plan.close()
+    ref_p, ref_pp = incore_wave(ooc, p0, pm1, kappa, calls, k, fmt, rate, ro_fmt, ro_rate, src, w)
+    assert np.array_equal(got_p.view(np.uint32), ref_p.view(np.uint32))
+    assert np.array_equal(got_pp.view(np.uint32), ref_pp.view(np.uint32))
+
+
+@pytest.mark.parametrize("fmt,rate", FMTS)
+def test_set_get_field_roundtrip(ooc, fmt, rate):
+    x = smooth_random_field((32, 16, 20), 4.0, seed=8)
+    plan = ooc.Plan(nx=20, ny=16, nz=32, stencil="heat7", k=2, rw_format=fmt, rw_rate=rate, slab_planes=8)
+    try:
+        plan.set_field(0, x)
+        got = plan.get_field(0)
+    finally:
+        plan.close()
+    ref = oracle.storage_roundtrip(x, fmt, rate).astype(np.float32)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+
+
+def test_heat7_ooc_against_oracle_pipeline(ooc):
+    # The configuration of the 128^3 heat case: 4 slabs of 32 planes, k = 2,
+    # 8 steps, FR4 at 16 bits/value.
+    shape = (128, 128, 128)
+    u0, _ = sine_modes_field(shape, seed=0)
+    plan = ooc.Plan(nx=128, ny=128, nz=128, stencil="heat7", k=2, rw_format="fr4", rw_rate=16, slab_planes=32)
+    try:
+        plan.set_field(0, u0)
+        plan.step(8)
+        got = plan.get_field(0)
+        info = plan.info()
+    finally:
+        plan.close()
+    assert info["nslab"] == 4
+    pipe = oracle.heat7_storage_pipeline(u0, 8, 2, "fr4", 16)
+    exact = oracle.heat7_run(u0.astype(np.float64), 8)
+    assert oracle.error_metrics(got, pipe)["rel_l2"] < 5e-5
+    assert oracle.error_metrics(got, exact)["rel_l2"] < 1e-4
+
+
+def test_budget_forces_streaming_and_matches_single_slab(ooc):
+    shape = (96, 32, 32)
+    u0, _ = sine_modes_field(shape, seed=2)
+    outs = []
+    for budget in (1 << 28, 300_000):
+        plan = ooc.Plan(nx=32, ny=32, nz=96, stencil="heat7", k=3, rw_format="fr4", rw_rate=12,
+                        device_budget_bytes=budget)
+        try:
+            plan.set_field(0, u0)
+            plan.step(9)
+            outs.append((plan.info()["nslab"], plan.get_field(0)))
+        finally:
+            plan.close()
+    assert outs[0][0] == 1 and outs[1][0] > 3
+    assert np.array_equal(outs[0][1].view(np.uint32), outs[1][1].view(np.uint32))
+
+
+def test_full_size_heat_benchmark_configuration(ooc):
+    # The 1024^3 heat workload exactly as bench.py runs it (1 GiB device
+    # budget, k = 4, 64 steps, FR4 at 16 bits/value): bit-identical to the
+    # in-core GPU reference, and within the stated error of the FP64 oracle
+    # on a sampled sub-box (central 128^3, exact dependency cone).
+    n, nsteps, k = 1024, 64, 4
+    u0 = smooth_random_field((n, n, n), 32.0, seed=2)
+    plan = ooc.Plan(nx=n, ny=n, nz=n, stencil="heat7", k=k, rw_format="fr4", rw_rate=16,
+                    device_budget_bytes=1 << 30)
+    try:
+        assert plan.device_bytes <= 1 << 30
+        plan.set_field(0, u0)
+        plan.step(nsteps)
+        got = plan.get_field(0)
+    finally:
+        plan.close()
+    ref = incore_heat(ooc, u0, [nsteps], k, "fr4", 16)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+    c0, c1 = n // 2 - 64, n // 2 + 64
+    sub = u0[c0 - nsteps:c1 + nsteps, c0 - nsteps:c1 + nsteps, c0 - nsteps:c1 + nsteps].astype(np.float64)
+    exact = oracle.heat7_run(sub, nsteps)[nsteps:-nsteps, nsteps:-nsteps, nsteps:-nsteps]
+    m = oracle.error_metrics(got[c0:c1, c0:c1, c0:c1], exact)
+    assert m["rel_l2"] < 1e-4, m

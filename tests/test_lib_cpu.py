@@ -1,0 +1,120 @@
+"""CPU-only checks of the C-ABI library: it builds, loads, exports every
+symbol include/ooc.h declares, and its host-side planning logic (shape and
+rate validation, budget-derived slab thickness) behaves as documented.  No
+kernel is launched here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2109_05410_gb300 as ooc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    ooc.build()
+    return ooc.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "ooc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ooc_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_functions()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_status_strings(L):
+    assert ooc.ooc_status_string(0) == "ok"
+    assert "budget" in ooc.ooc_status_string(2)
+    assert ooc.ooc_status_string(99) == "unknown status"
+
+
+def test_compressed_bytes(L):
+    assert ooc.ooc_compressed_bytes(1024, 1024, 1024, 16) == 1024 ** 3 * 2
+    assert ooc.ooc_compressed_bytes(8, 8, 8, 24) == 512 * 3
+    assert ooc.ooc_compressed_bytes(6, 8, 8, 16) == 0  # not a multiple of 4
+    assert ooc.ooc_compressed_bytes(8, 8, 8, 65) == 0
+
+
+def make_cfg(**kw):
+    c = ooc.OocConfig()
+    c.nx, c.ny, c.nz = kw.get("n", (64, 64, 64))
+    c.stencil = kw.get("stencil", ooc.OOC_HEAT7)
+    c.k = kw.get("k", 2)
+    c.r = 1.0 / 6.0
+    c.rw_format = kw.get("rw_format", ooc.OOC_FMT_FR4)
+    c.rw_rate = kw.get("rw_rate", 16)
+    c.ro_format = kw.get("ro_format", ooc.OOC_FMT_FP32)
+    c.ro_rate = kw.get("ro_rate", 16)
+    c.device_budget_bytes = kw.get("budget", 0)
+    c.slab_planes = kw.get("slab_planes", 0)
+    return c
+
+
+def plan_create(L, c):
+    h = ctypes.c_void_p()
+    d, hb = ctypes.c_size_t(), ctypes.c_size_t()
+    s = L.ooc_plan_create(ctypes.byref(c), ctypes.byref(h), ctypes.byref(d), ctypes.byref(hb))
+    info = None
+    if s == 0:
+        i = ooc.OocPlanInfo()
+        assert L.ooc_plan_get_info(h, ctypes.byref(i)) == 0
+        info = i.as_dict()
+        L.ooc_plan_destroy(h)
+    return s, d.value, hb.value, info
+
+
+def test_plan_validation(L):
+    assert plan_create(L, make_cfg(n=(64, 64, 62), slab_planes=8))[0] == 1
+    assert plan_create(L, make_cfg(k=0, slab_planes=8))[0] == 1
+    assert plan_create(L, make_cfg(rw_rate=0, slab_planes=8))[0] == 1
+    assert plan_create(L, make_cfg(rw_rate=65, slab_planes=8))[0] == 1
+    assert plan_create(L, make_cfg(stencil=3, slab_planes=8))[0] == 1
+    assert plan_create(L, make_cfg(slab_planes=6))[0] == 1
+    assert plan_create(L, make_cfg(rw_format=7, slab_planes=8))[0] == 1
+    assert plan_create(L, make_cfg())[0] == 1  # neither a budget nor a slab thickness
+
+
+def test_budget_derivation(L):
+    # The device budget forces streaming even though the grid would fit:
+    # the plan picks the largest 4-aligned slab that fits the arena.
+    plane = 1024 * 1024 * 4
+    s, dev, host, info = plan_create(L, make_cfg(n=(1024, 1024, 1024), k=4, rw_format=ooc.OOC_FMT_FR4, rw_rate=16,
+                                                 budget=1 << 30))
+    assert s == 0
+    assert dev <= 1 << 30
+    T = info["slab_planes"]
+    assert T % 4 == 0 and T >= 32
+    assert info["nslab"] == -(-1024 // T)
+    assert info["common_planes"] == 4 and info["halo"] == 1
+    assert info["ring_planes"] >= T + 4 + 2
+    assert host == 1024 ** 3 * 2
+    # one more slab plane would not fit
+    s2, dev2, _, _ = plan_create(L, make_cfg(n=(1024, 1024, 1024), k=4, rw_rate=16, slab_planes=T + 4))
+    assert s2 == 0 and dev2 > 1 << 30
+    # FP32 storage lands slabs directly in a ring twice as deep
+    s3, dev3, host3, info3 = plan_create(L, make_cfg(n=(1024, 1024, 1024), k=4, rw_format=ooc.OOC_FMT_FP32,
+                                                     budget=1 << 30))
+    assert s3 == 0 and host3 == 1024 ** 3 * 4
+    assert info3["ring_planes"] >= 2 * info3["slab_planes"] + 4 + 2
+    # a budget below one 4-plane slab is refused
+    s4 = plan_create(L, make_cfg(n=(1024, 1024, 1024), k=4, budget=8 * plane))[0]
+    assert s4 == 2
+
+
+def test_wave_plan_geometry(L):
+    s, dev, host, info = plan_create(L, make_cfg(n=(128, 128, 128), stencil=ooc.OOC_WAVE25, k=10,
+                                                 rw_format=ooc.OOC_FMT_FR4, rw_rate=16, ro_format=ooc.OOC_FMT_FR4,
+                                                 ro_rate=16, slab_planes=32))
+    assert s == 0
+    assert info["halo"] == 4 and info["common_planes"] == 40 and info["nrings"] == 3
+    assert host == 3 * 128 ** 3 * 2
