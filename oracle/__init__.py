@@ -71,6 +71,9 @@ def lib():
                 "oracle_wave25_step": (None, [vp, vp, vp, vp, i64, i64, i64, i64, dbl]),
                 "oracle_wave25_run": (None, [vp, vp, vp, vp, i64, i64, i64, i64, vp, i64, i64]),
                 "oracle_threads": (i32, []),
+                "oracle_wave25_traces": (i32, [vp, i64, i64, i64, i64, vp, i64, vp, i64, vp]),
+                "oracle_wave25_adjoint_grad": (i32, [vp, i64, i64, i64, i64, vp, i64, vp, i64, vp, vp]),
+                "oracle_wave25_born": (i32, [vp, vp, i64, i64, i64, i64, vp, i64, vp, i64, vp]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(L, name)
@@ -253,6 +256,57 @@ def wave25_run(p, p_prev, kappa, nsteps, src=-1, w=None, t0=0):
     lib().oracle_wave25_run(_p(a), _p(b), _p(k), _p(tmp), nx, ny, nz, int(src),
                             None if ww is None else _p(ww), int(t0), int(nsteps))
     return a, b
+
+
+# --------------------------------------------------------------------------- adjoint
+def _rec(rec):
+    return np.ascontiguousarray(rec, dtype=np.int64)
+
+
+def wave25_traces(kappa, src, w, nsteps, rec):
+    """FP64 forward from rest; returns traces [nsteps, nrec] (p^1..p^N at
+    the flat receiver indices ``rec``)."""
+    k = np.ascontiguousarray(kappa, dtype=np.float64)
+    nz, ny, nx = k.shape
+    r = _rec(rec)
+    ww = np.ascontiguousarray(w, dtype=np.float64)
+    out = np.zeros((nsteps, r.size), dtype=np.float64)
+    if lib().oracle_wave25_traces(_p(k), nx, ny, nz, int(src), _p(ww), int(nsteps), _p(r), r.size, _p(out)) != 0:
+        raise MemoryError("oracle_wave25_traces")
+    return out
+
+
+def wave25_adjoint_grad(kappa, src, w, nsteps, rec, res):
+    """dJ/dkappa for dJ/dtraces = ``res`` [nsteps, nrec] (FP64 discrete
+    adjoint)."""
+    k = np.ascontiguousarray(kappa, dtype=np.float64)
+    nz, ny, nx = k.shape
+    r = _rec(rec)
+    ww = np.ascontiguousarray(w, dtype=np.float64)
+    rr = np.ascontiguousarray(res, dtype=np.float64)
+    g = np.zeros_like(k)
+    if lib().oracle_wave25_adjoint_grad(_p(k), nx, ny, nz, int(src), _p(ww), int(nsteps), _p(r), r.size, _p(rr),
+                                        _p(g)) != 0:
+        raise MemoryError("oracle_wave25_adjoint_grad")
+    return g
+
+
+def wave25_born(kappa, dkappa, src, w, nsteps, rec):
+    k = np.ascontiguousarray(kappa, dtype=np.float64)
+    dk = np.ascontiguousarray(dkappa, dtype=np.float64)
+    nz, ny, nx = k.shape
+    r = _rec(rec)
+    ww = np.ascontiguousarray(w, dtype=np.float64)
+    out = np.zeros((nsteps, r.size), dtype=np.float64)
+    if lib().oracle_wave25_born(_p(k), _p(dk), nx, ny, nz, int(src), _p(ww), int(nsteps), _p(r), r.size,
+                                _p(out)) != 0:
+        raise MemoryError("oracle_wave25_born")
+    return out
+
+
+def misfit(traces, d):
+    r = np.asarray(traces, dtype=np.float64) - np.asarray(d, dtype=np.float64)
+    return 0.5 * float(np.sum(r * r))
 
 
 # --------------------------------------------------------------------------- pipelines
