@@ -137,6 +137,49 @@ ooc_status ooc_wave25_steps(float *d_p, float *d_pprev, const float *d_kappa, in
                             int64_t nz, int64_t sx, int64_t sy, int64_t sz, const float *h_w, int64_t t,
                             int64_t nsteps, void *stream);
 
+/* ---- Adjoint (gradient of a receiver misfit w.r.t. velocity) -------------
+ * Not in the paper: a differentiation workload on its 25-point propagator.
+ * Forward, n = 0..N-1, from rest (p^0 = p^{-1} = 0):
+ *   p^{n+1} = 2 p^n - p^{n-1} + kappa L(p^n) + w[n] delta_src,  tr[n] = p^{n+1}(rec)
+ * Adjoint for dJ/dtr = res:  mu^m = 2 mu^{m+1} - mu^{m+2} + L(kappa mu^{m+1})
+ * + S^T res[m-1], m = N..1;  dJ/dkappa = sum_n mu^{n+1} L(p^n) (FP64).
+ * Receivers are flat indices (int64, device, distinct). */
+
+/* d_out[i] = d_field[d_idx[i]], i < n (device pointers). */
+ooc_status ooc_gather(const float *d_field, const int64_t *d_idx, int64_t n, float *d_out, void *stream);
+/* d_field[d_idx[i]] += d_val[i]; indices must be distinct. */
+ooc_status ooc_scatter_add(float *d_field, const int64_t *d_idx, int64_t n, const float *d_val, void *stream);
+/* One adjoint step on dense fields: d_out = 2 mu - mu_prev + L(kappa * mu);
+ * d_out may alias d_mu_prev (then it is updated in place). */
+ooc_status ooc_wave25_adjoint_step(const float *d_mu, const float *d_mu_prev, float *d_out, const float *d_kappa,
+                                   int64_t nx, int64_t ny, int64_t nz, void *stream);
+/* d_grad[i] += (double)mu[i] * (double)L(p)[i]; d_grad 32-byte aligned. */
+ooc_status ooc_wave25_grad_accum(double *d_grad, const float *d_mu, const float *d_p, int64_t nx, int64_t ny,
+                                 int64_t nz, void *stream);
+/* kappa = (v * dt/dx)^2 and dJ/dv = dJ/dkappa * 2 v (dt/dx)^2, n values. */
+ooc_status ooc_kappa_from_velocity(const float *d_v, float *d_kappa, int64_t n, double dt_over_dx, void *stream);
+ooc_status ooc_velocity_grad(const double *d_grad_kappa, const float *d_v, float *d_grad_v, int64_t n,
+                             double dt_over_dx, void *stream);
+/* Pinned host bytes for checkpoints every `every` steps at `rate` bits/value
+ * (0 = FP32): ceil(N/every) checkpoints of (p^{kK}, p^{kK-1}).  Device work
+ * bytes for the forward and backward runs (K + 5 fields at most). */
+size_t ooc_wave25_ckpt_bytes(int64_t nx, int64_t ny, int64_t nz, int64_t nsteps, int64_t every, int rate);
+size_t ooc_wave25_adjoint_work_bytes(int64_t nx, int64_t ny, int64_t nz, int64_t every, int rate);
+/* Forward run from rest writing d_traces[nsteps][nrec] and the checkpoints
+ * (h_ckpt pinned).  streams[0] computes, streams[1] copies checkpoints.
+ * Blocks until done (OOC_E_TIMEOUT after 10 minutes). */
+ooc_status ooc_wave25_forward_ckpt(const float *d_kappa, int64_t nx, int64_t ny, int64_t nz, int64_t sx, int64_t sy,
+                                   int64_t sz, const float *h_w, int64_t nsteps, const int64_t *d_rec, int64_t nrec,
+                                   float *d_traces, int64_t every, int rate, void *h_ckpt, size_t ckpt_bytes,
+                                   void *d_work, size_t work_bytes, void *const streams[2]);
+/* Backward run: d_grad = dJ/dkappa (FP64, device, overwritten) for the
+ * residual d_res[nsteps][nrec], replaying each segment from its checkpoint. */
+ooc_status ooc_wave25_backward_ckpt(const float *d_kappa, int64_t nx, int64_t ny, int64_t nz, int64_t sx, int64_t sy,
+                                    int64_t sz, const float *h_w, int64_t nsteps, const int64_t *d_rec, int64_t nrec,
+                                    const float *d_res, int64_t every, int rate, const void *h_ckpt,
+                                    size_t ckpt_bytes, double *d_grad, void *d_work, size_t work_bytes,
+                                    void *const streams[2]);
+
 /* Plan an out-of-core run (Section III decomposition with Section V-A
  * units).  Validates `cfg`, chooses the slab thickness T (largest multiple of
  * 4 that fits device_budget_bytes unless cfg->slab_planes is set) and

@@ -21,6 +21,9 @@ __all__ = [
     "OocConfig", "OocStats", "OocPlanInfo", "OocError", "lib", "build",
     "ooc_status_string", "ooc_compressed_bytes", "ooc_compress", "ooc_decompress",
     "ooc_bf16_pack", "ooc_bf16_unpack", "ooc_heat7_steps", "ooc_wave25_steps", "Plan",
+    "ooc_gather", "ooc_scatter_add", "ooc_wave25_adjoint_step", "ooc_wave25_grad_accum", "ooc_kappa_from_velocity",
+    "ooc_velocity_grad", "ooc_wave25_ckpt_bytes", "ooc_wave25_adjoint_work_bytes", "ooc_wave25_forward_ckpt",
+    "ooc_wave25_backward_ckpt", "WaveFn", "wave_forward",
 ]
 
 OOC_HEAT7, OOC_WAVE25 = 1, 2
@@ -96,6 +99,24 @@ _SIGS = {
     "ooc_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(OocStats)]),
     "ooc_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
     "ooc_plan_destroy": (None, [ctypes.c_void_p]),
+    "ooc_gather": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
+    "ooc_scatter_add": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    "ooc_wave25_adjoint_step": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int64] * 3 + [ctypes.c_void_p]),
+    "ooc_wave25_grad_accum": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int64] * 3 + [ctypes.c_void_p]),
+    "ooc_kappa_from_velocity": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
+                                               ctypes.c_void_p]),
+    "ooc_velocity_grad": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int64, ctypes.c_double, ctypes.c_void_p]),
+    "ooc_wave25_ckpt_bytes": (ctypes.c_size_t, [ctypes.c_int64] * 5 + [ctypes.c_int]),
+    "ooc_wave25_adjoint_work_bytes": (ctypes.c_size_t, [ctypes.c_int64] * 4 + [ctypes.c_int]),
+    "ooc_wave25_forward_ckpt": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int64] * 6
+                                + [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                   ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                   ctypes.c_size_t, ctypes.c_void_p * 2]),
+    "ooc_wave25_backward_ckpt": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int64] * 6
+                                 + [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                    ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p * 2]),
 }
 
 
@@ -207,6 +228,97 @@ def ooc_wave25_steps(d_p, d_pprev, d_kappa, nsteps, src=None, w=None, t=0, strea
     return d_p, d_pprev
 
 
+def ooc_gather(d_field, d_idx, d_out=None, stream=None):
+    import torch
+    if d_out is None:
+        d_out = torch.empty(d_idx.numel(), dtype=torch.float32, device=d_field.device)
+    _check(lib().ooc_gather(_ptr(d_field), _ptr(d_idx), d_idx.numel(), _ptr(d_out), _stream(stream)), "ooc_gather")
+    return d_out
+
+
+def ooc_scatter_add(d_field, d_idx, d_val, stream=None):
+    _check(lib().ooc_scatter_add(_ptr(d_field), _ptr(d_idx), d_idx.numel(), _ptr(d_val), _stream(stream)),
+           "ooc_scatter_add")
+    return d_field
+
+
+def ooc_wave25_adjoint_step(d_mu, d_mu_prev, d_kappa, d_out=None, stream=None):
+    """d_out = 2 mu - mu_prev + L(kappa mu) (in place on d_mu_prev if d_out is None)."""
+    nz, ny, nx = d_mu.shape
+    if d_out is None:
+        d_out = d_mu_prev
+    _check(lib().ooc_wave25_adjoint_step(_ptr(d_mu), _ptr(d_mu_prev), _ptr(d_out), _ptr(d_kappa), nx, ny, nz,
+                                         _stream(stream)), "ooc_wave25_adjoint_step")
+    return d_out
+
+
+def ooc_wave25_grad_accum(d_grad, d_mu, d_p, stream=None):
+    nz, ny, nx = d_mu.shape
+    _check(lib().ooc_wave25_grad_accum(_ptr(d_grad), _ptr(d_mu), _ptr(d_p), nx, ny, nz, _stream(stream)),
+           "ooc_wave25_grad_accum")
+    return d_grad
+
+
+def ooc_kappa_from_velocity(d_v, dt_over_dx, d_kappa=None, stream=None):
+    import torch
+    if d_kappa is None:
+        d_kappa = torch.empty_like(d_v)
+    _check(lib().ooc_kappa_from_velocity(_ptr(d_v), _ptr(d_kappa), d_v.numel(), float(dt_over_dx), _stream(stream)),
+           "ooc_kappa_from_velocity")
+    return d_kappa
+
+
+def ooc_velocity_grad(d_grad_kappa, d_v, dt_over_dx, d_grad_v=None, stream=None):
+    import torch
+    if d_grad_v is None:
+        d_grad_v = torch.empty_like(d_v)
+    _check(lib().ooc_velocity_grad(_ptr(d_grad_kappa), _ptr(d_v), _ptr(d_grad_v), d_v.numel(), float(dt_over_dx),
+                                   _stream(stream)), "ooc_velocity_grad")
+    return d_grad_v
+
+
+def ooc_wave25_ckpt_bytes(shape, nsteps, every, rate):
+    nz, ny, nx = shape
+    return int(lib().ooc_wave25_ckpt_bytes(nx, ny, nz, nsteps, every, rate))
+
+
+def ooc_wave25_adjoint_work_bytes(shape, every, rate):
+    nz, ny, nx = shape
+    return int(lib().ooc_wave25_adjoint_work_bytes(nx, ny, nz, every, rate))
+
+
+def _src_args(src, w, nsteps):
+    if src is None or w is None:
+        return -1, -1, -1, None, None
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    if w.size < nsteps:
+        raise ValueError("source series shorter than nsteps")
+    return src[0], src[1], src[2], w, w.ctypes.data_as(ctypes.c_void_p)
+
+
+def ooc_wave25_forward_ckpt(d_kappa, nsteps, d_rec, d_traces, every, rate, h_ckpt, d_work, streams, src=None, w=None):
+    nz, ny, nx = d_kappa.shape
+    sx, sy, sz, w_keep, wp = _src_args(src, w, nsteps)
+    arr = (ctypes.c_void_p * 2)(*[s.cuda_stream for s in streams])
+    _check(lib().ooc_wave25_forward_ckpt(_ptr(d_kappa), nx, ny, nz, sx, sy, sz, wp, int(nsteps), _ptr(d_rec),
+                                         d_rec.numel(), _ptr(d_traces), int(every), int(rate), _ptr(h_ckpt),
+                                         h_ckpt.numel(), _ptr(d_work), d_work.numel(), arr),
+           "ooc_wave25_forward_ckpt")
+    return d_traces
+
+
+def ooc_wave25_backward_ckpt(d_kappa, nsteps, d_rec, d_res, every, rate, h_ckpt, d_grad, d_work, streams, src=None,
+                             w=None):
+    nz, ny, nx = d_kappa.shape
+    sx, sy, sz, w_keep, wp = _src_args(src, w, nsteps)
+    arr = (ctypes.c_void_p * 2)(*[s.cuda_stream for s in streams])
+    _check(lib().ooc_wave25_backward_ckpt(_ptr(d_kappa), nx, ny, nz, sx, sy, sz, wp, int(nsteps), _ptr(d_rec),
+                                          d_rec.numel(), _ptr(d_res), int(every), int(rate), _ptr(h_ckpt),
+                                          h_ckpt.numel(), _ptr(d_grad), _ptr(d_work), d_work.numel(), arr),
+           "ooc_wave25_backward_ckpt")
+    return d_grad
+
+
 def _fmt(v):
     return FORMATS[v] if isinstance(v, str) else int(v)
 
@@ -292,3 +404,6 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+from .autograd import WaveFn, wave_forward  # noqa: E402

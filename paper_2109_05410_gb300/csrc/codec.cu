@@ -27,6 +27,8 @@ namespace {
 
 constexpr int kPrec = 26;  // block-floating-point precision (bits)
 constexpr int kThreads = 128;
+constexpr int kPlaneStride = 65;  // words per thread for its plane masks
+constexpr int kSlack = 8;         // words past a block's 2R that a coder may touch
 
 // ---- sequency order ---------------------------------------------------------
 // r-th coefficient of the coding order: sort by level sum of (i, j, k) with
@@ -202,98 +204,97 @@ __device__ __forceinline__ void transpose32(uint32_t (&a)[64])
 }
 
 // ---- bit writer / reader over a thread's shared-memory words ------------------
+// Appends bit fields to a thread's words, least-significant bit first,
+// through a 32-bit accumulator.  No budget check: the budget B = 64R bits is
+// exactly 2R words, so the coder runs until a plane ends at or past B and only
+// the first 2R words are kept; the thread's slot has slack for the overrun.
 struct BitWriter {
     uint32_t *dst;
     int widx;
-    int nacc;  // valid bits in acc, < 32 between calls
-    int left;  // budget bits still writable
-    uint64_t acc;
+    uint32_t acc;
+    int nacc;  // pending bits in acc, < 32
+    int pos;   // bits appended so far
 
-    // Append the low `len` (0..64) bits of v; bits of v above len are zero.
-    __device__ __forceinline__ void raw(uint64_t v, int len)
+    __device__ __forceinline__ static uint32_t low_mask(int l)  // l in [0, 32]
     {
-        const uint64_t lo = acc | (v << nacc);
-        const uint64_t hi = nacc ? (v >> (64 - nacc)) : 0ull;
+        return (uint32_t)((1ull << l) - 1ull);
+    }
+    // Append the low `len` (0..32) bits of v; bits of v above len are zero.
+    __device__ __forceinline__ void app(uint32_t v, int len)
+    {
+        const uint32_t lo = acc | (v << nacc);
+        const uint32_t carry = __funnelshift_lc(v, 0u, nacc);  // v >> (32 - nacc)
         const int tot = nacc + len;
-        if (tot >= 64) {
-            dst[widx] = (uint32_t)lo;
-            dst[widx + 1] = (uint32_t)(lo >> 32);
-            widx += 2;
-            acc = hi;
-            nacc = tot - 64;
-        } else if (tot >= 32) {
-            dst[widx++] = (uint32_t)lo;
-            acc = lo >> 32;
+        pos += len;
+        if (tot >= 32) {
+            dst[widx++] = lo;
+            acc = carry;
             nacc = tot - 32;
         } else {
             acc = lo;
             nacc = tot;
         }
     }
-    // Append min(len, left) low bits of v (bits above len zero).
-    __device__ __forceinline__ void put(uint64_t v, int len)
+    __device__ __forceinline__ void app64(uint64_t v, int len)  // len in [0, 64]
     {
-        if (len > left) {
-            len = left;
-            v &= (1ull << len) - 1ull;  // len < 64 here
-        }
-        if (len <= 0)
-            return;
-        left -= len;
-        raw(v, len);
+        const int l1 = len < 32 ? len : 32;
+        app((uint32_t)v, l1);
+        app((uint32_t)(v >> 32), len - l1);
+    }
+    __device__ __forceinline__ void zeros(int len)  // len in [0, 64]
+    {
+        const int l1 = len < 32 ? len : 32;
+        app(0u, l1);
+        app(0u, len - l1);
     }
     __device__ __forceinline__ void finish(int words)
     {
-        if (nacc > 0) {
-            dst[widx++] = (uint32_t)acc;
-            nacc = 0;
-        }
+        if (nacc > 0)
+            dst[widx++] = acc;
         while (widx < words)
             dst[widx++] = 0u;
     }
 };
 
+// Reads bit fields of a thread's words.  The words past the block's 2R are
+// zero (slack), so bits past the budget read as 0, which is what a
+// truncated stream means; only the implied-one rule needs the budget.
 struct BitReader {
-    const uint32_t *src;  // may be read up to 2 words past the block
+    const uint32_t *src;
     int pos;
-    int end;
 
-    __device__ __forceinline__ uint64_t peek(int len) const  // 1 <= len <= 64
+    __device__ __forceinline__ uint32_t get(int len)  // len in [0, 32]
     {
         const int w = pos >> 5, sh = pos & 31;
-        uint64_t v = ((uint64_t)src[w] | ((uint64_t)src[w + 1] << 32)) >> sh;
-        if (sh != 0 && len > 64 - sh)
-            v |= (uint64_t)src[w + 2] << (64 - sh);
-        return len >= 64 ? v : (v & ((1ull << len) - 1ull));
-    }
-    __device__ __forceinline__ uint64_t read(int len)  // bits beyond `end` read as 0
-    {
-        const int av = end - pos;
-        if (len > av)
-            len = av;
-        if (len <= 0)
-            return 0;
-        const uint64_t v = peek(len);
+        const uint32_t v = __funnelshift_r(src[w], src[w + 1], sh) & BitWriter::low_mask(len);
         pos += len;
         return v;
+    }
+    __device__ __forceinline__ uint64_t peek64(int len) const  // 1 <= len <= 63
+    {
+        const int w = pos >> 5, sh = pos & 31;
+        const uint32_t a = __funnelshift_r(src[w], src[w + 1], sh);
+        const uint32_t b = __funnelshift_r(src[w + 1], src[w + 2], sh);
+        return (((uint64_t)b << 32) | a) & ((1ull << len) - 1ull);
     }
 };
 
 // ---- one block ----------------------------------------------------------------
-__device__ __forceinline__ void encode_block(uint32_t (&v)[64], int rate, uint32_t *dst)
+__device__ __forceinline__ void encode_block(uint32_t (&v)[64], int rate, uint32_t *dst, uint32_t *pm)
 {
     const int words = 2 * rate;
     uint32_t mx = 0;
 #pragma unroll
     for (int i = 0; i < 64; ++i)
         mx = max(mx, v[i] & 0x7FFFFFFFu);
-    BitWriter w{dst, 0, 0, 64 * rate, 0ull};
+    BitWriter w{dst, 0, 0u, 0, 0};
+    const int budget = 64 * rate;
     if (mx == 0u) {
         w.finish(words);
         return;
     }
     const int emax = (int)(mx >> 23) - 126;  // largest frexp exponent, >= -126
-    w.put(1u | ((uint32_t)((emax + 127) & 0xFF) << 1), 9);
+    w.app(1u | ((uint32_t)((emax + 127) & 0xFF) << 1), 9);
 
     // q = trunc(x * 2^(26 - emax)), with the power of two split in two
     // normal factors; the first product is exact whenever the result can be
@@ -311,76 +312,72 @@ __device__ __forceinline__ void encode_block(uint32_t (&v)[64], int rate, uint32
     to_coding_order(v, q, std::make_integer_sequence<int, 64>{});
     transpose32<0>(v);   // v[p]      = bits p of coefficients 0..31
     transpose32<32>(v);  // v[32 + p] = bits p of coefficients 32..63
-
-    // Plane p: the refinement bits of the n significant coefficients, then
-    // the significance part S.  With the new ones of the plane at offsets
-    // t_1 < .. < t_m past n, S holds a group bit 1 at 0, the j-th new one at
-    // D_j = t_j + j, a group bit 1 at D_j + 1 for j < m, and a closing group
-    // bit 0 if coefficients remain; when t_m is the last coefficient its one
-    // is implied and not written.  S is built with one step per new one.
-    int n = 0;
+    // The plane loop below stays a compact loop (no unrolling) and reads the
+    // plane masks from this thread's shared-memory slot.
 #pragma unroll
-    for (int p = 31; p >= 0; --p) {
-        if (w.left <= 0)
-            break;
-        const uint64_t X = ((uint64_t)v[32 + p] << 32) | v[p];
-        w.put(n >= 64 ? X : (X & ((1ull << n) - 1ull)), n);
-        if (n < 64) {
-            const uint64_t rest = X >> n;
-            if (rest == 0ull) {
-                w.put(0ull, 1);
+    for (int i = 0; i < 64; ++i)
+        pm[i] = v[i];
+
+    // Plane p (31 .. 0) is written as: the refinement bits of the n
+    // significant coefficients; then, for each new one at offset t past n,
+    // a segment (group bit 1, the zeros before it, the one); then a closing
+    // group bit 0 if coefficients remain.  When a new one is the last
+    // coefficient its one is implied and not written.  The loop emits one
+    // such chunk per iteration, so every lane of a warp runs the same small
+    // body whatever plane it is in.
+    int p = 31, n = 0, nstart = 0, prev = -1;
+    bool ref = true;  // next chunk: plane p's refinement bits
+    uint64_t X = ((uint64_t)pm[32 + 31] << 32) | pm[31];
+    uint64_t rest = 0ull;
+#pragma unroll 1
+    while (p >= 0 && w.pos < budget) {
+        uint64_t chunk;
+        int len;
+        bool plane_done;
+        if (ref) {
+            chunk = n >= 64 ? X : (X & ((1ull << n) - 1ull));
+            len = n;
+            rest = n < 64 ? (X >> n) : 0ull;
+            nstart = n;
+            prev = -1;
+            ref = false;
+            plane_done = n >= 64;
+        } else if (rest == 0ull) {
+            chunk = 0ull;  // closing group bit (n < 64 here)
+            len = 1;
+            plane_done = true;
+        } else {
+            const int t = __ffsll((long long)rest) - 1;
+            const int gap = t - prev - 1;
+            rest &= rest - 1ull;
+            if (nstart + t == 63) {  // last coefficient: group bit and zeros, its one implied
+                chunk = 1ull;
+                len = gap + 1;
+                n = 64;
+                plane_done = true;
             } else {
-                uint64_t dlo = 0ull, dhi = 0ull, rr = rest;
-                int j = 0, tm = 0;
-                while (rr != 0ull) {
-                    tm = __ffsll((long long)rr) - 1;
-                    ++j;
-                    const int d = tm + j;
-                    if (d < 64)
-                        dlo |= 1ull << d;
-                    else
-                        dhi |= 1ull << (d - 64);
-                    rr &= rr - 1ull;
-                }
-                const int dm = tm + j;  // position of the last new one
-                uint64_t glo = dlo << 1, ghi = (dhi << 1) | (dlo >> 63);
-                if (dm + 1 < 64)
-                    glo &= ~(1ull << (dm + 1));
-                else if (dm + 1 < 128)
-                    ghi &= ~(1ull << (dm + 1 - 64));
-                uint64_t slo = 1ull | dlo | glo, shi = dhi | ghi;
-                int ls;
-                if (n + tm == 63) {  // last coefficient reached: its one is implied
-                    if (dm < 64)
-                        slo &= ~(1ull << dm);
-                    else
-                        shi &= ~(1ull << (dm - 64));
-                    ls = dm;
-                    n = 64;
-                } else {
-                    n += tm + 1;
-                    ls = dm + 1 + (n < 64 ? 1 : 0);
-                }
-                if (ls <= 64) {
-                    w.put(slo, ls);
-                } else {
-                    w.put(slo, 64);
-                    if (ls <= 128) {
-                        w.put(shi, ls - 64);
-                    } else {
-                        w.put(shi, 64);
-                        w.put(0ull, ls - 128);
-                    }
-                }
+                chunk = 1ull | (2ull << gap);
+                len = gap + 2;
+                prev = t;
+                n = nstart + t + 1;
+                plane_done = false;
             }
+        }
+        w.app64(chunk, len);
+        if (plane_done) {
+            --p;
+            ref = true;
+            if (p >= 0)
+                X = ((uint64_t)pm[32 + p] << 32) | pm[p];
         }
     }
     w.finish(words);
 }
 
-__device__ __forceinline__ void decode_block(const uint32_t *src, int rate, float (&out)[64])
+__device__ __forceinline__ void decode_block(const uint32_t *src, int rate, float (&out)[64], uint32_t *pm)
 {
-    BitReader r{src, 0, 64 * rate};
+    BitReader r{src, 9};
+    const int budget = 64 * rate;
     if ((src[0] & 1u) == 0u) {
 #pragma unroll
         for (int i = 0; i < 64; ++i)
@@ -388,43 +385,46 @@ __device__ __forceinline__ void decode_block(const uint32_t *src, int rate, floa
         return;
     }
     const int emax = (int)((src[0] >> 1) & 0xFFu) - 127;
-    r.pos = 9;
-    uint32_t u[64];
     int n = 0;
-#pragma unroll
-    for (int p = 31; p >= 0; --p) {
-        uint64_t X = 0;
-        if (r.pos < r.end) {
-            if (n > 0)
-                X = r.read(n);
-            if (n < 64) {
-                while (r.pos < r.end) {
-                    if (r.read(1) == 0ull)
-                        break;
-                    const int len = 63 - n;  // explicit scan bits at most
-                    const int av = r.end - r.pos;
-                    const int m = len < av ? len : av;
-                    const uint64_t s = m > 0 ? r.peek(m) : 0ull;
-                    if (s != 0ull) {
-                        const int t = __ffsll((long long)s) - 1;
-                        r.pos += t + 1;
-                        X |= 1ull << (n + t);
-                        n += t + 1;
-                    } else if (av >= len) {
-                        r.pos += len;
-                        X |= 1ull << 63;  // implied one of the last coefficient
+    int p = 31;
+#pragma unroll 1
+    for (; p >= 0 && r.pos < budget; --p) {
+        const int n1 = n < 32 ? n : 32;
+        uint32_t xl = r.get(n1);
+        uint32_t xh = r.get(n - n1);
+        if (n < 64) {
+            uint64_t X = 0ull;  // the plane's new ones
+            while (r.get(1) != 0u) {
+                const int len = 63 - n;  // explicit scan bits at most
+                const uint64_t sc = len > 0 ? r.peek64(len) : 0ull;
+                if (sc != 0ull) {
+                    const int t = __ffsll((long long)sc) - 1;
+                    r.pos += t + 1;
+                    X |= 1ull << (n + t);
+                    n += t + 1;
+                } else {
+                    if (r.pos + len <= budget) {  // scan complete: last coefficient's one implied
+                        X |= 1ull << 63;
                         n = 64;
-                        break;
-                    } else {
-                        r.pos = r.end;
-                        break;
                     }
+                    r.pos += len;
+                    break;
                 }
             }
+            xl |= (uint32_t)X;
+            xh |= (uint32_t)(X >> 32);
         }
-        u[p] = (uint32_t)X;
-        u[32 + p] = (uint32_t)(X >> 32);
+        pm[p] = xl;
+        pm[32 + p] = xh;
     }
+    for (; p >= 0; --p) {  // planes past the budget
+        pm[p] = 0u;
+        pm[32 + p] = 0u;
+    }
+    uint32_t u[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i)
+        u[i] = pm[i];
     transpose32<0>(u);
     transpose32<32>(u);
     int32_t q[64];
@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(kThreads) fr4_encode_kernel(ConstRing in, int6
                                                              int64_t nblk, int rate, uint32_t *__restrict__ out)
 {
     extern __shared__ uint32_t smem[];
-    const int words = 2 * rate, stride = words + 1;
+    const int words = 2 * rate, stride = words + kSlack + 1;
     const int64_t first = (int64_t)blockIdx.x * kThreads;
     const int64_t b = first + threadIdx.x;
     if (b < nblk) {
@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(kThreads) fr4_encode_kernel(ConstRing in, int6
                 v[16 * k + 4 * j + 2] = __float_as_uint(f.z);
                 v[16 * k + 4 * j + 3] = __float_as_uint(f.w);
             }
-        encode_block(v, rate, smem + threadIdx.x * stride);
+        encode_block(v, rate, smem + threadIdx.x * stride, smem + kThreads * stride + threadIdx.x * kPlaneStride);
     }
     __syncthreads();
     const int64_t left = nblk - first;
@@ -482,21 +482,22 @@ __global__ void __launch_bounds__(kThreads) fr4_decode_kernel(const uint32_t *__
                                                              int64_t z0, int64_t nblk, int rate, Ring out)
 {
     extern __shared__ uint32_t smem[];
-    const int words = 2 * rate, stride = words + 1;
+    const int words = 2 * rate, stride = words + kSlack + 1;
     const int64_t first = (int64_t)blockIdx.x * kThreads;
     const int64_t left = nblk - first;
     const int nvalid = left < kThreads ? (int)left : kThreads;
     const uint32_t *src = in + first * words;
     for (int o = threadIdx.x; o < nvalid * words; o += kThreads)
         smem[(o / words) * stride + (o % words)] = __ldg(src + o);
-    if (threadIdx.x < 2)
-        smem[kThreads * stride + threadIdx.x] = 0u;  // reader slack past the last block
+#pragma unroll
+    for (int j = 0; j < kSlack; ++j)  // bits past the block read as 0
+        smem[threadIdx.x * stride + words + j] = 0u;
     __syncthreads();
     const int64_t b = first + threadIdx.x;
     if (b >= nblk)
         return;
     float f[64];
-    decode_block(smem + threadIdx.x * stride, rate, f);
+    decode_block(smem + threadIdx.x * stride, rate, f, smem + kThreads * stride + threadIdx.x * kPlaneStride);
     const int64_t nbx = nx >> 2, nby = ny >> 2;
     const int64_t bx = b % nbx, t2 = b / nbx, by = t2 % nby, bz = t2 / nby;
     const int64_t slot = ring_slot(z0 + 4 * bz, out.zbase, out.nslot);
@@ -509,7 +510,13 @@ __global__ void __launch_bounds__(kThreads) fr4_decode_kernel(const uint32_t *__
                 make_float4(f[16 * k + 4 * j], f[16 * k + 4 * j + 1], f[16 * k + 4 * j + 2], f[16 * k + 4 * j + 3]);
 }
 
-size_t smem_bytes(int rate) { return ((size_t)kThreads * (2 * rate + 1) + 2) * sizeof(uint32_t); }
+// Shared memory per CTA: each thread's compressed words plus kSlack words
+// of slack (stride 2R + kSlack + 1, odd, so that the threads' slots start in
+// different banks), then each thread's 64 plane masks (stride 65).
+size_t smem_bytes(int rate)
+{
+    return ((size_t)kThreads * (2 * rate + kSlack + 1) + (size_t)kThreads * kPlaneStride) * sizeof(uint32_t);
+}
 
 cudaError_t ensure_smem_attr()
 {

@@ -42,6 +42,10 @@ cudaError_t launch_heat7(ConstRing in, Ring out, int64_t nx, int64_t ny, int64_t
                          float r, cudaStream_t st);
 cudaError_t launch_wave25(ConstRing p, Ring pprev_out, ConstRing kappa, int64_t nx, int64_t ny, int64_t nz,
                           int64_t z0, int64_t z1, int64_t sx, int64_t sy, int64_t sz, float w, cudaStream_t st);
+// Same step with p_prev read from `pprev` and p' written to `pnew` (may alias).
+cudaError_t launch_wave25_to(ConstRing p, ConstRing pprev, Ring pnew, ConstRing kappa, int64_t nx, int64_t ny,
+                             int64_t nz, int64_t z0, int64_t z1, int64_t sx, int64_t sy, int64_t sz, float w,
+                             cudaStream_t st);
 // Codec over the 4-aligned plane range [z0, z1) of a ring; the stream part
 // for those planes is contiguous (2*rate words per block).
 cudaError_t launch_fr4_encode(ConstRing in, int64_t nx, int64_t ny, int64_t z0, int64_t z1, int rate,

@@ -21,8 +21,8 @@
 //   u' = u + r (u[x-1] + u[x+1] + u[y-1] + u[y+1] + u[z-1] + u[z+1] - 6u)
 // wave25 (Section VI's 25-point propagator, HALO = 4, Table I), leapfrog:
 //   p' = 2p - p_prev + kappa * sum_axes[c0 p + sum_m c_m (p[+m] + p[-m])]
-// p' overwrites p_prev in place: each point's p_prev is read only by the
-// thread that writes p' there.
+// p' overwrites p_prev in place (or goes to a separate array): each point's
+// p_prev is read only by the thread that writes p' there.
 #include "common.cuh"
 
 namespace ooc {
@@ -41,24 +41,19 @@ struct Grid3 {
     int64_t nx, ny, nz, plane;
 };
 
-// 128-bit load of the 4 points at (x4..x4+3, y, z) or zeros outside the grid.
-__device__ __forceinline__ float4 ld4(const float *base, const Grid3 &g, int64_t z, int64_t slot, int64_t x4,
-                                      int64_t y)
+// All rings of one launch share the slot geometry (Z, zbase), so one 32-bit
+// slot counter per z-step addresses every field; it advances with wrap-around.
+__device__ __forceinline__ int wrap_add(int s, int d, int nslot)
 {
-    if (z < 0 || z >= g.nz || y < 0 || y >= g.ny || x4 < 0 || x4 >= g.nx)
-        return zero4();
-    return __ldg(reinterpret_cast<const float4 *>(base + slot * g.plane + y * g.nx + x4));
+    s += d;
+    return s >= nslot ? s - nslot : s;
 }
 
-__device__ __forceinline__ float ld1(const float *base, const Grid3 &g, int64_t z, int64_t slot, int64_t x, int64_t y)
-{
-    if (z < 0 || z >= g.nz || y < 0 || y >= g.ny || x < 0 || x >= g.nx)
-        return 0.0f;
-    return __ldg(base + slot * g.plane + y * g.nx + x);
-}
+__device__ __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
 
 __global__ void __launch_bounds__(kTX *kHeatTY)
-    heat7_kernel(ConstRing in, Ring out, Grid3 g, int64_t z0, int64_t z1, int64_t zchunk, float r)
+    heat7_kernel(const float *__restrict__ in, float *__restrict__ out, int nslot, int64_t zbase, Grid3 g,
+                 int64_t z0, int64_t z1, int64_t zchunk, float r)
 {
     __shared__ float4 tile[2][kHeatTY + 2][kTX];
     const int lane = threadIdx.x, ty = threadIdx.y;
@@ -67,32 +62,47 @@ __global__ void __launch_bounds__(kTX *kHeatTY)
     const int64_t y0 = (int64_t)blockIdx.y * kHeatTY;
     const int64_t y = y0 + ty;
     const int64_t za = z0 + (int64_t)blockIdx.z * zchunk;
-    const int64_t zb = min(za + zchunk, z1);
+    const int cnt = (int)(min(za + zchunk, z1) - za);
+    const int64_t nz = g.nz, plane = g.plane;
+    // loop-invariant in-grid flags and in-plane offsets
     const bool inside = x4 < g.nx && y < g.ny;
-    // halo duties: edge warps load one y-halo row, edge lanes one x value
-    const int64_t yh = ty == 0 ? y0 - 1 : (ty == kHeatTY - 1 ? y0 + kHeatTY : -1);
-    const bool row_halo = ty == 0 || ty == kHeatTY - 1;
-    const int64_t xh = lane == 0 ? xs - 1 : xs + kSeg;
-    const bool col_halo = lane == 0 || lane == kTX - 1;
+    const int64_t off = inside ? y * g.nx + x4 : 0;
+    const int64_t yh = ty == 0 ? y0 - 1 : y0 + kHeatTY;  // halo row of the edge warps
+    const bool hrow = (ty == 0 || ty == kHeatTY - 1) && yh >= 0 && yh < g.ny && x4 < g.nx;
+    const int64_t hoff = hrow ? yh * g.nx + x4 : 0;
+    const int64_t xh = lane == 0 ? xs - 1 : xs + kSeg;  // halo column of the edge lanes
+    const bool hcol = (lane == 0 || lane == kTX - 1) && xh >= 0 && xh < g.nx && y < g.ny;
+    const int64_t xoff = hcol ? y * g.nx + xh : 0;
+    const float4 z4 = zero4();
 
-    int64_t s = ring_slot(za - 1, in.zbase, in.nslot);  // slot of plane za - 1
-    float4 prev = ld4(in.base, g, za - 1, s, x4, y);
-    s = next_slot(s, in.nslot);
-    float4 cur = ld4(in.base, g, za, s, x4, y);
-    float4 hyv = row_halo ? ld4(in.base, g, za, s, x4, yh) : zero4();
-    float hx = col_halo ? ld1(in.base, g, za, s, xh, y) : 0.f;
-    s = next_slot(s, in.nslot);
-    float4 nxt = ld4(in.base, g, za + 1, s, x4, y);
-    int64_t s_next = s;  // slot of plane z + 1
-    int64_t s_out = ring_slot(za, out.zbase, out.nslot);
-    for (int64_t z = za; z < zb; ++z) {
-        // prefetch plane z + 2 and the halo of plane z + 1
-        const int64_t s_pf = next_slot(s_next, in.nslot);
-        const float4 pf = ld4(in.base, g, z + 2, s_pf, x4, y);
-        const float4 hyv_n = row_halo ? ld4(in.base, g, z + 1, s_next, x4, yh) : zero4();
-        const float hx_n = col_halo ? ld1(in.base, g, z + 1, s_next, xh, y) : 0.f;
+    int s = (int)ring_slot(za, zbase, nslot);  // slot of plane z
+    const float *pm = in + (int64_t)wrap_add(s, nslot - 1, nslot) * plane;
+    const float *p0 = in + (int64_t)s * plane;
+    const float *p1 = in + (int64_t)wrap_add(s, 1, nslot) * plane;
+    const float *p2 = in + (int64_t)wrap_add(s, 2, nslot) * plane;
+    // register queue z-1 .. z+2 and the halos of planes z, z+1: loads run
+    // two planes ahead of their use
+    float4 prev = (inside && za >= 1) ? ldg4(pm + off) : z4;
+    float4 cur = (inside && za < nz) ? ldg4(p0 + off) : z4;
+    float4 nxt = (inside && za + 1 < nz) ? ldg4(p1 + off) : z4;
+    float4 nn = (inside && za + 2 < nz) ? ldg4(p2 + off) : z4;
+    float4 hyv = (hrow && za < nz) ? ldg4(p0 + hoff) : z4;
+    float4 hyv1 = (hrow && za + 1 < nz) ? ldg4(p1 + hoff) : z4;
+    float hx = (hcol && za < nz) ? __ldg(p0 + xoff) : 0.f;
+    float hx1 = (hcol && za + 1 < nz) ? __ldg(p1 + xoff) : 0.f;
+    int64_t z = za;
+    // unrolled twice so that the register queue rotates by renaming
+#pragma unroll 2
+    for (int i = 0; i < cnt; ++i, ++z) {
+        const int s2 = wrap_add(s, 2, nslot), s3 = wrap_add(s, 3, nslot);
+        const float *q2 = in + (int64_t)s2 * plane;
+        const float *q3 = in + (int64_t)s3 * plane;
+        const float4 pfv = (inside && z + 3 < nz) ? ldg4(q3 + off) : z4;
+        const bool v2 = z + 2 < nz;
+        const float4 hyv2 = (hrow && v2) ? ldg4(q2 + hoff) : z4;
+        const float hx2 = (hcol && v2) ? __ldg(q2 + xoff) : 0.f;
 
-        const int b = (int)((z - za) & 1);
+        const int b = i & 1;
         tile[b][ty + 1][lane] = cur;
         if (ty == 0)
             tile[b][0][lane] = hyv;
@@ -113,28 +123,30 @@ __global__ void __launch_bounds__(kTX *kHeatTY)
         o.z = cur.z + r * (((cur.y + cur.w) + (up.z + dn.z)) + (prev.z + nxt.z) - 6.0f * cur.z);
         o.w = cur.w + r * (((cur.z + xr) + (up.w + dn.w)) + (prev.w + nxt.w) - 6.0f * cur.w);
         if (inside)
-            *reinterpret_cast<float4 *>(out.base + s_out * g.plane + y * g.nx + x4) = o;
+            *reinterpret_cast<float4 *>(out + (int64_t)s * plane + off) = o;
         prev = cur;
         cur = nxt;
-        nxt = pf;
-        hyv = hyv_n;
-        hx = hx_n;
-        s_next = s_pf;
-        s_out = next_slot(s_out, out.nslot);
+        nxt = nn;
+        nn = pfv;
+        hyv = hyv1;
+        hyv1 = hyv2;
+        hx = hx1;
+        hx1 = hx2;
+        s = wrap_add(s, 1, nslot);
     }
 }
 
-// x-neighbour m (1..4) to the left / right of point j (0..3) of the thread,
-// given its own 4 points c and the 4-point groups to the left (l) and right (rr).
+// x-neighbour at offset idx in [-4, 7] from the thread's first point, given
+// its own 4 points c and the 4-point groups to its left (l) and right (rr).
 __device__ __forceinline__ float pick(const float (&l)[4], const float (&c)[4], const float (&rr)[4], int idx)
 {
-    // idx in [-4, 7]: -4..-1 -> l[idx+4], 0..3 -> c[idx], 4..7 -> rr[idx-4]
     return idx < 0 ? l[idx + 4] : (idx < 4 ? c[idx] : rr[idx - 4]);
 }
 
-__global__ void __launch_bounds__(kTX *kWaveTY)
-    wave25_kernel(ConstRing pin, Ring pout, ConstRing kap, Grid3 g, int64_t z0, int64_t z1, int64_t zchunk,
-                  int64_t sx, int64_t sy, int64_t sz, float w)
+__global__ void __launch_bounds__(kTX *kWaveTY, 2)
+    wave25_kernel(const float *__restrict__ pin, const float *pprev, float *pout, const float *__restrict__ kap, int nslot,
+                  int64_t zbase, Grid3 g, int64_t z0, int64_t z1, int64_t zchunk, int64_t sx, int64_t sy, int64_t sz,
+                  float w)
 {
     constexpr int R = 4;
     __shared__ float4 tile[2][kWaveTY + 2 * R][kTX];
@@ -144,55 +156,52 @@ __global__ void __launch_bounds__(kTX *kWaveTY)
     const int64_t y0 = (int64_t)blockIdx.y * kWaveTY;
     const int64_t y = y0 + ty;
     const int64_t za = z0 + (int64_t)blockIdx.z * zchunk;
-    const int64_t zb = min(za + zchunk, z1);
+    const int cnt = (int)(min(za + zchunk, z1) - za);
+    const int64_t nz = g.nz, plane = g.plane;
     const bool inside = x4 < g.nx && y < g.ny;
-    // warp ty loads y-halo row: 4 above (ty < 4) or 4 below (ty >= 4)
-    const int hrow = ty < R ? ty : kWaveTY + ty;  // tile row it fills
+    const int64_t off = inside ? y * g.nx + x4 : 0;
+    // warp ty loads one y-halo row: 4 above (ty < 4) or 4 below (ty >= 4)
+    const int hr = ty < R ? ty : kWaveTY + ty;  // tile row it fills
     const int64_t yh = ty < R ? y0 - R + ty : y0 + kWaveTY + (ty - R);
-    const int64_t xh = lane == 0 ? xs - 4 : xs + kSeg;  // x-halo group (lanes 0, 31)
-    const bool col_halo = lane == 0 || lane == kTX - 1;
+    const bool hrow = yh >= 0 && yh < g.ny && x4 < g.nx;
+    const int64_t hoff = hrow ? yh * g.nx + x4 : 0;
+    // lanes 0 and 31 load the 4-point group beyond the segment's ends
+    const int64_t xh = lane == 0 ? xs - 4 : xs + kSeg;
+    const bool hcol = (lane == 0 || lane == kTX - 1) && xh >= 0 && xh < g.nx && y < g.ny;
+    const int64_t xoff = hcol ? y * g.nx + xh : 0;
+    const bool src_here = inside && y == sy && sx >= x4 && sx < x4 + 4;
+    const float4 z4 = zero4();
 
+    int s = (int)ring_slot(za, zbase, nslot);  // slot of plane z
     // q[j] = p at plane z - 4 + j of this thread's 4 points
     float4 q[2 * R + 1];
-    int64_t sq = ring_slot(za - R, pin.zbase, pin.nslot);
 #pragma unroll
     for (int j = 0; j < 2 * R + 1; ++j) {
-        q[j] = ld4(pin.base, g, za - R + j, sq, x4, y);
-        if (j < 2 * R)
-            sq = next_slot(sq, pin.nslot);
+        const int64_t zj = za - R + j;
+        const float *pj = pin + (int64_t)wrap_add(s, nslot - R + j >= nslot ? j - R : nslot - R + j, nslot) * plane;
+        q[j] = (inside && zj >= 0 && zj < nz) ? ldg4(pj + off) : z4;
     }
-    // sq: slot of plane za + 4
-    int64_t s_c = ring_slot(za, pin.zbase, pin.nslot);
-    int64_t s_o = ring_slot(za, pout.zbase, pout.nslot);
-    int64_t s_k = ring_slot(za, kap.zbase, kap.nslot);
-    float4 hyv = ld4(pin.base, g, za, s_c, x4, yh);
-    float4 hxv = col_halo ? ld4(pin.base, g, za, s_c, xh, y) : zero4();
-    float4 ppv = inside && za < zb ? *reinterpret_cast<const float4 *>(pout.base + s_o * g.plane + y * g.nx + x4)
-                                   : zero4();
-    float4 kv = inside && za < zb ? __ldg(reinterpret_cast<const float4 *>(kap.base + s_k * g.plane + y * g.nx + x4))
-                                  : zero4();
-    for (int64_t z = za; z < zb; ++z) {
-        // prefetch for plane z + 1: its p at z + 5 (queue head), halos, p_prev, kappa
-        const int64_t sq_n = next_slot(sq, pin.nslot);
-        const int64_t s_c1 = next_slot(s_c, pin.nslot);
-        const int64_t s_o1 = next_slot(s_o, pout.nslot);
-        const int64_t s_k1 = next_slot(s_k, kap.nslot);
-        const bool more = z + 1 < zb;
-        const float4 pf = ld4(pin.base, g, z + R + 1, sq_n, x4, y);
-        const float4 hyv_n = more ? ld4(pin.base, g, z + 1, s_c1, x4, yh) : zero4();
-        const float4 hxv_n = (more && col_halo) ? ld4(pin.base, g, z + 1, s_c1, xh, y) : zero4();
-        const float4 ppv_n = (more && inside)
-                                 ? *reinterpret_cast<const float4 *>(pout.base + s_o1 * g.plane + y * g.nx + x4)
-                                 : zero4();
-        const float4 kv_n = (more && inside)
-                                ? __ldg(reinterpret_cast<const float4 *>(kap.base + s_k1 * g.plane + y * g.nx + x4))
-                                : zero4();
+    const float *pc = pin + (int64_t)s * plane;
+    float4 hyv = (hrow && za < nz) ? ldg4(pc + hoff) : z4;
+    float4 hxv = (hcol && za < nz) ? ldg4(pc + xoff) : z4;
+    float4 ppv = inside ? *reinterpret_cast<const float4 *>(pprev + (int64_t)s * plane + off) : z4;
+    float4 kv = inside ? ldg4(kap + (int64_t)s * plane + off) : z4;
+    int64_t z = za;
+    for (int i = 0; i < cnt; ++i, ++z) {
+        const int s1 = wrap_add(s, 1, nslot), s5 = wrap_add(s, R + 1, nslot);
+        const int64_t b1 = (int64_t)s1 * plane;
+        // prefetch for plane z + 1: p at z + 5 (queue head), halos, p_prev, kappa
+        const bool more = i + 1 < cnt;
+        const float4 pfv = (inside && z + R + 1 < nz) ? ldg4(pin + (int64_t)s5 * plane + off) : z4;
+        const float4 hyv_n = (more && hrow) ? ldg4(pin + b1 + hoff) : z4;
+        const float4 hxv_n = (more && hcol) ? ldg4(pin + b1 + xoff) : z4;
+        const float4 ppv_n = (more && inside) ? *reinterpret_cast<const float4 *>(pprev + b1 + off) : z4;
+        const float4 kv_n = (more && inside) ? ldg4(kap + b1 + off) : z4;
 
-        const int b = (int)((z - za) & 1);
+        const int b = i & 1;
         const float4 c = q[R];
         tile[b][ty + R][lane] = c;
-        tile[b][hrow][lane] = hyv;
-        // x-neighbour groups from the adjacent lanes (edge lanes: the halo)
+        tile[b][hr][lane] = hyv;
         float4 lf, rt;
         lf.x = __shfl_up_sync(0xffffffffu, c.x, 1);
         lf.y = __shfl_up_sync(0xffffffffu, c.y, 1);
@@ -207,52 +216,51 @@ __global__ void __launch_bounds__(kTX *kWaveTY)
         if (lane == kTX - 1)
             rt = hxv;
         __syncthreads();
-        float4 ym[R], yp[R];
-#pragma unroll
-        for (int m = 1; m <= R; ++m) {
-            ym[m - 1] = tile[b][ty + R - m][lane];
-            yp[m - 1] = tile[b][ty + R + m][lane];
-        }
         const float L[4] = {lf.x, lf.y, lf.z, lf.w};
         const float C[4] = {c.x, c.y, c.z, c.w};
         const float Rt[4] = {rt.x, rt.y, rt.z, rt.w};
-        const float cf[R] = {kC1, kC2, kC3, kC4};
-        float o[4];
         const float PP[4] = {ppv.x, ppv.y, ppv.z, ppv.w};
         const float KV[4] = {kv.x, kv.y, kv.z, kv.w};
+        const float cf[R] = {kC1, kC2, kC3, kC4};
+        float lap[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            float lap = (3.0f * kC0) * C[j];
+        for (int j = 0; j < 4; ++j)
+            lap[j] = (3.0f * kC0) * C[j];
 #pragma unroll
-            for (int m = 1; m <= R; ++m) {
+        for (int m = 1; m <= R; ++m) {
+            const float4 ym = tile[b][ty + R - m][lane];
+            const float4 yp = tile[b][ty + R + m][lane];
+            const float YM[4] = {ym.x, ym.y, ym.z, ym.w};
+            const float YP[4] = {yp.x, yp.y, yp.z, yp.w};
+            const float ZM[4] = {q[R - m].x, q[R - m].y, q[R - m].z, q[R - m].w};
+            const float ZP[4] = {q[R + m].x, q[R + m].y, q[R + m].z, q[R + m].w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
                 const float xsum = pick(L, C, Rt, j - m) + pick(L, C, Rt, j + m);
-                const float ysum = (&ym[m - 1].x)[j] + (&yp[m - 1].x)[j];
-                const float zsum = (&q[R - m].x)[j] + (&q[R + m].x)[j];
-                lap += cf[m - 1] * ((xsum + ysum) + zsum);
+                lap[j] += cf[m - 1] * ((xsum + (YM[j] + YP[j])) + (ZM[j] + ZP[j]));
             }
-            o[j] = 2.0f * C[j] - PP[j] + KV[j] * lap;
         }
-        if (inside) {
-            if (z == sz && y == sy) {
+        float o[4];
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (sx == x4 + j)
-                        o[j] += w;
-            }
-            *reinterpret_cast<float4 *>(pout.base + s_o * g.plane + y * g.nx + x4) = make_float4(o[0], o[1], o[2], o[3]);
+        for (int j = 0; j < 4; ++j)
+            o[j] = 2.0f * C[j] - PP[j] + KV[j] * lap[j];
+        if (src_here && z == sz) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (sx == x4 + j)
+                    o[j] += w;
         }
+        if (inside)
+            *reinterpret_cast<float4 *>(pout + (int64_t)s * plane + off) = make_float4(o[0], o[1], o[2], o[3]);
 #pragma unroll
         for (int j = 0; j < 2 * R; ++j)
             q[j] = q[j + 1];
-        q[2 * R] = pf;
+        q[2 * R] = pfv;
         hyv = hyv_n;
         hxv = hxv_n;
         ppv = ppv_n;
         kv = kv_n;
-        sq = sq_n;
-        s_c = s_c1;
-        s_o = s_o1;
-        s_k = s_k1;
+        s = s1;
     }
 }
 
@@ -315,13 +323,16 @@ cudaError_t launch_heat7(ConstRing in, Ring out, int64_t nx, int64_t ny, int64_t
     const int64_t gx = (nx + kSeg - 1) / kSeg, gy = (ny + kHeatTY - 1) / kHeatTY;
     const int64_t chunk = choose_chunk(gx * gy, z1 - z0, 8, 3, res);
     const int64_t gz = (z1 - z0 + chunk - 1) / chunk;
+    if (in.nslot != out.nslot || in.zbase != out.zbase || in.nslot > (1ll << 30))
+        return cudaErrorInvalidValue;
     heat7_kernel<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)gz), dim3(kTX, kHeatTY), 0, st>>>(
-        in, out, Grid3{nx, ny, nz, nx * ny}, z0, z1, chunk, r);
+        in.base, out.base, (int)in.nslot, in.zbase, Grid3{nx, ny, nz, nx * ny}, z0, z1, chunk, r);
     return cudaGetLastError();
 }
 
-cudaError_t launch_wave25(ConstRing p, Ring pprev_out, ConstRing kappa, int64_t nx, int64_t ny, int64_t nz,
-                          int64_t z0, int64_t z1, int64_t sx, int64_t sy, int64_t sz, float w, cudaStream_t st)
+cudaError_t launch_wave25_to(ConstRing p, ConstRing pprev, Ring pnew, ConstRing kappa, int64_t nx, int64_t ny,
+                             int64_t nz, int64_t z0, int64_t z1, int64_t sx, int64_t sy, int64_t sz, float w,
+                             cudaStream_t st)
 {
     if (z1 <= z0)
         return cudaSuccess;
@@ -331,9 +342,20 @@ cudaError_t launch_wave25(ConstRing p, Ring pprev_out, ConstRing kappa, int64_t 
     const int64_t gx = (nx + kSeg - 1) / kSeg, gy = (ny + kWaveTY - 1) / kWaveTY;
     const int64_t chunk = choose_chunk(gx * gy, z1 - z0, 16, 9, res);
     const int64_t gz = (z1 - z0 + chunk - 1) / chunk;
+    if (p.nslot != pnew.nslot || p.zbase != pnew.zbase || p.nslot != kappa.nslot || p.zbase != kappa.zbase ||
+        p.nslot != pprev.nslot || p.zbase != pprev.zbase || p.nslot > (1ll << 30))
+        return cudaErrorInvalidValue;
     wave25_kernel<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)gz), dim3(kTX, kWaveTY), 0, st>>>(
-        p, pprev_out, kappa, Grid3{nx, ny, nz, nx * ny}, z0, z1, chunk, sx, sy, sz, w);
+        p.base, pprev.base, pnew.base, kappa.base, (int)p.nslot, p.zbase, Grid3{nx, ny, nz, nx * ny}, z0, z1, chunk,
+        sx, sy, sz, w);
     return cudaGetLastError();
+}
+
+cudaError_t launch_wave25(ConstRing p, Ring pprev_out, ConstRing kappa, int64_t nx, int64_t ny, int64_t nz,
+                          int64_t z0, int64_t z1, int64_t sx, int64_t sy, int64_t sz, float w, cudaStream_t st)
+{
+    return launch_wave25_to(p, ConstRing{pprev_out.base, pprev_out.nslot, pprev_out.zbase}, pprev_out, kappa, nx, ny,
+                            nz, z0, z1, sx, sy, sz, w, st);
 }
 
 cudaError_t launch_swap(float *a, float *b, int64_t n, cudaStream_t st)
