@@ -137,6 +137,26 @@ ooc_status ooc_wave25_steps(float *d_p, float *d_pprev, const float *d_kappa, in
                             int64_t nz, int64_t sx, int64_t sy, int64_t sz, const float *h_w, int64_t t,
                             int64_t nsteps, void *stream);
 
+/* Largest grid, in points, that ooc_heat7_steps_noalloc accepts: the size of
+ * its fixed scratch array (4 Mi floats, 16 MiB). */
+#define OOC_NOALLOC_MAX_POINTS (4ll * 1024 * 1024)
+
+/* The paper has no counterpart to this call.  It runs the same nsteps heat7
+ * steps as ooc_heat7_steps on d_u (device, result in place) but takes no
+ * scratch field, for callers that cannot provide one: code whose device
+ * memory is owned by a host application or framework allocator with nothing
+ * to spare, or a time-critical loop that must not allocate because an
+ * allocation there can fail or stall.  The second field lives in a fixed
+ * array inside the library (OOC_NOALLOC_MAX_POINTS floats, kept on every GPU
+ * that loads the library until the process exits); no call allocates
+ * anything.  Grids with more points return OOC_E_INVALID.  The first call
+ * on a device looks up the array's device address for that device, so make
+ * that first call before any stream capture begins.  All calls share the
+ * array: calls that overlap on the GPU race on it, so the caller must order
+ * them.  Results are bit-identical to ooc_heat7_steps. */
+ooc_status ooc_heat7_steps_noalloc(float *d_u, int64_t nx, int64_t ny, int64_t nz, double r, int64_t nsteps,
+                                   void *stream);
+
 /* ---- Adjoint (gradient of a receiver misfit w.r.t. velocity) -------------
  * Not in the paper: a differentiation workload on its 25-point propagator.
  * Forward, n = 0..N-1, from rest (p^0 = p^{-1} = 0):

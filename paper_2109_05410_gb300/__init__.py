@@ -20,7 +20,7 @@ __all__ = [
     "OOC_HEAT7", "OOC_WAVE25", "OOC_FMT_FP32", "OOC_FMT_BF16", "OOC_FMT_FR4",
     "OocConfig", "OocStats", "OocPlanInfo", "OocError", "lib", "build",
     "ooc_status_string", "ooc_compressed_bytes", "ooc_compress", "ooc_decompress",
-    "ooc_bf16_pack", "ooc_bf16_unpack", "ooc_heat7_steps", "ooc_wave25_steps", "Plan",
+    "ooc_bf16_pack", "ooc_bf16_unpack", "ooc_heat7_steps", "ooc_heat7_steps_noalloc", "ooc_wave25_steps", "Plan",
     "ooc_gather", "ooc_scatter_add", "ooc_wave25_adjoint_step", "ooc_wave25_grad_accum", "ooc_kappa_from_velocity",
     "ooc_velocity_grad", "ooc_wave25_ckpt_bytes", "ooc_wave25_adjoint_work_bytes", "ooc_wave25_forward_ckpt",
     "ooc_wave25_backward_ckpt", "WaveFn", "wave_forward",
@@ -99,6 +99,8 @@ _SIGS = {
     "ooc_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(OocStats)]),
     "ooc_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
     "ooc_plan_destroy": (None, [ctypes.c_void_p]),
+    "ooc_heat7_steps_noalloc": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int64] * 3
+                                + [ctypes.c_double, ctypes.c_int64, ctypes.c_void_p]),
     "ooc_gather": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "ooc_scatter_add": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                        ctypes.c_void_p]),
@@ -209,6 +211,18 @@ def ooc_heat7_steps(d_u, d_tmp, nsteps, r=1.0 / 6.0, stream=None):
     _check(lib().ooc_heat7_steps(_ptr(d_u), _ptr(d_tmp), nx, ny, nz, float(r), int(nsteps), _stream(stream)),
            "ooc_heat7_steps")
     return d_u
+
+
+def ooc_heat7_steps_noalloc(d_u, nsteps, r=1.0 / 6.0, stream=None):
+    """ooc_heat7_steps without a scratch field: the library's fixed scratch
+    array (OOC_NOALLOC_MAX_POINTS points) holds the second field."""
+    nz, ny, nx = d_u.shape
+    _check(lib().ooc_heat7_steps_noalloc(_ptr(d_u), nx, ny, nz, float(r), int(nsteps), _stream(stream)),
+           "ooc_heat7_steps_noalloc")
+    return d_u
+
+
+OOC_NOALLOC_MAX_POINTS = 4 * 1024 * 1024
 
 
 def ooc_wave25_steps(d_p, d_pprev, d_kappa, nsteps, src=None, w=None, t=0, stream=None):
