@@ -241,12 +241,6 @@ struct BitWriter {
         app((uint32_t)v, l1);
         app((uint32_t)(v >> 32), len - l1);
     }
-    __device__ __forceinline__ void zeros(int len)  // len in [0, 64]
-    {
-        const int l1 = len < 32 ? len : 32;
-        app(0u, l1);
-        app(0u, len - l1);
-    }
     __device__ __forceinline__ void finish(int words)
     {
         if (nacc > 0)

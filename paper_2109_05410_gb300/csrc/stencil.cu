@@ -33,8 +33,6 @@ constexpr int kHeatTY = 8;
 constexpr int kWaveTY = 8;
 constexpr int kSeg = 4 * kTX;
 
-__device__ __forceinline__ int64_t next_slot(int64_t s, int64_t nslot) { return s + 1 == nslot ? 0 : s + 1; }
-
 __device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
 struct Grid3 {
