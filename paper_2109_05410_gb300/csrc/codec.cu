@@ -235,11 +235,27 @@ struct BitWriter {
             nacc = tot;
         }
     }
-    __device__ __forceinline__ void app64(uint64_t v, int len)  // len in [0, 64]
+    // Append the low `len` (0..64) bits of v in one step.
+    __device__ __forceinline__ void app64(uint64_t v, int len)
     {
-        const int l1 = len < 32 ? len : 32;
-        app((uint32_t)v, l1);
-        app((uint32_t)(v >> 32), len - l1);
+        const uint64_t lo = (uint64_t)acc | (v << nacc);
+        const uint32_t hi = __funnelshift_lc((uint32_t)(v >> 32), 0u, nacc);  // bits 64.. of the sum
+        const int tot = nacc + len;
+        pos += len;
+        if (tot >= 64) {
+            dst[widx] = (uint32_t)lo;
+            dst[widx + 1] = (uint32_t)(lo >> 32);
+            widx += 2;
+            acc = hi;
+            nacc = tot - 64;
+        } else if (tot >= 32) {
+            dst[widx++] = (uint32_t)lo;
+            acc = (uint32_t)(lo >> 32);
+            nacc = tot - 32;
+        } else {
+            acc = (uint32_t)lo;
+            nacc = tot;
+        }
     }
     __device__ __forceinline__ void finish(int words)
     {
@@ -250,26 +266,43 @@ struct BitWriter {
     }
 };
 
-// Reads bit fields of a thread's words.  The words past the block's 2R are
-// zero (slack), so bits past the budget read as 0, which is what a
-// truncated stream means; only the implied-one rule needs the budget.
+// Reads bit fields of a thread's words through a 64-bit buffer holding at
+// least 32 unread bits; it loads one shared-memory word per 32 bits read.
+// The words past the block's 2R are zero (slack), so bits past the budget
+// read as 0, which is what a truncated stream means; only the implied-one
+// rule needs the budget.
 struct BitReader {
     const uint32_t *src;
-    int pos;
+    uint64_t buf;  // unread bits, least significant first
+    int avail;     // valid bits in buf, >= 32
+    int wnext;     // next word to load
+    int pos;       // bits consumed
 
+    __device__ __forceinline__ void init(const uint32_t *s, int start)
+    {
+        src = s;
+        const int w = start >> 5, sh = start & 31;
+        buf = ((uint64_t)s[w] | ((uint64_t)s[w + 1] << 32)) >> sh;
+        avail = 64 - sh;
+        wnext = w + 2;
+        pos = start;
+    }
+    __device__ __forceinline__ void skip(int len)  // len in [0, 32]
+    {
+        buf >>= len;
+        avail -= len;
+        pos += len;
+        if (avail < 32) {
+            buf |= (uint64_t)src[wnext++] << avail;
+            avail += 32;
+        }
+    }
+    __device__ __forceinline__ uint32_t peek32() const { return (uint32_t)buf; }
     __device__ __forceinline__ uint32_t get(int len)  // len in [0, 32]
     {
-        const int w = pos >> 5, sh = pos & 31;
-        const uint32_t v = __funnelshift_r(src[w], src[w + 1], sh) & BitWriter::low_mask(len);
-        pos += len;
+        const uint32_t v = (uint32_t)buf & BitWriter::low_mask(len);
+        skip(len);
         return v;
-    }
-    __device__ __forceinline__ uint64_t peek64(int len) const  // 1 <= len <= 63
-    {
-        const int w = pos >> 5, sh = pos & 31;
-        const uint32_t a = __funnelshift_r(src[w], src[w + 1], sh);
-        const uint32_t b = __funnelshift_r(src[w + 1], src[w + 2], sh);
-        return (((uint64_t)b << 32) | a) & ((1ull << len) - 1ull);
     }
 };
 
@@ -335,11 +368,16 @@ __device__ __forceinline__ void encode_block(uint32_t (&v)[64], int rate, uint32
             nstart = n;
             prev = -1;
             ref = false;
-            plane_done = n >= 64;
-        } else if (rest == 0ull) {
-            chunk = 0ull;  // closing group bit (n < 64 here)
-            len = 1;
-            plane_done = true;
+            plane_done = n >= 64 || rest == 0ull;
+            if (n < 64 && rest == 0ull) {  // nothing new: the closing group bit 0 follows
+                if (len < 64) {
+                    len += 1;
+                } else {
+                    w.app64(chunk, len);
+                    chunk = 0ull;
+                    len = 1;
+                }
+            }
         } else {
             const int t = __ffsll((long long)rest) - 1;
             const int gap = t - prev - 1;
@@ -354,7 +392,16 @@ __device__ __forceinline__ void encode_block(uint32_t (&v)[64], int rate, uint32
                 len = gap + 2;
                 prev = t;
                 n = nstart + t + 1;
-                plane_done = false;
+                plane_done = rest == 0ull;
+                if (plane_done) {  // closing group bit 0 (n < 64 here)
+                    if (len < 64) {
+                        len += 1;
+                    } else {
+                        w.app64(chunk, len);
+                        chunk = 0ull;
+                        len = 1;
+                    }
+                }
             }
         }
         w.app64(chunk, len);
@@ -370,7 +417,6 @@ __device__ __forceinline__ void encode_block(uint32_t (&v)[64], int rate, uint32
 
 __device__ __forceinline__ void decode_block(const uint32_t *src, int rate, float (&out)[64], uint32_t *pm)
 {
-    BitReader r{src, 9};
     const int budget = 64 * rate;
     if ((src[0] & 1u) == 0u) {
 #pragma unroll
@@ -379,6 +425,8 @@ __device__ __forceinline__ void decode_block(const uint32_t *src, int rate, floa
         return;
     }
     const int emax = (int)((src[0] >> 1) & 0xFFu) - 127;
+    BitReader r;
+    r.init(src, 9);
     int n = 0;
     int p = 31;
 #pragma unroll 1
@@ -388,22 +436,60 @@ __device__ __forceinline__ void decode_block(const uint32_t *src, int rate, floa
         uint32_t xh = r.get(n - n1);
         if (n < 64) {
             uint64_t X = 0ull;  // the plane's new ones
-            while (r.get(1) != 0u) {
-                const int len = 63 - n;  // explicit scan bits at most
-                const uint64_t sc = len > 0 ? r.peek64(len) : 0ull;
-                if (sc != 0ull) {
-                    const int t = __ffsll((long long)sc) - 1;
-                    r.pos += t + 1;
+            for (;;) {
+                const uint32_t wv = r.peek32();
+                if ((wv & 1u) == 0u) {  // group test: nothing more in this plane
+                    r.skip(1);
+                    break;
+                }
+                const int len = 63 - n;  // explicit scan bits at most (after the group bit)
+                const int m = len < 31 ? len : 31;
+                const uint32_t sc = (wv >> 1) & BitWriter::low_mask(m);
+                if (sc != 0u) {
+                    const int t = __ffs((int)sc) - 1;
+                    r.skip(t + 2);
                     X |= 1ull << (n + t);
                     n += t + 1;
-                } else {
-                    if (r.pos + len <= budget) {  // scan complete: last coefficient's one implied
+                    continue;
+                }
+                if (len <= 31) {  // whole scan zero: the last coefficient's one is implied
+                    if (r.pos + 1 + len <= budget) {
                         X |= 1ull << 63;
                         n = 64;
                     }
-                    r.pos += len;
+                    r.skip(1 + len);
                     break;
                 }
+                // long scan whose first 31 bits are zero
+                r.skip(32);
+                int done = 31;
+                bool found = false;
+                for (;;) {
+                    const int rem = len - done;
+                    const int mm = rem < 32 ? rem : 32;
+                    const uint32_t s2 = r.peek32() & BitWriter::low_mask(mm);
+                    if (s2 != 0u) {
+                        const int f = __ffs((int)s2);
+                        const int t = done + f - 1;
+                        r.skip(f);
+                        X |= 1ull << (n + t);
+                        n += t + 1;
+                        found = true;
+                        break;
+                    }
+                    if (rem <= 32) {
+                        if (r.pos + rem <= budget) {
+                            X |= 1ull << 63;
+                            n = 64;
+                        }
+                        r.skip(rem);
+                        break;
+                    }
+                    r.skip(32);
+                    done += 32;
+                }
+                if (!found)
+                    break;
             }
             xl |= (uint32_t)X;
             xh |= (uint32_t)(X >> 32);
@@ -468,8 +554,19 @@ __global__ void __launch_bounds__(kThreads) fr4_encode_kernel(ConstRing in, int6
     const int64_t left = nblk - first;
     const int nvalid = left < kThreads ? (int)left : kThreads;
     uint32_t *dst = out + first * words;
-    for (int o = threadIdx.x; o < nvalid * words; o += kThreads)
-        dst[o] = smem[(o / words) * stride + (o % words)];
+    // word o of the CTA's output is word (o mod words) of block (o / words);
+    // o advances by kThreads, so block and word advance incrementally
+    int blk = threadIdx.x / words, wd = threadIdx.x - blk * words;
+    const int step_blk = kThreads / words, step_wd = kThreads - step_blk * words;
+    for (int o = threadIdx.x; o < nvalid * words; o += kThreads) {
+        dst[o] = smem[blk * stride + wd];
+        blk += step_blk;
+        wd += step_wd;
+        if (wd >= words) {
+            wd -= words;
+            ++blk;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kThreads) fr4_decode_kernel(const uint32_t *__restrict__ in, int64_t nx, int64_t ny,
@@ -481,8 +578,19 @@ __global__ void __launch_bounds__(kThreads) fr4_decode_kernel(const uint32_t *__
     const int64_t left = nblk - first;
     const int nvalid = left < kThreads ? (int)left : kThreads;
     const uint32_t *src = in + first * words;
-    for (int o = threadIdx.x; o < nvalid * words; o += kThreads)
-        smem[(o / words) * stride + (o % words)] = __ldg(src + o);
+    {
+        int blk = threadIdx.x / words, wd = threadIdx.x - blk * words;
+        const int step_blk = kThreads / words, step_wd = kThreads - step_blk * words;
+        for (int o = threadIdx.x; o < nvalid * words; o += kThreads) {
+            smem[blk * stride + wd] = __ldg(src + o);
+            blk += step_blk;
+            wd += step_wd;
+            if (wd >= words) {
+                wd -= words;
+                ++blk;
+            }
+        }
+    }
 #pragma unroll
     for (int j = 0; j < kSlack; ++j)  // bits past the block read as 0
         smem[threadIdx.x * stride + words + j] = 0u;
