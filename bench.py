@@ -9,8 +9,13 @@ compressed-vs-uncompressed comparison.  Error is stated against the FP64
 oracle on a sampled central 128^3 sub-box (exact dependency cone).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload heat1024|kernels512|wave1024|precision|adjoint512]
 
-Prints one JSON line (rank 0).  N > 1 runs N independent replicas (the
+Prints one JSON line (rank 0).  The default workload is the headline; the
+others measure the remaining configurations: one launch of each kernel on a
+512^3 field (kernels512, the ncu capture case), the 1024^3 wave with the
+paper's four storage codes (wave1024), the long-horizon precision study
+(precision) and the checkpointed adjoint at 512^3 (adjoint512).  N > 1 runs N independent replicas (the
 method works on one GPU; there is no data-path collective).
 """
 from __future__ import annotations
@@ -35,12 +40,26 @@ K = 4
 BUDGET = 1 << 30
 MAIN = ("fr4", 16)
 COMPARE = [("fp32", 0), ("bf16", 0), ("fr4", 8), ("fr4", 12), ("fr4", 24)]
+# DRAM traffic per point of one heat7 launch, from `ncu --set full` on the
+# 512^3 case (dram__bytes_read.sum + dram__bytes_write.sum over 134.2 M
+# points; profiles/kernels_512cube_full.md).  Traffic is proportional to the
+# points a launch processes, so the bench scales it to its own launches.  It
+# is only valid for the stencil source it was measured on (sha256 prefix).
+HEAT7_TRAFFIC_PER_POINT = 7.80
+HEAT7_TRAFFIC_SRC_SHA = "4dd2925f74c35334"
 METRIC = "Gpts/s out-of-core (compressed vs uncompressed, same GB300) at stated L2 error; % roofline"
 WORKLOAD = "heat7 1024^3 FP32, device budget 1 GiB, k=4, 64 steps/bench step"
 
 
 def fmt_name(fmt, rate):
     return f"fr4-{rate}" if fmt == "fr4" else fmt
+
+
+def stencil_source_sha():
+    import hashlib
+    path = os.path.join(ROOT, "paper_2109_05410_gb300", "csrc", "stencil.cu")
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 def load_peaks():
@@ -267,8 +286,11 @@ def run_gpu(args, world, rank, local):
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     dk = kernels[dom]
     launches = max(dk["launches"], 1)
+    traffic = None
+    if dom == "heat7_stencil" and stencil_source_sha() == HEAT7_TRAFFIC_SRC_SHA:
+        traffic = HEAT7_TRAFFIC_PER_POINT * (dk["bytes"] / 8) / launches
     roofline = {"bound": "hbm", "kernel": dom, "achieved": dk["GBs"], "peak": hbm_peak, "unit": "GB/s",
-                "frac": dk["frac_hbm"], "traffic": None,
+                "frac": dk["frac_hbm"], "traffic": traffic,
                 "bytes_per_launch": dk["bytes"] / launches, "ms_per_launch": dk["ms"] / launches,
                 "peak_source": peak_src}
     h2d_GBs = st["h2d_bytes"] / (st["ms_h2d"] / 1e3) / 1e9 if st["ms_h2d"] > 0 else None
@@ -369,18 +391,282 @@ def run_gpu(args, world, rank, local):
     return 0
 
 
+# --------------------------------------------------------------------------- other workloads
+def _cuda_events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_kernels512(args, world, rank, local):
+    """Each kernel once per step on a 512^3 smooth field (the ncu capture case):
+    FR4 encode and decode at R = 16, two in-core heat7 steps, two in-core
+    wave25 steps; CUDA-event times per kernel class."""
+    import torch
+
+    import paper_2109_05410_gb300 as ooc
+    from synth import smooth_random_field
+    torch.cuda.set_device(local)
+    ooc.build()
+    ooc.lib()
+    n = 512
+    pts = n ** 3
+    d = torch.from_numpy(smooth_random_field((n, n, n), 32.0, seed=2)).cuda()
+    w = torch.empty(ooc.ooc_compressed_bytes(n, n, n, 16), dtype=torch.uint8, device="cuda")
+    out = torch.empty_like(d)
+    tmp = torch.empty_like(d)
+    kap = torch.full_like(d, 0.1)
+    pp = torch.zeros_like(d)
+    ops = {
+        "fr4_encode": (lambda: ooc.ooc_compress(d, 16, d_out=w), 1, (4 + 2) * pts),
+        "fr4_decode": (lambda: ooc.ooc_decompress(w, (n, n, n), 16, d_out=out), 1, (4 + 2) * pts),
+        "heat7": (lambda: ooc.ooc_heat7_steps(d, tmp, 2), 2, 8 * pts),
+        "wave25": (lambda: ooc.ooc_wave25_steps(d, pp, kap, 2), 2, 16 * pts),
+    }
+    res = {}
+    for name, (fn, nl, by) in ops.items():
+        for _ in range(args.warmup):
+            fn()
+        e0, e1 = _cuda_events(torch)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(max(args.steps, 1)):
+            fn()
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / max(args.steps, 1) / nl
+        res[name] = {"ms_per_launch": ms, "GBs": by / (ms / 1e3) / 1e9}
+    if rank == 0:
+        print(json.dumps({"workload": "kernels512", "kernels": res, "n_gpus": world, "steps": args.steps,
+                          "warmup": args.warmup}), flush=True)
+    return 0
+
+
+def wave_inputs(n, seed=3):
+    from synth import layered_velocity, ricker
+    shape = (n, n, n)
+    v = layered_velocity(shape, seed=seed)
+    dx = 10.0
+    dt = 0.4 * dx / v.max()
+    kappa = ((v * dt / dx) ** 2).astype(np.float32)
+    src = (n // 2, n // 2, n // 2)
+    return kappa, src, dt
+
+
+def run_wave1024(args, world, rank, local):
+    """3D acoustic wave, 25-point, 1024^3, device budget 4 GiB, k = 10: the
+    paper's four codes (FP32; read-write fields at 16 bits/value; read-only
+    kappa at 16 bits/value; both), 200 time steps per bench step."""
+    import torch
+
+    import paper_2109_05410_gb300 as ooc
+    from synth import ricker
+    torch.cuda.set_device(local)
+    ooc.build()
+    ooc.lib()
+    n, k, nsteps = 1024, 10, 200
+    kappa, src, dt = wave_inputs(n)
+    total_steps = nsteps * (args.warmup + args.steps + 1)
+    w = (ricker(total_steps, dt) * float(kappa[src[2], src[1], src[0]])).astype(np.float32)
+    zero = np.zeros((n, n, n), dtype=np.float32)
+    codes = {"code1_fp32": ("fp32", "fp32"), "code2_rw_fr4-16": ("fr4", "fp32"),
+             "code3_ro_fr4-16": ("fp32", "fr4"), "code4_rw_ro_fr4-16": ("fr4", "fr4")}
+    out = {}
+    finals = {}
+    for name, (rw, ro) in codes.items():
+        plan = ooc.Plan(nx=n, ny=n, nz=n, stencil="wave25", k=k, rw_format=rw, rw_rate=16, ro_format=ro,
+                        ro_rate=16, device_budget_bytes=4 << 30, profile=0)
+        plan.set_field(0, zero)
+        plan.set_field(1, zero)
+        plan.set_field(2, kappa)
+        plan.set_source(*src, w)
+        for _ in range(args.warmup):
+            plan.step(nsteps)
+        ms = timed_steps(torch, plan, nsteps, args.steps)
+        t = sum(ms) / args.steps
+        out[name] = {"Gpts": n ** 3 * nsteps / (t / 1e3) / 1e9, "ms_per_step": t,
+                     "slab_planes": plan.info()["slab_planes"], "nslab": plan.info()["nslab"],
+                     "device_bytes": plan.info()["device_bytes"]}
+        finals[name] = plan.get_field(0)[n // 2 - 64:n // 2 + 64].astype(np.float64)
+        plan.close()
+        del plan
+        torch.cuda.empty_cache()
+    ref = finals["code1_fp32"]
+    for name in codes:
+        dd = finals[name] - ref
+        out[name]["rel_l2_vs_fp32_storage"] = float(np.linalg.norm(dd) / np.linalg.norm(ref))
+    if rank == 0:
+        steps_done = nsteps * (args.warmup + args.steps)
+        print(json.dumps({"workload": "wave1024", "metric": "Gpts/s", "value": out["code4_rw_ro_fr4-16"]["Gpts"],
+                          "unit": "Gpts/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "time_steps_per_bench_step": nsteps, "k": k, "device_budget_bytes": 4 << 30,
+                          "speedup_code4_vs_code1": out["code4_rw_ro_fr4-16"]["Gpts"] / out["code1_fp32"]["Gpts"],
+                          "codes": out, "error_note": f"rel-L2 of the central 128 planes after {steps_done} steps "
+                          "against the same pipeline with FP32 storage (an FP64 oracle at 1024^3 x 2000 steps "
+                          "is out of reach of the host cores; see the precision workload)"}), flush=True)
+    return 0
+
+
+def run_precision(args, world, rank, local):
+    """Long-horizon precision study: wave25 at 192^3, 4320 steps, k = 10,
+    storage FP32, BF16, FR4 at 8/12/16/24 bits/value (both read-write levels
+    and kappa), FP32 compute; rel-L2, max-abs and the mean pointwise relative
+    error on 100 sampled points per plane against the FP64 oracle every 100
+    steps, and Gpts/s per format."""
+    import torch
+
+    import paper_2109_05410_gb300 as ooc
+    from synth import ricker
+    torch.cuda.set_device(local)
+    ooc.build()
+    ooc.lib()
+    n, k, total, every = 192, 10, 4320, 100
+    kappa, src, dt = wave_inputs(n)
+    w = (ricker(total, dt) * float(kappa[src[2], src[1], src[0]])).astype(np.float32)
+    zero = np.zeros((n, n, n), dtype=np.float32)
+    marks = list(range(every, total + 1, every))
+    if total not in marks:
+        marks.append(total)
+    fmts = [("fp32", 16), ("bf16", 16), ("fr4", 8), ("fr4", 12), ("fr4", 16), ("fr4", 24)]
+    snaps = {}
+    speed = {}
+    for fmt, rate in fmts:
+        name = fmt_name(fmt, rate)
+        plan = ooc.Plan(nx=n, ny=n, nz=n, stencil="wave25", k=k, rw_format=fmt, rw_rate=rate, ro_format=fmt,
+                        ro_rate=rate, slab_planes=32, profile=0)
+        plan.set_field(0, zero)
+        plan.set_field(1, zero)
+        plan.set_field(2, kappa)
+        plan.set_source(*src, w)
+        done, tms = 0, 0.0
+        snaps[name] = []
+        for m in marks:
+            e0, e1 = _cuda_events(torch)
+            e0.record(plan.streams[0])
+            plan.step(m - done)
+            e1.record(plan.streams[2])
+            e1.synchronize()
+            tms += e0.elapsed_time(e1)
+            done = m
+            snaps[name].append(plan.get_field(0))
+        speed[name] = n ** 3 * total / (tms / 1e3) / 1e9
+        plan.close()
+        del plan
+        torch.cuda.empty_cache()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    p = np.zeros((n, n, n))
+    pp = np.zeros((n, n, n))
+    kap64 = kappa.astype(np.float64)
+    srcf = (src[2] * n + src[1]) * n + src[0]
+    done = 0
+    t0 = time.perf_counter()
+    errs = {name: [] for name in snaps}
+    for i, m in enumerate(marks):
+        p, pp = oracle.wave25_run(p, pp, kap64, m - done, src=srcf, w=w.astype(np.float64), t0=done)
+        done = m
+        for name in snaps:
+            e = oracle.error_metrics(snaps[name][i], p)
+            errs[name].append([m, e["rel_l2"], e["max_abs"], e["mean_rel_sampled"]])
+    t_oracle = time.perf_counter() - t0
+    line = {"workload": "precision", "grid": [n, n, n], "steps": total, "k": k, "slab_planes": 32,
+            "note": "192^3 instead of 384^3: the FP64 oracle over 4320 steps at 384^3 takes > 15 min on the "
+                    "16 host cores",
+            "formats": {name: {"Gpts": speed[name], "errors_every_100": errs[name]} for name in snaps},
+            "oracle_seconds": t_oracle, "oracle_threads": oracle.threads()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_adjoint512(args, world, rank, local):
+    """Adjoint at 512^3: forward 1500 steps with FR4-16 checkpoints every 10
+    steps in pinned host memory, backward replay + discrete adjoint, gradient
+    w.r.t. kappa; checked against a central difference of the misfit along a
+    smooth random direction (GPU FP32 forward, FP64 misfit)."""
+    import torch
+
+    import paper_2109_05410_gb300 as ooc
+    from synth import layered_velocity, ricker, smooth_random_field
+    torch.cuda.set_device(local)
+    ooc.build()
+    ooc.lib()
+    n, N, every, rate = 512, 1500, 10, 16
+    shape = (n, n, n)
+    v_true = layered_velocity(shape, seed=3)
+    dx = 10.0
+    dt = 0.4 * dx / (v_true.max() * 1.05)
+    c = dt / dx
+    pert = np.clip(smooth_random_field(shape, 16.0, seed=13, dtype=np.float64), -1, 1)
+    v = (v_true * (1.0 + 0.02 * pert)).astype(np.float32)
+    src = (n // 2, n // 2, n // 2)
+    w = (ricker(N, dt) * float((v_true[src[2], src[1], src[0]] * c) ** 2) * 1e3).astype(np.float32)
+    rec = torch.tensor([(8 * n + y) * n + x for y in range(0, n, 8) for x in range(0, n, 8)], dtype=torch.int64,
+                       device="cuda")
+    streams = [torch.cuda.current_stream(), torch.cuda.Stream()]
+    work = torch.empty(ooc.ooc_wave25_adjoint_work_bytes(shape, every, rate), dtype=torch.uint8, device="cuda")
+    t_pin = time.perf_counter()
+    h_ckpt = torch.empty(ooc.ooc_wave25_ckpt_bytes(shape, N, every, rate), dtype=torch.uint8, pin_memory=True)
+    t_pin = time.perf_counter() - t_pin
+    kap_true = ooc.ooc_kappa_from_velocity(torch.from_numpy(v_true.astype(np.float32)).cuda(), c)
+    d = torch.empty((N, rec.numel()), device="cuda")
+    ooc.ooc_wave25_forward_ckpt(kap_true, N, rec, d, every, rate, h_ckpt, work, streams, src=src, w=w)
+    del kap_true
+    kap = ooc.ooc_kappa_from_velocity(torch.from_numpy(v).cuda(), c)
+    tr = torch.empty_like(d)
+    e0, e1 = _cuda_events(torch)
+    e0.record()
+    ooc.ooc_wave25_forward_ckpt(kap, N, rec, tr, every, rate, h_ckpt, work, streams, src=src, w=w)
+    e1.record()
+    e1.synchronize()
+    ms_fwd = e0.elapsed_time(e1)
+    res = (tr - d).contiguous()
+    g = torch.empty(shape, dtype=torch.float64, device="cuda")
+    e0, e1 = _cuda_events(torch)
+    e0.record()
+    ooc.ooc_wave25_backward_ckpt(kap, N, rec, res, every, rate, h_ckpt, g, work, streams, src=src, w=w)
+    e1.record()
+    e1.synchronize()
+    ms_bwd = e0.elapsed_time(e1)
+
+    def misfit(kk):
+        t = torch.empty_like(d)
+        ooc.ooc_wave25_forward_ckpt(kk, N, rec, t, every, rate, h_ckpt, work, streams, src=src, w=w)
+        return 0.5 * float(((t.double() - d.double()) ** 2).sum())
+
+    delta = torch.from_numpy(np.clip(smooth_random_field(shape, 8.0, seed=21, dtype=np.float64), -1, 1)
+                             .astype(np.float32)).cuda() * kap
+    eps = 1e-3
+    fd = (misfit(kap + eps * delta) - misfit(kap - eps * delta)) / (2 * eps)
+    an = float((g * delta.double()).sum())
+    if rank == 0:
+        print(json.dumps({"workload": "adjoint512", "grid": list(shape), "steps": N, "ckpt_every": every,
+                          "ckpt_rate": rate, "ckpt_bytes_pinned": h_ckpt.numel(), "pin_seconds": t_pin,
+                          "ms_forward": ms_fwd, "ms_backward": ms_bwd,
+                          "Gpts_forward": n ** 3 * N / (ms_fwd / 1e3) / 1e9,
+                          "Gpts_backward": n ** 3 * N / (ms_bwd / 1e3) / 1e9,
+                          "fd_directional": fd, "adjoint_directional": an,
+                          "rel_diff": abs(fd - an) / abs(fd) if fd else None,
+                          "fd_note": "central difference, eps 1e-3 of a smooth kappa-relative direction, GPU FP32 "
+                                     "forward with FP64 misfit sums"}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="heat1024",
+                    choices=["heat1024", "kernels512", "wave1024", "precision", "adjoint512"])
     args = ap.parse_args()
     world, rank, local = dist_init(args)
     try:
         if args.impl == "reference":
             return run_reference(args, world, rank)
-        return run_gpu(args, world, rank, local)
+        runner = {"heat1024": run_gpu, "kernels512": run_kernels512, "wave1024": run_wave1024,
+                  "precision": run_precision, "adjoint512": run_adjoint512}[args.workload]
+        return runner(args, world, rank, local)
     finally:
         if world > 1:
             import torch.distributed as dist
