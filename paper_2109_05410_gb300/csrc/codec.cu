@@ -29,6 +29,7 @@ constexpr int kPrec = 26;  // block-floating-point precision (bits)
 constexpr int kThreads = 128;
 constexpr int kPlaneStride = 65;  // words per thread for its plane masks
 constexpr int kSlack = 8;         // words past a block's 2R that a coder may touch
+constexpr int kMetaStride = 17;   // words per thread: 32 16-bit plane offsets (encoder)
 
 // ---- sequency order ---------------------------------------------------------
 // r-th coefficient of the coding order: sort by level sum of (i, j, k) with
@@ -204,67 +205,10 @@ __device__ __forceinline__ void transpose32(uint32_t (&a)[64])
 }
 
 // ---- bit writer / reader over a thread's shared-memory words ------------------
-// Appends bit fields to a thread's words, least-significant bit first,
-// through a 32-bit accumulator.  No budget check: the budget B = 64R bits is
-// exactly 2R words, so the coder runs until a plane ends at or past B and only
-// the first 2R words are kept; the thread's slot has slack for the overrun.
-struct BitWriter {
-    uint32_t *dst;
-    int widx;
-    uint32_t acc;
-    int nacc;  // pending bits in acc, < 32
-    int pos;   // bits appended so far
-
-    __device__ __forceinline__ static uint32_t low_mask(int l)  // l in [0, 32]
-    {
-        return (uint32_t)((1ull << l) - 1ull);
-    }
-    // Append the low `len` (0..32) bits of v; bits of v above len are zero.
-    __device__ __forceinline__ void app(uint32_t v, int len)
-    {
-        const uint32_t lo = acc | (v << nacc);
-        const uint32_t carry = __funnelshift_lc(v, 0u, nacc);  // v >> (32 - nacc)
-        const int tot = nacc + len;
-        pos += len;
-        if (tot >= 32) {
-            dst[widx++] = lo;
-            acc = carry;
-            nacc = tot - 32;
-        } else {
-            acc = lo;
-            nacc = tot;
-        }
-    }
-    // Append the low `len` (0..64) bits of v in one step.
-    __device__ __forceinline__ void app64(uint64_t v, int len)
-    {
-        const uint64_t lo = (uint64_t)acc | (v << nacc);
-        const uint32_t hi = __funnelshift_lc((uint32_t)(v >> 32), 0u, nacc);  // bits 64.. of the sum
-        const int tot = nacc + len;
-        pos += len;
-        if (tot >= 64) {
-            dst[widx] = (uint32_t)lo;
-            dst[widx + 1] = (uint32_t)(lo >> 32);
-            widx += 2;
-            acc = hi;
-            nacc = tot - 64;
-        } else if (tot >= 32) {
-            dst[widx++] = (uint32_t)lo;
-            acc = (uint32_t)(lo >> 32);
-            nacc = tot - 32;
-        } else {
-            acc = (uint32_t)lo;
-            nacc = tot;
-        }
-    }
-    __device__ __forceinline__ void finish(int words)
-    {
-        if (nacc > 0)
-            dst[widx++] = acc;
-        while (widx < words)
-            dst[widx++] = 0u;
-    }
-};
+__device__ __forceinline__ uint32_t low_mask(int l)  // l in [0, 32]
+{
+    return (uint32_t)((1ull << l) - 1ull);
+}
 
 // Reads bit fields of a thread's words through a 64-bit buffer holding at
 // least 32 unread bits; it loads one shared-memory word per 32 bits read.
@@ -300,28 +244,43 @@ struct BitReader {
     __device__ __forceinline__ uint32_t peek32() const { return (uint32_t)buf; }
     __device__ __forceinline__ uint32_t get(int len)  // len in [0, 32]
     {
-        const uint32_t v = (uint32_t)buf & BitWriter::low_mask(len);
+        const uint32_t v = (uint32_t)buf & low_mask(len);
         skip(len);
         return v;
     }
 };
 
+// OR a 64-bit field into a thread's zeroed words at bit offset `off`
+// (least significant bit first); touches words off/32 .. off/32 + 2.
+__device__ __forceinline__ void or_bits(uint32_t *w, int off, uint64_t v)
+{
+    const int i = off >> 5, sh = off & 31;
+    const uint32_t a = (uint32_t)v, b = (uint32_t)(v >> 32);
+    w[i] |= a << sh;
+    w[i + 1] |= __funnelshift_l(a, b, sh);
+    w[i + 2] |= __funnelshift_l(b, 0u, sh);
+}
+
+__device__ __forceinline__ void set_bit(uint32_t *w, int pos) { w[pos >> 5] |= 1u << (pos & 31); }
+
 // ---- one block ----------------------------------------------------------------
-__device__ __forceinline__ void encode_block(uint32_t (&v)[64], int rate, uint32_t *dst, uint32_t *pm)
+__device__ __forceinline__ void encode_block(uint32_t (&v)[64], int rate, uint32_t *dst, uint32_t *pm,
+                                             uint32_t *meta)
 {
     const int words = 2 * rate;
     uint32_t mx = 0;
 #pragma unroll
     for (int i = 0; i < 64; ++i)
         mx = max(mx, v[i] & 0x7FFFFFFFu);
-    BitWriter w{dst, 0, 0u, 0, 0};
     const int budget = 64 * rate;
-    if (mx == 0u) {
-        w.finish(words);
+    // The coder ORs bit fields into a zeroed buffer of 2R words plus slack;
+    // bits it writes past the budget land in the slack and are not kept.
+    for (int i = 0; i < words + kSlack; ++i)
+        dst[i] = 0u;
+    if (mx == 0u)
         return;
-    }
     const int emax = (int)(mx >> 23) - 126;  // largest frexp exponent, >= -126
-    w.app(1u | ((uint32_t)((emax + 127) & 0xFF) << 1), 9);
+    dst[0] = 1u | ((uint32_t)((emax + 127) & 0xFF) << 1);
 
     // q = trunc(x * 2^(26 - emax)), with the power of two split in two
     // normal factors; the first product is exact whenever the result can be
@@ -347,72 +306,71 @@ __device__ __forceinline__ void encode_block(uint32_t (&v)[64], int rate, uint32
 
     // Plane p (31 .. 0) is written as: the refinement bits of the n
     // significant coefficients; then, for each new one at offset t past n,
-    // a segment (group bit 1, the zeros before it, the one); then a closing
+    // a group bit 1, the zeros before it and the one itself; then a closing
     // group bit 0 if coefficients remain.  When a new one is the last
-    // coefficient its one is implied and not written.  The loop emits one
-    // such chunk per iteration, so every lane of a warp runs the same small
-    // body whatever plane it is in.
-    int p = 31, n = 0, nstart = 0, prev = -1;
-    bool ref = true;  // next chunk: plane p's refinement bits
-    uint64_t X = ((uint64_t)pm[32 + 31] << 32) | pm[31];
+    // coefficient its one is implied and not written.
+    //
+    // Pass 1 walks the planes: each plane's length follows in O(1) from its
+    // mask (popcount, highest bit), so its offset is known and its
+    // refinement bits are written in place.  Planes with new ones record
+    // where their significance part starts.  Pass 2 then writes the ones of
+    // the significance parts, one new coefficient per iteration, so the
+    // lanes of a warp stay in step whatever their planes look like.
+    int off = 9, n = 0;
+    uint32_t newmask = 0u;  // planes whose significance part has ones
+#pragma unroll 1
+    for (int p = 31; p >= 0 && off < budget; --p) {
+        const uint64_t X = ((uint64_t)pm[32 + p] << 32) | pm[p];
+        if (n > 0)
+            or_bits(dst, off, n >= 64 ? X : (X & ((1ull << n) - 1ull)));
+        if (n >= 64) {
+            off += 64;
+            continue;
+        }
+        const uint64_t rest = X >> n;
+        if (rest == 0ull) {
+            off += n + 1;  // refinement bits and the closing group bit 0
+            continue;
+        }
+        const int m = __popcll((long long)rest);
+        const int tl = 63 - __clzll((long long)rest);  // offset of the last new one
+        const int n_new = n + tl + 1;
+        reinterpret_cast<uint16_t *>(meta)[p] = (uint16_t)(off + n);
+        newmask |= 1u << p;
+        // n refinement bits, m group bits 1, tl + 1 scanned bits (the last
+        // one implied when it is coefficient 63), a closing 0 if n_new < 64
+        off += n + m + tl + 1 - (n_new == 64 ? 1 : 0) + (n_new < 64 ? 1 : 0);
+        n = n_new;
+    }
+    // Pass 2: significance ones.  Segment j (1-based) of a plane starts with
+    // its group bit at base + t_{j-1} + j (t_0 = -1) and ends with its one at
+    // base + t_j + j.  Planes are visited from the top, as in pass 1, so a
+    // plane's n is the previous visited plane's n plus its last offset + 1.
+    int base = 0, nq = 0, nnext = 0, j = 0, prev_end = 0;
     uint64_t rest = 0ull;
 #pragma unroll 1
-    while (p >= 0 && w.pos < budget) {
-        uint64_t chunk;
-        int len;
-        bool plane_done;
-        if (ref) {
-            chunk = n >= 64 ? X : (X & ((1ull << n) - 1ull));
-            len = n;
-            rest = n < 64 ? (X >> n) : 0ull;
-            nstart = n;
-            prev = -1;
-            ref = false;
-            plane_done = n >= 64 || rest == 0ull;
-            if (n < 64 && rest == 0ull) {  // nothing new: the closing group bit 0 follows
-                if (len < 64) {
-                    len += 1;
-                } else {
-                    w.app64(chunk, len);
-                    chunk = 0ull;
-                    len = 1;
-                }
-            }
-        } else {
-            const int t = __ffsll((long long)rest) - 1;
-            const int gap = t - prev - 1;
-            rest &= rest - 1ull;
-            if (nstart + t == 63) {  // last coefficient: group bit and zeros, its one implied
-                chunk = 1ull;
-                len = gap + 1;
-                n = 64;
-                plane_done = true;
-            } else {
-                chunk = 1ull | (2ull << gap);
-                len = gap + 2;
-                prev = t;
-                n = nstart + t + 1;
-                plane_done = rest == 0ull;
-                if (plane_done) {  // closing group bit 0 (n < 64 here)
-                    if (len < 64) {
-                        len += 1;
-                    } else {
-                        w.app64(chunk, len);
-                        chunk = 0ull;
-                        len = 1;
-                    }
-                }
-            }
+    for (;;) {
+        if (rest == 0ull) {
+            if (newmask == 0u)
+                break;
+            const int pl = 31 - __clz((int)newmask);
+            newmask ^= 1u << pl;
+            base = reinterpret_cast<const uint16_t *>(meta)[pl];
+            nq = nnext;
+            rest = (((uint64_t)pm[32 + pl] << 32) | pm[pl]) >> nq;
+            j = 0;
+            prev_end = base - 1;  // position of the previous segment's one
         }
-        w.app64(chunk, len);
-        if (plane_done) {
-            --p;
-            ref = true;
-            if (p >= 0)
-                X = ((uint64_t)pm[32 + p] << 32) | pm[p];
-        }
+        const int t = __ffsll((long long)rest) - 1;
+        rest &= rest - 1ull;
+        ++j;
+        set_bit(dst, prev_end + 1);  // group bit of this segment
+        const int d = base + t + j;
+        if (nq + t != 63)            // the last coefficient's one is implied
+            set_bit(dst, d);
+        prev_end = d;
+        nnext = nq + t + 1;
     }
-    w.finish(words);
 }
 
 __device__ __forceinline__ void decode_block(const uint32_t *src, int rate, float (&out)[64], uint32_t *pm)
@@ -444,7 +402,7 @@ __device__ __forceinline__ void decode_block(const uint32_t *src, int rate, floa
                 }
                 const int len = 63 - n;  // explicit scan bits at most (after the group bit)
                 const int m = len < 31 ? len : 31;
-                const uint32_t sc = (wv >> 1) & BitWriter::low_mask(m);
+                const uint32_t sc = (wv >> 1) & low_mask(m);
                 if (sc != 0u) {
                     const int t = __ffs((int)sc) - 1;
                     r.skip(t + 2);
@@ -467,7 +425,7 @@ __device__ __forceinline__ void decode_block(const uint32_t *src, int rate, floa
                 for (;;) {
                     const int rem = len - done;
                     const int mm = rem < 32 ? rem : 32;
-                    const uint32_t s2 = r.peek32() & BitWriter::low_mask(mm);
+                    const uint32_t s2 = r.peek32() & low_mask(mm);
                     if (s2 != 0u) {
                         const int f = __ffs((int)s2);
                         const int t = done + f - 1;
@@ -548,7 +506,8 @@ __global__ void __launch_bounds__(kThreads) fr4_encode_kernel(ConstRing in, int6
                 v[16 * k + 4 * j + 2] = __float_as_uint(f.z);
                 v[16 * k + 4 * j + 3] = __float_as_uint(f.w);
             }
-        encode_block(v, rate, smem + threadIdx.x * stride, smem + kThreads * stride + threadIdx.x * kPlaneStride);
+        encode_block(v, rate, smem + threadIdx.x * stride, smem + kThreads * stride + threadIdx.x * kPlaneStride,
+                     smem + kThreads * (stride + kPlaneStride) + threadIdx.x * kMetaStride);
     }
     __syncthreads();
     const int64_t left = nblk - first;
@@ -615,9 +574,11 @@ __global__ void __launch_bounds__(kThreads) fr4_decode_kernel(const uint32_t *__
 // Shared memory per CTA: each thread's compressed words plus kSlack words
 // of slack (stride 2R + kSlack + 1, odd, so that the threads' slots start in
 // different banks), then each thread's 64 plane masks (stride 65).
-size_t smem_bytes(int rate)
+size_t smem_bytes(int rate, bool encoder)
 {
-    return ((size_t)kThreads * (2 * rate + kSlack + 1) + (size_t)kThreads * kPlaneStride) * sizeof(uint32_t);
+    return ((size_t)kThreads * (2 * rate + kSlack + 1) +
+            (size_t)kThreads * (kPlaneStride + (encoder ? kMetaStride : 0))) *
+           sizeof(uint32_t);
 }
 
 cudaError_t ensure_smem_attr()
@@ -626,10 +587,10 @@ cudaError_t ensure_smem_attr()
     if (done)
         return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(fr4_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_bytes(64));
+                                         (int)smem_bytes(64, true));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(fr4_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_bytes(64));
+                                 (int)smem_bytes(64, false));
     if (e == cudaSuccess)
         done = true;
     return e;
@@ -647,7 +608,7 @@ cudaError_t launch_fr4_encode(ConstRing in, int64_t nx, int64_t ny, int64_t z0, 
     if (e != cudaSuccess)
         return e;
     const int64_t grid = (nblk + kThreads - 1) / kThreads;
-    fr4_encode_kernel<<<(unsigned)grid, kThreads, smem_bytes(rate), st>>>(in, nx, ny, z0, nblk, rate, out);
+    fr4_encode_kernel<<<(unsigned)grid, kThreads, smem_bytes(rate, true), st>>>(in, nx, ny, z0, nblk, rate, out);
     return cudaGetLastError();
 }
 
@@ -661,7 +622,7 @@ cudaError_t launch_fr4_decode(const uint32_t *in, int64_t nx, int64_t ny, int64_
     if (e != cudaSuccess)
         return e;
     const int64_t grid = (nblk + kThreads - 1) / kThreads;
-    fr4_decode_kernel<<<(unsigned)grid, kThreads, smem_bytes(rate), st>>>(in, nx, ny, z0, nblk, rate, out);
+    fr4_decode_kernel<<<(unsigned)grid, kThreads, smem_bytes(rate, false), st>>>(in, nx, ny, z0, nblk, rate, out);
     return cudaGetLastError();
 }
 
