@@ -45,8 +45,8 @@ COMPARE = [("fp32", 0), ("bf16", 0), ("fr4", 8), ("fr4", 12), ("fr4", 24)]
 # points; profiles/kernels_512cube_full.md).  Traffic is proportional to the
 # points a launch processes, so the bench scales it to its own launches.  It
 # is only valid for the stencil source it was measured on (sha256 prefix).
-HEAT7_TRAFFIC_PER_POINT = 7.80
-HEAT7_TRAFFIC_SRC_SHA = "4dd2925f74c35334"
+HEAT7_TRAFFIC_PER_POINT = 7.81
+HEAT7_TRAFFIC_SRC_SHA = "4c3d04d28747aef7"
 METRIC = "Gpts/s out-of-core (compressed vs uncompressed, same GB300) at stated L2 error; % roofline"
 WORKLOAD = "heat7 1024^3 FP32, device budget 1 GiB, k=4, 64 steps/bench step"
 
@@ -398,8 +398,9 @@ def _cuda_events(torch):
 
 def run_kernels512(args, world, rank, local):
     """Each kernel once per step on a 512^3 smooth field (the ncu capture case):
-    FR4 encode and decode at R = 16, two in-core heat7 steps, two in-core
-    wave25 steps; CUDA-event times per kernel class."""
+    FR4 encode and decode at R = 16, two in-core heat7 steps, two fused heat7
+    pairs (two steps per launch), two in-core wave25 steps; CUDA-event times
+    per kernel class."""
     import torch
 
     import paper_2109_05410_gb300 as ooc
@@ -416,13 +417,14 @@ def run_kernels512(args, world, rank, local):
     kap = torch.full_like(d, 0.1)
     pp = torch.zeros_like(d)
     ops = {
-        "fr4_encode": (lambda: ooc.ooc_compress(d, 16, d_out=w), 1, (4 + 2) * pts),
-        "fr4_decode": (lambda: ooc.ooc_decompress(w, (n, n, n), 16, d_out=out), 1, (4 + 2) * pts),
-        "heat7": (lambda: ooc.ooc_heat7_steps(d, tmp, 2), 2, 8 * pts),
-        "wave25": (lambda: ooc.ooc_wave25_steps(d, pp, kap, 2), 2, 16 * pts),
+        "fr4_encode": (lambda: ooc.ooc_compress(d, 16, d_out=w), 1, (4 + 2) * pts, 0),
+        "fr4_decode": (lambda: ooc.ooc_decompress(w, (n, n, n), 16, d_out=out), 1, (4 + 2) * pts, 0),
+        "heat7": (lambda: ooc.ooc_heat7_steps(d, tmp, 2), 2, 8 * pts, 1),
+        "heat7_fused_pair": (lambda: ooc.ooc_heat7_steps_fused(d, tmp, 4), 2, 8 * pts, 2),
+        "wave25": (lambda: ooc.ooc_wave25_steps(d, pp, kap, 2), 2, 16 * pts, 1),
     }
     res = {}
-    for name, (fn, nl, by) in ops.items():
+    for name, (fn, nl, by, spl) in ops.items():
         for _ in range(args.warmup):
             fn()
         e0, e1 = _cuda_events(torch)
@@ -434,6 +436,9 @@ def run_kernels512(args, world, rank, local):
         e1.synchronize()
         ms = e0.elapsed_time(e1) / max(args.steps, 1) / nl
         res[name] = {"ms_per_launch": ms, "GBs": by / (ms / 1e3) / 1e9}
+        if spl:
+            res[name]["steps_per_launch"] = spl
+            res[name]["Gpts_steps_per_s"] = pts * spl / (ms / 1e3) / 1e9
     if rank == 0:
         print(json.dumps({"workload": "kernels512", "kernels": res, "n_gpus": world, "steps": args.steps,
                           "warmup": args.warmup}), flush=True)

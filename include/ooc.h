@@ -72,6 +72,9 @@ typedef struct {
     int32_t slab_planes;         /* slab thickness T (multiple of 4); 0 = largest that fits */
     int32_t profile;             /* 1 = time every launch and copy with CUDA events */
     int64_t wait_timeout_ms;     /* deadline for host waits on the GPU; 0 = 600000 */
+    int32_t heat_steps_per_launch; /* heat7: 1 = one step per launch (0 = default = 1); 2 = each pair
+                                      of the k steps in one launch with the intermediate level kept on
+                                      chip.  Results are bit-identical.  wave25: 0 or 1. */
 } ooc_config;
 
 typedef struct ooc_plan ooc_plan;
@@ -136,6 +139,15 @@ ooc_status ooc_heat7_steps(float *d_u, float *d_tmp, int64_t nx, int64_t ny, int
 ooc_status ooc_wave25_steps(float *d_p, float *d_pprev, const float *d_kappa, int64_t nx, int64_t ny,
                             int64_t nz, int64_t sx, int64_t sy, int64_t sz, const float *h_w, int64_t t,
                             int64_t nsteps, void *stream);
+
+/* The nsteps heat7 steps of ooc_heat7_steps with each pair of steps in one
+ * kernel launch (temporal blocking inside the kernel, Section III: the
+ * intermediate level stays in shared memory and registers, so HBM carries
+ * one read and one write of the field per two steps).  An odd last step
+ * runs alone.  Same arguments and errors as ooc_heat7_steps; results are
+ * bit-identical to it. */
+ooc_status ooc_heat7_steps_fused(float *d_u, float *d_tmp, int64_t nx, int64_t ny, int64_t nz, double r,
+                                 int64_t nsteps, void *stream);
 
 /* Largest grid, in points, that ooc_heat7_steps_noalloc accepts: the size of
  * its fixed scratch array (4 Mi floats, 16 MiB). */

@@ -20,7 +20,7 @@ __all__ = [
     "OOC_HEAT7", "OOC_WAVE25", "OOC_FMT_FP32", "OOC_FMT_BF16", "OOC_FMT_FR4",
     "OocConfig", "OocStats", "OocPlanInfo", "OocError", "lib", "build",
     "ooc_status_string", "ooc_compressed_bytes", "ooc_compress", "ooc_decompress",
-    "ooc_bf16_pack", "ooc_bf16_unpack", "ooc_heat7_steps", "ooc_heat7_steps_noalloc", "ooc_wave25_steps", "Plan",
+    "ooc_bf16_pack", "ooc_bf16_unpack", "ooc_heat7_steps", "ooc_heat7_steps_fused", "ooc_heat7_steps_noalloc", "ooc_wave25_steps", "Plan",
     "ooc_gather", "ooc_scatter_add", "ooc_wave25_adjoint_step", "ooc_wave25_grad_accum", "ooc_kappa_from_velocity",
     "ooc_velocity_grad", "ooc_wave25_ckpt_bytes", "ooc_wave25_adjoint_work_bytes", "ooc_wave25_forward_ckpt",
     "ooc_wave25_backward_ckpt", "WaveFn", "wave_forward",
@@ -40,6 +40,7 @@ class OocConfig(ctypes.Structure):
         ("ro_format", ctypes.c_int32), ("ro_rate", ctypes.c_int32),
         ("device_budget_bytes", ctypes.c_int64), ("slab_planes", ctypes.c_int32),
         ("profile", ctypes.c_int32), ("wait_timeout_ms", ctypes.c_int64),
+        ("heat_steps_per_launch", ctypes.c_int32),
     ]
 
 
@@ -85,6 +86,8 @@ _SIGS = {
     "ooc_bf16_unpack": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "ooc_heat7_steps": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p] + [ctypes.c_int64] * 3
                         + [ctypes.c_double, ctypes.c_int64, ctypes.c_void_p]),
+    "ooc_heat7_steps_fused": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p] + [ctypes.c_int64] * 3
+                              + [ctypes.c_double, ctypes.c_int64, ctypes.c_void_p]),
     "ooc_wave25_steps": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int64] * 6
                          + [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]),
     "ooc_plan_create": (ctypes.c_int, [ctypes.POINTER(OocConfig), ctypes.POINTER(ctypes.c_void_p),
@@ -210,6 +213,14 @@ def ooc_heat7_steps(d_u, d_tmp, nsteps, r=1.0 / 6.0, stream=None):
     nz, ny, nx = d_u.shape
     _check(lib().ooc_heat7_steps(_ptr(d_u), _ptr(d_tmp), nx, ny, nz, float(r), int(nsteps), _stream(stream)),
            "ooc_heat7_steps")
+    return d_u
+
+
+def ooc_heat7_steps_fused(d_u, d_tmp, nsteps, r=1.0 / 6.0, stream=None):
+    """ooc_heat7_steps with each pair of steps in one launch (bit-identical)."""
+    nz, ny, nx = d_u.shape
+    _check(lib().ooc_heat7_steps_fused(_ptr(d_u), _ptr(d_tmp), nx, ny, nz, float(r), int(nsteps), _stream(stream)),
+           "ooc_heat7_steps_fused")
     return d_u
 
 
@@ -342,7 +353,7 @@ class Plan:
     streams (H2D, compute, D2H).  Configuration keys mirror ``ooc_config``:
     nx, ny, nz, stencil ('heat7'|'wave25'), k, r, rw_format, rw_rate,
     ro_format, ro_rate, device_budget_bytes, slab_planes, profile,
-    wait_timeout_ms."""
+    wait_timeout_ms, heat_steps_per_launch."""
 
     def __init__(self, device=0, **kw):
         import torch
@@ -360,6 +371,7 @@ class Plan:
         c.slab_planes = kw.get("slab_planes", 0)
         c.profile = int(kw.get("profile", 0))
         c.wait_timeout_ms = kw.get("wait_timeout_ms", 0)
+        c.heat_steps_per_launch = int(kw.get("heat_steps_per_launch", 0))
         self.config = c
         self.shape = (c.nz, c.ny, c.nx)
         self._h = ctypes.c_void_p()

@@ -126,6 +126,29 @@ ooc_status ooc_heat7_steps(float *d_u, float *d_tmp, int64_t nx, int64_t ny, int
     return OOC_OK;
 }
 
+ooc_status ooc_heat7_steps_fused(float *d_u, float *d_tmp, int64_t nx, int64_t ny, int64_t nz, double r,
+                                 int64_t nsteps, void *stream)
+{
+    if (!d_u || !d_tmp || !dims_ok(nx, ny, nz) || nsteps < 0 || d_u == d_tmp)
+        return OOC_E_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    float *a = d_u, *b = d_tmp;
+    for (int64_t s = 0; s < nsteps; s += 2) {
+        cudaError_t e = s + 2 <= nsteps
+                            ? launch_heat7x2(ConstRing{a, nz, 0}, Ring{b, nz, 0}, nx, ny, nz, 0, nz, 0, nz, nullptr, 0,
+                                             nullptr, 0, (float)r, st)
+                            : launch_heat7(ConstRing{a, nz, 0}, Ring{b, nz, 0}, nx, ny, nz, 0, nz, (float)r, st);
+        if (e != cudaSuccess)
+            return OOC_E_CUDA;
+        float *t = a;
+        a = b;
+        b = t;
+    }
+    if (a != d_u)
+        return cuda_status(cudaMemcpyAsync(d_u, a, sizeof(float) * nx * ny * nz, cudaMemcpyDeviceToDevice, st));
+    return OOC_OK;
+}
+
 ooc_status ooc_wave25_steps(float *d_p, float *d_pprev, const float *d_kappa, int64_t nx, int64_t ny, int64_t nz,
                             int64_t sx, int64_t sy, int64_t sz, const float *h_w, int64_t t, int64_t nsteps,
                             void *stream)

@@ -40,6 +40,15 @@ constexpr float kC4 = -1.0f / 560.0f;
 // cudaGetLastError() of the launch.
 cudaError_t launch_heat7(ConstRing in, Ring out, int64_t nx, int64_t ny, int64_t nz, int64_t z0, int64_t z1,
                          float r, cudaStream_t st);
+// Two heat7 steps in one launch: level s on [lo, hi) computed on chip from
+// ring `in` (level s-1), level s+1 written to ring `out` on [z0, z1).  The
+// two level-s planes below lo are read from band_in (planes bin_lo,
+// bin_lo+1, nx*ny floats each; NULL when lo has no planes below it), and
+// level s on [bout_lo, bout_lo+2) is written to band_out (NULL: not saved).
+// `in` and `out` must be different buffers.
+cudaError_t launch_heat7x2(ConstRing in, Ring out, int64_t nx, int64_t ny, int64_t nz, int64_t z0, int64_t z1,
+                           int64_t lo, int64_t hi, const float *band_in, int64_t bin_lo, float *band_out,
+                           int64_t bout_lo, float r, cudaStream_t st);
 cudaError_t launch_wave25(ConstRing p, Ring pprev_out, ConstRing kappa, int64_t nx, int64_t ny, int64_t nz,
                           int64_t z0, int64_t z1, int64_t sx, int64_t sy, int64_t sz, float w, cudaStream_t st);
 // Same step with p_prev read from `pprev` and p' written to `pnew` (may alias).

@@ -61,6 +61,8 @@ struct ooc_plan {
     ooc_config cfg{};
     int64_t T = 0, nslab = 0, W = 0, h = 0, Z = 0;
     int nrw = 0, nfield = 0, nring = 0;
+    int spl = 1;  // heat7 steps per stencil launch (1 or 2)
+    size_t off_band = 0, band_bytes = 0;  // level-s bands of the fused launches
     int fmt[3] = {0, 0, 0}, rate[3] = {0, 0, 0};
     int64_t fplane[3] = {0, 0, 0};  // storage bytes per plane, per field
     int64_t plane_elems = 0;
@@ -120,6 +122,11 @@ size_t layout(ooc_plan *p, int64_t T)
             p->off_out[b][f] = off;
             off += align256(p->out_bytes_field[f]);
         }
+    // Fused heat7 pairs: the intermediate level's top 2h planes of each slab,
+    // for the next slab; one band per pair of the pass and slab parity.
+    p->off_band = off;
+    p->band_bytes = p->spl == 2 ? (size_t)(2 * h) * p->plane_elems * sizeof(float) : 0;
+    off += align256(p->band_bytes) * 2 * (size_t)(p->cfg.k / 2);
     (void)any_staged;
     p->Z = Z;
     return off;
@@ -131,6 +138,15 @@ Ring ring_view(ooc_plan *p, int r, int64_t zbase)
 }
 
 ConstRing cring(const Ring &r) { return ConstRing{r.base, r.nslot, r.zbase}; }
+
+// Band of pair j written by slabs of parity `parity`.
+float *band(ooc_plan *p, int64_t j, int64_t parity)
+{
+    return (float *)(p->dev + p->off_band + align256(p->band_bytes) * (size_t)(2 * j + parity));
+}
+
+// Stencil launches of a pass of kp steps (heat7 pairs when fused).
+int64_t stencil_launches(const ooc_plan *p, int64_t kp) { return p->spl == 2 ? kp / 2 + (kp & 1) : kp; }
 
 // Copy planes [z0, z1) between a ring and contiguous memory (split at wrap).
 cudaError_t copy_ring(ooc_plan *p, int r, int64_t zbase, int64_t z0, int64_t z1, char *hostp, bool to_device,
@@ -237,7 +253,7 @@ int input_ring(const ooc_plan *p, int f) { return f; }
 int output_ring(const ooc_plan *p, int f, int64_t kp)
 {
     if (f == 0)
-        return (int)(kp & 1);
+        return (int)(stencil_launches(p, kp) & 1);  // launch j reads ring j&1, writes the other
     return (int)((kp + 1) & 1);  // wave p^{t+kp-1}
 }
 
@@ -294,11 +310,15 @@ ooc_status ooc_plan_create(const ooc_config *cfg, ooc_plan **out, size_t *device
         return OOC_E_INVALID;
     if (c.slab_planes < 0 || c.slab_planes % 4 || c.device_budget_bytes < 0)
         return OOC_E_INVALID;
+    if (c.heat_steps_per_launch < 0 || c.heat_steps_per_launch > 2 ||
+        (c.stencil == OOC_WAVE25 && c.heat_steps_per_launch > 1))
+        return OOC_E_INVALID;
     ooc_plan *p = new (std::nothrow) ooc_plan();
     if (!p)
         return OOC_E_ALLOC;
     p->cfg = c;
     p->h = c.stencil == OOC_HEAT7 ? 1 : 4;
+    p->spl = c.stencil == OOC_HEAT7 && c.heat_steps_per_launch == 2 ? 2 : 1;
     p->W = round4((int64_t)c.k * p->h);
     p->nrw = c.stencil == OOC_HEAT7 ? 1 : 2;
     p->nfield = c.stencil == OOC_HEAT7 ? 1 : 3;
@@ -544,15 +564,30 @@ ooc_status ooc_step(ooc_plan *p, int64_t nsteps)
                 }
             }
             OOC_CUDA(cudaEventRecord(p->ev_dec[e], sC));
-            for (int64_t s = 1; s <= kp; ++s) {
+            for (int64_t s = 1, j = 0; s <= kp; ++j) {
+                // launch j: steps s (and s+1 when paired), ring j&1 -> the other
+                const int64_t len = p->spl == 2 && s + 1 <= kp ? 2 : 1;
                 int64_t lo, hi;
-                step_window(p, i, kp, s, &lo, &hi);
-                if (hi <= lo)
+                step_window(p, i, kp, s + len - 1, &lo, &hi);
+                if (hi <= lo) {
+                    s += len;
                     continue;
+                }
                 size_t pi;
                 OOC_TRY(prof_begin(p, sC, 1, &pi));
-                if (!wave) {
-                    OOC_CUDA(launch_heat7(cring(ring_view(p, (int)((s - 1) & 1), zb)), ring_view(p, (int)(s & 1), zb),
+                if (!wave && len == 2) {
+                    // level s on [lo_s, hi_s) stays on chip; its 2h planes
+                    // below lo_s come from slab i-1's band, its top 2h
+                    // planes go to this slab's band
+                    int64_t lo_s, hi_s;
+                    step_window(p, i, kp, s, &lo_s, &hi_s);
+                    const float *bin = i > 0 ? band(p, j, (i - 1) & 1) : nullptr;
+                    float *bout = i + 1 < p->nslab ? band(p, j, i & 1) : nullptr;
+                    OOC_CUDA(launch_heat7x2(cring(ring_view(p, (int)(j & 1), zb)), ring_view(p, (int)((j + 1) & 1), zb),
+                                            nx, ny, nz, lo, hi, lo_s, hi_s, bin, lo_s - 2 * p->h, bout,
+                                            hi_s - 2 * p->h, r, sC));
+                } else if (!wave) {
+                    OOC_CUDA(launch_heat7(cring(ring_view(p, (int)(j & 1), zb)), ring_view(p, (int)((j + 1) & 1), zb),
                                           nx, ny, nz, lo, hi, r, sC));
                 } else {
                     const int64_t n = t0 + s - 1;  // computing p^{n+1}
@@ -563,6 +598,7 @@ ooc_status ooc_step(ooc_plan *p, int64_t nsteps)
                 }
                 OOC_TRY(prof_end(p, sC, pi));
                 p->stats.kernel_launches++;
+                s += len;
             }
             bool any_enc = false;
             for (int f = 0; f < p->nrw; ++f)

@@ -31,6 +31,21 @@ namespace {
 constexpr int kTX = 32;  // threads per row segment (4 points each: 128 x)
 constexpr int kHeatTY = 8;
 constexpr int kWaveTY = 8;
+#define OOC_PRAGMA_(x) _Pragma(#x)
+#define OOC_PRAGMA(x) OOC_PRAGMA_(x)
+#ifndef OOC_HEAT_UNROLL
+#define OOC_HEAT_UNROLL 8
+#endif
+#ifndef OOC_HEATX2_UNROLL
+#define OOC_HEATX2_UNROLL 4
+#endif
+#ifndef OOC_WAVE_UNROLL
+#define OOC_WAVE_UNROLL 18
+#endif
+#ifndef OOC_HEATX2_TY
+#define OOC_HEATX2_TY 8
+#endif
+constexpr int kHeatX2TY = OOC_HEATX2_TY;  // level s+1 rows per CTA of the fused kernel
 constexpr int kSeg = 4 * kTX;
 
 __device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
@@ -48,6 +63,30 @@ __device__ __forceinline__ int wrap_add(int s, int d, int nslot)
 }
 
 __device__ __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+
+// One heat7 point in a fixed operation order, written with rounding
+// intrinsics so that the compiler cannot contract or reorder it: every heat
+// kernel uses it, and a fused two-step launch reproduces two single-step
+// launches bit for bit.
+//   u' = u + r * (((x- + x+) + (y- + y+)) + (z- + z+) - 6 u)
+__device__ __forceinline__ float heat_pt(float c, float xl, float xr, float up, float dn, float zm, float zp, float r)
+{
+    const float t = __fadd_rn(__fadd_rn(__fadd_rn(xl, xr), __fadd_rn(up, dn)), __fadd_rn(zm, zp));
+    return __fmaf_rn(r, __fmaf_rn(-6.0f, c, t), c);
+}
+
+// Four consecutive x points; xl / xr are the neighbours left of c.x and
+// right of c.w.
+__device__ __forceinline__ float4 heat_pt4(float4 c, float xl, float xr, float4 up, float4 dn, float4 zm, float4 zp,
+                                           float r)
+{
+    float4 o;
+    o.x = heat_pt(c.x, xl, c.y, up.x, dn.x, zm.x, zp.x, r);
+    o.y = heat_pt(c.y, c.x, c.z, up.y, dn.y, zm.y, zp.y, r);
+    o.z = heat_pt(c.z, c.y, c.w, up.z, dn.z, zm.z, zp.z, r);
+    o.w = heat_pt(c.w, c.z, xr, up.w, dn.w, zm.w, zp.w, r);
+    return o;
+}
 
 __global__ void __launch_bounds__(kTX *kHeatTY)
     heat7_kernel(const float *__restrict__ in, float *__restrict__ out, int nslot, int64_t zbase, Grid3 g,
@@ -90,7 +129,7 @@ __global__ void __launch_bounds__(kTX *kHeatTY)
     float hx1 = (hcol && za + 1 < nz) ? __ldg(p1 + xoff) : 0.f;
     int64_t z = za;
     // unrolled twice so that the register queue rotates by renaming
-#pragma unroll 2
+OOC_PRAGMA(unroll OOC_HEAT_UNROLL)
     for (int i = 0; i < cnt; ++i, ++z) {
         const int s2 = wrap_add(s, 2, nslot), s3 = wrap_add(s, 3, nslot);
         const float *q2 = in + (int64_t)s2 * plane;
@@ -115,13 +154,131 @@ __global__ void __launch_bounds__(kTX *kHeatTY)
         __syncthreads();
         const float4 up = tile[b][ty][lane];
         const float4 dn = tile[b][ty + 2][lane];
-        float4 o;
-        o.x = cur.x + r * (((xl + cur.y) + (up.x + dn.x)) + (prev.x + nxt.x) - 6.0f * cur.x);
-        o.y = cur.y + r * (((cur.x + cur.z) + (up.y + dn.y)) + (prev.y + nxt.y) - 6.0f * cur.y);
-        o.z = cur.z + r * (((cur.y + cur.w) + (up.z + dn.z)) + (prev.z + nxt.z) - 6.0f * cur.z);
-        o.w = cur.w + r * (((cur.z + xr) + (up.w + dn.w)) + (prev.w + nxt.w) - 6.0f * cur.w);
+        const float4 o = heat_pt4(cur, xl, xr, up, dn, prev, nxt, r);
         if (inside)
             *reinterpret_cast<float4 *>(out + (int64_t)s * plane + off) = o;
+        prev = cur;
+        cur = nxt;
+        nxt = nn;
+        nn = pfv;
+        hyv = hyv1;
+        hyv1 = hyv2;
+        hx = hx1;
+        hx1 = hx2;
+        s = wrap_add(s, 1, nslot);
+    }
+}
+
+// Two heat7 steps per launch: levels s and s+1 of a pair, with level s kept
+// on chip (temporal blocking inside the kernel, so HBM carries 8 bytes per
+// point for two steps instead of 16).
+//
+// A CTA owns an output tile of 120 x TYO points of level s+1 and marches z.
+// Warp w holds row y0 - 1 + w of level s (rows y0-1 .. y0+TYO) over 128 x
+// (the tile and 4 points on each side), computed from level s-1 with the
+// register queue, shuffles and shared-memory rows of heat7_kernel.  Level s
+// of plane z goes to a shared-memory row; level s+1 of plane z-1 is then
+// formed on the inner warps and lanes from the level-s rows of planes
+// z-2..z.  One barrier per plane: both shared arrays are double buffered.
+//
+// Level s is computed on the planes [lo, hi) only.  Its two planes below
+// lo come from band_in (planes bin_lo, bin_lo+1: left by the previous slab
+// of the pipeline), and the two planes [bout_lo, bout_lo+2) are saved to
+// band_out for the next slab.  Outside the grid every level is zero.
+template <int TYO>
+__global__ void __launch_bounds__(kTX *(TYO + 2))
+    heat7x2_kernel(const float *__restrict__ in, float *__restrict__ out, int nslot, int64_t zbase, Grid3 g,
+                   int64_t z0, int64_t z1, int64_t zchunk, int64_t lo, int64_t hi, const float *__restrict__ band_in,
+                   int64_t bin_lo, float *__restrict__ band_out, int64_t bout_lo, float r)
+{
+    constexpr int NW = TYO + 2;
+    __shared__ float4 ta[2][TYO + 4][kTX];  // level s-1, rows y0-2 .. y0+TYO+1
+    __shared__ float4 tb[2][TYO + 2][kTX];  // level s, rows y0-1 .. y0+TYO
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int64_t xs = (int64_t)blockIdx.x * (kSeg - 8) - 4;
+    const int64_t x4 = xs + 4 * lane;
+    const int64_t y0 = (int64_t)blockIdx.y * TYO;
+    const int64_t y = y0 - 1 + w;
+    const int64_t za = z0 + (int64_t)blockIdx.z * zchunk;
+    const int cnt = (int)(min(za + zchunk, z1) - za);
+    const int64_t nz = g.nz, plane = g.plane;
+    const bool xin = x4 >= 0 && x4 < g.nx;
+    const bool yin = y >= 0 && y < g.ny;
+    const bool inside = xin && yin;
+    const int64_t off = inside ? y * g.nx + x4 : 0;
+    const int64_t yh = w == 0 ? y0 - 2 : y0 + TYO + 1;  // halo row of the edge warps
+    const bool hrow = (w == 0 || w == NW - 1) && yh >= 0 && yh < g.ny && xin;
+    const int64_t hoff = hrow ? yh * g.nx + x4 : 0;
+    const int64_t xh = lane == 0 ? xs - 1 : xs + kSeg;  // halo column of the edge lanes
+    const bool hcol = (lane == 0 || lane == kTX - 1) && xh >= 0 && xh < g.nx && yin;
+    const int64_t xoff = hcol ? y * g.nx + xh : 0;
+    const bool mid = w >= 1 && w <= TYO;                        // warp produces level s+1
+    const bool own = inside && mid && lane >= 1 && lane <= kTX - 2;  // and this thread stores it
+    const float4 z4 = zero4();
+
+    int64_t z = za - 1;  // plane of level s produced in the current iteration
+    int s = (int)ring_slot(z, zbase, nslot);
+    const float *pm = in + (int64_t)wrap_add(s, nslot - 1, nslot) * plane;
+    const float *p0 = in + (int64_t)s * plane;
+    const float *p1 = in + (int64_t)wrap_add(s, 1, nslot) * plane;
+    const float *p2 = in + (int64_t)wrap_add(s, 2, nslot) * plane;
+    // level s-1 queue z-1 .. z+2 and the halos of planes z, z+1
+    float4 prev = (inside && z >= 1) ? ldg4(pm + off) : z4;
+    float4 cur = (inside && z >= 0) ? ldg4(p0 + off) : z4;
+    float4 nxt = (inside && z + 1 < nz) ? ldg4(p1 + off) : z4;
+    float4 nn = (inside && z + 2 < nz) ? ldg4(p2 + off) : z4;
+    float4 hyv = (hrow && z >= 0) ? ldg4(p0 + hoff) : z4;
+    float4 hyv1 = (hrow && z + 1 < nz) ? ldg4(p1 + hoff) : z4;
+    float hx = (hcol && z >= 0) ? __ldg(p0 + xoff) : 0.f;
+    float hx1 = (hcol && z + 1 < nz) ? __ldg(p1 + xoff) : 0.f;
+    float4 sm2 = z4, sm1 = z4;  // level s at planes z-2, z-1
+OOC_PRAGMA(unroll OOC_HEATX2_UNROLL)
+    for (int i = 0; i < cnt + 2; ++i, ++z) {
+        const int s2 = wrap_add(s, 2, nslot), s3 = wrap_add(s, 3, nslot);
+        const float4 pfv = (inside && z + 3 < nz) ? ldg4(in + (int64_t)s3 * plane + off) : z4;
+        const bool v2 = z + 2 >= 0 && z + 2 < nz;
+        const float4 hyv2 = (hrow && v2) ? ldg4(in + (int64_t)s2 * plane + hoff) : z4;
+        const float hx2 = (hcol && v2) ? __ldg(in + (int64_t)s2 * plane + xoff) : 0.f;
+
+        const int b = i & 1;
+        ta[b][w + 1][lane] = cur;
+        if (w == 0)
+            ta[b][0][lane] = hyv;
+        if (w == NW - 1)
+            ta[b][TYO + 3][lane] = hyv;
+        float xl = __shfl_up_sync(0xffffffffu, cur.w, 1);
+        float xr = __shfl_down_sync(0xffffffffu, cur.x, 1);
+        if (lane == 0)
+            xl = hx;
+        if (lane == kTX - 1)
+            xr = hx;
+        __syncthreads();
+        // level s at plane z (z is uniform over the CTA)
+        float4 sv = z4;
+        if (z >= lo && z < hi) {
+            const float4 up = ta[b][w][lane];
+            const float4 dn = ta[b][w + 2][lane];
+            const float4 o = heat_pt4(cur, xl, xr, up, dn, prev, nxt, r);
+            sv = inside ? o : z4;
+        } else if (band_in != nullptr && z >= bin_lo && z < bin_lo + 2 && inside) {
+            sv = ldg4(band_in + (z - bin_lo) * plane + off);
+        }
+        if (band_out != nullptr && own && z >= bout_lo && z < bout_lo + 2)
+            *reinterpret_cast<float4 *>(band_out + (z - bout_lo) * plane + off) = sv;
+        tb[b][w][lane] = sv;
+        // level s+1 at plane z-1 from the level-s rows of plane z-1 (written
+        // in the previous iteration) and planes z-2, z in registers
+        if (i >= 2 && mid) {
+            const float4 up = tb[b ^ 1][w - 1][lane];
+            const float4 dn = tb[b ^ 1][w + 1][lane];
+            const float yl = __shfl_up_sync(0xffffffffu, sm1.w, 1);
+            const float yr = __shfl_down_sync(0xffffffffu, sm1.x, 1);
+            const float4 o = heat_pt4(sm1, yl, yr, up, dn, sm2, sv, r);
+            if (own)
+                *reinterpret_cast<float4 *>(out + (int64_t)wrap_add(s, nslot - 1, nslot) * plane + off) = o;
+        }
+        sm2 = sm1;
+        sm1 = sv;
         prev = cur;
         cur = nxt;
         nxt = nn;
@@ -185,6 +342,7 @@ __global__ void __launch_bounds__(kTX *kWaveTY, 2)
     float4 ppv = inside ? *reinterpret_cast<const float4 *>(pprev + (int64_t)s * plane + off) : z4;
     float4 kv = inside ? ldg4(kap + (int64_t)s * plane + off) : z4;
     int64_t z = za;
+OOC_PRAGMA(unroll OOC_WAVE_UNROLL)
     for (int i = 0; i < cnt; ++i, ++z) {
         const int s1 = wrap_add(s, 1, nslot), s5 = wrap_add(s, R + 1, nslot);
         const int64_t b1 = (int64_t)s1 * plane;
@@ -325,6 +483,27 @@ cudaError_t launch_heat7(ConstRing in, Ring out, int64_t nx, int64_t ny, int64_t
         return cudaErrorInvalidValue;
     heat7_kernel<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)gz), dim3(kTX, kHeatTY), 0, st>>>(
         in.base, out.base, (int)in.nslot, in.zbase, Grid3{nx, ny, nz, nx * ny}, z0, z1, chunk, r);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_heat7x2(ConstRing in, Ring out, int64_t nx, int64_t ny, int64_t nz, int64_t z0, int64_t z1,
+                           int64_t lo, int64_t hi, const float *band_in, int64_t bin_lo, float *band_out,
+                           int64_t bout_lo, float r, cudaStream_t st)
+{
+    if (z1 <= z0)
+        return cudaSuccess;
+    constexpr int TYO = kHeatX2TY;
+    static int res = 0;
+    if (res == 0)
+        res = resident((const void *)heat7x2_kernel<TYO>, kTX * (TYO + 2));
+    const int64_t gx = (nx + kSeg - 9) / (kSeg - 8), gy = (ny + TYO - 1) / TYO;
+    const int64_t chunk = choose_chunk(gx * gy, z1 - z0, 8, 5, res);
+    const int64_t gz = (z1 - z0 + chunk - 1) / chunk;
+    if (in.nslot != out.nslot || in.zbase != out.zbase || in.nslot > (1ll << 30) || in.base == out.base)
+        return cudaErrorInvalidValue;
+    heat7x2_kernel<TYO><<<dim3((unsigned)gx, (unsigned)gy, (unsigned)gz), dim3(kTX, TYO + 2), 0, st>>>(
+        in.base, out.base, (int)in.nslot, in.zbase, Grid3{nx, ny, nz, nx * ny}, z0, z1, chunk, lo, hi, band_in, bin_lo,
+        band_out, bout_lo, r);
     return cudaGetLastError();
 }
 

@@ -67,13 +67,17 @@ def incore_wave(ooc, p0, pm1, kappa, calls, k, fmt, rate, ro_fmt, ro_rate, src, 
 FMTS = [("fp32", 16), ("bf16", 16), ("fr4", 8), ("fr4", 16), ("fr4", 24)]
 
 
+@pytest.mark.parametrize("spl", [1, 2])
 @pytest.mark.parametrize("fmt,rate", FMTS)
 @pytest.mark.parametrize("T,k,calls", [(4, 1, [5]), (8, 2, [7]), (12, 3, [10]), (28, 2, [3, 4]), (64, 4, [9]),
                                        (32, 5, [11]), (8, 6, [13])])
-def test_heat7_ooc_bit_identical_to_incore(ooc, fmt, rate, T, k, calls):
+def test_heat7_ooc_bit_identical_to_incore(ooc, fmt, rate, T, k, calls, spl):
+    # spl = heat7 steps per launch (2: pairs fused, level s on chip); the
+    # in-core reference always runs one step per launch
     shape = (64, 24, 32)  # nz = 64: thin last slabs for T = 12, 28
     u0, _ = sine_modes_field(shape, seed=4)
-    plan = ooc.Plan(nx=32, ny=24, nz=64, stencil="heat7", k=k, rw_format=fmt, rw_rate=rate, slab_planes=T)
+    plan = ooc.Plan(nx=32, ny=24, nz=64, stencil="heat7", k=k, rw_format=fmt, rw_rate=rate, slab_planes=T,
+                    heat_steps_per_launch=spl)
     try:
         plan.set_field(0, u0)
         for n in calls:
@@ -86,6 +90,26 @@ def test_heat7_ooc_bit_identical_to_incore(ooc, fmt, rate, T, k, calls):
     assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
     assert st["steps_done"] == sum(calls)
     assert st["passes"] == len(pass_lengths(calls, k))
+
+
+@pytest.mark.parametrize("fmt,rate", [("fp32", 16), ("fr4", 16)])
+@pytest.mark.parametrize("T,k,calls", [(8, 2, [6]), (12, 4, [8, 3]), (16, 5, [10]), (4, 4, [4])])
+def test_heat7_fused_ooc_several_tiles(ooc, fmt, rate, T, k, calls):
+    # several 120-wide x tiles and 8-row y tiles with ragged tails, so the
+    # bands of the fused pairs cross tile edges
+    nz, ny, nx = 48, 36, 248
+    u0 = smooth_random_field((nz, ny, nx), 5.0, seed=8)
+    plan = ooc.Plan(nx=nx, ny=ny, nz=nz, stencil="heat7", k=k, rw_format=fmt, rw_rate=rate, slab_planes=T,
+                    heat_steps_per_launch=2)
+    try:
+        plan.set_field(0, u0)
+        for n in calls:
+            plan.step(n)
+        got = plan.get_field(0)
+    finally:
+        plan.close()
+    ref = incore_heat(ooc, u0, calls, k, fmt, rate)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
 
 
 def wave_inputs(shape, nsteps, seed=3):

@@ -43,6 +43,30 @@ def test_heat7_matches_fp64(ooc, shape, nsteps):
     assert m["max_abs"] < 2e-6 * max(1.0, np.abs(ref).max())
 
 
+@pytest.mark.parametrize("shape", [(36, 20, 44), (4, 4, 4), (8, 20, 244), (24, 36, 124), (40, 68, 256), (12, 8, 120)])
+@pytest.mark.parametrize("nsteps", [1, 2, 3, 6])
+def test_heat7_fused_pairs_bit_identical(ooc, shape, nsteps):
+    # Two steps per launch (level s on chip) against one step per launch:
+    # same arithmetic, so the bits agree.  The shapes span several 120-wide
+    # x tiles and 8-row y tiles with ragged tails, and nz down to one block.
+    u0 = smooth_random_field(shape, 6.0, seed=11)
+    a = torch.from_numpy(u0).cuda()
+    b = a.clone()
+    ooc.ooc_heat7_steps(a, torch.empty_like(a), nsteps)
+    ooc.ooc_heat7_steps_fused(b, torch.empty_like(b), nsteps)
+    torch.cuda.synchronize()
+    assert np.array_equal(a.cpu().numpy().view(np.uint32), b.cpu().numpy().view(np.uint32))
+
+
+def test_heat7_fused_matches_fp64(ooc):
+    u0, _ = sine_modes_field((64, 72, 136), seed=2)
+    d = torch.from_numpy(u0).cuda()
+    ooc.ooc_heat7_steps_fused(d, torch.empty_like(d), 8)
+    torch.cuda.synchronize()
+    m = oracle.error_metrics(d.cpu().numpy(), oracle.heat7_run(u0.astype(np.float64), 8))
+    assert m["rel_l2"] < HEAT_TOL, m
+
+
 def test_heat7_sine_mode_closed_form(ooc):
     shape, k = (64, 48, 80), (3, 2, 1)
     u0 = sine_mode(shape, k)

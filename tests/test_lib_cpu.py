@@ -57,6 +57,7 @@ def make_cfg(**kw):
     c.ro_rate = kw.get("ro_rate", 16)
     c.device_budget_bytes = kw.get("budget", 0)
     c.slab_planes = kw.get("slab_planes", 0)
+    c.heat_steps_per_launch = kw.get("spl", 0)
     return c
 
 
@@ -82,6 +83,21 @@ def test_plan_validation(L):
     assert plan_create(L, make_cfg(slab_planes=6))[0] == 1
     assert plan_create(L, make_cfg(rw_format=7, slab_planes=8))[0] == 1
     assert plan_create(L, make_cfg())[0] == 1  # neither a budget nor a slab thickness
+    assert plan_create(L, make_cfg(spl=3, slab_planes=8))[0] == 1
+    assert plan_create(L, make_cfg(spl=-1, slab_planes=8))[0] == 1
+    assert plan_create(L, make_cfg(spl=2, stencil=ooc.OOC_WAVE25, slab_planes=32, k=2))[0] == 1
+    assert plan_create(L, make_cfg(spl=1, stencil=ooc.OOC_WAVE25, slab_planes=32, k=2))[0] == 0
+
+
+def test_fused_pairs_reserve_bands(L):
+    # Fused heat7 pairs keep, per pair of the pass and slab parity, the 2h
+    # top planes of the intermediate level for the next slab.
+    plane = 64 * 64 * 4
+    for k in (1, 2, 4, 5):
+        s1, d1, _, _ = plan_create(L, make_cfg(k=k, slab_planes=16, spl=1))
+        s2, d2, _, _ = plan_create(L, make_cfg(k=k, slab_planes=16, spl=2))
+        assert s1 == 0 and s2 == 0
+        assert d2 - d1 == 2 * (k // 2) * 2 * plane
 
 
 def test_budget_derivation(L):
