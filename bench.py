@@ -302,13 +302,16 @@ def run_gpu(args, world, rank, local):
     # ---- end to end through the public API with host FP32 buffers ---------------
     plan = make_plan(ooc, *MAIN, profile=0)
     e2e_ms = []
-    host_out = np.empty((N, N, N), dtype=np.float32)
+    # the user's FP32 input and output live in pinned host memory
+    pinned_in = torch.from_numpy(u0).pin_memory()
+    pinned_out = torch.empty((N, N, N), dtype=torch.float32, pin_memory=True)
+    host_in, host_out = pinned_in.numpy(), pinned_out.numpy()
     for rep in range(1 + min(args.steps, 2)):
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(plan.streams[0])
-        plan.set_field(0, u0)
+        plan.set_field(0, host_in)
         plan.step(NSTEPS)
         plan.get_field(0, out=host_out)
         e1.record(plan.streams[2])
@@ -317,7 +320,7 @@ def run_gpu(args, world, rank, local):
             e2e_ms.append(e0.elapsed_time(e1))
     st_e2e = plan.stats()
     plan.close()
-    del plan
+    del plan, pinned_in, pinned_out
     torch.cuda.empty_cache()
     e2e_ms_max = max_over_ranks(world, statistics.mean(e2e_ms), dev)
     e2e_value = world * pts * NSTEPS / (e2e_ms_max / 1e3) / 1e9
@@ -383,7 +386,7 @@ def run_gpu(args, world, rank, local):
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "Gpts/s", "h2d_bytes_per_step": int(h2d_step),
                 "d2h_bytes_per_step": int(d2h_step),
-                "what": "ooc_set_field(host FP32) + ooc_step(64) + ooc_get_field(host FP32)"},
+                "what": "ooc_set_field(pinned host FP32) + ooc_step(64) + ooc_get_field(pinned host FP32)"},
         "gpu_launches": int(st["kernel_launches"]),
         "clocks": clk.summary(),
     }

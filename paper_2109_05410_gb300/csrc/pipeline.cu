@@ -459,17 +459,33 @@ ooc_status ooc_set_field(ooc_plan *p, int field, const float *host_src)
         std::memcpy(img, host_src, pb * nz);
         return OOC_OK;
     }
-    cudaStream_t st = p->st[1];
-    for (int64_t z0 = 0; z0 < nz; z0 += p->T) {
+    // Slab j lands in ring j&1 (H2D stream), is encoded into staging buffer
+    // j&1 (compute stream) and copied to the host image (D2H stream), so
+    // the three overlap across slabs; events guard the reuse of ring and
+    // staging buffer j&1 by slab j+2.
+    cudaStream_t sH = p->st[0], sC = p->st[1], sD = p->st[2];
+    int64_t j = 0;
+    for (int64_t z0 = 0; z0 < nz; z0 += p->T, ++j) {
         const int64_t z1 = z0 + p->T < nz ? z0 + p->T : nz;
         const int64_t zb = (p->Z - z0 % p->Z) % p->Z;  // plane z0 -> slot 0
-        OOC_CUDA(copy_ring(p, 0, zb, z0, z1, (char *)(host_src + (size_t)z0 * p->plane_elems), true, st));
-        char *stage = p->dev + p->off_in[0][field];
-        OOC_TRY(encode_from(p, field, cring(ring_view(p, 0, zb)), stage, z0, z1, st));
+        const int b = (int)(j & 1);
+        const int e = (int)(j % kEv), e2 = (int)((j + kEv - 2) % kEv);
+        if (j >= 2)
+            OOC_CUDA(cudaStreamWaitEvent(sH, p->ev_comp[e2], 0));
+        OOC_CUDA(copy_ring(p, b, zb, z0, z1, (char *)(host_src + (size_t)z0 * p->plane_elems), true, sH));
+        OOC_CUDA(cudaEventRecord(p->ev_h2d[e], sH));
+        OOC_CUDA(cudaStreamWaitEvent(sC, p->ev_h2d[e], 0));
+        if (j >= 2)
+            OOC_CUDA(cudaStreamWaitEvent(sC, p->ev_d2h[e2], 0));
+        char *stage = p->dev + p->off_in[b][field];
+        OOC_TRY(encode_from(p, field, cring(ring_view(p, b, zb)), stage, z0, z1, sC));
+        OOC_CUDA(cudaEventRecord(p->ev_comp[e], sC));
+        OOC_CUDA(cudaStreamWaitEvent(sD, p->ev_comp[e], 0));
         OOC_CUDA(cudaMemcpyAsync(img + (size_t)z0 * p->fplane[field], stage, (size_t)(z1 - z0) * p->fplane[field],
-                                 cudaMemcpyDeviceToHost, st));
-        OOC_CUDA(cudaStreamSynchronize(st));
+                                 cudaMemcpyDeviceToHost, sD));
+        OOC_CUDA(cudaEventRecord(p->ev_d2h[e], sD));
     }
+    OOC_TRY(wait_event(p, p->ev_d2h[(j - 1) % kEv]));
     return OOC_OK;
 }
 
@@ -484,17 +500,31 @@ ooc_status ooc_get_field(ooc_plan *p, int field, float *host_dst)
         std::memcpy(host_dst, img, pb * nz);
         return OOC_OK;
     }
-    cudaStream_t st = p->st[1];
-    for (int64_t z0 = 0; z0 < nz; z0 += p->T) {
+    // Mirror of ooc_set_field: H2D of slab j's storage into staging buffer
+    // j&1, decode into ring j&1, D2H of the FP32 planes, overlapped.
+    cudaStream_t sH = p->st[0], sC = p->st[1], sD = p->st[2];
+    int64_t j = 0;
+    for (int64_t z0 = 0; z0 < nz; z0 += p->T, ++j) {
         const int64_t z1 = z0 + p->T < nz ? z0 + p->T : nz;
         const int64_t zb = (p->Z - z0 % p->Z) % p->Z;
-        char *stage = p->dev + p->off_in[0][field];
+        const int b = (int)(j & 1);
+        const int e = (int)(j % kEv), e2 = (int)((j + kEv - 2) % kEv);
+        char *stage = p->dev + p->off_in[b][field];
+        if (j >= 2)
+            OOC_CUDA(cudaStreamWaitEvent(sH, p->ev_dec[e2], 0));
         OOC_CUDA(cudaMemcpyAsync(stage, img + (size_t)z0 * p->fplane[field], (size_t)(z1 - z0) * p->fplane[field],
-                                 cudaMemcpyHostToDevice, st));
-        OOC_TRY(decode_into(p, field, stage, ring_view(p, 0, zb), z0, z1, st));
-        OOC_CUDA(copy_ring(p, 0, zb, z0, z1, (char *)(host_dst + (size_t)z0 * p->plane_elems), false, st));
-        OOC_CUDA(cudaStreamSynchronize(st));
+                                 cudaMemcpyHostToDevice, sH));
+        OOC_CUDA(cudaEventRecord(p->ev_h2d[e], sH));
+        OOC_CUDA(cudaStreamWaitEvent(sC, p->ev_h2d[e], 0));
+        if (j >= 2)
+            OOC_CUDA(cudaStreamWaitEvent(sC, p->ev_d2h[e2], 0));
+        OOC_TRY(decode_into(p, field, stage, ring_view(p, b, zb), z0, z1, sC));
+        OOC_CUDA(cudaEventRecord(p->ev_dec[e], sC));
+        OOC_CUDA(cudaStreamWaitEvent(sD, p->ev_dec[e], 0));
+        OOC_CUDA(copy_ring(p, b, zb, z0, z1, (char *)(host_dst + (size_t)z0 * p->plane_elems), false, sD));
+        OOC_CUDA(cudaEventRecord(p->ev_d2h[e], sD));
     }
+    OOC_TRY(wait_event(p, p->ev_d2h[(j - 1) % kEv]));
     return OOC_OK;
 }
 

@@ -163,6 +163,28 @@ def test_set_get_field_roundtrip(ooc, fmt, rate):
     assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
 
 
+@pytest.mark.parametrize("fmt,rate", [("bf16", 16), ("fr4", 12)])
+def test_set_get_many_slabs_pinned_wave_fields(ooc, fmt, rate):
+    # 8 slabs with a ragged last one, so the overlapped set/get reuse each
+    # ring and staging buffer several times; pinned host buffers (fully
+    # asynchronous copies); the three wave fields must not disturb each other.
+    nz, ny, nx = 92, 12, 16
+    xs = [smooth_random_field((nz, ny, nx), 3.0 + f, seed=20 + f) for f in range(3)]
+    plan = ooc.Plan(nx=nx, ny=ny, nz=nz, stencil="wave25", k=1, rw_format=fmt, rw_rate=rate, ro_format=fmt,
+                    ro_rate=rate, slab_planes=12)
+    try:
+        for f in range(3):
+            src = torch.from_numpy(xs[f]).pin_memory()
+            plan.set_field(f, src.numpy())
+        for f in range(3):
+            dst = torch.empty((nz, ny, nx), dtype=torch.float32, pin_memory=True)
+            plan.get_field(f, out=dst.numpy())
+            ref = oracle.storage_roundtrip(xs[f], fmt, rate).astype(np.float32)
+            assert np.array_equal(dst.numpy().view(np.uint32), ref.view(np.uint32)), f
+    finally:
+        plan.close()
+
+
 def test_heat7_ooc_against_oracle_pipeline(ooc):
     # The configuration of the 128^3 heat case: 4 slabs of 32 planes, k = 2,
     # 8 steps, FR4 at 16 bits/value.
