@@ -541,6 +541,9 @@ ooc_status ooc_step(ooc_plan *p, int64_t nsteps)
     cudaStream_t sH = p->st[0], sC = p->st[1], sD = p->st[2];
     p->prof_used = 0;
     const int64_t npass = (nsteps + k - 1) / k;
+    bool direct = false;  // some field lands in its ring without staging
+    for (int f = 0; f < p->nfield; ++f)
+        direct |= !staged(p, f);
     int64_t g = 0;  // slab visits in this call
     for (int64_t pass = 0; pass < npass; ++pass) {
         const int64_t kp = (pass + 1) * k <= nsteps ? k : nsteps - pass * k;
@@ -551,11 +554,18 @@ ooc_status ooc_step(ooc_plan *p, int64_t nsteps)
             const SlabGeom sg = slab_geom(p, i, Wp);
             const int e = (int)(g % kEv);
             // ---- H2D: input units R_i and C_i (slab 0 also C_{-1}) -------------
-            int64_t need = g - 2;  // ring slots / staging of slab g-2 are free
+            // FP32 fields land in the rings, whose slots slab g-2's D2H may
+            // still read; staged fields land in staging buffer g&1, free
+            // once slab g-2's decode has run (ev_dec below).
+            int64_t need = direct ? g - 2 : -1;
             if (pass > 0) {
                 // the host units read here were written by slabs i, i+1 of the
-                // previous pass
-                const int64_t gp = g - p->nslab + (i + 1 < p->nslab ? 1 : 0);
+                // previous pass.  The event ring holds the last kEv slabs, so
+                // an older slab is covered by waiting for slab g-3 (the D2H
+                // stream runs in order).
+                int64_t gp = g - p->nslab + (i + 1 < p->nslab ? 1 : 0);
+                if (gp < g - 3)
+                    gp = g - 3;
                 if (gp > need)
                     need = gp;
             }
