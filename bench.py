@@ -45,8 +45,8 @@ COMPARE = [("fp32", 0), ("bf16", 0), ("fr4", 8), ("fr4", 12), ("fr4", 24)]
 # points; profiles/kernels_512cube_full.md).  Traffic is proportional to the
 # points a launch processes, so the bench scales it to its own launches.  It
 # is only valid for the stencil source it was measured on (sha256 prefix).
-HEAT7_TRAFFIC_PER_POINT = 7.81
-HEAT7_TRAFFIC_SRC_SHA = "4c3d04d28747aef7"
+HEAT7_TRAFFIC_PER_POINT = 7.82
+HEAT7_TRAFFIC_SRC_SHA = "448a2369da4f5f54"
 METRIC = "Gpts/s out-of-core (compressed vs uncompressed, same GB300) at stated L2 error; % roofline"
 WORKLOAD = "heat7 1024^3 FP32, device budget 1 GiB, k=4, 64 steps/bench step"
 

@@ -44,11 +44,12 @@ __global__ void __launch_bounds__(kTX *kTY, 2)
 {
     __shared__ float4 tile[2][kTY + 2 * kR][kTX];
     const int lane = threadIdx.x, ty = threadIdx.y;
-    const int64_t xs = (int64_t)blockIdx.x * kSeg;
+    const int64_t gx = (nx + kSeg - 1) / kSeg;  // x tiles; blockIdx.x = by * gx + bx
+    const int64_t xs = (int64_t)(blockIdx.x % gx) * kSeg;
     const int64_t x4 = xs + 4 * lane;
-    const int64_t y0 = (int64_t)blockIdx.y * kTY;
+    const int64_t y0 = (int64_t)(blockIdx.x / gx) * kTY;
     const int64_t y = y0 + ty;
-    const int64_t za = (int64_t)blockIdx.z * zchunk;
+    const int64_t za = (int64_t)blockIdx.y * zchunk;
     const int cnt = (int)(min(za + zchunk, nz) - za);
     const int64_t plane = nx * ny;
     const bool inside = x4 < nx && y < ny;
@@ -202,7 +203,9 @@ cudaError_t launch_aux(const float *a, const float *kap, const float *b, float *
         nchunk = nz / 16 > 0 ? nz / 16 : 1;
     const int64_t chunk = (nz + nchunk - 1) / nchunk;
     const int64_t gz = (nz + chunk - 1) / chunk;
-    wave25_aux_kernel<MODE><<<dim3((unsigned)gx, (unsigned)gy, (unsigned)gz), dim3(kTX, kTY), 0, st>>>(
+    if (gx * gy > 0x7fffffffll)
+        return cudaErrorInvalidValue;
+    wave25_aux_kernel<MODE><<<dim3((unsigned)(gx * gy), (unsigned)gz), dim3(kTX, kTY), 0, st>>>(
         a, kap, b, out, mu, g, nx, ny, nz, chunk);
     return cudaGetLastError();
 }

@@ -29,7 +29,7 @@ namespace ooc {
 namespace {
 
 constexpr int kTX = 32;  // threads per row segment (4 points each: 128 x)
-constexpr int kHeatTY = 8;
+constexpr int kHeatTY = 2;  // rows per CTA: small CTAs balance the waves of short windows
 constexpr int kWaveTY = 8;
 #define OOC_PRAGMA_(x) _Pragma(#x)
 #define OOC_PRAGMA(x) OOC_PRAGMA_(x)
@@ -94,11 +94,12 @@ __global__ void __launch_bounds__(kTX *kHeatTY)
 {
     __shared__ float4 tile[2][kHeatTY + 2][kTX];
     const int lane = threadIdx.x, ty = threadIdx.y;
-    const int64_t xs = (int64_t)blockIdx.x * kSeg;
+    const int64_t gx = (g.nx + kSeg - 1) / kSeg;  // x tiles; blockIdx.x = by * gx + bx
+    const int64_t xs = (int64_t)(blockIdx.x % gx) * kSeg;
     const int64_t x4 = xs + 4 * lane;
-    const int64_t y0 = (int64_t)blockIdx.y * kHeatTY;
+    const int64_t y0 = (int64_t)(blockIdx.x / gx) * kHeatTY;
     const int64_t y = y0 + ty;
-    const int64_t za = z0 + (int64_t)blockIdx.z * zchunk;
+    const int64_t za = z0 + (int64_t)blockIdx.y * zchunk;
     const int cnt = (int)(min(za + zchunk, z1) - za);
     const int64_t nz = g.nz, plane = g.plane;
     // loop-invariant in-grid flags and in-plane offsets
@@ -195,11 +196,12 @@ __global__ void __launch_bounds__(kTX *(TYO + 2))
     __shared__ float4 ta[2][TYO + 4][kTX];  // level s-1, rows y0-2 .. y0+TYO+1
     __shared__ float4 tb[2][TYO + 2][kTX];  // level s, rows y0-1 .. y0+TYO
     const int lane = threadIdx.x, w = threadIdx.y;
-    const int64_t xs = (int64_t)blockIdx.x * (kSeg - 8) - 4;
+    const int64_t gx = (g.nx + kSeg - 9) / (kSeg - 8);  // x tiles; blockIdx.x = by * gx + bx
+    const int64_t xs = (int64_t)(blockIdx.x % gx) * (kSeg - 8) - 4;
     const int64_t x4 = xs + 4 * lane;
-    const int64_t y0 = (int64_t)blockIdx.y * TYO;
+    const int64_t y0 = (int64_t)(blockIdx.x / gx) * TYO;
     const int64_t y = y0 - 1 + w;
-    const int64_t za = z0 + (int64_t)blockIdx.z * zchunk;
+    const int64_t za = z0 + (int64_t)blockIdx.y * zchunk;
     const int cnt = (int)(min(za + zchunk, z1) - za);
     const int64_t nz = g.nz, plane = g.plane;
     const bool xin = x4 >= 0 && x4 < g.nx;
@@ -306,11 +308,12 @@ __global__ void __launch_bounds__(kTX *kWaveTY, 2)
     constexpr int R = 4;
     __shared__ float4 tile[2][kWaveTY + 2 * R][kTX];
     const int lane = threadIdx.x, ty = threadIdx.y;
-    const int64_t xs = (int64_t)blockIdx.x * kSeg;
+    const int64_t gx = (g.nx + kSeg - 1) / kSeg;  // x tiles; blockIdx.x = by * gx + bx
+    const int64_t xs = (int64_t)(blockIdx.x % gx) * kSeg;
     const int64_t x4 = xs + 4 * lane;
-    const int64_t y0 = (int64_t)blockIdx.y * kWaveTY;
+    const int64_t y0 = (int64_t)(blockIdx.x / gx) * kWaveTY;
     const int64_t y = y0 + ty;
-    const int64_t za = z0 + (int64_t)blockIdx.z * zchunk;
+    const int64_t za = z0 + (int64_t)blockIdx.y * zchunk;
     const int cnt = (int)(min(za + zchunk, z1) - za);
     const int64_t nz = g.nz, plane = g.plane;
     const bool inside = x4 < g.nx && y < g.ny;
@@ -479,9 +482,9 @@ cudaError_t launch_heat7(ConstRing in, Ring out, int64_t nx, int64_t ny, int64_t
     const int64_t gx = (nx + kSeg - 1) / kSeg, gy = (ny + kHeatTY - 1) / kHeatTY;
     const int64_t chunk = choose_chunk(gx * gy, z1 - z0, 8, 3, res);
     const int64_t gz = (z1 - z0 + chunk - 1) / chunk;
-    if (in.nslot != out.nslot || in.zbase != out.zbase || in.nslot > (1ll << 30))
+    if (in.nslot != out.nslot || in.zbase != out.zbase || in.nslot > (1ll << 30) || gx * gy > 0x7fffffffll)
         return cudaErrorInvalidValue;
-    heat7_kernel<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)gz), dim3(kTX, kHeatTY), 0, st>>>(
+    heat7_kernel<<<dim3((unsigned)(gx * gy), (unsigned)gz), dim3(kTX, kHeatTY), 0, st>>>(
         in.base, out.base, (int)in.nslot, in.zbase, Grid3{nx, ny, nz, nx * ny}, z0, z1, chunk, r);
     return cudaGetLastError();
 }
@@ -499,9 +502,10 @@ cudaError_t launch_heat7x2(ConstRing in, Ring out, int64_t nx, int64_t ny, int64
     const int64_t gx = (nx + kSeg - 9) / (kSeg - 8), gy = (ny + TYO - 1) / TYO;
     const int64_t chunk = choose_chunk(gx * gy, z1 - z0, 8, 5, res);
     const int64_t gz = (z1 - z0 + chunk - 1) / chunk;
-    if (in.nslot != out.nslot || in.zbase != out.zbase || in.nslot > (1ll << 30) || in.base == out.base)
+    if (in.nslot != out.nslot || in.zbase != out.zbase || in.nslot > (1ll << 30) || in.base == out.base ||
+        gx * gy > 0x7fffffffll)
         return cudaErrorInvalidValue;
-    heat7x2_kernel<TYO><<<dim3((unsigned)gx, (unsigned)gy, (unsigned)gz), dim3(kTX, TYO + 2), 0, st>>>(
+    heat7x2_kernel<TYO><<<dim3((unsigned)(gx * gy), (unsigned)gz), dim3(kTX, TYO + 2), 0, st>>>(
         in.base, out.base, (int)in.nslot, in.zbase, Grid3{nx, ny, nz, nx * ny}, z0, z1, chunk, lo, hi, band_in, bin_lo,
         band_out, bout_lo, r);
     return cudaGetLastError();
@@ -520,9 +524,9 @@ cudaError_t launch_wave25_to(ConstRing p, ConstRing pprev, Ring pnew, ConstRing 
     const int64_t chunk = choose_chunk(gx * gy, z1 - z0, 16, 9, res);
     const int64_t gz = (z1 - z0 + chunk - 1) / chunk;
     if (p.nslot != pnew.nslot || p.zbase != pnew.zbase || p.nslot != kappa.nslot || p.zbase != kappa.zbase ||
-        p.nslot != pprev.nslot || p.zbase != pprev.zbase || p.nslot > (1ll << 30))
+        p.nslot != pprev.nslot || p.zbase != pprev.zbase || p.nslot > (1ll << 30) || gx * gy > 0x7fffffffll)
         return cudaErrorInvalidValue;
-    wave25_kernel<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)gz), dim3(kTX, kWaveTY), 0, st>>>(
+    wave25_kernel<<<dim3((unsigned)(gx * gy), (unsigned)gz), dim3(kTX, kWaveTY), 0, st>>>(
         p.base, pprev.base, pnew.base, kappa.base, (int)p.nslot, p.zbase, Grid3{nx, ny, nz, nx * ny}, z0, z1, chunk,
         sx, sy, sz, w);
     return cudaGetLastError();
