@@ -215,18 +215,23 @@ __device__ __forceinline__ uint32_t low_mask(int l)  // l in [0, 32]
 // The words past the block's 2R are zero (slack), so bits past the budget
 // read as 0, which is what a truncated stream means; only the implied-one
 // rule needs the budget.
+// Reads a block's words straight from the stream (through the L1 cache);
+// words past the block's nwords read as 0, so bits past the budget are 0.
 struct BitReader {
     const uint32_t *src;
     uint64_t buf;  // unread bits, least significant first
     int avail;     // valid bits in buf, >= 32
     int wnext;     // next word to load
     int pos;       // bits consumed
+    int nwords;    // words of the block
 
-    __device__ __forceinline__ void init(const uint32_t *s, int start)
+    __device__ __forceinline__ uint32_t word(int i) const { return i < nwords ? __ldg(src + i) : 0u; }
+    __device__ __forceinline__ void init(const uint32_t *s, int start, int n)
     {
         src = s;
+        nwords = n;
         const int w = start >> 5, sh = start & 31;
-        buf = ((uint64_t)s[w] | ((uint64_t)s[w + 1] << 32)) >> sh;
+        buf = ((uint64_t)word(w) | ((uint64_t)word(w + 1) << 32)) >> sh;
         avail = 64 - sh;
         wnext = w + 2;
         pos = start;
@@ -237,7 +242,7 @@ struct BitReader {
         avail -= len;
         pos += len;
         if (avail < 32) {
-            buf |= (uint64_t)src[wnext++] << avail;
+            buf |= (uint64_t)word(wnext++) << avail;
             avail += 32;
         }
     }
@@ -376,15 +381,16 @@ __device__ __forceinline__ void encode_block(uint32_t (&v)[64], int rate, uint32
 __device__ __forceinline__ void decode_block(const uint32_t *src, int rate, float (&out)[64], uint32_t *pm)
 {
     const int budget = 64 * rate;
-    if ((src[0] & 1u) == 0u) {
+    const uint32_t w0 = __ldg(src);
+    if ((w0 & 1u) == 0u) {
 #pragma unroll
         for (int i = 0; i < 64; ++i)
             out[i] = 0.0f;
         return;
     }
-    const int emax = (int)((src[0] >> 1) & 0xFFu) - 127;
+    const int emax = (int)((w0 >> 1) & 0xFFu) - 127;
     BitReader r;
-    r.init(src, 9);
+    r.init(src, 9, 2 * rate);
     int n = 0;
     int p = 31;
 #pragma unroll 1
@@ -531,34 +537,12 @@ __global__ void __launch_bounds__(kThreads) fr4_encode_kernel(ConstRing in, int6
 __global__ void __launch_bounds__(kThreads) fr4_decode_kernel(const uint32_t *__restrict__ in, int64_t nx, int64_t ny,
                                                              int64_t z0, int64_t nblk, int rate, Ring out)
 {
-    extern __shared__ uint32_t smem[];
-    const int words = 2 * rate, stride = words + kSlack + 1;
-    const int64_t first = (int64_t)blockIdx.x * kThreads;
-    const int64_t left = nblk - first;
-    const int nvalid = left < kThreads ? (int)left : kThreads;
-    const uint32_t *src = in + first * words;
-    {
-        int blk = threadIdx.x / words, wd = threadIdx.x - blk * words;
-        const int step_blk = kThreads / words, step_wd = kThreads - step_blk * words;
-        for (int o = threadIdx.x; o < nvalid * words; o += kThreads) {
-            smem[blk * stride + wd] = __ldg(src + o);
-            blk += step_blk;
-            wd += step_wd;
-            if (wd >= words) {
-                wd -= words;
-                ++blk;
-            }
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < kSlack; ++j)  // bits past the block read as 0
-        smem[threadIdx.x * stride + words + j] = 0u;
-    __syncthreads();
-    const int64_t b = first + threadIdx.x;
+    extern __shared__ uint32_t smem[];  // each thread's plane masks
+    const int64_t b = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (b >= nblk)
         return;
     float f[64];
-    decode_block(smem + threadIdx.x * stride, rate, f, smem + kThreads * stride + threadIdx.x * kPlaneStride);
+    decode_block(in + b * (2 * rate), rate, f, smem + threadIdx.x * kPlaneStride);
     const int64_t nbx = nx >> 2, nby = ny >> 2;
     const int64_t bx = b % nbx, t2 = b / nbx, by = t2 % nby, bz = t2 / nby;
     const int64_t slot = ring_slot(z0 + 4 * bz, out.zbase, out.nslot);
@@ -571,13 +555,15 @@ __global__ void __launch_bounds__(kThreads) fr4_decode_kernel(const uint32_t *__
                 make_float4(f[16 * k + 4 * j], f[16 * k + 4 * j + 1], f[16 * k + 4 * j + 2], f[16 * k + 4 * j + 3]);
 }
 
-// Shared memory per CTA: each thread's compressed words plus kSlack words
-// of slack (stride 2R + kSlack + 1, odd, so that the threads' slots start in
-// different banks), then each thread's 64 plane masks (stride 65).
+// Shared memory per CTA (encoder): each thread's compressed words plus
+// kSlack words of slack (stride 2R + kSlack + 1, odd, so that the threads'
+// slots start in different banks), then each thread's 64 plane masks
+// (stride 65) and plane offsets.  The decoder keeps only the plane masks.
 size_t smem_bytes(int rate, bool encoder)
 {
-    return ((size_t)kThreads * (2 * rate + kSlack + 1) +
-            (size_t)kThreads * (kPlaneStride + (encoder ? kMetaStride : 0))) *
+    if (!encoder)  // the decoder reads its words from the stream directly
+        return (size_t)kThreads * kPlaneStride * sizeof(uint32_t);
+    return ((size_t)kThreads * (2 * rate + kSlack + 1) + (size_t)kThreads * (kPlaneStride + kMetaStride)) *
            sizeof(uint32_t);
 }
 
