@@ -64,6 +64,9 @@ def lib():
                 "fr4_transform_inverse": (i32, [vp]),
                 "fr4_order": (None, [vp]),
                 "fr4_encode_planes": (i64, [vp, i64, vp]),
+                "fr4_encode_var": (i64, [vp, i64, i64, i64, i32, dbl, vp, i64, vp]),
+                "fr4_decode_var": (i32, [vp, vp, i64, i64, i64, i32, dbl, vp]),
+                "fr4_var_max_words_per_block": (i64, []),
                 "fr4_decode_planes": (i64, [vp, i64, vp]),
                 "oracle_heat7_step": (None, [vp, vp, i64, i64, i64, dbl]),
                 "oracle_heat7_run": (None, [vp, vp, i64, i64, i64, dbl, i64]),
@@ -98,12 +101,18 @@ def compressed_bytes(shape, rate):
     return int(lib().fr4_compressed_bytes(nx, ny, nz, rate))
 
 
+def _nblocks(shape):
+    nz, ny, nx = shape
+    return ((nx + 3) // 4) * ((ny + 3) // 4) * ((nz + 3) // 4)
+
+
 def fr4_encode(field, rate):
-    """Encode a float32 [nz, ny, nx] field (dims multiples of 4) at ``rate``
-    bits per value; returns uint32 words (2*rate per 4^3 block)."""
+    """Encode a float32 [nz, ny, nx] field at ``rate`` bits per value;
+    returns uint32 words (2*rate per 4^3 block; partial blocks at the far
+    faces are padded with the nearest value inside the field)."""
     f = np.ascontiguousarray(field, dtype=np.float32)
     nz, ny, nx = f.shape
-    out = np.zeros(nx * ny * nz * rate // 32, dtype=np.uint32)
+    out = np.zeros(_nblocks(f.shape) * 2 * rate, dtype=np.uint32)
     rc = lib().fr4_encode(_p(f), nx, ny, nz, rate, _p(out))
     if rc != 0:
         raise RuntimeError(f"fr4_encode failed ({rc})")
@@ -113,12 +122,44 @@ def fr4_encode(field, rate):
 def fr4_decode(words, shape, rate):
     w = np.ascontiguousarray(words, dtype=np.uint32)
     nz, ny, nx = shape
-    if w.size != nx * ny * nz * rate // 32:
+    if w.size != _nblocks(shape) * 2 * rate:
         raise ValueError("stream size does not match shape and rate")
     out = np.empty(shape, dtype=np.float32)
     rc = lib().fr4_decode(_p(w), nx, ny, nz, rate, _p(out))
     if rc < 0:
         raise RuntimeError(f"fr4_decode failed ({rc})")
+    return out
+
+
+MODE_PRECISION = 1
+MODE_ACCURACY = 2
+
+
+def fr4_encode_var(field, mode, param):
+    """Variable-size modes (fixed precision: ``param`` planes; fixed
+    accuracy: ``param`` = tolerance).  Returns (words, index) with block b in
+    words[index[b]:index[b+1]]."""
+    f = np.ascontiguousarray(field, dtype=np.float32)
+    nz, ny, nx = f.shape
+    nb = _nblocks(f.shape)
+    cap = nb * int(lib().fr4_var_max_words_per_block())
+    out = np.zeros(cap, dtype=np.uint32)
+    index = np.zeros(nb + 1, dtype=np.uint64)
+    n = lib().fr4_encode_var(_p(f), nx, ny, nz, mode, float(param), _p(out), cap, _p(index))
+    if n < 0:
+        raise RuntimeError("fr4_encode_var failed")
+    return out[:n].copy(), index
+
+
+def fr4_decode_var(words, index, shape, mode, param):
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    idx = np.ascontiguousarray(index, dtype=np.uint64)
+    nz, ny, nx = shape
+    if idx.size != _nblocks(shape) + 1 or int(idx[-1]) > w.size:
+        raise ValueError("index does not match shape or stream")
+    out = np.empty(shape, dtype=np.float32)
+    if lib().fr4_decode_var(_p(w), _p(idx), nx, ny, nz, mode, float(param), _p(out)) != 0:
+        raise RuntimeError("fr4_decode_var failed")
     return out
 
 

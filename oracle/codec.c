@@ -17,8 +17,8 @@
  * of Said and Pearlman's S+P transform), not ZFP's.  This file is the
  * definition that the GPU codec must match bit for bit.
  *
- * Stream layout: a field of nx*ny*nz values (all multiples of 4, x fastest)
- * is cut into 4^3 blocks ordered bx fastest, then by, then bz.  Each block
+ * Stream layout: a field of nx*ny*nz values (x fastest) is cut into 4^3
+ * blocks ordered bx fastest, then by, then bz.  Each block
  * takes exactly B = 64*R bits = 2*R 32-bit little-endian words.  Bit j of a
  * block is bit (j mod 32) of its word j/32; multi-bit fields are written
  * least-significant bit first.
@@ -52,6 +52,29 @@
  *     budget is spent, possibly mid-plane.  Unwritten bits stay 0.
  * Decoding mirrors every step; bits never received read as 0.  The value
  * is rebuilt as RN_float( RN_float(q) * 2^(emax - 26) ).
+ *
+ * Partial blocks.  A field whose sides are not multiples of 4 is cut into
+ * ceil(n/4) blocks per axis; a block reaching past the field takes, for
+ * each missing point, the value of the nearest point inside the field
+ * (each coordinate clamped to [0, n-1]).  Decoding writes only the points
+ * inside the field.
+ *
+ * Variable-size modes (codec variants beyond the paper's fixed rate; the
+ * paper names the comparison of other compressors as future work):
+ *  - fixed precision P (1..32): planes 31 .. 32-P are coded, with no bit
+ *    budget;
+ *  - fixed accuracy tol > 0: planes 31 .. pmin are coded, with
+ *    pmin = clamp(L - (emax - 26) - 4, 0, 32) and L = floor(log2 tol).  The
+ *    dropped planes carry less than (2/3) 2^pmin in negabinary, and the
+ *    inverse lifting amplifies a coefficient error by at most 2.25 per axis
+ *    (its largest row sum), 11.4 in 3D; 2^(pmin + emax - 26) <= tol/16 keeps
+ *    that part below tol/2.  Blocks whose pmin clamps to 0 are coded to
+ *    full precision.
+ * Each variable-size block starts on a 32-bit word and is padded with zero
+ * bits to a whole word; block b occupies words [index[b], index[b+1]) of
+ * the stream, index[0] = 0.  A block takes at most FR4_VAR_MAX_WORDS words:
+ * 9 header bits and at most 129 bits per plane (n refinement bits, at most
+ * 64 - n scan bits and 64 - n + 1 group bits).
  */
 #include <math.h>
 #include <stdint.h>
@@ -60,6 +83,10 @@
 
 #define FR4_PREC 26
 #define FR4_PLANES 32
+#define FR4_VAR_MAX_WORDS 130
+#define FR4_MODE_RATE 0
+#define FR4_MODE_PRECISION 1
+#define FR4_MODE_ACCURACY 2
 
 /* ---- bit stream with a hard budget ------------------------------------ */
 typedef struct {
@@ -214,10 +241,10 @@ static int32_t from_negabinary(uint32_t u)
 }
 
 /* ---- step 6: embedded bit-plane coding ----------------------------------- */
-static void encode_planes(bitstream *s, const uint32_t *u)
+static void encode_planes(bitstream *s, const uint32_t *u, int pmin)
 {
     int n = 0;
-    for (int p = FR4_PLANES - 1; p >= 0; p--) {
+    for (int p = FR4_PLANES - 1; p >= pmin; p--) {
         for (int i = 0; i < n; i++)
             if (!put_bit(s, u[i] >> p))
                 return;
@@ -245,11 +272,11 @@ static void encode_planes(bitstream *s, const uint32_t *u)
     }
 }
 
-static void decode_planes(bitstream *s, uint32_t *u)
+static void decode_planes(bitstream *s, uint32_t *u, int pmin)
 {
     int n = 0;
     unsigned b;
-    for (int p = FR4_PLANES - 1; p >= 0; p--) {
+    for (int p = FR4_PLANES - 1; p >= pmin; p--) {
         for (int i = 0; i < n; i++) {
             if (!get_bit(s, &b))
                 return;
@@ -278,11 +305,24 @@ static void decode_planes(bitstream *s, uint32_t *u)
 }
 
 /* ---- one block ------------------------------------------------------------ */
-/* Encode block x[64] into words[0 .. 2R-1] (zeroed here). */
-static void encode_block(const float *x, int rate, uint32_t *words)
+/* Lowest coded plane of a block with exponent emax (step 6's range). */
+static int plane_floor(int mode, double param, int emax)
 {
-    bitstream s = {words, 0, 64 * (int64_t)rate};
-    memset(words, 0, sizeof(uint32_t) * 2 * (size_t)rate);
+    if (mode == FR4_MODE_PRECISION)
+        return FR4_PLANES - (int)param;
+    if (mode == FR4_MODE_ACCURACY) {
+        int e;
+        frexp(param, &e); /* param = m 2^e, m in [0.5, 1): floor(log2) = e - 1 */
+        int pmin = (e - 1) - (emax - FR4_PREC) - 4;
+        return pmin < 0 ? 0 : (pmin > FR4_PLANES ? FR4_PLANES : pmin);
+    }
+    return 0;
+}
+
+/* Encode block x[64] into s (words zeroed by the caller): steps 1-6 with
+ * the plane range of `mode`.  Returns the bits written. */
+static int64_t encode_block_mode(const float *x, bitstream *s, int mode, double param)
+{
     int emax = INT32_MIN;
     for (int i = 0; i < 64; i++)
         if (x[i] != 0.0f) {
@@ -291,12 +331,12 @@ static void encode_block(const float *x, int rate, uint32_t *words)
                 emax = e;
         }
     if (emax == INT32_MIN) {
-        put_bit(&s, 0);
-        return;
+        put_bit(s, 0);
+        return s->pos;
     }
-    put_bit(&s, 1);
+    put_bit(s, 1);
     for (int j = 0; j < 8; j++)
-        put_bit(&s, (unsigned)(emax + 127) >> j);
+        put_bit(s, (unsigned)(emax + 127) >> j);
     int32_t q[64];
     for (int i = 0; i < 64; i++)
         q[i] = (int32_t)trunc(ldexp((double)x[i], FR4_PREC - emax));
@@ -304,14 +344,14 @@ static void encode_block(const float *x, int rate, uint32_t *words)
     uint32_t u[64];
     for (int r = 0; r < 64; r++)
         u[r] = to_negabinary(q[order_table[r]]);
-    encode_planes(&s, u);
+    encode_planes(s, u, plane_floor(mode, param, emax));
+    return s->pos;
 }
 
-static void decode_block(const uint32_t *words, int rate, float *x)
+static void decode_block_mode(bitstream *s, float *x, int mode, double param)
 {
-    bitstream s = {(uint32_t *)words, 0, 64 * (int64_t)rate};
-    unsigned b;
-    get_bit(&s, &b);
+    unsigned b = 0;
+    get_bit(s, &b);
     if (!b) {
         for (int i = 0; i < 64; i++)
             x[i] = 0.0f;
@@ -319,12 +359,13 @@ static void decode_block(const uint32_t *words, int rate, float *x)
     }
     int field = 0;
     for (int j = 0; j < 8; j++) {
-        get_bit(&s, &b);
+        b = 0;
+        get_bit(s, &b);
         field |= (int)b << j;
     }
     int emax = field - 127;
     uint32_t u[64] = {0};
-    decode_planes(&s, u);
+    decode_planes(s, u, plane_floor(mode, param, emax));
     int32_t q[64];
     for (int r = 0; r < 64; r++)
         q[order_table[r]] = from_negabinary(u[r]);
@@ -335,45 +376,73 @@ static void decode_block(const uint32_t *words, int rate, float *x)
     }
 }
 
+/* Fixed rate: block x[64] into words[0 .. 2R-1] (zeroed here). */
+static void encode_block(const float *x, int rate, uint32_t *words)
+{
+    bitstream s = {words, 0, 64 * (int64_t)rate};
+    memset(words, 0, sizeof(uint32_t) * 2 * (size_t)rate);
+    encode_block_mode(x, &s, FR4_MODE_RATE, 0.0);
+}
+
+static void decode_block(const uint32_t *words, int rate, float *x)
+{
+    bitstream s = {(uint32_t *)words, 0, 64 * (int64_t)rate};
+    decode_block_mode(&s, x, FR4_MODE_RATE, 0.0);
+}
+
 /* ---- exported API (ctypes) ----------------------------------------------- */
+static int64_t nblocks(int64_t n) { return (n + 3) / 4; }
+
 /* Returns the compressed byte count of an nx*ny*nz field at `rate`. */
 int64_t fr4_compressed_bytes(int64_t nx, int64_t ny, int64_t nz, int rate)
 {
-    return nx * ny * nz * (int64_t)rate / 8;
+    return nblocks(nx) * nblocks(ny) * nblocks(nz) * 8 * (int64_t)rate;
 }
 
-static void gather_block(const float *f, int64_t nx, int64_t ny, int64_t bx, int64_t by, int64_t bz, float *x)
+static int64_t clamp_index(int64_t i, int64_t n) { return i < n ? i : n - 1; }
+
+/* Block (bx, by, bz) of the field, missing points taken from the nearest
+ * point inside (partial blocks). */
+static void gather_block(const float *f, int64_t nx, int64_t ny, int64_t nz, int64_t bx, int64_t by, int64_t bz,
+                         float *x)
 {
     for (int k = 0; k < 4; k++)
         for (int j = 0; j < 4; j++)
-            for (int i = 0; i < 4; i++)
-                x[i + 4 * j + 16 * k] = f[((4 * bz + k) * ny + (4 * by + j)) * nx + 4 * bx + i];
+            for (int i = 0; i < 4; i++) {
+                int64_t z = clamp_index(4 * bz + k, nz), y = clamp_index(4 * by + j, ny);
+                int64_t xx = clamp_index(4 * bx + i, nx);
+                x[i + 4 * j + 16 * k] = f[(z * ny + y) * nx + xx];
+            }
 }
 
-static void scatter_block(float *f, int64_t nx, int64_t ny, int64_t bx, int64_t by, int64_t bz, const float *x)
+static void scatter_block(float *f, int64_t nx, int64_t ny, int64_t nz, int64_t bx, int64_t by, int64_t bz,
+                          const float *x)
 {
     for (int k = 0; k < 4; k++)
         for (int j = 0; j < 4; j++)
-            for (int i = 0; i < 4; i++)
-                f[((4 * bz + k) * ny + (4 * by + j)) * nx + 4 * bx + i] = x[i + 4 * j + 16 * k];
+            for (int i = 0; i < 4; i++) {
+                int64_t z = 4 * bz + k, y = 4 * by + j, xx = 4 * bx + i;
+                if (z < nz && y < ny && xx < nx)
+                    f[(z * ny + y) * nx + xx] = x[i + 4 * j + 16 * k];
+            }
 }
 
 /* Encode a dense field.  Returns 0, or -1 on bad arguments, or -2 if a
  * forward lifting value left int32 (which the range bound rules out). */
 int fr4_encode(const float *field, int64_t nx, int64_t ny, int64_t nz, int rate, uint32_t *out)
 {
-    if (nx <= 0 || ny <= 0 || nz <= 0 || nx % 4 || ny % 4 || nz % 4 || rate < 1 || rate > 64)
+    if (nx <= 0 || ny <= 0 || nz <= 0 || rate < 1 || rate > 64)
         return -1;
     if (!order_ready)
         build_order();
     fr4_forward_wrapped = 0;
-    int64_t nbx = nx / 4, nby = ny / 4, nbz = nz / 4;
+    int64_t nbx = nblocks(nx), nby = nblocks(ny), nbz = nblocks(nz);
     float x[64];
     for (int64_t bz = 0; bz < nbz; bz++)
         for (int64_t by = 0; by < nby; by++)
             for (int64_t bx = 0; bx < nbx; bx++) {
                 int64_t b = bx + nbx * (by + nby * bz);
-                gather_block(field, nx, ny, bx, by, bz, x);
+                gather_block(field, nx, ny, nz, bx, by, bz, x);
                 encode_block(x, rate, out + b * 2 * rate);
             }
     return fr4_forward_wrapped ? -2 : 0;
@@ -383,22 +452,87 @@ int fr4_encode(const float *field, int64_t nx, int64_t ny, int64_t nz, int rate,
  * inverse lifting wrapped (possible only for streams no input produces). */
 int fr4_decode(const uint32_t *in, int64_t nx, int64_t ny, int64_t nz, int rate, float *field)
 {
-    if (nx <= 0 || ny <= 0 || nz <= 0 || nx % 4 || ny % 4 || nz % 4 || rate < 1 || rate > 64)
+    if (nx <= 0 || ny <= 0 || nz <= 0 || rate < 1 || rate > 64)
         return -1;
     if (!order_ready)
         build_order();
     fr4_inverse_wrapped = 0;
-    int64_t nbx = nx / 4, nby = ny / 4, nbz = nz / 4;
+    int64_t nbx = nblocks(nx), nby = nblocks(ny), nbz = nblocks(nz);
     float x[64];
     for (int64_t bz = 0; bz < nbz; bz++)
         for (int64_t by = 0; by < nby; by++)
             for (int64_t bx = 0; bx < nbx; bx++) {
                 int64_t b = bx + nbx * (by + nby * bz);
                 decode_block(in + b * 2 * rate, rate, x);
-                scatter_block(field, nx, ny, bx, by, bz, x);
+                scatter_block(field, nx, ny, nz, bx, by, bz, x);
             }
     return fr4_inverse_wrapped ? 1 : 0;
 }
+
+static int var_mode_ok(int mode, double param)
+{
+    if (mode == FR4_MODE_PRECISION)
+        return param >= 1.0 && param <= 32.0 && param == floor(param);
+    if (mode == FR4_MODE_ACCURACY)
+        return param > 0.0 && isfinite(param);
+    return 0;
+}
+
+/* Variable-size modes: encode into out (capacity cap_words >= blocks *
+ * FR4_VAR_MAX_WORDS is always enough) and index[0 .. blocks].  Returns the
+ * total words, or -1 on bad arguments / too small a capacity. */
+int64_t fr4_encode_var(const float *field, int64_t nx, int64_t ny, int64_t nz, int mode, double param, uint32_t *out,
+                       int64_t cap_words, uint64_t *index)
+{
+    if (nx <= 0 || ny <= 0 || nz <= 0 || !var_mode_ok(mode, param))
+        return -1;
+    if (!order_ready)
+        build_order();
+    int64_t nbx = nblocks(nx), nby = nblocks(ny), nbz = nblocks(nz);
+    float x[64];
+    uint32_t words[FR4_VAR_MAX_WORDS];
+    int64_t at = 0;
+    for (int64_t bz = 0; bz < nbz; bz++)
+        for (int64_t by = 0; by < nby; by++)
+            for (int64_t bx = 0; bx < nbx; bx++) {
+                int64_t b = bx + nbx * (by + nby * bz);
+                gather_block(field, nx, ny, nz, bx, by, bz, x);
+                memset(words, 0, sizeof(words));
+                bitstream s = {words, 0, 32 * FR4_VAR_MAX_WORDS};
+                int64_t nw = (encode_block_mode(x, &s, mode, param) + 31) / 32;
+                if (at + nw > cap_words)
+                    return -1;
+                index[b] = (uint64_t)at;
+                memcpy(out + at, words, sizeof(uint32_t) * (size_t)nw);
+                at += nw;
+            }
+    index[nbx * nby * nbz] = (uint64_t)at;
+    return at;
+}
+
+/* Decode a variable-size stream with its index.  Returns 0 or -1. */
+int fr4_decode_var(const uint32_t *in, const uint64_t *index, int64_t nx, int64_t ny, int64_t nz, int mode,
+                   double param, float *field)
+{
+    if (nx <= 0 || ny <= 0 || nz <= 0 || !var_mode_ok(mode, param))
+        return -1;
+    if (!order_ready)
+        build_order();
+    int64_t nbx = nblocks(nx), nby = nblocks(ny), nbz = nblocks(nz);
+    float x[64];
+    for (int64_t bz = 0; bz < nbz; bz++)
+        for (int64_t by = 0; by < nby; by++)
+            for (int64_t bx = 0; bx < nbx; bx++) {
+                int64_t b = bx + nbx * (by + nby * bz);
+                int64_t nw = (int64_t)(index[b + 1] - index[b]);
+                bitstream s = {(uint32_t *)(in + index[b]), 0, 32 * nw};
+                decode_block_mode(&s, x, mode, param);
+                scatter_block(field, nx, ny, nz, bx, by, bz, x);
+            }
+    return 0;
+}
+
+int64_t fr4_var_max_words_per_block(void) { return FR4_VAR_MAX_WORDS; }
 
 /* Test hooks: the individual steps, exposed so that tests can pin each one. */
 void fr4_lift_forward4(int32_t *a) { lift_forward(a, 1); }
@@ -415,13 +549,13 @@ void fr4_order(int *out)
 int64_t fr4_encode_planes(const uint32_t *u, int64_t budget_bits, uint32_t *words)
 {
     bitstream s = {words, 0, budget_bits};
-    encode_planes(&s, u);
+    encode_planes(&s, u, 0);
     return s.pos;
 }
 int64_t fr4_decode_planes(const uint32_t *words, int64_t budget_bits, uint32_t *u)
 {
     bitstream s = {(uint32_t *)words, 0, budget_bits};
     memset(u, 0, 64 * sizeof(uint32_t));
-    decode_planes(&s, u);
+    decode_planes(&s, u, 0);
     return s.pos;
 }
