@@ -442,9 +442,36 @@ def run_kernels512(args, world, rank, local):
         if spl:
             res[name]["steps_per_launch"] = spl
             res[name]["Gpts_steps_per_s"] = pts * spl / (ms / 1e3) / 1e9
+    # codec variants: variable-size blocks (two encode passes with a prefix
+    # sum and a host read of the size in between; one decode pass)
+    var = {}
+    for name, mode, param in (("precision16", ooc.OOC_FR4_PRECISION, 16), ("accuracy1e-4", ooc.OOC_FR4_ACCURACY, 1e-4)):
+        stream, index = ooc.ooc_compress_var(d, mode, param)
+        times = {}
+        for what, fn in (("encode", lambda: ooc.ooc_compress_var(d, mode, param, d_out=stream_buf, d_index=index)),
+                         ("decode", lambda: ooc.ooc_decompress_var(stream, index, (n, n, n), mode, param, d_out=out))):
+            if what == "encode":
+                stream_buf = torch.empty(ooc.ooc_compress_var_bound(n, n, n), dtype=torch.uint8, device="cuda")
+            for _ in range(max(args.warmup, 1)):
+                fn()
+            e0, e1 = _cuda_events(torch)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(max(args.steps, 1)):
+                fn()
+            e1.record()
+            e1.synchronize()
+            times[what] = e0.elapsed_time(e1) / max(args.steps, 1)
+        bits = stream.numel() * 8 / pts
+        err = float((ooc.ooc_decompress_var(stream, index, (n, n, n), mode, param) - d).abs().max())
+        var[name] = {"bits_per_value": bits, "max_abs_err": err, "encode_ms": times["encode"],
+                     "decode_ms": times["decode"],
+                     "encode_GBs": (4 + bits / 8) * pts / (times["encode"] / 1e3) / 1e9,
+                     "decode_GBs": (4 + bits / 8) * pts / (times["decode"] / 1e3) / 1e9}
+        del stream, index, stream_buf
     if rank == 0:
-        print(json.dumps({"workload": "kernels512", "kernels": res, "n_gpus": world, "steps": args.steps,
-                          "warmup": args.warmup}), flush=True)
+        print(json.dumps({"workload": "kernels512", "kernels": res, "codec_variants": var, "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup}), flush=True)
     return 0
 
 

@@ -104,7 +104,9 @@ const char *ooc_status_string(ooc_status s);
 
 /* Bytes of an nx*ny*nz FP32 field stored by the fixed-rate codec at `rate`
  * bits per value (Section IV: R bits per value, a size fixed in advance):
- * nx*ny*nz*rate/8.  Returns 0 for invalid arguments. */
+ * ceil(nx/4)*ceil(ny/4)*ceil(nz/4) blocks of 8*rate bytes, i.e.
+ * nx*ny*nz*rate/8 when the sides are multiples of 4.  Returns 0 for invalid
+ * arguments. */
 size_t ooc_compressed_bytes(int64_t nx, int64_t ny, int64_t nz, int rate);
 
 /* Compress an FP32 device field d_in[nz][ny][nx] into d_out (device,
@@ -112,16 +114,59 @@ size_t ooc_compressed_bytes(int64_t nx, int64_t ny, int64_t nz, int rate);
  * asynchronously.  Rate 1..64 bits/value.  Inputs must be finite.  The
  * stream layout is 4^3 blocks, bx fastest, each exactly 2*rate 32-bit
  * words, so any 4-aligned z range is a contiguous byte range (Section V-A's
- * separately compressed units).  Returns OOC_E_INVALID on bad shapes, rates,
+ * separately compressed units).  Sides need not be multiples of 4: a block
+ * reaching past the field is padded with the value of the nearest point
+ * inside it.  d_in must be 16-byte aligned when nx is a multiple of 4, and
+ * 4-byte aligned otherwise.  Returns OOC_E_INVALID on bad shapes, rates,
  * alignment or out_cap < required; OOC_E_CUDA if the launch fails. */
 ooc_status ooc_compress(const float *d_in, int64_t nx, int64_t ny, int64_t nz, int rate,
                         void *d_out, size_t out_cap, void *stream);
 
 /* Inverse of ooc_compress: d_in holds in_bytes >= ooc_compressed_bytes(...)
- * bytes of codec stream (device); writes d_out[nz][ny][nx] (device).  Any
- * word content decodes without faulting. */
+ * bytes of codec stream (device); writes d_out[nz][ny][nx] (device, only
+ * the points inside the field).  Any word content decodes without
+ * faulting. */
 ooc_status ooc_decompress(const void *d_in, size_t in_bytes, int64_t nx, int64_t ny, int64_t nz,
                           int rate, float *d_out, void *stream);
+
+/* ---- Codec variants with variable-size blocks ------------------------------
+ * Not used by the paper, which needs a size known in advance (Section IV);
+ * it names comparing other compressors as future work.  The same block
+ * coder codes bit planes 31 .. pmin with no bit budget:
+ *   OOC_FR4_PRECISION, param = P in 1..32:  pmin = 32 - P;
+ *   OOC_FR4_ACCURACY,  param = tol > 0:     pmin = L - (emax - 26) - 4
+ *     clamped to [0, 32], L = floor(log2 tol), emax the block's exponent;
+ *     |x - x'| <= tol for every value unless pmin clamps to 0 (the block
+ *     is then kept to full precision).
+ * Block b occupies the 32-bit words [index[b], index[b+1]) of the stream
+ * (index[0] = 0, index[nblocks] = total words); a block is at most 130
+ * words.  Partial blocks as in ooc_compress. */
+#define OOC_FR4_RATE 0
+#define OOC_FR4_PRECISION 1
+#define OOC_FR4_ACCURACY 2
+
+/* Worst-case stream bytes (130 words per block) and the device scratch
+ * ooc_compress_var needs, for an nx*ny*nz field. */
+size_t ooc_compress_var_bound(int64_t nx, int64_t ny, int64_t nz);
+size_t ooc_var_scratch_bytes(int64_t nx, int64_t ny, int64_t nz);
+
+/* Compress d_in (device, 4-byte aligned) in a variable-size mode into d_out
+ * (device, out_cap bytes) and d_index (device, nblocks + 1 uint64).
+ * d_scratch: ooc_var_scratch_bytes(...) device bytes.  Runs on `stream`
+ * and returns when the size is known: *out_bytes (host) = 4 * total words.
+ * Two passes: block sizes, a prefix sum into d_index, then the blocks.  If
+ * the stream would exceed out_cap, returns OOC_E_INVALID after the first
+ * pass without writing d_out (d_index then holds the offsets). */
+ooc_status ooc_compress_var(const float *d_in, int64_t nx, int64_t ny, int64_t nz, int mode, double param,
+                            void *d_out, size_t out_cap, uint64_t *d_index, void *d_scratch,
+                            size_t scratch_bytes, size_t *out_bytes, void *stream);
+
+/* Decode a variable-size stream (in_bytes bytes at d_in, offsets d_index;
+ * device) into d_out[nz][ny][nx] (device), asynchronously on `stream`.
+ * Offsets are clamped to the stream and each block to 130 words, so any
+ * content decodes without faulting. */
+ooc_status ooc_decompress_var(const void *d_in, size_t in_bytes, const uint64_t *d_index, int64_t nx,
+                              int64_t ny, int64_t nz, int mode, double param, float *d_out, void *stream);
 
 /* BF16 storage: d_out[i] = bfloat16 of d_in[i], round to nearest even, NaN
  * kept quiet; and the exact widening back.  Device pointers, n values. */

@@ -19,7 +19,8 @@ from . import build as _build_mod
 __all__ = [
     "OOC_HEAT7", "OOC_WAVE25", "OOC_FMT_FP32", "OOC_FMT_BF16", "OOC_FMT_FR4",
     "OocConfig", "OocStats", "OocPlanInfo", "OocError", "lib", "build",
-    "ooc_status_string", "ooc_compressed_bytes", "ooc_compress", "ooc_decompress",
+    "ooc_status_string", "ooc_compressed_bytes", "ooc_compress", "ooc_decompress", "ooc_compress_var",
+    "ooc_decompress_var", "ooc_compress_var_bound", "ooc_var_scratch_bytes", "OOC_FR4_PRECISION", "OOC_FR4_ACCURACY",
     "ooc_bf16_pack", "ooc_bf16_unpack", "ooc_heat7_steps", "ooc_heat7_steps_fused", "ooc_heat7_steps_noalloc", "ooc_wave25_steps", "Plan",
     "ooc_gather", "ooc_scatter_add", "ooc_wave25_adjoint_step", "ooc_wave25_grad_accum", "ooc_kappa_from_velocity",
     "ooc_velocity_grad", "ooc_wave25_ckpt_bytes", "ooc_wave25_adjoint_work_bytes", "ooc_wave25_forward_ckpt",
@@ -82,6 +83,13 @@ _SIGS = {
                                                                               ctypes.c_size_t, ctypes.c_void_p]),
     "ooc_decompress": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t] + [ctypes.c_int64] * 3
                        + [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "ooc_compress_var_bound": (ctypes.c_size_t, [ctypes.c_int64] * 3),
+    "ooc_var_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int64] * 3),
+    "ooc_compress_var": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int64] * 3
+                         + [ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                            ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), ctypes.c_void_p]),
+    "ooc_decompress_var": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p] + [ctypes.c_int64] * 3
+                           + [ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
     "ooc_bf16_pack": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "ooc_bf16_unpack": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "ooc_heat7_steps": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p] + [ctypes.c_int64] * 3
@@ -190,6 +198,48 @@ def ooc_decompress(d_in, shape, rate, d_out=None, stream=None):
         d_out = torch.empty(shape, dtype=torch.float32, device=d_in.device)
     _check(lib().ooc_decompress(_ptr(d_in), d_in.numel() * d_in.element_size(), nx, ny, nz, rate, _ptr(d_out),
                                 _stream(stream)), "ooc_decompress")
+    return d_out
+
+
+OOC_FR4_PRECISION = 1
+OOC_FR4_ACCURACY = 2
+
+
+def ooc_compress_var_bound(nx, ny, nz):
+    return int(lib().ooc_compress_var_bound(nx, ny, nz))
+
+
+def ooc_var_scratch_bytes(nx, ny, nz):
+    return int(lib().ooc_var_scratch_bytes(nx, ny, nz))
+
+
+def ooc_compress_var(d_in, mode, param, d_out=None, d_index=None, stream=None):
+    """Variable-size modes (OOC_FR4_PRECISION: param = planes P;
+    OOC_FR4_ACCURACY: param = tolerance).  Returns (stream bytes as a uint8
+    CUDA tensor view of d_out, index as an int64 CUDA tensor of nblocks + 1
+    word offsets).  Synchronises ``stream`` to learn the size."""
+    import torch
+    nz, ny, nx = d_in.shape
+    nblk = ((nx + 3) // 4) * ((ny + 3) // 4) * ((nz + 3) // 4)
+    if d_out is None:
+        d_out = torch.empty(max(ooc_compress_var_bound(nx, ny, nz), 4), dtype=torch.uint8, device=d_in.device)
+    if d_index is None:
+        d_index = torch.empty(nblk + 1, dtype=torch.int64, device=d_in.device)
+    scratch = torch.empty(max(ooc_var_scratch_bytes(nx, ny, nz), 8), dtype=torch.uint8, device=d_in.device)
+    used = ctypes.c_size_t(0)
+    _check(lib().ooc_compress_var(_ptr(d_in), nx, ny, nz, int(mode), float(param), _ptr(d_out),
+                                  d_out.numel() * d_out.element_size(), _ptr(d_index), _ptr(scratch),
+                                  scratch.numel(), ctypes.byref(used), _stream(stream)), "ooc_compress_var")
+    return d_out[:used.value], d_index
+
+
+def ooc_decompress_var(d_in, d_index, shape, mode, param, d_out=None, stream=None):
+    import torch
+    nz, ny, nx = shape
+    if d_out is None:
+        d_out = torch.empty(shape, dtype=torch.float32, device=d_in.device)
+    _check(lib().ooc_decompress_var(_ptr(d_in), d_in.numel() * d_in.element_size(), _ptr(d_index), nx, ny, nz,
+                                    int(mode), float(param), _ptr(d_out), _stream(stream)), "ooc_decompress_var")
     return d_out
 
 

@@ -1,5 +1,7 @@
 // api.cu -- stand-alone entry points of the C ABI: codec, BF16, in-core
 // stencil runs and status strings.  See include/ooc.h for the contract.
+#include <cmath>
+
 #include "common.cuh"
 
 using namespace ooc;
@@ -61,29 +63,131 @@ const char *ooc_status_string(ooc_status s)
 
 size_t ooc_compressed_bytes(int64_t nx, int64_t ny, int64_t nz, int rate)
 {
-    if (!dims_ok(nx, ny, nz) || rate < 1 || rate > 64)
+    if (nx <= 0 || ny <= 0 || nz <= 0 || rate < 1 || rate > 64 || nx > (1ll << 40) || ny > (1ll << 40) ||
+        nz > (1ll << 40))
         return 0;
-    return (size_t)nx * (size_t)ny * (size_t)nz * (size_t)rate / 8;
+    return (size_t)fr4_blocks(nx, ny, nz) * 8 * (size_t)rate;
 }
 
 ooc_status ooc_compress(const float *d_in, int64_t nx, int64_t ny, int64_t nz, int rate, void *d_out, size_t out_cap,
                         void *stream)
 {
-    if (!d_in || !d_out || !dims_ok(nx, ny, nz) || rate < 1 || rate > 64 || !aligned(d_in, 16) ||
-        !aligned(d_out, 4) || out_cap < ooc_compressed_bytes(nx, ny, nz, rate))
+    const size_t need = ooc_compressed_bytes(nx, ny, nz, rate);
+    if (!d_in || !d_out || need == 0 || !aligned(d_out, 4) || out_cap < need)
         return OOC_E_INVALID;
-    return cuda_status(launch_fr4_encode(ConstRing{d_in, nz, 0}, nx, ny, 0, nz, rate, (uint32_t *)d_out,
-                                         (cudaStream_t)stream));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dims_ok(nx, ny, nz)) {  // whole blocks: 128-bit loads
+        if (!aligned(d_in, 16))
+            return OOC_E_INVALID;
+        return cuda_status(launch_fr4_encode(ConstRing{d_in, nz, 0}, nx, ny, 0, nz, rate, (uint32_t *)d_out, st));
+    }
+    if (!aligned(d_in, 4))
+        return OOC_E_INVALID;
+    return cuda_status(
+        launch_fr4_encode_dense(d_in, nx, ny, nz, 2 * rate, OOC_FR4_RATE, 0, 0, (uint32_t *)d_out, nullptr, st));
 }
 
 ooc_status ooc_decompress(const void *d_in, size_t in_bytes, int64_t nx, int64_t ny, int64_t nz, int rate,
                           float *d_out, void *stream)
 {
-    if (!d_in || !d_out || !dims_ok(nx, ny, nz) || rate < 1 || rate > 64 || !aligned(d_in, 4) ||
-        !aligned(d_out, 16) || in_bytes < ooc_compressed_bytes(nx, ny, nz, rate))
+    const size_t need = ooc_compressed_bytes(nx, ny, nz, rate);
+    if (!d_in || !d_out || need == 0 || !aligned(d_in, 4) || in_bytes < need)
         return OOC_E_INVALID;
-    return cuda_status(launch_fr4_decode((const uint32_t *)d_in, nx, ny, 0, nz, rate, Ring{d_out, nz, 0},
-                                         (cudaStream_t)stream));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dims_ok(nx, ny, nz)) {
+        if (!aligned(d_out, 16))
+            return OOC_E_INVALID;
+        return cuda_status(launch_fr4_decode((const uint32_t *)d_in, nx, ny, 0, nz, rate, Ring{d_out, nz, 0}, st));
+    }
+    if (!aligned(d_out, 4))
+        return OOC_E_INVALID;
+    return cuda_status(launch_fr4_decode_dense((const uint32_t *)d_in, (int64_t)(in_bytes / 4), nullptr, nx, ny, nz,
+                                               2 * rate, OOC_FR4_RATE, 0, d_out, st));
+}
+
+namespace {
+
+constexpr int64_t kVarBlockWords = 130;
+
+// Mode parameter for the kernels: P, or L = floor(log2 tol).  False if the
+// mode or its parameter is invalid.
+bool var_mparam(int mode, double param, int *mparam)
+{
+    if (mode == OOC_FR4_PRECISION) {
+        if (!(param >= 1.0 && param <= 32.0) || param != std::floor(param))
+            return false;
+        *mparam = (int)param;
+        return true;
+    }
+    if (mode == OOC_FR4_ACCURACY) {
+        if (!(param > 0.0) || !std::isfinite(param))
+            return false;
+        int e = 0;
+        std::frexp(param, &e);  // param = m 2^e, m in [0.5, 1)
+        *mparam = e - 1;
+        return true;
+    }
+    return false;
+}
+
+bool shape_ok(int64_t nx, int64_t ny, int64_t nz)
+{
+    return nx > 0 && ny > 0 && nz > 0 && nx <= (1ll << 40) && ny <= (1ll << 40) && nz <= (1ll << 40);
+}
+
+}  // namespace
+
+size_t ooc_compress_var_bound(int64_t nx, int64_t ny, int64_t nz)
+{
+    return shape_ok(nx, ny, nz) ? (size_t)fr4_blocks(nx, ny, nz) * kVarBlockWords * 4 : 0;
+}
+
+size_t ooc_var_scratch_bytes(int64_t nx, int64_t ny, int64_t nz)
+{
+    return shape_ok(nx, ny, nz) ? scan_scratch_bytes(fr4_blocks(nx, ny, nz)) : 0;
+}
+
+ooc_status ooc_compress_var(const float *d_in, int64_t nx, int64_t ny, int64_t nz, int mode, double param,
+                            void *d_out, size_t out_cap, uint64_t *d_index, void *d_scratch, size_t scratch_bytes,
+                            size_t *out_bytes, void *stream)
+{
+    int mparam = 0;
+    if (!d_in || !d_out || !d_index || !d_scratch || !out_bytes || !shape_ok(nx, ny, nz) ||
+        !var_mparam(mode, param, &mparam) || !aligned(d_in, 4) || !aligned(d_out, 4) || !aligned(d_index, 8) ||
+        !aligned(d_scratch, 8) || scratch_bytes < ooc_var_scratch_bytes(nx, ny, nz))
+        return OOC_E_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t nblk = fr4_blocks(nx, ny, nz);
+    *out_bytes = 0;
+    // pass 1: block sizes, then offsets
+    cudaError_t e = launch_fr4_encode_dense(d_in, nx, ny, nz, (int)kVarBlockWords, mode, mparam, 0, nullptr,
+                                            d_index, st);
+    if (e == cudaSuccess)
+        e = launch_exclusive_scan(d_index, nblk, (uint64_t *)d_scratch, st);
+    uint64_t total = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&total, d_index + nblk, sizeof(total), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess)
+        return OOC_E_CUDA;
+    *out_bytes = (size_t)total * 4;
+    if (*out_bytes > out_cap)
+        return OOC_E_INVALID;
+    // pass 2: the blocks at their offsets
+    return cuda_status(launch_fr4_encode_dense(d_in, nx, ny, nz, (int)kVarBlockWords, mode, mparam, 1,
+                                               (uint32_t *)d_out, d_index, st));
+}
+
+ooc_status ooc_decompress_var(const void *d_in, size_t in_bytes, const uint64_t *d_index, int64_t nx, int64_t ny,
+                              int64_t nz, int mode, double param, float *d_out, void *stream)
+{
+    int mparam = 0;
+    if (!d_in || !d_index || !d_out || !shape_ok(nx, ny, nz) || !var_mparam(mode, param, &mparam) ||
+        !aligned(d_in, 4) || !aligned(d_index, 8) || !aligned(d_out, 4))
+        return OOC_E_INVALID;
+    return cuda_status(launch_fr4_decode_dense((const uint32_t *)d_in, (int64_t)(in_bytes / 4), d_index, nx, ny, nz,
+                                               (int)kVarBlockWords, mode, mparam, d_out, (cudaStream_t)stream));
 }
 
 ooc_status ooc_bf16_pack(const float *d_in, uint16_t *d_out, int64_t n, void *stream)

@@ -269,23 +269,43 @@ __device__ __forceinline__ void or_bits(uint32_t *w, int off, uint64_t v)
 __device__ __forceinline__ void set_bit(uint32_t *w, int pos) { w[pos >> 5] |= 1u << (pos & 31); }
 
 // ---- one block ----------------------------------------------------------------
-__device__ __forceinline__ void encode_block(uint32_t (&v)[64], int rate, uint32_t *dst, uint32_t *pm,
-                                             uint32_t *meta)
+// Lowest coded bit plane: 0 at a fixed rate; 32 - P at fixed precision P;
+// at fixed accuracy with L = floor(log2 tol), L - (emax - 26) - 4 clamped to
+// [0, 32] (the dropped planes then cost at most tol/2 after the inverse
+// transform's gain of 2.25 per axis).
+__device__ __forceinline__ int plane_floor(int mode, int mparam, int emax)
 {
-    const int words = 2 * rate;
+    if (mode == OOC_FR4_PRECISION)
+        return 32 - mparam;
+    if (mode == OOC_FR4_ACCURACY) {
+        const int p = mparam - (emax - kPrec) - 4;
+        return p < 0 ? 0 : (p > 32 ? 32 : p);
+    }
+    return 0;
+}
+
+// Encode one block into dst[0 .. words) (a bit budget of 32 words; words =
+// 2R at a fixed rate) with the plane range of `mode`.  Returns the coded
+// length in bits (exact for the variable-size modes, whose budget never
+// binds).
+__device__ __forceinline__ int encode_block(uint32_t (&v)[64], int words, int mode, int mparam, uint32_t *dst,
+                                            uint32_t *pm, uint32_t *meta)
+{
     uint32_t mx = 0;
 #pragma unroll
     for (int i = 0; i < 64; ++i)
         mx = max(mx, v[i] & 0x7FFFFFFFu);
-    const int budget = 64 * rate;
-    // The coder ORs bit fields into a zeroed buffer of 2R words plus slack;
-    // bits it writes past the budget land in the slack and are not kept.
+    const int budget = 32 * words;
+    // The coder ORs bit fields into a zeroed buffer of `words` words plus
+    // slack; bits it writes past the budget land in the slack and are not
+    // kept.
     for (int i = 0; i < words + kSlack; ++i)
         dst[i] = 0u;
     if (mx == 0u)
-        return;
+        return 1;
     const int emax = (int)(mx >> 23) - 126;  // largest frexp exponent, >= -126
     dst[0] = 1u | ((uint32_t)((emax + 127) & 0xFF) << 1);
+    const int pmin = plane_floor(mode, mparam, emax);
 
     // q = trunc(x * 2^(26 - emax)), with the power of two split in two
     // normal factors; the first product is exact whenever the result can be
@@ -324,7 +344,7 @@ __device__ __forceinline__ void encode_block(uint32_t (&v)[64], int rate, uint32
     int off = 9, n = 0;
     uint32_t newmask = 0u;  // planes whose significance part has ones
 #pragma unroll 1
-    for (int p = 31; p >= 0 && off < budget; --p) {
+    for (int p = 31; p >= pmin && off < budget; --p) {
         const uint64_t X = ((uint64_t)pm[32 + p] << 32) | pm[p];
         if (n > 0)
             or_bits(dst, off, n >= 64 ? X : (X & ((1ull << n) - 1ull)));
@@ -376,12 +396,16 @@ __device__ __forceinline__ void encode_block(uint32_t (&v)[64], int rate, uint32
         prev_end = d;
         nnext = nq + t + 1;
     }
+    return off;
 }
 
-__device__ __forceinline__ void decode_block(const uint32_t *src, int rate, float (&out)[64], uint32_t *pm)
+// Decode one block of `nwords` words (2R at a fixed rate) with the plane
+// range of `mode`.
+__device__ __forceinline__ void decode_block(const uint32_t *src, int nwords, int mode, int mparam,
+                                             float (&out)[64], uint32_t *pm)
 {
-    const int budget = 64 * rate;
-    const uint32_t w0 = __ldg(src);
+    const int budget = 32 * nwords;
+    const uint32_t w0 = nwords > 0 ? __ldg(src) : 0u;
     if ((w0 & 1u) == 0u) {
 #pragma unroll
         for (int i = 0; i < 64; ++i)
@@ -389,12 +413,13 @@ __device__ __forceinline__ void decode_block(const uint32_t *src, int rate, floa
         return;
     }
     const int emax = (int)((w0 >> 1) & 0xFFu) - 127;
+    const int pmin = plane_floor(mode, mparam, emax);
     BitReader r;
-    r.init(src, 9, 2 * rate);
+    r.init(src, 9, nwords);
     int n = 0;
     int p = 31;
 #pragma unroll 1
-    for (; p >= 0 && r.pos < budget; --p) {
+    for (; p >= pmin && r.pos < budget; --p) {
         const int n1 = n < 32 ? n : 32;
         uint32_t xl = r.get(n1);
         uint32_t xh = r.get(n - n1);
@@ -461,7 +486,7 @@ __device__ __forceinline__ void decode_block(const uint32_t *src, int rate, floa
         pm[p] = xl;
         pm[32 + p] = xh;
     }
-    for (; p >= 0; --p) {  // planes past the budget
+    for (; p >= 0; --p) {  // planes past the budget or below the coded range
         pm[p] = 0u;
         pm[32 + p] = 0u;
     }
@@ -512,7 +537,8 @@ __global__ void __launch_bounds__(kThreads) fr4_encode_kernel(ConstRing in, int6
                 v[16 * k + 4 * j + 2] = __float_as_uint(f.z);
                 v[16 * k + 4 * j + 3] = __float_as_uint(f.w);
             }
-        encode_block(v, rate, smem + threadIdx.x * stride, smem + kThreads * stride + threadIdx.x * kPlaneStride,
+        encode_block(v, words, OOC_FR4_RATE, 0, smem + threadIdx.x * stride,
+                     smem + kThreads * stride + threadIdx.x * kPlaneStride,
                      smem + kThreads * (stride + kPlaneStride) + threadIdx.x * kMetaStride);
     }
     __syncthreads();
@@ -542,7 +568,7 @@ __global__ void __launch_bounds__(kThreads) fr4_decode_kernel(const uint32_t *__
     if (b >= nblk)
         return;
     float f[64];
-    decode_block(in + b * (2 * rate), rate, f, smem + threadIdx.x * kPlaneStride);
+    decode_block(in + b * (2 * rate), 2 * rate, OOC_FR4_RATE, 0, f, smem + threadIdx.x * kPlaneStride);
     const int64_t nbx = nx >> 2, nby = ny >> 2;
     const int64_t bx = b % nbx, t2 = b / nbx, by = t2 % nby, bz = t2 / nby;
     const int64_t slot = ring_slot(z0 + 4 * bz, out.zbase, out.nslot);
@@ -553,6 +579,218 @@ __global__ void __launch_bounds__(kThreads) fr4_decode_kernel(const uint32_t *__
         for (int j = 0; j < 4; ++j)
             *reinterpret_cast<float4 *>(p + ((int64_t)k * ny + j) * nx) =
                 make_float4(f[16 * k + 4 * j], f[16 * k + 4 * j + 1], f[16 * k + 4 * j + 2], f[16 * k + 4 * j + 3]);
+}
+
+// ---- dense fields of any shape, fixed rate and variable-size modes -------------
+constexpr int kVarWords = 130;  // largest variable-size block (9 + 32 * 129 bits)
+
+// Block (bx, by, bz) of a dense field; a block reaching past the field takes
+// the value of the nearest point inside it (each coordinate clamped).
+__device__ __forceinline__ void gather_clamped(const float *in, int64_t nx, int64_t ny, int64_t nz, int64_t bx,
+                                               int64_t by, int64_t bz, uint32_t (&v)[64])
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int64_t z = min(4 * bz + k, nz - 1);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float *row = in + (z * ny + min(4 * by + j, ny - 1)) * nx;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                v[16 * k + 4 * j + i] = __float_as_uint(__ldg(row + min(4 * bx + i, nx - 1)));
+        }
+    }
+}
+
+// Fixed rate (mode OOC_FR4_RATE): `words` words per block, the CTA's output
+// staged and written with coalesced stores.  Variable-size modes: phase 0
+// writes each block's word count to index[b]; phase 1 (index now holding
+// offsets) writes block b's words at out + index[b].
+__global__ void __launch_bounds__(kThreads)
+    fr4_encode_dense_kernel(const float *__restrict__ in, int64_t nx, int64_t ny, int64_t nz, int64_t nblk, int words,
+                            int mode, int mparam, int phase, uint32_t *__restrict__ out, uint64_t *__restrict__ index)
+{
+    extern __shared__ uint32_t smem[];
+    const int stride = words + kSlack + 1;
+    const int64_t first = (int64_t)blockIdx.x * kThreads;
+    const int64_t b = first + threadIdx.x;
+    uint32_t *mine = smem + threadIdx.x * stride;
+    int bits = 0;
+    if (b < nblk) {
+        const int64_t nbx = (nx + 3) >> 2, nby = (ny + 3) >> 2;
+        const int64_t bx = b % nbx, t2 = b / nbx, by = t2 % nby, bz = t2 / nby;
+        uint32_t v[64];
+        gather_clamped(in, nx, ny, nz, bx, by, bz, v);
+        bits = encode_block(v, words, mode, mparam, mine, smem + kThreads * stride + threadIdx.x * kPlaneStride,
+                            smem + kThreads * (stride + kPlaneStride) + threadIdx.x * kMetaStride);
+    }
+    if (mode != OOC_FR4_RATE) {  // uniform over the grid: no barrier on this path
+        if (b >= nblk)
+            return;
+        const int nw = (bits + 31) >> 5;
+        if (phase == 0) {
+            index[b] = (uint64_t)nw;
+            return;
+        }
+        uint32_t *dst = out + index[b];
+        for (int i = 0; i < nw; ++i)
+            dst[i] = mine[i];
+        return;
+    }
+    __syncthreads();
+    const int64_t left = nblk - first;
+    const int nvalid = left < kThreads ? (int)left : kThreads;
+    uint32_t *dst = out + first * words;
+    int blk = threadIdx.x / words, wd = threadIdx.x - blk * words;
+    const int step_blk = kThreads / words, step_wd = kThreads - step_blk * words;
+    for (int o = threadIdx.x; o < nvalid * words; o += kThreads) {
+        dst[o] = smem[blk * stride + wd];
+        blk += step_blk;
+        wd += step_wd;
+        if (wd >= words) {
+            wd -= words;
+            ++blk;
+        }
+    }
+}
+
+// Fixed rate: block b is words [b * words, (b + 1) * words).  Variable-size:
+// words [index[b], index[b + 1]), clamped to the stream and to kVarWords.
+// Only the points inside the field are written.
+__global__ void __launch_bounds__(kThreads)
+    fr4_decode_dense_kernel(const uint32_t *__restrict__ in, int64_t in_words, const uint64_t *__restrict__ index,
+                            int64_t nx, int64_t ny, int64_t nz, int64_t nblk, int words, int mode, int mparam,
+                            float *__restrict__ out)
+{
+    extern __shared__ uint32_t smem[];  // each thread's plane masks
+    const int64_t b = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (b >= nblk)
+        return;
+    const uint32_t *src;
+    int nw;
+    if (mode == OOC_FR4_RATE) {
+        src = in + b * words;
+        nw = words;
+    } else {
+        uint64_t lo = __ldg(index + b), hi = __ldg(index + b + 1);
+        lo = lo < (uint64_t)in_words ? lo : (uint64_t)in_words;
+        hi = hi < (uint64_t)in_words ? hi : (uint64_t)in_words;
+        const uint64_t n = hi > lo ? hi - lo : 0;
+        nw = (int)(n < (uint64_t)kVarWords ? n : (uint64_t)kVarWords);
+        src = in + lo;
+    }
+    float f[64];
+    decode_block(src, nw, mode, mparam, f, smem + threadIdx.x * kPlaneStride);
+    const int64_t nbx = (nx + 3) >> 2, nby = (ny + 3) >> 2;
+    const int64_t bx = b % nbx, t2 = b / nbx, by = t2 % nby, bz = t2 / nby;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int64_t z = 4 * bz + k, y = 4 * by + j, x = 4 * bx + i;
+                if (z < nz && y < ny && x < nx)
+                    out[(z * ny + y) * nx + x] = f[16 * k + 4 * j + i];
+            }
+}
+
+// ---- exclusive prefix sum of block sizes into offsets -----------------------------
+constexpr int kScan = 1024;
+
+// Exclusive scan of x over the CTA (1024 threads); *total gets the sum.
+__device__ __forceinline__ uint64_t cta_exclusive_scan(uint64_t x, uint64_t *warp_tot, uint64_t *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t s = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t t = __shfl_up_sync(0xffffffffu, s, d);
+        if (lane >= d)
+            s += t;
+    }
+    if (lane == 31)
+        warp_tot[warp] = s;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t w = warp_tot[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint64_t t = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d)
+                w += t;
+        }
+        warp_tot[lane] = w;
+    }
+    __syncthreads();
+    const uint64_t before = (warp > 0 ? warp_tot[warp - 1] : 0ull) + s - x;
+    *total = warp_tot[31];
+    __syncthreads();  // warp_tot is reused by the caller's next scan
+    return before;
+}
+
+// v[0..n) -> exclusive prefix within tiles of 1024; tile totals to sums.
+__global__ void __launch_bounds__(kScan) scan_tiles_kernel(uint64_t *v, int64_t n, uint64_t *sums)
+{
+    __shared__ uint64_t warp_tot[32];
+    const int64_t i = (int64_t)blockIdx.x * kScan + threadIdx.x;
+    const uint64_t x = i < n ? v[i] : 0ull;
+    uint64_t total;
+    const uint64_t before = cta_exclusive_scan(x, warp_tot, &total);
+    if (i < n)
+        v[i] = before;
+    if (threadIdx.x == 0)
+        sums[blockIdx.x] = total;
+}
+
+// sums[0..m) -> exclusive prefix (one CTA, chunks of 1024); sums[m] = total.
+__global__ void __launch_bounds__(kScan) scan_sums_kernel(uint64_t *sums, int64_t m)
+{
+    __shared__ uint64_t warp_tot[32];
+    uint64_t carry = 0;
+    for (int64_t base = 0; base < m; base += kScan) {
+        const int64_t i = base + threadIdx.x;
+        const uint64_t x = i < m ? sums[i] : 0ull;
+        uint64_t total;
+        const uint64_t before = cta_exclusive_scan(x, warp_tot, &total);
+        if (i < m)
+            sums[i] = carry + before;
+        carry += total;
+    }
+    if (threadIdx.x == 0)
+        sums[m] = carry;
+}
+
+__global__ void __launch_bounds__(kScan) add_tile_offsets_kernel(uint64_t *v, int64_t n, const uint64_t *sums,
+                                                                 int64_t m)
+{
+    const int64_t i = (int64_t)blockIdx.x * kScan + threadIdx.x;
+    if (i < n)
+        v[i] += sums[blockIdx.x];
+    if (i == 0)
+        v[n] = sums[m];
+}
+
+size_t dense_smem_bytes(int words, bool encoder)
+{
+    if (!encoder)
+        return (size_t)kThreads * kPlaneStride * sizeof(uint32_t);
+    return (size_t)kThreads * (words + kSlack + 1 + kPlaneStride + kMetaStride) * sizeof(uint32_t);
+}
+
+cudaError_t ensure_dense_smem_attr()
+{
+    static bool done = false;
+    if (done)
+        return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(fr4_encode_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)dense_smem_bytes(kVarWords, true));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fr4_decode_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)dense_smem_bytes(kVarWords, false));
+    if (e == cudaSuccess)
+        done = true;
+    return e;
 }
 
 // Shared memory per CTA (encoder): each thread's compressed words plus
@@ -609,6 +847,55 @@ cudaError_t launch_fr4_decode(const uint32_t *in, int64_t nx, int64_t ny, int64_
         return e;
     const int64_t grid = (nblk + kThreads - 1) / kThreads;
     fr4_decode_kernel<<<(unsigned)grid, kThreads, smem_bytes(rate, false), st>>>(in, nx, ny, z0, nblk, rate, out);
+    return cudaGetLastError();
+}
+
+
+int64_t fr4_blocks(int64_t nx, int64_t ny, int64_t nz) { return ((nx + 3) / 4) * ((ny + 3) / 4) * ((nz + 3) / 4); }
+
+cudaError_t launch_fr4_encode_dense(const float *in, int64_t nx, int64_t ny, int64_t nz, int words, int mode,
+                                    int mparam, int phase, uint32_t *out, uint64_t *index, cudaStream_t st)
+{
+    const int64_t nblk = fr4_blocks(nx, ny, nz);
+    if (nblk <= 0)
+        return cudaSuccess;
+    if (words < 1 || words > kVarWords)
+        return cudaErrorInvalidValue;
+    cudaError_t e = ensure_dense_smem_attr();
+    if (e != cudaSuccess)
+        return e;
+    const int64_t grid = (nblk + kThreads - 1) / kThreads;
+    fr4_encode_dense_kernel<<<(unsigned)grid, kThreads, dense_smem_bytes(words, true), st>>>(
+        in, nx, ny, nz, nblk, words, mode, mparam, phase, out, index);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fr4_decode_dense(const uint32_t *in, int64_t in_words, const uint64_t *index, int64_t nx,
+                                    int64_t ny, int64_t nz, int words, int mode, int mparam, float *out,
+                                    cudaStream_t st)
+{
+    const int64_t nblk = fr4_blocks(nx, ny, nz);
+    if (nblk <= 0)
+        return cudaSuccess;
+    cudaError_t e = ensure_dense_smem_attr();
+    if (e != cudaSuccess)
+        return e;
+    const int64_t grid = (nblk + kThreads - 1) / kThreads;
+    fr4_decode_dense_kernel<<<(unsigned)grid, kThreads, dense_smem_bytes(words, false), st>>>(
+        in, in_words, index, nx, ny, nz, nblk, words, mode, mparam, out);
+    return cudaGetLastError();
+}
+
+size_t scan_scratch_bytes(int64_t n) { return sizeof(uint64_t) * (size_t)((n + kScan - 1) / kScan + 1); }
+
+cudaError_t launch_exclusive_scan(uint64_t *v, int64_t n, uint64_t *scratch, cudaStream_t st)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    const int64_t m = (n + kScan - 1) / kScan;
+    scan_tiles_kernel<<<(unsigned)m, kScan, 0, st>>>(v, n, scratch);
+    scan_sums_kernel<<<1, kScan, 0, st>>>(scratch, m);
+    add_tile_offsets_kernel<<<(unsigned)m, kScan, 0, st>>>(v, n, scratch, m);
     return cudaGetLastError();
 }
 

@@ -116,5 +116,7 @@ def test_compress_argument_errors(ooc):
         ooc.ooc_compress(d, 16, d_out=out)  # capacity one word short
     with pytest.raises(ooc.OocError):
         ooc.ooc_compress(d, 0)
+    # whole-block shapes take 128-bit loads: the input must be 16-byte aligned
+    shifted = torch.zeros(8 * 8 * 8 + 1, device="cuda")[1:].view(8, 8, 8)
     with pytest.raises(ooc.OocError):
-        ooc.ooc_compress(torch.zeros((8, 8, 6), device="cuda"), 16)
+        ooc.ooc_compress(shifted, 16)

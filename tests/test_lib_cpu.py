@@ -41,7 +41,11 @@ def test_status_strings(L):
 def test_compressed_bytes(L):
     assert ooc.ooc_compressed_bytes(1024, 1024, 1024, 16) == 1024 ** 3 * 2
     assert ooc.ooc_compressed_bytes(8, 8, 8, 24) == 512 * 3
-    assert ooc.ooc_compressed_bytes(6, 8, 8, 16) == 0  # not a multiple of 4
+    assert ooc.ooc_compressed_bytes(6, 8, 8, 16) == 2 * 2 * 2 * 8 * 16  # partial blocks count whole
+    assert ooc.ooc_compressed_bytes(1, 1, 1, 8) == 64
+    assert ooc.ooc_compressed_bytes(0, 8, 8, 16) == 0
+    assert ooc.ooc_compress_var_bound(5, 5, 5) == 8 * 130 * 4
+    assert ooc.ooc_var_scratch_bytes(1024, 1024, 1024) == 8 * (16384 + 1)
     assert ooc.ooc_compressed_bytes(8, 8, 8, 65) == 0
 
 
