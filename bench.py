@@ -402,8 +402,8 @@ def _cuda_events(torch):
 def run_kernels512(args, world, rank, local):
     """Each kernel once per step on a 512^3 smooth field (the ncu capture case):
     FR4 encode and decode at R = 16, two in-core heat7 steps, two fused heat7
-    pairs (two steps per launch), two in-core wave25 steps; CUDA-event times
-    per kernel class."""
+    pairs (two steps per launch), two in-core wave25 steps, two FP64 heat7
+    steps; CUDA-event times per kernel class."""
     import torch
 
     import paper_2109_05410_gb300 as ooc
@@ -419,12 +419,15 @@ def run_kernels512(args, world, rank, local):
     tmp = torch.empty_like(d)
     kap = torch.full_like(d, 0.1)
     pp = torch.zeros_like(d)
+    d64 = d.double()
+    t64 = torch.empty_like(d64)
     ops = {
         "fr4_encode": (lambda: ooc.ooc_compress(d, 16, d_out=w), 1, (4 + 2) * pts, 0),
         "fr4_decode": (lambda: ooc.ooc_decompress(w, (n, n, n), 16, d_out=out), 1, (4 + 2) * pts, 0),
         "heat7": (lambda: ooc.ooc_heat7_steps(d, tmp, 2), 2, 8 * pts, 1),
         "heat7_fused_pair": (lambda: ooc.ooc_heat7_steps_fused(d, tmp, 4), 2, 8 * pts, 2),
         "wave25": (lambda: ooc.ooc_wave25_steps(d, pp, kap, 2), 2, 16 * pts, 1),
+        "heat7_f64": (lambda: ooc.ooc_heat7_steps_f64(d64, t64, 2), 2, 16 * pts, 1),
     }
     res = {}
     for name, (fn, nl, by, spl) in ops.items():

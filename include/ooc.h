@@ -185,6 +185,13 @@ ooc_status ooc_wave25_steps(float *d_p, float *d_pprev, const float *d_kappa, in
                             int64_t nz, int64_t sx, int64_t sy, int64_t sz, const float *h_w, int64_t t,
                             int64_t nsteps, void *stream);
 
+/* heat7 in double precision, as the paper's runs (Section VI): nsteps steps
+ * of d_u (device, FP64, result in place) with scratch d_tmp (device, same
+ * size, distinct).  nx, ny, nz multiples of 4, buffers 16-byte aligned.
+ * Same update and zero ghosts as ooc_heat7_steps, computed in FP64. */
+ooc_status ooc_heat7_steps_f64(double *d_u, double *d_tmp, int64_t nx, int64_t ny, int64_t nz, double r,
+                               int64_t nsteps, void *stream);
+
 /* The nsteps heat7 steps of ooc_heat7_steps with each pair of steps in one
  * kernel launch (temporal blocking inside the kernel, Section III: the
  * intermediate level stays in shared memory and registers, so HBM carries

@@ -21,7 +21,7 @@ __all__ = [
     "OocConfig", "OocStats", "OocPlanInfo", "OocError", "lib", "build",
     "ooc_status_string", "ooc_compressed_bytes", "ooc_compress", "ooc_decompress", "ooc_compress_var",
     "ooc_decompress_var", "ooc_compress_var_bound", "ooc_var_scratch_bytes", "OOC_FR4_PRECISION", "OOC_FR4_ACCURACY",
-    "ooc_bf16_pack", "ooc_bf16_unpack", "ooc_heat7_steps", "ooc_heat7_steps_fused", "ooc_heat7_steps_noalloc", "ooc_wave25_steps", "Plan",
+    "ooc_bf16_pack", "ooc_bf16_unpack", "ooc_heat7_steps", "ooc_heat7_steps_f64", "ooc_heat7_steps_fused", "ooc_heat7_steps_noalloc", "ooc_wave25_steps", "Plan",
     "ooc_gather", "ooc_scatter_add", "ooc_wave25_adjoint_step", "ooc_wave25_grad_accum", "ooc_kappa_from_velocity",
     "ooc_velocity_grad", "ooc_wave25_ckpt_bytes", "ooc_wave25_adjoint_work_bytes", "ooc_wave25_forward_ckpt",
     "ooc_wave25_backward_ckpt", "WaveFn", "wave_forward",
@@ -94,6 +94,8 @@ _SIGS = {
     "ooc_bf16_unpack": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "ooc_heat7_steps": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p] + [ctypes.c_int64] * 3
                         + [ctypes.c_double, ctypes.c_int64, ctypes.c_void_p]),
+    "ooc_heat7_steps_f64": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p] + [ctypes.c_int64] * 3
+                            + [ctypes.c_double, ctypes.c_int64, ctypes.c_void_p]),
     "ooc_heat7_steps_fused": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p] + [ctypes.c_int64] * 3
                               + [ctypes.c_double, ctypes.c_int64, ctypes.c_void_p]),
     "ooc_wave25_steps": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int64] * 6
@@ -263,6 +265,14 @@ def ooc_heat7_steps(d_u, d_tmp, nsteps, r=1.0 / 6.0, stream=None):
     nz, ny, nx = d_u.shape
     _check(lib().ooc_heat7_steps(_ptr(d_u), _ptr(d_tmp), nx, ny, nz, float(r), int(nsteps), _stream(stream)),
            "ooc_heat7_steps")
+    return d_u
+
+
+def ooc_heat7_steps_f64(d_u, d_tmp, nsteps, r=1.0 / 6.0, stream=None):
+    """heat7 in FP64 (float64 CUDA tensors [nz, ny, nx])."""
+    nz, ny, nx = d_u.shape
+    _check(lib().ooc_heat7_steps_f64(_ptr(d_u), _ptr(d_tmp), nx, ny, nz, float(r), int(nsteps), _stream(stream)),
+           "ooc_heat7_steps_f64")
     return d_u
 
 

@@ -230,6 +230,26 @@ ooc_status ooc_heat7_steps(float *d_u, float *d_tmp, int64_t nx, int64_t ny, int
     return OOC_OK;
 }
 
+ooc_status ooc_heat7_steps_f64(double *d_u, double *d_tmp, int64_t nx, int64_t ny, int64_t nz, double r,
+                               int64_t nsteps, void *stream)
+{
+    if (!d_u || !d_tmp || d_u == d_tmp || !dims_ok(nx, ny, nz) || nsteps < 0 || !aligned(d_u, 16) ||
+        !aligned(d_tmp, 16))
+        return OOC_E_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *a = d_u, *b = d_tmp;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        if (launch_heat7_f64(a, b, nx, ny, nz, r, st) != cudaSuccess)
+            return OOC_E_CUDA;
+        double *t = a;
+        a = b;
+        b = t;
+    }
+    if (a != d_u)
+        return cuda_status(cudaMemcpyAsync(d_u, a, sizeof(double) * nx * ny * nz, cudaMemcpyDeviceToDevice, st));
+    return OOC_OK;
+}
+
 ooc_status ooc_heat7_steps_fused(float *d_u, float *d_tmp, int64_t nx, int64_t ny, int64_t nz, double r,
                                  int64_t nsteps, void *stream)
 {

@@ -49,6 +49,9 @@ cudaError_t launch_heat7(ConstRing in, Ring out, int64_t nx, int64_t ny, int64_t
 cudaError_t launch_heat7x2(ConstRing in, Ring out, int64_t nx, int64_t ny, int64_t nz, int64_t z0, int64_t z1,
                            int64_t lo, int64_t hi, const float *band_in, int64_t bin_lo, float *band_out,
                            int64_t bout_lo, float r, cudaStream_t st);
+// FP64 heat7 step over a whole dense field (nx even, in != out).
+cudaError_t launch_heat7_f64(const double *in, double *out, int64_t nx, int64_t ny, int64_t nz, double r,
+                             cudaStream_t st);
 cudaError_t launch_wave25(ConstRing p, Ring pprev_out, ConstRing kappa, int64_t nx, int64_t ny, int64_t nz,
                           int64_t z0, int64_t z1, int64_t sx, int64_t sy, int64_t sz, float w, cudaStream_t st);
 // Same step with p_prev read from `pprev` and p' written to `pnew` (may alias).

@@ -67,6 +67,27 @@ def test_heat7_fused_matches_fp64(ooc):
     assert m["rel_l2"] < HEAT_TOL, m
 
 
+@pytest.mark.parametrize("shape,nsteps", [((64, 48, 80), 6), ((36, 20, 132), 5), ((4, 4, 4), 3)])
+def test_heat7_f64_matches_fp64_oracle(ooc, shape, nsteps):
+    # the same step in double precision: agreement to FP64 rounding
+    u0, _ = sine_modes_field(shape, seed=1)
+    d = torch.from_numpy(u0.astype(np.float64)).cuda()
+    ooc.ooc_heat7_steps_f64(d, torch.empty_like(d), nsteps)
+    ref = oracle.heat7_run(u0.astype(np.float64), nsteps)
+    got = d.cpu().numpy()
+    assert np.linalg.norm(got - ref) <= 1e-14 * np.linalg.norm(ref) * nsteps
+    assert np.abs(got - ref).max() <= 1e-14 * nsteps * max(1.0, np.abs(ref).max())
+
+
+def test_heat7_f64_sine_mode_closed_form(ooc):
+    shape, k = (64, 48, 80), (3, 2, 1)
+    u0 = sine_mode(shape, k).astype(np.float64)
+    lam = 1.0 - 2.0 / 6.0 * sum(1 - math.cos(math.pi * ka / (na + 1)) for ka, na in zip(k, (80, 48, 64)))
+    d = torch.from_numpy(u0).cuda()
+    ooc.ooc_heat7_steps_f64(d, torch.empty_like(d), 20)
+    assert np.abs(d.cpu().numpy() - lam ** 20 * u0).max() < 1e-13
+
+
 def test_heat7_sine_mode_closed_form(ooc):
     shape, k = (64, 48, 80), (3, 2, 1)
     u0 = sine_mode(shape, k)
