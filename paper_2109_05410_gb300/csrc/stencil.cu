@@ -40,7 +40,7 @@ constexpr int kWaveTY = 8;
 #define OOC_HEATX2_UNROLL 4
 #endif
 #ifndef OOC_WAVE_UNROLL
-#define OOC_WAVE_UNROLL 18
+#define OOC_WAVE_UNROLL 1
 #endif
 #ifndef OOC_HEATX2_TY
 #define OOC_HEATX2_TY 8
@@ -377,13 +377,45 @@ __device__ __forceinline__ float pick(const float (&l)[4], const float (&c)[4], 
     return idx < 0 ? l[idx + 4] : (idx < 4 ? c[idx] : rr[idx - 4]);
 }
 
+// cp.async (16-byte global -> shared copies that bypass the registers; a
+// source size of 0 fills zeros) and its group waits.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, bool valid)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// wave25 staging: p tiles of kWaveStages planes (8 own rows and 4 halo rows
+// on each side, plus the 4-point groups beyond each row end), and p_prev /
+// kappa rows of kWavePD + 1 planes.  Plane g's p tile travels with p_prev
+// and kappa of plane g - 4, in one copy group issued kWavePD + 4 planes
+// ahead of its use as the centre.
+constexpr int kWaveR = 4;
+constexpr int kWavePD = 2;                       // planes of copies in flight beyond the queue
+constexpr int kWaveStages = 2 * kWaveR - 3 + kWavePD;  // planes z .. z + 4 + kWavePD
+constexpr int kWaveKStages = kWavePD + 1;
+struct WaveSmem {
+    float4 p[kWaveStages][kWaveTY + 2 * kWaveR][kTX];
+    float4 xh[kWaveStages][kWaveTY][2];
+    float4 pp[kWaveKStages][kWaveTY][kTX];
+    float4 kk[kWaveKStages][kWaveTY][kTX];
+};
+
 __global__ void __launch_bounds__(kTX *kWaveTY, 2)
     wave25_kernel(const float *__restrict__ pin, const float *pprev, float *pout, const float *__restrict__ kap, int nslot,
                   int64_t zbase, Grid3 g, int64_t z0, int64_t z1, int64_t zchunk, int64_t sx, int64_t sy, int64_t sz,
                   float w)
 {
-    constexpr int R = 4;
-    __shared__ float4 tile[2][kWaveTY + 2 * R][kTX];
+    constexpr int R = kWaveR;
+    extern __shared__ __align__(16) unsigned char wave_smem[];
+    WaveSmem &sm = *reinterpret_cast<WaveSmem *>(wave_smem);
     const int lane = threadIdx.x, ty = threadIdx.y;
     const int64_t gx = (g.nx + kSeg - 1) / kSeg;  // x tiles; blockIdx.x = by * gx + bx
     const int64_t xs = (int64_t)(blockIdx.x % gx) * kSeg;
@@ -393,51 +425,65 @@ __global__ void __launch_bounds__(kTX *kWaveTY, 2)
     const int64_t za = z0 + (int64_t)blockIdx.y * zchunk;
     const int cnt = (int)(min(za + zchunk, z1) - za);
     const int64_t nz = g.nz, plane = g.plane;
-    const bool inside = x4 < g.nx && y < g.ny;
+    const bool xin = x4 < g.nx;
+    const bool inside = xin && y < g.ny;
     const int64_t off = inside ? y * g.nx + x4 : 0;
-    // warp ty loads one y-halo row: 4 above (ty < 4) or 4 below (ty >= 4)
-    const int hr = ty < R ? ty : kWaveTY + ty;  // tile row it fills
-    const int64_t yh = ty < R ? y0 - R + ty : y0 + kWaveTY + (ty - R);
-    const bool hrow = yh >= 0 && yh < g.ny && x4 < g.nx;
-    const int64_t hoff = hrow ? yh * g.nx + x4 : 0;
-    // lanes 0 and 31 load the 4-point group beyond the segment's ends
+    // copies of this thread: tile rows ty and ty + 8 (y0 - 4 + row), its own
+    // p_prev / kappa group, and (lanes 0, 31) the group beyond its row end
+    const int64_t ya = y0 - R + ty, yb = y0 - R + ty + kWaveTY;
+    const bool va = xin && ya >= 0 && ya < g.ny, vb = xin && yb >= 0 && yb < g.ny;
+    const int64_t offa = va ? ya * g.nx + x4 : 0, offb = vb ? yb * g.nx + x4 : 0;
     const int64_t xh = lane == 0 ? xs - 4 : xs + kSeg;
     const bool hcol = (lane == 0 || lane == kTX - 1) && xh >= 0 && xh < g.nx && y < g.ny;
     const int64_t xoff = hcol ? y * g.nx + xh : 0;
     const bool src_here = inside && y == sy && sx >= x4 && sx < x4 + 4;
     const float4 z4 = zero4();
 
+    // Copy group for plane gz = za + gi: its p tile from ring slot gslot, and
+    // p_prev / kappa of plane gz - 4 from slot kslot once that plane is in
+    // the chunk.  Both slots advance by one plane per group.
+    int gslot = (int)ring_slot(za, zbase, nslot), kslot = gslot;
+    auto issue = [&](int64_t gz, int gi) {
+        const bool vz = gz < nz;
+        const int st = gi % kWaveStages;
+        const float *pl = pin + (int64_t)gslot * plane;
+        cp_async16(&sm.p[st][ty][lane], vz && va ? pl + offa : pin, vz && va);
+        cp_async16(&sm.p[st][ty + kWaveTY][lane], vz && vb ? pl + offb : pin, vz && vb);
+        if (lane == 0 || lane == kTX - 1)
+            cp_async16(&sm.xh[st][ty][lane == 0 ? 0 : 1], vz && hcol ? pl + xoff : pin, vz && hcol);
+        gslot = wrap_add(gslot, 1, nslot);
+        if (gi >= R) {
+            const int ks = (gi - R) % kWaveKStages;
+            const int64_t kb = (int64_t)kslot * plane;
+            const bool vk = inside && gz - R < nz;
+            cp_async16(&sm.pp[ks][ty][lane], vk ? pprev + kb + off : pin, vk);
+            cp_async16(&sm.kk[ks][ty][lane], vk ? kap + kb + off : pin, vk);
+            kslot = wrap_add(kslot, 1, nslot);
+        }
+        cp_async_commit();
+    };
+
     int s = (int)ring_slot(za, zbase, nslot);  // slot of plane z
-    // q[j] = p at plane z - 4 + j of this thread's 4 points
+    // q[j] = p at plane z - 4 + j of this thread's 4 points; planes za - 4 ..
+    // za + 3 are read directly, later ones come from the staged tiles
     float4 q[2 * R + 1];
 #pragma unroll
-    for (int j = 0; j < 2 * R + 1; ++j) {
+    for (int j = 0; j < 2 * R; ++j) {
         const int64_t zj = za - R + j;
         const float *pj = pin + (int64_t)wrap_add(s, nslot - R + j >= nslot ? j - R : nslot - R + j, nslot) * plane;
         q[j] = (inside && zj >= 0 && zj < nz) ? ldg4(pj + off) : z4;
     }
-    const float *pc = pin + (int64_t)s * plane;
-    float4 hyv = (hrow && za < nz) ? ldg4(pc + hoff) : z4;
-    float4 hxv = (hcol && za < nz) ? ldg4(pc + xoff) : z4;
-    float4 ppv = inside ? *reinterpret_cast<const float4 *>(pprev + (int64_t)s * plane + off) : z4;
-    float4 kv = inside ? ldg4(kap + (int64_t)s * plane + off) : z4;
+    for (int gi = 0; gi < R + kWavePD; ++gi)
+        issue(za + gi, gi);
     int64_t z = za;
 OOC_PRAGMA(unroll OOC_WAVE_UNROLL)
     for (int i = 0; i < cnt; ++i, ++z) {
-        const int s1 = wrap_add(s, 1, nslot), s5 = wrap_add(s, R + 1, nslot);
-        const int64_t b1 = (int64_t)s1 * plane;
-        // prefetch for plane z + 1: p at z + 5 (queue head), halos, p_prev, kappa
-        const bool more = i + 1 < cnt;
-        const float4 pfv = (inside && z + R + 1 < nz) ? ldg4(pin + (int64_t)s5 * plane + off) : z4;
-        const float4 hyv_n = (more && hrow) ? ldg4(pin + b1 + hoff) : z4;
-        const float4 hxv_n = (more && hcol) ? ldg4(pin + b1 + xoff) : z4;
-        const float4 ppv_n = (more && inside) ? *reinterpret_cast<const float4 *>(pprev + b1 + off) : z4;
-        const float4 kv_n = (more && inside) ? ldg4(kap + b1 + off) : z4;
-
-        const int b = i & 1;
+        cp_async_wait<kWavePD - 1>();  // the group of plane z + 4 has landed
+        __syncthreads();               // ... for every thread; stage of z - 1 is free
+        issue(z + R + kWavePD, i + R + kWavePD);
+        const int st = i % kWaveStages, st4 = (i + R) % kWaveStages, ks = i % kWaveKStages;
+        q[2 * R] = sm.p[st4][ty + R][lane];
         const float4 c = q[R];
-        tile[b][ty + R][lane] = c;
-        tile[b][hr][lane] = hyv;
         float4 lf, rt;
         lf.x = __shfl_up_sync(0xffffffffu, c.x, 1);
         lf.y = __shfl_up_sync(0xffffffffu, c.y, 1);
@@ -448,10 +494,11 @@ OOC_PRAGMA(unroll OOC_WAVE_UNROLL)
         rt.z = __shfl_down_sync(0xffffffffu, c.z, 1);
         rt.w = __shfl_down_sync(0xffffffffu, c.w, 1);
         if (lane == 0)
-            lf = hxv;
+            lf = sm.xh[st][ty][0];
         if (lane == kTX - 1)
-            rt = hxv;
-        __syncthreads();
+            rt = sm.xh[st][ty][1];
+        const float4 ppv = sm.pp[ks][ty][lane];
+        const float4 kv = sm.kk[ks][ty][lane];
         const float L[4] = {lf.x, lf.y, lf.z, lf.w};
         const float C[4] = {c.x, c.y, c.z, c.w};
         const float Rt[4] = {rt.x, rt.y, rt.z, rt.w};
@@ -464,8 +511,8 @@ OOC_PRAGMA(unroll OOC_WAVE_UNROLL)
             lap[j] = (3.0f * kC0) * C[j];
 #pragma unroll
         for (int m = 1; m <= R; ++m) {
-            const float4 ym = tile[b][ty + R - m][lane];
-            const float4 yp = tile[b][ty + R + m][lane];
+            const float4 ym = sm.p[st][ty + R - m][lane];
+            const float4 yp = sm.p[st][ty + R + m][lane];
             const float YM[4] = {ym.x, ym.y, ym.z, ym.w};
             const float YP[4] = {yp.x, yp.y, yp.z, yp.w};
             const float ZM[4] = {q[R - m].x, q[R - m].y, q[R - m].z, q[R - m].w};
@@ -491,13 +538,9 @@ OOC_PRAGMA(unroll OOC_WAVE_UNROLL)
 #pragma unroll
         for (int j = 0; j < 2 * R; ++j)
             q[j] = q[j + 1];
-        q[2 * R] = pfv;
-        hyv = hyv_n;
-        hxv = hxv_n;
-        ppv = ppv_n;
-        kv = kv_n;
-        s = s1;
+        s = wrap_add(s, 1, nslot);
     }
+    cp_async_wait<0>();  // no copy may outlive the CTA's shared memory
 }
 
 // z-chunk so that the grid fills whole waves: pick the chunk count (1..8,
@@ -521,7 +564,7 @@ int64_t choose_chunk(int64_t ntiles, int64_t height, int64_t min_chunk, int64_t 
     return (height + best_n - 1) / best_n;
 }
 
-int resident(const void *fn, int threads)
+int resident(const void *fn, int threads, size_t dyn_smem = 0)
 {
     static int sms = 0;
     if (sms == 0) {
@@ -532,7 +575,7 @@ int resident(const void *fn, int threads)
             sms = 152;
     }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess || per_sm <= 0)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, dyn_smem) != cudaSuccess || per_sm <= 0)
         per_sm = 1;
     return per_sm * sms;
 }
@@ -611,15 +654,19 @@ cudaError_t launch_wave25_to(ConstRing p, ConstRing pprev, Ring pnew, ConstRing 
     if (z1 <= z0)
         return cudaSuccess;
     static int res = 0;
-    if (res == 0)
-        res = resident((const void *)wave25_kernel, kTX * kWaveTY);
+    if (res == 0) {
+        if (cudaFuncSetAttribute(wave25_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(WaveSmem)) !=
+            cudaSuccess)
+            return cudaErrorInvalidValue;
+        res = resident((const void *)wave25_kernel, kTX * kWaveTY, sizeof(WaveSmem));
+    }
     const int64_t gx = (nx + kSeg - 1) / kSeg, gy = (ny + kWaveTY - 1) / kWaveTY;
     const int64_t chunk = choose_chunk(gx * gy, z1 - z0, 16, 9, res);
     const int64_t gz = (z1 - z0 + chunk - 1) / chunk;
     if (p.nslot != pnew.nslot || p.zbase != pnew.zbase || p.nslot != kappa.nslot || p.zbase != kappa.zbase ||
         p.nslot != pprev.nslot || p.zbase != pprev.zbase || p.nslot > (1ll << 30) || gx * gy > 0x7fffffffll)
         return cudaErrorInvalidValue;
-    wave25_kernel<<<dim3((unsigned)(gx * gy), (unsigned)gz), dim3(kTX, kWaveTY), 0, st>>>(
+    wave25_kernel<<<dim3((unsigned)(gx * gy), (unsigned)gz), dim3(kTX, kWaveTY), sizeof(WaveSmem), st>>>(
         p.base, pprev.base, pnew.base, kappa.base, (int)p.nslot, p.zbase, Grid3{nx, ny, nz, nx * ny}, z0, z1, chunk,
         sx, sy, sz, w);
     return cudaGetLastError();
