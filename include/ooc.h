@@ -295,8 +295,15 @@ ooc_status ooc_set_source(ooc_plan *plan, int64_t sx, int64_t sy, int64_t sz, co
 
 /* Advance nsteps time steps: ceil(nsteps/k) passes of the slab pipeline
  * (the last pass may be shorter).  Returns after the last D2H has landed,
- * or OOC_E_TIMEOUT if that takes longer than wait_timeout_ms. */
+ * or OOC_E_TIMEOUT if that takes longer than wait_timeout_ms.  After a
+ * timeout the enqueued passes still run to completion on the plan's
+ * streams: synchronise those streams before touching the arenas.  The
+ * timed-out call is not counted in the plan's time or statistics. */
 ooc_status ooc_step(ooc_plan *plan, int64_t nsteps);
+
+/* Change the plan's host-wait deadline (ms; 0 = 600000).  The waits of
+ * ooc_step, ooc_set_field and ooc_get_field use it. */
+ooc_status ooc_plan_set_wait_timeout(ooc_plan *plan, int64_t wait_timeout_ms);
 
 ooc_status ooc_get_stats(const ooc_plan *plan, ooc_stats *stats);
 ooc_status ooc_reset_stats(ooc_plan *plan);

@@ -109,6 +109,7 @@ _SIGS = {
     "ooc_get_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "ooc_set_source": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int64] * 3 + [ctypes.c_void_p, ctypes.c_int64]),
     "ooc_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "ooc_plan_set_wait_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "ooc_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(OocStats)]),
     "ooc_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
     "ooc_plan_destroy": (None, [ctypes.c_void_p]),
@@ -471,6 +472,9 @@ class Plan:
 
     def step(self, nsteps):
         _check(lib().ooc_step(self._h, int(nsteps)), "ooc_step")
+
+    def set_wait_timeout(self, ms):
+        _check(lib().ooc_plan_set_wait_timeout(self._h, int(ms)), "ooc_plan_set_wait_timeout")
 
     def stats(self):
         s = OocStats()

@@ -717,6 +717,14 @@ ooc_status ooc_reset_stats(ooc_plan *p)
     return OOC_OK;
 }
 
+ooc_status ooc_plan_set_wait_timeout(ooc_plan *p, int64_t wait_timeout_ms)
+{
+    if (!p || wait_timeout_ms < 0)
+        return OOC_E_INVALID;
+    p->cfg.wait_timeout_ms = wait_timeout_ms;
+    return OOC_OK;
+}
+
 void ooc_plan_destroy(ooc_plan *p)
 {
     if (!p)

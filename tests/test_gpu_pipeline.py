@@ -245,3 +245,32 @@ def test_full_size_heat_benchmark_configuration(ooc):
     exact = oracle.heat7_run(sub, nsteps)[nsteps:-nsteps, nsteps:-nsteps, nsteps:-nsteps]
     m = oracle.error_metrics(got[c0:c1, c0:c1, c0:c1], exact)
     assert m["rel_l2"] < 1e-4, m
+
+
+def test_step_deadline_reports_timeout_and_work_completes(ooc):
+    # A host wait that runs past the plan's deadline returns OOC_E_TIMEOUT
+    # (status 5) without faulting anything: the enqueued passes still run,
+    # and after synchronising the plan gives the same field as a plan that
+    # waited normally.  64 steps of a 256^3 FR4-16 field take several
+    # milliseconds, far past a 1 ms deadline.
+    n = 256
+    u0 = smooth_random_field((n, n, n), 8.0, seed=12)
+    plan = ooc.Plan(nx=n, ny=n, nz=n, stencil="heat7", k=4, rw_format="fr4", rw_rate=16, slab_planes=32)
+    ref = ooc.Plan(nx=n, ny=n, nz=n, stencil="heat7", k=4, rw_format="fr4", rw_rate=16, slab_planes=32)
+    try:
+        plan.set_field(0, u0)
+        plan.set_wait_timeout(1)
+        with pytest.raises(ooc.OocError) as err:
+            plan.step(64)
+        assert err.value.status == 5
+        torch.cuda.synchronize()
+        plan.set_wait_timeout(0)
+        assert plan.stats()["steps_done"] == 0  # the timed-out call is not counted
+        got = plan.get_field(0)
+        ref.set_field(0, u0)
+        ref.step(64)
+        want = ref.get_field(0)
+    finally:
+        plan.close()
+        ref.close()
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
