@@ -221,9 +221,10 @@ struct BitReader {
     const uint32_t *src;
     uint64_t buf;  // unread bits, least significant first
     int avail;     // valid bits in buf, >= 32
-    int wnext;     // next word to load
+    int wnext;     // index of the word held in `pre`
     int pos;       // bits consumed
     int nwords;    // words of the block
+    uint32_t pre;  // word wnext, loaded one refill ahead so its latency hides
 
     __device__ __forceinline__ uint32_t word(int i) const { return i < nwords ? __ldg(src + i) : 0u; }
     __device__ __forceinline__ void init(const uint32_t *s, int start, int n)
@@ -235,6 +236,7 @@ struct BitReader {
         avail = 64 - sh;
         wnext = w + 2;
         pos = start;
+        pre = word(wnext);
     }
     __device__ __forceinline__ void skip(int len)  // len in [0, 32]
     {
@@ -242,8 +244,9 @@ struct BitReader {
         avail -= len;
         pos += len;
         if (avail < 32) {
-            buf |= (uint64_t)word(wnext++) << avail;
+            buf |= (uint64_t)pre << avail;
             avail += 32;
+            pre = word(++wnext);
         }
     }
     __device__ __forceinline__ uint32_t peek32() const { return (uint32_t)buf; }
