@@ -563,7 +563,9 @@ __global__ void __launch_bounds__(kThreads) fr4_encode_kernel(ConstRing in, int6
     }
 }
 
-__global__ void __launch_bounds__(kThreads) fr4_decode_kernel(const uint32_t *__restrict__ in, int64_t nx, int64_t ny,
+// 6 CTAs per SM (80 registers): measured faster than 5 CTAs at 96 registers
+// (R = 16 decode of 1024^3: 4.93 against 5.17 ms).
+__global__ void __launch_bounds__(kThreads, 6) fr4_decode_kernel(const uint32_t *__restrict__ in, int64_t nx, int64_t ny,
                                                              int64_t z0, int64_t nblk, int rate, Ring out)
 {
     extern __shared__ uint32_t smem[];  // each thread's plane masks
