@@ -29,7 +29,6 @@ constexpr int kPrec = 26;  // block-floating-point precision (bits)
 constexpr int kThreads = 128;
 constexpr int kPlaneStride = 65;  // words per thread for its plane masks
 constexpr int kSlack = 8;         // words past a block's 2R that a coder may touch
-constexpr int kMetaStride = 17;   // words per thread: 32 16-bit plane offsets (encoder)
 
 // ---- sequency order ---------------------------------------------------------
 // r-th coefficient of the coding order: sort by level sum of (i, j, k) with
@@ -292,7 +291,7 @@ __device__ __forceinline__ int plane_floor(int mode, int mparam, int emax)
 // length in bits (exact for the variable-size modes, whose budget never
 // binds).
 __device__ __forceinline__ int encode_block(uint32_t (&v)[64], int words, int mode, int mparam, uint32_t *dst,
-                                            uint32_t *pm, uint32_t *meta)
+                                            uint32_t *pm)
 {
     uint32_t mx = 0;
 #pragma unroll
@@ -363,7 +362,6 @@ __device__ __forceinline__ int encode_block(uint32_t (&v)[64], int words, int mo
         const int m = __popcll((long long)rest);
         const int tl = 63 - __clzll((long long)rest);  // offset of the last new one
         const int n_new = n + tl + 1;
-        reinterpret_cast<uint16_t *>(meta)[p] = (uint16_t)(off + n);
         newmask |= 1u << p;
         // n refinement bits, m group bits 1, tl + 1 scanned bits (the last
         // one implied when it is coefficient 63), a closing 0 if n_new < 64
@@ -373,8 +371,11 @@ __device__ __forceinline__ int encode_block(uint32_t (&v)[64], int words, int mo
     // Pass 2: significance ones.  Segment j (1-based) of a plane starts with
     // its group bit at base + t_{j-1} + j (t_0 = -1) and ends with its one at
     // base + t_j + j.  Planes are visited from the top, as in pass 1, so a
-    // plane's n is the previous visited plane's n plus its last offset + 1.
+    // plane's n is the previous visited plane's n plus its last offset + 1,
+    // and its offset follows in O(1): the planes skipped in between have no
+    // new ones and take n + 1 bits each (n < 64 while planes remain).
     int base = 0, nq = 0, nnext = 0, j = 0, prev_end = 0;
+    int off2 = 9, pprev = 32;  // start of the plane below the last visited one
     uint64_t rest = 0ull;
 #pragma unroll 1
     for (;;) {
@@ -383,9 +384,15 @@ __device__ __forceinline__ int encode_block(uint32_t (&v)[64], int words, int mo
                 break;
             const int pl = 31 - __clz((int)newmask);
             newmask ^= 1u << pl;
-            base = reinterpret_cast<const uint16_t *>(meta)[pl];
             nq = nnext;
+            off2 += (pprev - pl - 1) * (nq + 1);
+            base = off2 + nq;
             rest = (((uint64_t)pm[32 + pl] << 32) | pm[pl]) >> nq;
+            const int m = __popcll((long long)rest);
+            const int tl = 63 - __clzll((long long)rest);
+            const int nn = nq + tl + 1;
+            off2 += nq + m + tl + 1 - (nn == 64 ? 1 : 0) + (nn < 64 ? 1 : 0);
+            pprev = pl;
             j = 0;
             prev_end = base - 1;  // position of the previous segment's one
         }
@@ -541,8 +548,7 @@ __global__ void __launch_bounds__(kThreads) fr4_encode_kernel(ConstRing in, int6
                 v[16 * k + 4 * j + 3] = __float_as_uint(f.w);
             }
         encode_block(v, words, OOC_FR4_RATE, 0, smem + threadIdx.x * stride,
-                     smem + kThreads * stride + threadIdx.x * kPlaneStride,
-                     smem + kThreads * (stride + kPlaneStride) + threadIdx.x * kMetaStride);
+                     smem + kThreads * stride + threadIdx.x * kPlaneStride);
     }
     __syncthreads();
     const int64_t left = nblk - first;
@@ -626,8 +632,7 @@ __global__ void __launch_bounds__(kThreads)
         const int64_t bx = b % nbx, t2 = b / nbx, by = t2 % nby, bz = t2 / nby;
         uint32_t v[64];
         gather_clamped(in, nx, ny, nz, bx, by, bz, v);
-        bits = encode_block(v, words, mode, mparam, mine, smem + kThreads * stride + threadIdx.x * kPlaneStride,
-                            smem + kThreads * (stride + kPlaneStride) + threadIdx.x * kMetaStride);
+        bits = encode_block(v, words, mode, mparam, mine, smem + kThreads * stride + threadIdx.x * kPlaneStride);
     }
     if (mode != OOC_FR4_RATE) {  // uniform over the grid: no barrier on this path
         if (b >= nblk)
@@ -780,7 +785,7 @@ size_t dense_smem_bytes(int words, bool encoder)
 {
     if (!encoder)
         return (size_t)kThreads * kPlaneStride * sizeof(uint32_t);
-    return (size_t)kThreads * (words + kSlack + 1 + kPlaneStride + kMetaStride) * sizeof(uint32_t);
+    return (size_t)kThreads * (words + kSlack + 1 + kPlaneStride) * sizeof(uint32_t);
 }
 
 cudaError_t ensure_dense_smem_attr()
@@ -801,13 +806,12 @@ cudaError_t ensure_dense_smem_attr()
 // Shared memory per CTA (encoder): each thread's compressed words plus
 // kSlack words of slack (stride 2R + kSlack + 1, odd, so that the threads'
 // slots start in different banks), then each thread's 64 plane masks
-// (stride 65) and plane offsets.  The decoder keeps only the plane masks.
+// (stride 65).  The decoder keeps only the plane masks.
 size_t smem_bytes(int rate, bool encoder)
 {
     if (!encoder)  // the decoder reads its words from the stream directly
         return (size_t)kThreads * kPlaneStride * sizeof(uint32_t);
-    return ((size_t)kThreads * (2 * rate + kSlack + 1) + (size_t)kThreads * (kPlaneStride + kMetaStride)) *
-           sizeof(uint32_t);
+    return ((size_t)kThreads * (2 * rate + kSlack + 1) + (size_t)kThreads * kPlaneStride) * sizeof(uint32_t);
 }
 
 cudaError_t ensure_smem_attr()
