@@ -110,6 +110,7 @@ _SIGS = {
     "ooc_set_source": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int64] * 3 + [ctypes.c_void_p, ctypes.c_int64]),
     "ooc_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "ooc_plan_set_wait_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "ooc_plan_set_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "ooc_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(OocStats)]),
     "ooc_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
     "ooc_plan_destroy": (None, [ctypes.c_void_p]),
@@ -475,6 +476,9 @@ class Plan:
 
     def set_wait_timeout(self, ms):
         _check(lib().ooc_plan_set_wait_timeout(self._h, int(ms)), "ooc_plan_set_wait_timeout")
+
+    def set_profile(self, on):
+        _check(lib().ooc_plan_set_profile(self._h, 1 if on else 0), "ooc_plan_set_profile")
 
     def stats(self):
         s = OocStats()

@@ -725,6 +725,14 @@ ooc_status ooc_plan_set_wait_timeout(ooc_plan *p, int64_t wait_timeout_ms)
     return OOC_OK;
 }
 
+ooc_status ooc_plan_set_profile(ooc_plan *p, int profile)
+{
+    if (!p || (profile != 0 && profile != 1))
+        return OOC_E_INVALID;
+    p->cfg.profile = profile;
+    return OOC_OK;
+}
+
 void ooc_plan_destroy(ooc_plan *p)
 {
     if (!p)
