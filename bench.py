@@ -44,9 +44,10 @@ COMPARE = [("fp32", 0), ("bf16", 0), ("fr4", 8), ("fr4", 12), ("fr4", 24)]
 # 512^3 case (dram__bytes_read.sum + dram__bytes_write.sum over 134.2 M
 # points; profiles/kernels_512cube_full.md).  Traffic is proportional to the
 # points a launch processes, so the bench scales it to its own launches.  It
-# is only valid for the stencil source it was measured on (sha256 prefix).
+# is only valid for the stencil code it was measured on (sha256 prefix of the
+# source without comments).
 HEAT7_TRAFFIC_PER_POINT = 7.81
-HEAT7_TRAFFIC_SRC_SHA = "56d95f9a15193099"
+HEAT7_TRAFFIC_SRC_SHA = "a5bc7221708d0b10"
 METRIC = "Gpts/s out-of-core (compressed vs uncompressed, same GB300) at stated L2 error; % roofline"
 WORKLOAD = "heat7 1024^3 FP32, device budget 1 GiB, k=4, 64 steps/bench step"
 
@@ -56,10 +57,14 @@ def fmt_name(fmt, rate):
 
 
 def stencil_source_sha():
+    """sha256 prefix of stencil.cu with comments and blank lines removed, so
+    that the traffic measurement stays tied to the code, not its comments."""
     import hashlib
+    import re
     path = os.path.join(ROOT, "paper_2109_05410_gb300", "csrc", "stencil.cu")
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    with open(path) as f:
+        code = [re.sub(r"//.*$", "", line).rstrip() for line in f]
+    return hashlib.sha256("\n".join(l for l in code if l).encode()).hexdigest()[:16]
 
 
 def load_peaks():

@@ -15,9 +15,15 @@
 // along x).  The bit-plane stage turns the 64 negabinary words into 32
 // 64-bit plane masks with two in-register 32x32 bit transposes; each plane
 // is then written in O(1) chunks per newly significant coefficient
-// (find-first-set over the plane mask) instead of bit by bit.  The
-// compressed words of a CTA are staged in shared memory and written (or
-// read) with coalesced 32-bit accesses.
+// (find-first-set over the plane mask) instead of bit by bit.  The encoder
+// stages its CTA's compressed words in shared memory and writes them with
+// coalesced 32-bit stores; the decoder reads each block's words straight
+// from the stream through L1, one word ahead of their use.
+//
+// Also here: dense-field kernels for any shape (partial blocks padded with
+// the nearest inside value) and the variable-size fixed-precision and
+// fixed-accuracy modes, with a prefix sum that turns block sizes into
+// offsets.
 #include <utility>
 
 #include "common.cuh"

@@ -11,11 +11,14 @@
 //   - y-neighbours come from a shared-memory copy of the current plane
 //     (double buffered, one barrier per plane), whose halo rows are loaded by
 //     the edge warps;
-//   - z-neighbours live in a register queue; the next input plane and every
-//     halo value are prefetched one plane ahead so that a load is always in
-//     flight while the current plane is computed.
+//   - z-neighbours live in a register queue.  heat7 loads the planes two
+//     ahead of their use; wave25 stages each plane (tile, halos, p_prev,
+//     kappa) in shared memory with cp.async six planes ahead and fills its
+//     9-plane queue from there.
 // Each CTA marches a chunk of z; the chunk count is chosen from the
 // occupancy so that the grid fills whole waves of the 152 SMs.
+// Also here: heat7x2 (two heat7 steps per launch, the intermediate level on
+// chip) and an FP64 heat7 for whole fields.
 //
 // heat7 (Section III's neighbour average, 3D):
 //   u' = u + r (u[x-1] + u[x+1] + u[y-1] + u[y+1] + u[z-1] + u[z+1] - 6u)
