@@ -41,8 +41,8 @@ BUDGET = 1 << 30
 MAIN = ("fr4", 16)
 COMPARE = [("fp32", 0), ("bf16", 0), ("fr4", 8), ("fr4", 12), ("fr4", 24)]
 # DRAM traffic per point of one heat7 launch, from `ncu --set full` on the
-# 512^3 case (dram__bytes_read.sum + dram__bytes_write.sum over 134.2 M
-# points; profiles/kernels_512cube_full.md).  Traffic is proportional to the
+# 512^3 case of `--workload kernels512` (dram__bytes_read.sum +
+# dram__bytes_write.sum over 134.2 M points).  Traffic is proportional to the
 # points a launch processes, so the bench scales it to its own launches.  It
 # is only valid for the stencil code it was measured on (sha256 prefix of the
 # source without comments).
