@@ -430,7 +430,8 @@ def run_kernels512(args, world, rank, local):
     """Each kernel once per step on a 512^3 smooth field (the ncu capture case):
     FR4 encode and decode at R = 16, two in-core heat7 steps, two fused heat7
     pairs (two steps per launch), two in-core wave25 steps, two FP64 heat7
-    steps; CUDA-event times per kernel class."""
+    steps, BF16 pack and unpack, one adjoint step and one gradient update;
+    CUDA-event times per kernel class."""
     import torch
 
     import paper_2109_05410_gb300 as ooc
@@ -448,6 +449,7 @@ def run_kernels512(args, world, rank, local):
     pp = torch.zeros_like(d)
     d64 = d.double()
     t64 = torch.empty_like(d64)
+    b16 = torch.empty(d.shape, dtype=torch.int16, device="cuda")
     ops = {
         "fr4_encode": (lambda: ooc.ooc_compress(d, 16, d_out=w), 1, (4 + 2) * pts, 0),
         "fr4_decode": (lambda: ooc.ooc_decompress(w, (n, n, n), 16, d_out=out), 1, (4 + 2) * pts, 0),
@@ -455,6 +457,13 @@ def run_kernels512(args, world, rank, local):
         "heat7_fused_pair": (lambda: ooc.ooc_heat7_steps_fused(d, tmp, 4), 2, 8 * pts, 2),
         "wave25": (lambda: ooc.ooc_wave25_steps(d, pp, kap, 2), 2, 16 * pts, 1),
         "heat7_f64": (lambda: ooc.ooc_heat7_steps_f64(d64, t64, 2), 2, 16 * pts, 1),
+        "bf16_pack": (lambda: ooc.ooc_bf16_pack(d, d_out=b16), 1, 6 * pts, 0),
+        "bf16_unpack": (lambda: ooc.ooc_bf16_unpack(b16, d_out=out), 1, 6 * pts, 0),
+        # adjoint kernels: mu_prev <- 2 mu - mu_prev + L(kappa mu) (reads mu,
+        # kappa, mu_prev, writes 16 B per point); g += mu L(p) in FP64 (reads
+        # mu, p, g, writes g: 24 B per point)
+        "wave25_adjoint_step": (lambda: ooc.ooc_wave25_adjoint_step(d, pp, kap, d_out=out), 1, 16 * pts, 0),
+        "wave25_grad_accum": (lambda: ooc.ooc_wave25_grad_accum(t64, d, out), 1, 24 * pts, 0),
     }
     res = {}
     for name, (fn, nl, by, spl) in ops.items():

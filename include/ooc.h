@@ -169,7 +169,9 @@ ooc_status ooc_decompress_var(const void *d_in, size_t in_bytes, const uint64_t 
                               int64_t ny, int64_t nz, int mode, double param, float *d_out, void *stream);
 
 /* BF16 storage: d_out[i] = bfloat16 of d_in[i], round to nearest even, NaN
- * kept quiet; and the exact widening back.  Device pointers, n values. */
+ * kept quiet; and the exact widening back.  Device pointers, n values; the
+ * FP32 side 16-byte and the BF16 side 8-byte aligned (OOC_E_INVALID
+ * otherwise). */
 ooc_status ooc_bf16_pack(const float *d_in, uint16_t *d_out, int64_t n, void *stream);
 ooc_status ooc_bf16_unpack(const uint16_t *d_in, float *d_out, int64_t n, void *stream);
 
@@ -257,7 +259,10 @@ ooc_status ooc_wave25_forward_ckpt(const float *d_kappa, int64_t nx, int64_t ny,
                                    float *d_traces, int64_t every, int rate, void *h_ckpt, size_t ckpt_bytes,
                                    void *d_work, size_t work_bytes, void *const streams[2]);
 /* Backward run: d_grad = dJ/dkappa (FP64, device, overwritten) for the
- * residual d_res[nsteps][nrec], replaying each segment from its checkpoint. */
+ * residual d_res[nsteps][nrec], replaying each segment from its checkpoint.
+ * The adjoint state is carried as kappa * mu (the forward propagator's
+ * form) and the gradient divided by kappa at the end, so kappa must be
+ * positive everywhere (as (v dt/dx)^2 of a positive velocity is). */
 ooc_status ooc_wave25_backward_ckpt(const float *d_kappa, int64_t nx, int64_t ny, int64_t nz, int64_t sx, int64_t sy,
                                     int64_t sz, const float *h_w, int64_t nsteps, const int64_t *d_rec, int64_t nrec,
                                     const float *d_res, int64_t every, int rate, const void *h_ckpt,

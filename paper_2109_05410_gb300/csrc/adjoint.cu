@@ -15,6 +15,13 @@
 // FR4-compressed at `rate` bits/value (or FP32 with rate 0).  The backward
 // pass replays K steps from a checkpoint into a device history, so its
 // device footprint is K + 5 fields whatever the number of steps.
+//
+// The backward pass carries w = kappa mu instead of mu.  Multiplying the
+// adjoint recurrence by kappa gives
+//   w^m = 2 w^{m+1} - w^{m+2} + kappa L(w^{m+1}) + kappa S^T res[m-1],
+// the forward propagator's own form, so the adjoint step runs on the
+// forward wave25 kernel; and dJ/dkappa = (sum_n w^{n+1} L(p^n)) / kappa,
+// the sum accumulated in FP64 and divided once at the end (kappa > 0).
 #include <chrono>
 #include <cstring>
 #include <thread>
@@ -30,17 +37,13 @@ constexpr int kTX = 32, kTY = 8, kSeg = 4 * kTX, kR = 4;
 __device__ __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
 __device__ __forceinline__ float4 mul4(float4 a, float4 b) { return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w); }
 
-// In-core 25-point helper kernels on dense fields (plane z at z * nx * ny).
-// MODE 1 (adjoint step): out = 2 a - b + L(kappa * a); out may alias b.
-// MODE 2 (gradient):     g += (double) mu * (double) L(a).
-// The tiling follows the forward kernel: a warp owns 128 x-points, the
-// y-neighbours come from a shared-memory plane, the z-neighbours from a
-// register queue of the operand of L.
-template <int MODE>
+// Adjoint step in its mu form on dense fields (plane z at z * nx * ny):
+// out = 2 a - b + L(kappa * a); out may alias b.  The tiling follows the
+// forward kernel: a warp owns 128 x-points, the y-neighbours come from a
+// shared-memory plane, the z-neighbours from a register queue of kappa * a.
 __global__ void __launch_bounds__(kTX *kTY, 2)
-    wave25_aux_kernel(const float *__restrict__ a, const float *__restrict__ kap, const float *b, float *out,
-                      const float *__restrict__ mu, double *__restrict__ g, int64_t nx, int64_t ny, int64_t nz,
-                      int64_t zchunk)
+    wave25_adjoint_kernel(const float *__restrict__ a, const float *__restrict__ kap, const float *b, float *out,
+                          int64_t nx, int64_t ny, int64_t nz, int64_t zchunk)
 {
     __shared__ float4 tile[2][kTY + 2 * kR][kTX];
     const int lane = threadIdx.x, ty = threadIdx.y;
@@ -62,8 +65,8 @@ __global__ void __launch_bounds__(kTX *kTY, 2)
     const bool hcol = (lane == 0 || lane == kTX - 1) && xh >= 0 && xh < nx && y < ny;
     const int64_t xoff = hcol ? y * nx + xh : 0;
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    // operand of L at flat index i: a (MODE 2) or kappa * a (MODE 1)
-    auto opnd = [&](int64_t i) -> float4 { return MODE == 1 ? mul4(ldg4(a + i), ldg4(kap + i)) : ldg4(a + i); };
+    // operand of L at flat index i: kappa * a
+    auto opnd = [&](int64_t i) -> float4 { return mul4(ldg4(a + i), ldg4(kap + i)); };
 
     float4 q[2 * kR + 1];
 #pragma unroll
@@ -73,8 +76,8 @@ __global__ void __launch_bounds__(kTX *kTY, 2)
     }
     float4 hyv = hrow ? opnd(za * plane + hoff) : z4;
     float4 hxv = hcol ? opnd(za * plane + xoff) : z4;
-    float4 e1 = inside ? (MODE == 1 ? ldg4(a + za * plane + off) : ldg4(mu + za * plane + off)) : z4;
-    float4 e2 = (MODE == 1 && inside) ? *reinterpret_cast<const float4 *>(b + za * plane + off) : z4;
+    float4 e1 = inside ? ldg4(a + za * plane + off) : z4;
+    float4 e2 = inside ? *reinterpret_cast<const float4 *>(b + za * plane + off) : z4;
     int64_t z = za;
     for (int i = 0; i < cnt; ++i, ++z) {
         const bool more = i + 1 < cnt;
@@ -82,8 +85,8 @@ __global__ void __launch_bounds__(kTX *kTY, 2)
         const float4 pfv = (inside && z + kR + 1 < nz) ? opnd((z + kR + 1) * plane + off) : z4;
         const float4 hyv_n = (more && hrow) ? opnd(b1 + hoff) : z4;
         const float4 hxv_n = (more && hcol) ? opnd(b1 + xoff) : z4;
-        const float4 e1_n = (more && inside) ? (MODE == 1 ? ldg4(a + b1 + off) : ldg4(mu + b1 + off)) : z4;
-        const float4 e2_n = (MODE == 1 && more && inside) ? *reinterpret_cast<const float4 *>(b + b1 + off) : z4;
+        const float4 e1_n = (more && inside) ? ldg4(a + b1 + off) : z4;
+        const float4 e2_n = (more && inside) ? *reinterpret_cast<const float4 *>(b + b1 + off) : z4;
 
         const int bb = i & 1;
         const float4 c = q[kR];
@@ -121,24 +124,12 @@ __global__ void __launch_bounds__(kTX *kTY, 2)
                 lap[j] += cf[m - 1] * (((X[4 + j - m] + X[4 + j + m]) + (YM[j] + YP[j])) + (ZM[j] + ZP[j]));
         }
         if (inside) {
-            const int64_t idx = z * plane + off;
-            if (MODE == 1) {
-                const float A[4] = {e1.x, e1.y, e1.z, e1.w}, B[4] = {e2.x, e2.y, e2.z, e2.w};
-                float o[4];
+            const float A[4] = {e1.x, e1.y, e1.z, e1.w}, B[4] = {e2.x, e2.y, e2.z, e2.w};
+            float o[4];
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    o[j] = 2.0f * A[j] - B[j] + lap[j];
-                *reinterpret_cast<float4 *>(out + idx) = make_float4(o[0], o[1], o[2], o[3]);
-            } else {
-                double2 *gp = reinterpret_cast<double2 *>(g + idx);
-                double2 g0 = gp[0], g1 = gp[1];
-                g0.x += (double)e1.x * (double)lap[0];
-                g0.y += (double)e1.y * (double)lap[1];
-                g1.x += (double)e1.z * (double)lap[2];
-                g1.y += (double)e1.w * (double)lap[3];
-                gp[0] = g0;
-                gp[1] = g1;
-            }
+            for (int j = 0; j < 4; ++j)
+                o[j] = 2.0f * A[j] - B[j] + lap[j];
+            *reinterpret_cast<float4 *>(out + z * plane + off) = make_float4(o[0], o[1], o[2], o[3]);
         }
 #pragma unroll
         for (int j = 0; j < 2 * kR; ++j)
@@ -167,6 +158,23 @@ __global__ void scatter_add_kernel(float *f, const int64_t *__restrict__ idx, in
         f[idx[i]] += v[i];
 }
 
+// f[idx[i]] += v[i] * kap[idx[i]] (receiver residual injected into w = kappa mu).
+__global__ void scatter_add_scaled_kernel(float *f, const int64_t *__restrict__ idx, int64_t n,
+                                          const float *__restrict__ v, const float *__restrict__ kap)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const int64_t j = idx[i];
+        f[j] += v[i] * kap[j];
+    }
+}
+
+__global__ void divide_by_kappa_kernel(double *g, const float *__restrict__ kap, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        g[i] /= (double)kap[i];
+}
+
 __global__ void kappa_kernel(const float *__restrict__ v, float *__restrict__ kappa, int64_t n, float c)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -193,9 +201,8 @@ bool dims_ok(int64_t nx, int64_t ny, int64_t nz)
     return nx > 0 && ny > 0 && nz > 0 && nx % 4 == 0 && ny % 4 == 0 && nz % 4 == 0;
 }
 
-template <int MODE>
-cudaError_t launch_aux(const float *a, const float *kap, const float *b, float *out, const float *mu, double *g,
-                       int64_t nx, int64_t ny, int64_t nz, cudaStream_t st)
+cudaError_t launch_adjoint_step(const float *a, const float *kap, const float *b, float *out, int64_t nx, int64_t ny,
+                                int64_t nz, cudaStream_t st)
 {
     const int64_t gx = (nx + kSeg - 1) / kSeg, gy = (ny + kTY - 1) / kTY;
     int64_t nchunk = (152 * 4 + gx * gy - 1) / (gx * gy);
@@ -205,8 +212,8 @@ cudaError_t launch_aux(const float *a, const float *kap, const float *b, float *
     const int64_t gz = (nz + chunk - 1) / chunk;
     if (gx * gy > 0x7fffffffll)
         return cudaErrorInvalidValue;
-    wave25_aux_kernel<MODE><<<dim3((unsigned)(gx * gy), (unsigned)gz), dim3(kTX, kTY), 0, st>>>(
-        a, kap, b, out, mu, g, nx, ny, nz, chunk);
+    wave25_adjoint_kernel<<<dim3((unsigned)(gx * gy), (unsigned)gz), dim3(kTX, kTY), 0, st>>>(a, kap, b, out, nx, ny,
+                                                                                              nz, chunk);
     return cudaGetLastError();
 }
 
@@ -310,8 +317,7 @@ ooc_status ooc_wave25_adjoint_step(const float *d_mu, const float *d_mu_prev, fl
 {
     if (!d_mu || !d_mu_prev || !d_out || !d_kappa || !dims_ok(nx, ny, nz))
         return OOC_E_INVALID;
-    return launch_aux<1>(d_mu, d_kappa, d_mu_prev, d_out, nullptr, nullptr, nx, ny, nz, (cudaStream_t)stream) ==
-                   cudaSuccess
+    return launch_adjoint_step(d_mu, d_kappa, d_mu_prev, d_out, nx, ny, nz, (cudaStream_t)stream) == cudaSuccess
                ? OOC_OK
                : OOC_E_CUDA;
 }
@@ -321,10 +327,8 @@ ooc_status ooc_wave25_grad_accum(double *d_grad, const float *d_mu, const float 
 {
     if (!d_grad || !d_mu || !d_p || !dims_ok(nx, ny, nz) || ((uintptr_t)d_grad % 32))
         return OOC_E_INVALID;
-    return launch_aux<2>(d_p, nullptr, nullptr, nullptr, d_mu, d_grad, nx, ny, nz, (cudaStream_t)stream) ==
-                   cudaSuccess
-               ? OOC_OK
-               : OOC_E_CUDA;
+    return launch_wave25_grad(d_p, d_mu, d_grad, nx, ny, nz, (cudaStream_t)stream) == cudaSuccess ? OOC_OK
+                                                                                                : OOC_E_CUDA;
 }
 
 ooc_status ooc_kappa_from_velocity(const float *d_v, float *d_kappa, int64_t n, double dt_over_dx, void *stream)
@@ -484,18 +488,23 @@ ooc_status ooc_wave25_backward_ckpt(const float *d_kappa, int64_t nx, int64_t ny
                                       ConstRing{d_kappa, nz, 0}, nx, ny, nz, 0, nz, src ? sx : -1, sy, sz,
                                       src ? h_w[s] : 0.0f, sC));
         }
-        // adjoint through the segment
+        // adjoint through the segment, on w = kappa mu (mu1 / mu2 hold w)
         for (int64_t m = n1; m >= n0 + 1; --m) {
-            TRY_CUDA(launch_aux<1>(mu1, d_kappa, mu2, mu2, nullptr, nullptr, nx, ny, nz, sC));  // mu2 <- mu^m
-            if (nrec > 0)
-                TRY_CUDA(ooc_scatter_add(mu2, d_rec, nrec, d_res + (m - 1) * nrec, sC) == OOC_OK ? cudaSuccess
-                                                                                                : cudaErrorUnknown);
-            TRY_CUDA(launch_aux<2>(hist(m - n0), nullptr, nullptr, nullptr, mu2, d_grad, nx, ny, nz, sC));
+            TRY_CUDA(launch_wave25_to(ConstRing{mu1, nz, 0}, ConstRing{mu2, nz, 0}, Ring{mu2, nz, 0},
+                                      ConstRing{d_kappa, nz, 0}, nx, ny, nz, 0, nz, -1, -1, -1, 0.0f, sC));
+            if (nrec > 0) {  // + kappa S^T res[m-1]
+                scatter_add_scaled_kernel<<<(unsigned)((nrec + 255) / 256), 256, 0, sC>>>(
+                    mu2, d_rec, nrec, d_res + (m - 1) * nrec, d_kappa);
+                TRY_CUDA(cudaGetLastError());
+            }
+            TRY_CUDA(launch_wave25_grad(hist(m - n0), mu2, d_grad, nx, ny, nz, sC));  // += w^m L(p^{m-1})
             float *t = mu1;
             mu1 = mu2;
             mu2 = t;
         }
     }
+    divide_by_kappa_kernel<<<grid1d(n, 256), 256, 0, sC>>>(d_grad, d_kappa, n);
+    TRY_CUDA(cudaGetLastError());
     TRY_CUDA(cudaEventRecord(ev.e[4], sC));
     TRY_CUDA(cudaEventRecord(ev.e[5], sD));
     ooc_status st = wait_ev(ev.e[4], 600000);

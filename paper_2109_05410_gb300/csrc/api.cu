@@ -18,29 +18,64 @@ bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p % a) == 0; }
 
 ooc_status cuda_status(cudaError_t e) { return e == cudaSuccess ? OOC_OK : OOC_E_CUDA; }
 
+// Flat BF16 conversion.  Quads of 4 values move as 16-byte (FP32) and
+// 8-byte (BF16) accesses, four quads per thread per round so that several
+// loads are in flight; a tail of n mod 4 values is done by thread 0.
+__device__ __forceinline__ uint32_t bf16_rne_bits(uint32_t u)
+{
+    if ((u & 0x7FFFFFFFu) > 0x7F800000u)
+        return (u >> 16) | 0x40u;  // NaN stays a quiet NaN
+    return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+}
+
 __global__ void bf16_pack_flat(const float *in, uint16_t *out, int64_t n)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t u = __float_as_uint(in[i]);
-        uint32_t h;
-        if ((u & 0x7FFFFFFFu) > 0x7F800000u)
-            h = (u >> 16) | 0x40u;
-        else
-            h = (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
-        out[i] = (uint16_t)h;
+    const int64_t nq = n >> 2, stride = (int64_t)gridDim.x * blockDim.x;
+    const uint4 *in4 = reinterpret_cast<const uint4 *>(in);
+    uint2 *out2 = reinterpret_cast<uint2 *>(out);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += 4 * stride) {
+        uint4 v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (i + k * stride < nq)
+                v[k] = __ldg(in4 + i + k * stride);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (i + k * stride < nq)
+                out2[i + k * stride] = make_uint2(bf16_rne_bits(v[k].x) | (bf16_rne_bits(v[k].y) << 16),
+                                                  bf16_rne_bits(v[k].z) | (bf16_rne_bits(v[k].w) << 16));
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int64_t j = nq << 2; j < n; ++j)
+            out[j] = (uint16_t)bf16_rne_bits(__float_as_uint(in[j]));
 }
 
 __global__ void bf16_unpack_flat(const uint16_t *in, float *out, int64_t n)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = __uint_as_float((uint32_t)in[i] << 16);
+    const int64_t nq = n >> 2, stride = (int64_t)gridDim.x * blockDim.x;
+    const uint2 *in2 = reinterpret_cast<const uint2 *>(in);
+    uint4 *out4 = reinterpret_cast<uint4 *>(out);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += 4 * stride) {
+        uint2 v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (i + k * stride < nq)
+                v[k] = __ldg(in2 + i + k * stride);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (i + k * stride < nq)
+                out4[i + k * stride] = make_uint4(v[k].x << 16, v[k].x & 0xFFFF0000u, v[k].y << 16,
+                                                  v[k].y & 0xFFFF0000u);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int64_t j = nq << 2; j < n; ++j)
+            out[j] = __uint_as_float((uint32_t)in[j] << 16);
 }
 
 unsigned flat_grid(int64_t n)
 {
-    int64_t b = (n + 255) / 256;
-    return (unsigned)(b < 1 ? 1 : (b > 152 * 32 ? 152 * 32 : b));
+    int64_t b = (n / 4 + 255) / 256;
+    return (unsigned)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
 }
 
 }  // namespace
@@ -196,6 +231,8 @@ ooc_status ooc_bf16_pack(const float *d_in, uint16_t *d_out, int64_t n, void *st
         return OOC_E_INVALID;
     if (n == 0)
         return OOC_OK;
+    if (!aligned(d_in, 16) || !aligned(d_out, 8))
+        return OOC_E_INVALID;
     bf16_pack_flat<<<flat_grid(n), 256, 0, (cudaStream_t)stream>>>(d_in, d_out, n);
     return cuda_status(cudaGetLastError());
 }
@@ -206,6 +243,8 @@ ooc_status ooc_bf16_unpack(const uint16_t *d_in, float *d_out, int64_t n, void *
         return OOC_E_INVALID;
     if (n == 0)
         return OOC_OK;
+    if (!aligned(d_in, 8) || !aligned(d_out, 16))
+        return OOC_E_INVALID;
     bf16_unpack_flat<<<flat_grid(n), 256, 0, (cudaStream_t)stream>>>(d_in, d_out, n);
     return cuda_status(cudaGetLastError());
 }

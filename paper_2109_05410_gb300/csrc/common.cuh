@@ -40,6 +40,10 @@ constexpr float kC4 = -1.0f / 560.0f;
 // cudaGetLastError() of the launch.
 cudaError_t launch_heat7(ConstRing in, Ring out, int64_t nx, int64_t ny, int64_t nz, int64_t z0, int64_t z1,
                          float r, cudaStream_t st);
+// g[i] += (double) mu[i] * (double) L(p)[i] over whole dense fields (the
+// 25-point Laplacian without kappa); g 32-byte aligned.
+cudaError_t launch_wave25_grad(const float *p, const float *mu, double *g, int64_t nx, int64_t ny, int64_t nz,
+                               cudaStream_t st);
 // Two heat7 steps in one launch: level s on [lo, hi) computed on chip from
 // ring `in` (level s-1), level s+1 written to ring `out` on [z0, z1).  The
 // two level-s planes below lo are read from band_in (planes bin_lo,

@@ -411,10 +411,14 @@ struct WaveSmem {
     float4 kk[kWaveKStages][kWaveTY][kTX];
 };
 
+// MODE 0: the leapfrog step above.  MODE 1 (gradient of the adjoint run):
+// gsum[own] += (double) pprev * (double) L(pin) in FP64, with `pprev` the
+// adjoint field and kappa, pout and the source unused.
+template <int MODE>
 __global__ void __launch_bounds__(kTX *kWaveTY, 2)
     wave25_kernel(const float *__restrict__ pin, const float *pprev, float *pout, const float *__restrict__ kap, int nslot,
                   int64_t zbase, Grid3 g, int64_t z0, int64_t z1, int64_t zchunk, int64_t sx, int64_t sy, int64_t sz,
-                  float w)
+                  float w, double *__restrict__ gsum)
 {
     constexpr int R = kWaveR;
     extern __shared__ __align__(16) unsigned char wave_smem[];
@@ -460,7 +464,8 @@ __global__ void __launch_bounds__(kTX *kWaveTY, 2)
             const int64_t kb = (int64_t)kslot * plane;
             const bool vk = inside && gz - R < nz;
             cp_async16(&sm.pp[ks][ty][lane], vk ? pprev + kb + off : pin, vk);
-            cp_async16(&sm.kk[ks][ty][lane], vk ? kap + kb + off : pin, vk);
+            if (MODE == 0)
+                cp_async16(&sm.kk[ks][ty][lane], vk ? kap + kb + off : pin, vk);
             kslot = wrap_add(kslot, 1, nslot);
         }
         cp_async_commit();
@@ -501,7 +506,7 @@ OOC_PRAGMA(unroll OOC_WAVE_UNROLL)
         if (lane == kTX - 1)
             rt = sm.xh[st][ty][1];
         const float4 ppv = sm.pp[ks][ty][lane];
-        const float4 kv = sm.kk[ks][ty][lane];
+        const float4 kv = MODE == 0 ? sm.kk[ks][ty][lane] : z4;
         const float L[4] = {lf.x, lf.y, lf.z, lf.w};
         const float C[4] = {c.x, c.y, c.z, c.w};
         const float Rt[4] = {rt.x, rt.y, rt.z, rt.w};
@@ -526,18 +531,29 @@ OOC_PRAGMA(unroll OOC_WAVE_UNROLL)
                 lap[j] += cf[m - 1] * ((xsum + (YM[j] + YP[j])) + (ZM[j] + ZP[j]));
             }
         }
-        float o[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            o[j] = 2.0f * C[j] - PP[j] + KV[j] * lap[j];
-        if (src_here && z == sz) {
+        if (MODE == 0) {
+            float o[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-                if (sx == x4 + j)
-                    o[j] += w;
+                o[j] = 2.0f * C[j] - PP[j] + KV[j] * lap[j];
+            if (src_here && z == sz) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (sx == x4 + j)
+                        o[j] += w;
+            }
+            if (inside)
+                *reinterpret_cast<float4 *>(pout + (int64_t)s * plane + off) = make_float4(o[0], o[1], o[2], o[3]);
+        } else if (inside) {
+            double2 *gp = reinterpret_cast<double2 *>(gsum + (int64_t)s * plane + off);
+            double2 g0 = gp[0], g1 = gp[1];
+            g0.x += (double)PP[0] * (double)lap[0];
+            g0.y += (double)PP[1] * (double)lap[1];
+            g1.x += (double)PP[2] * (double)lap[2];
+            g1.y += (double)PP[3] * (double)lap[3];
+            gp[0] = g0;
+            gp[1] = g1;
         }
-        if (inside)
-            *reinterpret_cast<float4 *>(pout + (int64_t)s * plane + off) = make_float4(o[0], o[1], o[2], o[3]);
 #pragma unroll
         for (int j = 0; j < 2 * R; ++j)
             q[j] = q[j + 1];
@@ -658,10 +674,10 @@ cudaError_t launch_wave25_to(ConstRing p, ConstRing pprev, Ring pnew, ConstRing 
         return cudaSuccess;
     static int res = 0;
     if (res == 0) {
-        if (cudaFuncSetAttribute(wave25_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(WaveSmem)) !=
-            cudaSuccess)
+        if (cudaFuncSetAttribute(wave25_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(WaveSmem)) != cudaSuccess)
             return cudaErrorInvalidValue;
-        res = resident((const void *)wave25_kernel, kTX * kWaveTY, sizeof(WaveSmem));
+        res = resident((const void *)wave25_kernel<0>, kTX * kWaveTY, sizeof(WaveSmem));
     }
     const int64_t gx = (nx + kSeg - 1) / kSeg, gy = (ny + kWaveTY - 1) / kWaveTY;
     const int64_t chunk = choose_chunk(gx * gy, z1 - z0, 16, 9, res);
@@ -669,9 +685,29 @@ cudaError_t launch_wave25_to(ConstRing p, ConstRing pprev, Ring pnew, ConstRing 
     if (p.nslot != pnew.nslot || p.zbase != pnew.zbase || p.nslot != kappa.nslot || p.zbase != kappa.zbase ||
         p.nslot != pprev.nslot || p.zbase != pprev.zbase || p.nslot > (1ll << 30) || gx * gy > 0x7fffffffll)
         return cudaErrorInvalidValue;
-    wave25_kernel<<<dim3((unsigned)(gx * gy), (unsigned)gz), dim3(kTX, kWaveTY), sizeof(WaveSmem), st>>>(
+    wave25_kernel<0><<<dim3((unsigned)(gx * gy), (unsigned)gz), dim3(kTX, kWaveTY), sizeof(WaveSmem), st>>>(
         p.base, pprev.base, pnew.base, kappa.base, (int)p.nslot, p.zbase, Grid3{nx, ny, nz, nx * ny}, z0, z1, chunk,
-        sx, sy, sz, w);
+        sx, sy, sz, w, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wave25_grad(const float *p, const float *mu, double *g, int64_t nx, int64_t ny, int64_t nz,
+                               cudaStream_t st)
+{
+    static int res = 0;
+    if (res == 0) {
+        if (cudaFuncSetAttribute(wave25_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(WaveSmem)) != cudaSuccess)
+            return cudaErrorInvalidValue;
+        res = resident((const void *)wave25_kernel<1>, kTX * kWaveTY, sizeof(WaveSmem));
+    }
+    const int64_t gx = (nx + kSeg - 1) / kSeg, gy = (ny + kWaveTY - 1) / kWaveTY;
+    const int64_t chunk = choose_chunk(gx * gy, nz, 16, 9, res);
+    const int64_t gz = (nz + chunk - 1) / chunk;
+    if (gx * gy > 0x7fffffffll || nz > (1ll << 30))
+        return cudaErrorInvalidValue;
+    wave25_kernel<1><<<dim3((unsigned)(gx * gy), (unsigned)gz), dim3(kTX, kWaveTY), sizeof(WaveSmem), st>>>(
+        p, mu, nullptr, nullptr, (int)nz, 0, Grid3{nx, ny, nz, nx * ny}, 0, nz, chunk, -1, -1, -1, 0.0f, g);
     return cudaGetLastError();
 }
 

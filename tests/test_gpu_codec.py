@@ -81,6 +81,25 @@ def test_bf16_pack_bit_exact(ooc):
     assert np.array_equal(back.cpu().numpy().view(np.uint32), oracle.bf16_to_f32(oracle.bf16_bits(x)).view(np.uint32))
 
 
+@pytest.mark.parametrize("n", [1, 3, 4, 7, 1025, 4096 * 5 + 3, (1 << 22) + 2])
+def test_bf16_ragged_lengths(ooc, n):
+    # quads of 4 values per vector access, the n mod 4 tail separately, and
+    # lengths spanning several rounds of the grid-stride loop
+    rng = np.random.default_rng(n)
+    x = rng.normal(size=n).astype(np.float32) * np.float32(3.0)
+    packed = ooc.ooc_bf16_pack(torch.from_numpy(x).cuda())
+    back = ooc.ooc_bf16_unpack(packed)
+    torch.cuda.synchronize()
+    assert np.array_equal(packed.cpu().numpy().view(np.uint16), oracle.bf16_bits(x))
+    assert np.array_equal(back.cpu().numpy().view(np.uint32), oracle.bf16_to_f32(oracle.bf16_bits(x)).view(np.uint32))
+
+
+def test_bf16_misaligned_pointers_refused(ooc):
+    d = torch.zeros(65, device="cuda")
+    with pytest.raises(ooc.OocError):
+        ooc.ooc_bf16_pack(d[1:])
+
+
 def test_full_size_sampled_blocks(ooc):
     # The 1024^3 field of the heat benchmark, compressed on the GPU in one
     # launch; sampled 4^3 blocks are encoded by the oracle one by one and
