@@ -274,3 +274,37 @@ def test_step_deadline_reports_timeout_and_work_completes(ooc):
         plan.close()
         ref.close()
     assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_heat7_8cube_two_slabs_against_brute_force(ooc, k):
+    # The smallest pipeline: 8^3, two slabs of 4 planes, h = 1.  FP32 storage
+    # is bit-identical to the in-core kernel, and both agree with a per-point
+    # FP64 evaluation (each step written out with an explicit neighbour
+    # lookup, as in the oracle's brute-force pin) to FP32 rounding.
+    rng = np.random.default_rng(21)
+    u0 = rng.normal(size=(8, 8, 8)).astype(np.float32)
+    nsteps = 4
+    plan = ooc.Plan(nx=8, ny=8, nz=8, stencil="heat7", k=k, rw_format="fp32", slab_planes=4)
+    try:
+        assert plan.info()["nslab"] == 2
+        plan.set_field(0, u0)
+        plan.step(nsteps)
+        got = plan.get_field(0)
+    finally:
+        plan.close()
+    ref = incore_heat(ooc, u0, [nsteps], k, "fp32", 16)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+    u = u0.astype(np.float64)
+    for _ in range(nsteps):
+        v = np.empty_like(u)
+        for z in range(8):
+            for y in range(8):
+                for x in range(8):
+                    def at(dz, dy, dx):
+                        zz, yy, xx = z + dz, y + dy, x + dx
+                        return u[zz, yy, xx] if 0 <= zz < 8 and 0 <= yy < 8 and 0 <= xx < 8 else 0.0
+                    nb = at(0, 0, -1) + at(0, 0, 1) + at(0, -1, 0) + at(0, 1, 0) + at(-1, 0, 0) + at(1, 0, 0)
+                    v[z, y, x] = u[z, y, x] + (nb - 6.0 * u[z, y, x]) / 6.0
+        u = v
+    assert np.abs(got.astype(np.float64) - u).max() < 1e-6 * max(1.0, np.abs(u).max())
