@@ -44,10 +44,10 @@ COMPARE = [("fp32", 0), ("bf16", 0), ("fr4", 8), ("fr4", 12), ("fr4", 24)]
 # 512^3 case of `--workload kernels512` (dram__bytes_read.sum +
 # dram__bytes_write.sum over 134.2 M points).  Traffic is proportional to the
 # points a launch processes, so the bench scales it to its own launches.  It
-# is only valid for the stencil code it was measured on (sha256 prefix of the
+# is only valid for the heat7 code it was measured on (sha256 prefix of that
 # source without comments).
 HEAT7_TRAFFIC_PER_POINT = 7.81
-HEAT7_TRAFFIC_SRC_SHA = "a5bc7221708d0b10"
+HEAT7_TRAFFIC_SRC_SHA = "84af1791e2586024"
 METRIC = "Gpts/s out-of-core (compressed vs uncompressed, same GB300) at stated L2 error; % roofline"
 WORKLOAD = "heat7 1024^3 FP32, device budget 1 GiB, k=4, 64 steps/bench step"
 
@@ -57,13 +57,16 @@ def fmt_name(fmt, rate):
 
 
 def stencil_source_sha():
-    """sha256 prefix of stencil.cu with comments and blank lines removed, so
-    that the traffic measurement stays tied to the code, not its comments."""
+    """sha256 prefix of the heat7 kernel's source: stencil.cu up to the
+    kernel that follows heat7_kernel, with comments and blank lines removed
+    (the traffic measurement is tied to that code)."""
     import hashlib
     import re
-    path = os.path.join(ROOT, "paper_2109_05410_gb300", "csrc", "stencil.cu")
-    with open(path) as f:
-        code = [re.sub(r"//.*$", "", line).rstrip() for line in f]
+    with open(os.path.join(ROOT, "paper_2109_05410_gb300", "csrc", "stencil.cu")) as f:
+        text = f.read()
+    end = text.find("// Two heat7 steps per launch")
+    text = text[:end if end >= 0 else len(text)]
+    code = [re.sub(r"//.*$", "", line).rstrip() for line in text.split("\n")]
     return hashlib.sha256("\n".join(l for l in code if l).encode()).hexdigest()[:16]
 
 
@@ -309,8 +312,9 @@ def run_gpu(args, world, rank, local):
                 "frac": dk["frac_hbm"], "traffic": traffic,
                 "bytes_per_launch": dk["bytes"] / launches, "ms_per_launch": dk["ms"] / launches,
                 "peak_source": peak_src,
-                "timing": "per-launch CUDA events on the compute stream over a second timed region of the same "
-                          "steps (whole-job rate with the events: %.1f Gpts/s)" % value_profiled}
+                "timing": "CUDA events on the compute stream around each slab's stencil launches (and each "
+                          "codec launch) over a second timed region of the same steps; mean launch = bracketed "
+                          "time / launches (whole-job rate with the events: %.1f Gpts/s)" % value_profiled}
     h2d_GBs = st["h2d_bytes"] / (st["ms_h2d"] / 1e3) / 1e9 if st["ms_h2d"] > 0 else None
     d2h_GBs = st["d2h_bytes"] / (st["ms_d2h"] / 1e3) / 1e9 if st["ms_d2h"] > 0 else None
     plan.close()

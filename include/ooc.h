@@ -85,7 +85,10 @@ typedef struct {
     int64_t slabs;             /* slab visits executed */
     int64_t h2d_bytes, d2h_bytes;
     int64_t kernel_launches;   /* launches of this library's kernels in ooc_step */
-    /* Filled only with profile = 1 (summed CUDA-event durations, ms): */
+    /* Filled only with profile = 1 (summed CUDA-event durations, ms, and the
+     * launches or copies they cover).  The stencil launches of a slab share
+     * one event pair, so ms_stencil / n_stencil is their mean duration
+     * including the gaps between them. */
     double ms_decode, ms_stencil, ms_encode, ms_h2d, ms_d2h;
     int64_t n_decode, n_stencil, n_encode, n_h2d, n_d2h;
     double ms_last_step;       /* wall time of the last ooc_step call (host clock) */

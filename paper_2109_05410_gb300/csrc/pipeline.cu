@@ -52,7 +52,8 @@ int fmt_bits(int fmt, int rate)
 
 struct ProfPair {
     cudaEvent_t a, b;
-    int kind;  // 0 decode, 1 stencil, 2 encode, 3 h2d, 4 d2h
+    int kind;   // 0 decode, 1 stencil, 2 encode, 3 h2d, 4 d2h
+    int count;  // launches or copies between a and b
 };
 
 }  // namespace
@@ -204,6 +205,7 @@ ooc_status prof_begin(ooc_plan *p, cudaStream_t st, int kind, size_t *idx)
     }
     *idx = p->prof_used++;
     p->prof[*idx].kind = kind;
+    p->prof[*idx].count = 1;
     return cudaEventRecord(p->prof[*idx].a, st) == cudaSuccess ? OOC_OK : OOC_E_CUDA;
 }
 
@@ -604,6 +606,10 @@ ooc_status ooc_step(ooc_plan *p, int64_t nsteps)
                 }
             }
             OOC_CUDA(cudaEventRecord(p->ev_dec[e], sC));
+            // one event pair around the slab's stencil launches (events
+            // between consecutive kernels would keep them from overlapping)
+            size_t pst = (size_t)-1;
+            int nst = 0;
             for (int64_t s = 1, j = 0; s <= kp; ++j) {
                 // launch j: steps s (and s+1 when paired), ring j&1 -> the other
                 const int64_t len = p->spl == 2 && s + 1 <= kp ? 2 : 1;
@@ -613,8 +619,8 @@ ooc_status ooc_step(ooc_plan *p, int64_t nsteps)
                     s += len;
                     continue;
                 }
-                size_t pi;
-                OOC_TRY(prof_begin(p, sC, 1, &pi));
+                if (nst++ == 0)
+                    OOC_TRY(prof_begin(p, sC, 1, &pst));
                 if (!wave && len == 2) {
                     // level s on [lo_s, hi_s) stays on chip; its 2h planes
                     // below lo_s come from slab i-1's band, its top 2h
@@ -636,9 +642,13 @@ ooc_status ooc_step(ooc_plan *p, int64_t nsteps)
                                            cring(ring_view(p, 2, zb)), nx, ny, nz, lo, hi, src ? p->sx : -1, p->sy,
                                            p->sz, src ? p->w[n] : 0.0f, sC));
                 }
-                OOC_TRY(prof_end(p, sC, pi));
                 p->stats.kernel_launches++;
                 s += len;
+            }
+            if (nst > 0) {
+                OOC_TRY(prof_end(p, sC, pst));
+                if (pst != (size_t)-1)
+                    p->prof[pst].count = nst;
             }
             bool any_enc = false;
             for (int f = 0; f < p->nrw; ++f)
@@ -687,7 +697,7 @@ ooc_status ooc_step(ooc_plan *p, int64_t nsteps)
             OOC_CUDA(cudaEventElapsedTime(&ms, p->prof[j].a, p->prof[j].b));
             switch (p->prof[j].kind) {
             case 0: p->stats.ms_decode += ms; p->stats.n_decode++; break;
-            case 1: p->stats.ms_stencil += ms; p->stats.n_stencil++; break;
+            case 1: p->stats.ms_stencil += ms; p->stats.n_stencil += p->prof[j].count; break;
             case 2: p->stats.ms_encode += ms; p->stats.n_encode++; break;
             case 3: p->stats.ms_h2d += ms; p->stats.n_h2d++; break;
             default: p->stats.ms_d2h += ms; p->stats.n_d2h++; break;
