@@ -75,6 +75,8 @@ typedef struct {
     int32_t heat_steps_per_launch; /* heat7: 1 = one step per launch (0 = default = 1); 2 = each pair
                                       of the k steps in one launch with the intermediate level kept on
                                       chip.  Results are bit-identical.  wave25: 0 or 1. */
+    int32_t graph_mode;          /* 0 = heat7 calls without profiling are captured once per distinct
+                                    nsteps as a CUDA graph and replayed; 1 = always launch directly */
 } ooc_config;
 
 typedef struct ooc_plan ooc_plan;

@@ -41,7 +41,7 @@ class OocConfig(ctypes.Structure):
         ("ro_format", ctypes.c_int32), ("ro_rate", ctypes.c_int32),
         ("device_budget_bytes", ctypes.c_int64), ("slab_planes", ctypes.c_int32),
         ("profile", ctypes.c_int32), ("wait_timeout_ms", ctypes.c_int64),
-        ("heat_steps_per_launch", ctypes.c_int32),
+        ("heat_steps_per_launch", ctypes.c_int32), ("graph_mode", ctypes.c_int32),
     ]
 
 
@@ -415,7 +415,7 @@ class Plan:
     streams (H2D, compute, D2H).  Configuration keys mirror ``ooc_config``:
     nx, ny, nz, stencil ('heat7'|'wave25'), k, r, rw_format, rw_rate,
     ro_format, ro_rate, device_budget_bytes, slab_planes, profile,
-    wait_timeout_ms, heat_steps_per_launch."""
+    wait_timeout_ms, heat_steps_per_launch, graph_mode."""
 
     def __init__(self, device=0, **kw):
         import torch
@@ -434,6 +434,7 @@ class Plan:
         c.profile = int(kw.get("profile", 0))
         c.wait_timeout_ms = kw.get("wait_timeout_ms", 0)
         c.heat_steps_per_launch = int(kw.get("heat_steps_per_launch", 0))
+        c.graph_mode = int(kw.get("graph_mode", 0))
         self.config = c
         self.shape = (c.nz, c.ny, c.nx)
         self._h = ctypes.c_void_p()

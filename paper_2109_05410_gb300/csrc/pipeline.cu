@@ -80,6 +80,12 @@ struct ooc_plan {
     cudaStream_t st[3] = {nullptr, nullptr, nullptr};
     cudaEvent_t ev_h2d[kEv], ev_dec[kEv], ev_comp[kEv], ev_d2h[kEv];
     bool events_made = false;
+    // CUDA graph of one ooc_step(graph_nsteps) call, replayed while the
+    // call's launches stay the same (heat7 without per-launch profiling)
+    cudaGraphExec_t graph = nullptr;
+    int64_t graph_nsteps = 0;
+    ooc_stats graph_delta{};  // counters one replay adds
+    cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr}, ev_done = nullptr;
     std::vector<ProfPair> prof;
     size_t prof_used = 0;
     // run state
@@ -290,6 +296,235 @@ void step_window(const ooc_plan *p, int64_t i, int64_t kp, int64_t s, int64_t *l
     *hi = u;
 }
 
+// Enqueue the passes of ooc_step(nsteps) on the plan's three streams; the
+// last D2H records p->ev_d2h[(*slabs - 1) % kEv].  Counters go to `st`.
+ooc_status enqueue_steps(ooc_plan *p, int64_t nsteps, ooc_stats *st, int64_t *slabs)
+{
+    const int64_t nx = p->cfg.nx, ny = p->cfg.ny, nz = p->cfg.nz, k = p->cfg.k;
+    const bool wave = p->cfg.stencil == OOC_WAVE25;
+    const float r = (float)p->cfg.r;
+    cudaStream_t sH = p->st[0], sC = p->st[1], sD = p->st[2];
+    p->prof_used = 0;
+    const int64_t npass = (nsteps + k - 1) / k;
+    bool direct = false;  // some field lands in its ring without staging
+    for (int f = 0; f < p->nfield; ++f)
+        direct |= !staged(p, f);
+    int64_t g = 0;  // slab visits in this call
+    for (int64_t pass = 0; pass < npass; ++pass) {
+        const int64_t kp = (pass + 1) * k <= nsteps ? k : nsteps - pass * k;
+        const int64_t Wp = round4(kp * p->h);
+        const int64_t zb = (pass * nz) % p->Z;
+        const int64_t t0 = p->time + pass * k;
+        for (int64_t i = 0; i < p->nslab; ++i, ++g) {
+            const SlabGeom sg = slab_geom(p, i, Wp);
+            const int e = (int)(g % kEv);
+            // ---- H2D: input units R_i and C_i (slab 0 also C_{-1}) -------------
+            // FP32 fields land in the rings, whose slots slab g-2's D2H may
+            // still read; staged fields land in staging buffer g&1, free
+            // once slab g-2's decode has run (ev_dec below).
+            int64_t need = direct ? g - 2 : -1;
+            if (pass > 0) {
+                // the host units read here were written by slabs i, i+1 of the
+                // previous pass.  The event ring holds the last kEv slabs, so
+                // an older slab is covered by waiting for slab g-3 (the D2H
+                // stream runs in order).
+                int64_t gp = g - p->nslab + (i + 1 < p->nslab ? 1 : 0);
+                if (gp < g - 3)
+                    gp = g - 3;
+                if (gp > need)
+                    need = gp;
+            }
+            if (need >= 0)
+                OOC_CUDA(cudaStreamWaitEvent(sH, p->ev_d2h[need % kEv], 0));
+            if (g >= 2)
+                OOC_CUDA(cudaStreamWaitEvent(sH, p->ev_dec[(g - 2) % kEv], 0));
+            if (sg.in_hi > sg.in_lo) {
+                size_t pi;
+                OOC_TRY(prof_begin(p, sH, 3, &pi));
+                for (int f = 0; f < p->nfield; ++f) {
+                    char *src = p->host + p->off_host[f] + (size_t)sg.in_lo * p->fplane[f];
+                    const size_t nb = (size_t)(sg.in_hi - sg.in_lo) * p->fplane[f];
+                    if (staged(p, f))
+                        OOC_CUDA(cudaMemcpyAsync(p->dev + p->off_in[g & 1][f], src, nb, cudaMemcpyHostToDevice, sH));
+                    else
+                        OOC_CUDA(copy_ring(p, input_ring(p, f), zb, sg.in_lo, sg.in_hi, src, true, sH));
+                    st->h2d_bytes += (int64_t)nb;
+                }
+                OOC_TRY(prof_end(p, sH, pi));
+            }
+            OOC_CUDA(cudaEventRecord(p->ev_h2d[e], sH));
+
+            // ---- compute: decode, k stencil steps, encode ---------------------
+            OOC_CUDA(cudaStreamWaitEvent(sC, p->ev_h2d[e], 0));
+            if (sg.in_hi > sg.in_lo) {
+                for (int f = 0; f < p->nfield; ++f) {
+                    if (!staged(p, f))
+                        continue;
+                    size_t pi;
+                    OOC_TRY(prof_begin(p, sC, 0, &pi));
+                    OOC_TRY(decode_into(p, f, p->dev + p->off_in[g & 1][f], ring_view(p, input_ring(p, f), zb),
+                                        sg.in_lo, sg.in_hi, sC));
+                    OOC_TRY(prof_end(p, sC, pi));
+                    st->kernel_launches++;
+                }
+            }
+            OOC_CUDA(cudaEventRecord(p->ev_dec[e], sC));
+            // one event pair around the slab's stencil launches (events
+            // between consecutive kernels would keep them from overlapping)
+            size_t pst = (size_t)-1;
+            int nst = 0;
+            for (int64_t s = 1, j = 0; s <= kp; ++j) {
+                // launch j: steps s (and s+1 when paired), ring j&1 -> the other
+                const int64_t len = p->spl == 2 && s + 1 <= kp ? 2 : 1;
+                int64_t lo, hi;
+                step_window(p, i, kp, s + len - 1, &lo, &hi);
+                if (hi <= lo) {
+                    s += len;
+                    continue;
+                }
+                if (nst++ == 0)
+                    OOC_TRY(prof_begin(p, sC, 1, &pst));
+                if (!wave && len == 2) {
+                    // level s on [lo_s, hi_s) stays on chip; its 2h planes
+                    // below lo_s come from slab i-1's band, its top 2h
+                    // planes go to this slab's band
+                    int64_t lo_s, hi_s;
+                    step_window(p, i, kp, s, &lo_s, &hi_s);
+                    const float *bin = i > 0 ? band(p, j, (i - 1) & 1) : nullptr;
+                    float *bout = i + 1 < p->nslab ? band(p, j, i & 1) : nullptr;
+                    OOC_CUDA(launch_heat7x2(cring(ring_view(p, (int)(j & 1), zb)), ring_view(p, (int)((j + 1) & 1), zb),
+                                            nx, ny, nz, lo, hi, lo_s, hi_s, bin, lo_s - 2 * p->h, bout,
+                                            hi_s - 2 * p->h, r, sC));
+                } else if (!wave) {
+                    OOC_CUDA(launch_heat7(cring(ring_view(p, (int)(j & 1), zb)), ring_view(p, (int)((j + 1) & 1), zb),
+                                          nx, ny, nz, lo, hi, r, sC));
+                } else {
+                    const int64_t n = t0 + s - 1;  // computing p^{n+1}
+                    const bool src = p->sx >= 0 && n < (int64_t)p->w.size() && p->sz >= lo && p->sz < hi;
+                    OOC_CUDA(launch_wave25(cring(ring_view(p, (int)((s - 1) & 1), zb)), ring_view(p, (int)(s & 1), zb),
+                                           cring(ring_view(p, 2, zb)), nx, ny, nz, lo, hi, src ? p->sx : -1, p->sy,
+                                           p->sz, src ? p->w[n] : 0.0f, sC));
+                }
+                st->kernel_launches++;
+                s += len;
+            }
+            if (nst > 0) {
+                OOC_TRY(prof_end(p, sC, pst));
+                if (pst != (size_t)-1)
+                    p->prof[pst].count = nst;
+            }
+            bool any_enc = false;
+            for (int f = 0; f < p->nrw; ++f)
+                any_enc |= staged(p, f);
+            if (any_enc && g >= 2)
+                OOC_CUDA(cudaStreamWaitEvent(sC, p->ev_d2h[(g - 2) % kEv], 0));
+            for (int f = 0; f < p->nrw; ++f) {
+                if (!staged(p, f))
+                    continue;
+                size_t pi;
+                OOC_TRY(prof_begin(p, sC, 2, &pi));
+                OOC_TRY(encode_from(p, f, cring(ring_view(p, output_ring(p, f, kp), zb)),
+                                    p->dev + p->off_out[g & 1][f], sg.a, sg.b, sC));
+                OOC_TRY(prof_end(p, sC, pi));
+                st->kernel_launches++;
+            }
+            OOC_CUDA(cudaEventRecord(p->ev_comp[e], sC));
+
+            // ---- D2H: units C_{i-1} and R_i ---------------------------------
+            OOC_CUDA(cudaStreamWaitEvent(sD, p->ev_comp[e], 0));
+            {
+                size_t pi;
+                OOC_TRY(prof_begin(p, sD, 4, &pi));
+                for (int f = 0; f < p->nrw; ++f) {
+                    char *dst = p->host + p->off_host[f] + (size_t)sg.a * p->fplane[f];
+                    const size_t nb = (size_t)(sg.b - sg.a) * p->fplane[f];
+                    if (staged(p, f))
+                        OOC_CUDA(cudaMemcpyAsync(dst, p->dev + p->off_out[g & 1][f], nb, cudaMemcpyDeviceToHost, sD));
+                    else
+                        OOC_CUDA(copy_ring(p, output_ring(p, f, kp), zb, sg.a, sg.b, dst, false, sD));
+                    st->d2h_bytes += (int64_t)nb;
+                }
+                OOC_TRY(prof_end(p, sD, pi));
+            }
+            OOC_CUDA(cudaEventRecord(p->ev_d2h[e], sD));
+            st->slabs++;
+        }
+        st->passes++;
+    }
+    *slabs = g;
+    return OOC_OK;
+}
+
+ooc_status ensure_graph_events(ooc_plan *p)
+{
+    if (p->ev_done)
+        return OOC_OK;
+    if (cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_join[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_join[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_done, cudaEventDisableTiming) != cudaSuccess)
+        return OOC_E_CUDA;
+    return OOC_OK;
+}
+
+void drop_graph(ooc_plan *p)
+{
+    if (p->graph)
+        cudaGraphExecDestroy(p->graph);
+    p->graph = nullptr;
+    p->graph_nsteps = 0;
+}
+
+// Capture ooc_step(nsteps) into p->graph: the compute stream forks to the
+// copy streams and joins them back, so one launch on it replays the call.
+ooc_status capture_graph(ooc_plan *p, int64_t nsteps)
+{
+    drop_graph(p);
+    OOC_TRY(ensure_graph_events(p));
+    cudaStream_t sH = p->st[0], sC = p->st[1], sD = p->st[2];
+    OOC_CUDA(cudaStreamBeginCapture(sC, cudaStreamCaptureModeThreadLocal));
+    ooc_stats delta{};
+    int64_t slabs = 0;
+    ooc_status s = OOC_OK;
+    if (cudaEventRecord(p->ev_fork, sC) != cudaSuccess || cudaStreamWaitEvent(sH, p->ev_fork, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(sD, p->ev_fork, 0) != cudaSuccess)
+        s = OOC_E_CUDA;
+    if (s == OOC_OK)
+        s = enqueue_steps(p, nsteps, &delta, &slabs);
+    if (s == OOC_OK &&
+        (cudaEventRecord(p->ev_join[0], sH) != cudaSuccess || cudaEventRecord(p->ev_join[1], sD) != cudaSuccess ||
+         cudaStreamWaitEvent(sC, p->ev_join[0], 0) != cudaSuccess ||
+         cudaStreamWaitEvent(sC, p->ev_join[1], 0) != cudaSuccess))
+        s = OOC_E_CUDA;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(sC, &graph);
+    if (s == OOC_OK && e != cudaSuccess)
+        s = OOC_E_CUDA;
+    if (s == OOC_OK && cudaGraphInstantiate(&p->graph, graph, 0) != cudaSuccess) {
+        p->graph = nullptr;
+        s = OOC_E_CUDA;
+    }
+    if (graph)
+        cudaGraphDestroy(graph);
+    if (s != OOC_OK) {
+        cudaGetLastError();
+        drop_graph(p);
+        return s;
+    }
+    p->graph_nsteps = nsteps;
+    p->graph_delta = delta;
+    return OOC_OK;
+}
+
+void add_counters(ooc_stats *to, const ooc_stats &d)
+{
+    to->passes += d.passes;
+    to->slabs += d.slabs;
+    to->h2d_bytes += d.h2d_bytes;
+    to->d2h_bytes += d.d2h_bytes;
+    to->kernel_launches += d.kernel_launches;
+}
+
 }  // namespace
 
 extern "C" {
@@ -311,6 +546,8 @@ ooc_status ooc_plan_create(const ooc_config *cfg, ooc_plan **out, size_t *device
     if (!fmt_ok(c.rw_format, c.rw_rate) || (c.stencil == OOC_WAVE25 && !fmt_ok(c.ro_format, c.ro_rate)))
         return OOC_E_INVALID;
     if (c.slab_planes < 0 || c.slab_planes % 4 || c.device_budget_bytes < 0)
+        return OOC_E_INVALID;
+    if (c.graph_mode < 0 || c.graph_mode > 1)
         return OOC_E_INVALID;
     if (c.heat_steps_per_launch < 0 || c.heat_steps_per_launch > 2 ||
         (c.stencil == OOC_WAVE25 && c.heat_steps_per_launch > 1))
@@ -537,158 +774,25 @@ ooc_status ooc_step(ooc_plan *p, int64_t nsteps)
     if (nsteps == 0)
         return OOC_OK;
     const auto t_start = std::chrono::steady_clock::now();
-    const int64_t nx = p->cfg.nx, ny = p->cfg.ny, nz = p->cfg.nz, k = p->cfg.k;
-    const bool wave = p->cfg.stencil == OOC_WAVE25;
-    const float r = (float)p->cfg.r;
-    cudaStream_t sH = p->st[0], sC = p->st[1], sD = p->st[2];
     p->prof_used = 0;
-    const int64_t npass = (nsteps + k - 1) / k;
-    bool direct = false;  // some field lands in its ring without staging
-    for (int f = 0; f < p->nfield; ++f)
-        direct |= !staged(p, f);
-    int64_t g = 0;  // slab visits in this call
-    for (int64_t pass = 0; pass < npass; ++pass) {
-        const int64_t kp = (pass + 1) * k <= nsteps ? k : nsteps - pass * k;
-        const int64_t Wp = round4(kp * p->h);
-        const int64_t zb = (pass * nz) % p->Z;
-        const int64_t t0 = p->time + pass * k;
-        for (int64_t i = 0; i < p->nslab; ++i, ++g) {
-            const SlabGeom sg = slab_geom(p, i, Wp);
-            const int e = (int)(g % kEv);
-            // ---- H2D: input units R_i and C_i (slab 0 also C_{-1}) -------------
-            // FP32 fields land in the rings, whose slots slab g-2's D2H may
-            // still read; staged fields land in staging buffer g&1, free
-            // once slab g-2's decode has run (ev_dec below).
-            int64_t need = direct ? g - 2 : -1;
-            if (pass > 0) {
-                // the host units read here were written by slabs i, i+1 of the
-                // previous pass.  The event ring holds the last kEv slabs, so
-                // an older slab is covered by waiting for slab g-3 (the D2H
-                // stream runs in order).
-                int64_t gp = g - p->nslab + (i + 1 < p->nslab ? 1 : 0);
-                if (gp < g - 3)
-                    gp = g - 3;
-                if (gp > need)
-                    need = gp;
-            }
-            if (need >= 0)
-                OOC_CUDA(cudaStreamWaitEvent(sH, p->ev_d2h[need % kEv], 0));
-            if (g >= 2)
-                OOC_CUDA(cudaStreamWaitEvent(sH, p->ev_dec[(g - 2) % kEv], 0));
-            if (sg.in_hi > sg.in_lo) {
-                size_t pi;
-                OOC_TRY(prof_begin(p, sH, 3, &pi));
-                for (int f = 0; f < p->nfield; ++f) {
-                    char *src = p->host + p->off_host[f] + (size_t)sg.in_lo * p->fplane[f];
-                    const size_t nb = (size_t)(sg.in_hi - sg.in_lo) * p->fplane[f];
-                    if (staged(p, f))
-                        OOC_CUDA(cudaMemcpyAsync(p->dev + p->off_in[g & 1][f], src, nb, cudaMemcpyHostToDevice, sH));
-                    else
-                        OOC_CUDA(copy_ring(p, input_ring(p, f), zb, sg.in_lo, sg.in_hi, src, true, sH));
-                    p->stats.h2d_bytes += (int64_t)nb;
-                }
-                OOC_TRY(prof_end(p, sH, pi));
-            }
-            OOC_CUDA(cudaEventRecord(p->ev_h2d[e], sH));
-
-            // ---- compute: decode, k stencil steps, encode ---------------------
-            OOC_CUDA(cudaStreamWaitEvent(sC, p->ev_h2d[e], 0));
-            if (sg.in_hi > sg.in_lo) {
-                for (int f = 0; f < p->nfield; ++f) {
-                    if (!staged(p, f))
-                        continue;
-                    size_t pi;
-                    OOC_TRY(prof_begin(p, sC, 0, &pi));
-                    OOC_TRY(decode_into(p, f, p->dev + p->off_in[g & 1][f], ring_view(p, input_ring(p, f), zb),
-                                        sg.in_lo, sg.in_hi, sC));
-                    OOC_TRY(prof_end(p, sC, pi));
-                    p->stats.kernel_launches++;
-                }
-            }
-            OOC_CUDA(cudaEventRecord(p->ev_dec[e], sC));
-            // one event pair around the slab's stencil launches (events
-            // between consecutive kernels would keep them from overlapping)
-            size_t pst = (size_t)-1;
-            int nst = 0;
-            for (int64_t s = 1, j = 0; s <= kp; ++j) {
-                // launch j: steps s (and s+1 when paired), ring j&1 -> the other
-                const int64_t len = p->spl == 2 && s + 1 <= kp ? 2 : 1;
-                int64_t lo, hi;
-                step_window(p, i, kp, s + len - 1, &lo, &hi);
-                if (hi <= lo) {
-                    s += len;
-                    continue;
-                }
-                if (nst++ == 0)
-                    OOC_TRY(prof_begin(p, sC, 1, &pst));
-                if (!wave && len == 2) {
-                    // level s on [lo_s, hi_s) stays on chip; its 2h planes
-                    // below lo_s come from slab i-1's band, its top 2h
-                    // planes go to this slab's band
-                    int64_t lo_s, hi_s;
-                    step_window(p, i, kp, s, &lo_s, &hi_s);
-                    const float *bin = i > 0 ? band(p, j, (i - 1) & 1) : nullptr;
-                    float *bout = i + 1 < p->nslab ? band(p, j, i & 1) : nullptr;
-                    OOC_CUDA(launch_heat7x2(cring(ring_view(p, (int)(j & 1), zb)), ring_view(p, (int)((j + 1) & 1), zb),
-                                            nx, ny, nz, lo, hi, lo_s, hi_s, bin, lo_s - 2 * p->h, bout,
-                                            hi_s - 2 * p->h, r, sC));
-                } else if (!wave) {
-                    OOC_CUDA(launch_heat7(cring(ring_view(p, (int)(j & 1), zb)), ring_view(p, (int)((j + 1) & 1), zb),
-                                          nx, ny, nz, lo, hi, r, sC));
-                } else {
-                    const int64_t n = t0 + s - 1;  // computing p^{n+1}
-                    const bool src = p->sx >= 0 && n < (int64_t)p->w.size() && p->sz >= lo && p->sz < hi;
-                    OOC_CUDA(launch_wave25(cring(ring_view(p, (int)((s - 1) & 1), zb)), ring_view(p, (int)(s & 1), zb),
-                                           cring(ring_view(p, 2, zb)), nx, ny, nz, lo, hi, src ? p->sx : -1, p->sy,
-                                           p->sz, src ? p->w[n] : 0.0f, sC));
-                }
-                p->stats.kernel_launches++;
-                s += len;
-            }
-            if (nst > 0) {
-                OOC_TRY(prof_end(p, sC, pst));
-                if (pst != (size_t)-1)
-                    p->prof[pst].count = nst;
-            }
-            bool any_enc = false;
-            for (int f = 0; f < p->nrw; ++f)
-                any_enc |= staged(p, f);
-            if (any_enc && g >= 2)
-                OOC_CUDA(cudaStreamWaitEvent(sC, p->ev_d2h[(g - 2) % kEv], 0));
-            for (int f = 0; f < p->nrw; ++f) {
-                if (!staged(p, f))
-                    continue;
-                size_t pi;
-                OOC_TRY(prof_begin(p, sC, 2, &pi));
-                OOC_TRY(encode_from(p, f, cring(ring_view(p, output_ring(p, f, kp), zb)),
-                                    p->dev + p->off_out[g & 1][f], sg.a, sg.b, sC));
-                OOC_TRY(prof_end(p, sC, pi));
-                p->stats.kernel_launches++;
-            }
-            OOC_CUDA(cudaEventRecord(p->ev_comp[e], sC));
-
-            // ---- D2H: units C_{i-1} and R_i ---------------------------------
-            OOC_CUDA(cudaStreamWaitEvent(sD, p->ev_comp[e], 0));
-            {
-                size_t pi;
-                OOC_TRY(prof_begin(p, sD, 4, &pi));
-                for (int f = 0; f < p->nrw; ++f) {
-                    char *dst = p->host + p->off_host[f] + (size_t)sg.a * p->fplane[f];
-                    const size_t nb = (size_t)(sg.b - sg.a) * p->fplane[f];
-                    if (staged(p, f))
-                        OOC_CUDA(cudaMemcpyAsync(dst, p->dev + p->off_out[g & 1][f], nb, cudaMemcpyDeviceToHost, sD));
-                    else
-                        OOC_CUDA(copy_ring(p, output_ring(p, f, kp), zb, sg.a, sg.b, dst, false, sD));
-                    p->stats.d2h_bytes += (int64_t)nb;
-                }
-                OOC_TRY(prof_end(p, sD, pi));
-            }
-            OOC_CUDA(cudaEventRecord(p->ev_d2h[e], sD));
-            p->stats.slabs++;
-        }
-        p->stats.passes++;
+    // A call's launches depend only on nsteps for heat7 (the wave's source
+    // amplitudes follow the plan's time), so heat7 calls without per-launch
+    // profiling replay a captured graph.
+    const bool graphed = p->cfg.stencil == OOC_HEAT7 && !p->cfg.profile && p->cfg.graph_mode == 0;
+    if (graphed) {
+        if (!p->graph || p->graph_nsteps != nsteps)
+            OOC_TRY(capture_graph(p, nsteps));
+        OOC_CUDA(cudaGraphLaunch(p->graph, p->st[1]));
+        OOC_CUDA(cudaEventRecord(p->ev_done, p->st[1]));
+        OOC_TRY(wait_event(p, p->ev_done));
+        add_counters(&p->stats, p->graph_delta);
+    } else {
+        ooc_stats delta{};
+        int64_t g = 0;
+        OOC_TRY(enqueue_steps(p, nsteps, &delta, &g));
+        add_counters(&p->stats, delta);
+        OOC_TRY(wait_event(p, p->ev_d2h[(g - 1) % kEv]));
     }
-    OOC_TRY(wait_event(p, p->ev_d2h[(g - 1) % kEv]));
     p->time += nsteps;
     p->stats.steps_done += nsteps;
     if (p->cfg.profile) {
@@ -759,6 +863,10 @@ void ooc_plan_destroy(ooc_plan *p)
         cudaEventDestroy(pp.a);
         cudaEventDestroy(pp.b);
     }
+    drop_graph(p);
+    for (cudaEvent_t e : {p->ev_fork, p->ev_join[0], p->ev_join[1], p->ev_done})
+        if (e)
+            cudaEventDestroy(e);
     delete p;
 }
 

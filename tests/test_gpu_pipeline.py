@@ -308,3 +308,28 @@ def test_heat7_8cube_two_slabs_against_brute_force(ooc, k):
                     v[z, y, x] = u[z, y, x] + (nb - 6.0 * u[z, y, x]) / 6.0
         u = v
     assert np.abs(got.astype(np.float64) - u).max() < 1e-6 * max(1.0, np.abs(u).max())
+
+
+@pytest.mark.parametrize("fmt,rate", [("fp32", 16), ("fr4", 16), ("bf16", 16)])
+def test_graph_replay_matches_direct_launches(ooc, fmt, rate):
+    # heat7 calls without profiling are captured as a CUDA graph per
+    # distinct nsteps and replayed; calls of 8, 8, 5, 8 steps (replay,
+    # recapture, recapture) give the bits of direct launches
+    shape = (48, 40, 36)
+    u0 = smooth_random_field(shape, 5.0, seed=31)
+    out = {}
+    for mode in (0, 1):
+        plan = ooc.Plan(nx=36, ny=40, nz=48, stencil="heat7", k=4, rw_format=fmt, rw_rate=rate, slab_planes=12,
+                        graph_mode=mode)
+        try:
+            plan.set_field(0, u0)
+            for n in (8, 8, 5, 8):
+                plan.step(n)
+            out[mode] = plan.get_field(0)
+            st = plan.stats()
+        finally:
+            plan.close()
+        assert st["steps_done"] == 29 and st["passes"] == 2 + 2 + 2 + 2
+    assert np.array_equal(out[0].view(np.uint32), out[1].view(np.uint32))
+    ref = incore_heat(ooc, u0, [8, 8, 5, 8], 4, fmt, rate)
+    assert np.array_equal(out[0].view(np.uint32), ref.view(np.uint32))
