@@ -247,6 +247,30 @@ def test_full_size_heat_benchmark_configuration(ooc):
     assert m["rel_l2"] < 1e-4, m
 
 
+def test_full_size_wave_benchmark_configuration(ooc):
+    # The 1024^3 wave workload's code 4 (read-write levels and kappa at FR4-16,
+    # 4 GiB device budget, k = 10) over two passes with the source on:
+    # bit-identical to the in-core GPU reference with the same storage round
+    # trips, at the size the bench runs.
+    n, k, nsteps = 1024, 10, 20
+    kappa, p0, pm1, src, w = wave_inputs((n, n, n), nsteps)
+    plan = ooc.Plan(nx=n, ny=n, nz=n, stencil="wave25", k=k, rw_format="fr4", rw_rate=16, ro_format="fr4",
+                    ro_rate=16, device_budget_bytes=4 << 30)
+    try:
+        assert plan.device_bytes <= 4 << 30 and plan.info()["nslab"] > 1
+        plan.set_field(0, p0)
+        plan.set_field(1, pm1)
+        plan.set_field(2, kappa)
+        plan.set_source(*src, w)
+        plan.step(nsteps)
+        got_p, got_pp = plan.get_field(0), plan.get_field(1)
+    finally:
+        plan.close()
+    ref_p, ref_pp = incore_wave(ooc, p0, pm1, kappa, [nsteps], k, "fr4", 16, "fr4", 16, src, w)
+    assert np.array_equal(got_p.view(np.uint32), ref_p.view(np.uint32))
+    assert np.array_equal(got_pp.view(np.uint32), ref_pp.view(np.uint32))
+
+
 def test_step_deadline_reports_timeout_and_work_completes(ooc):
     # A host wait that runs past the plan's deadline returns OOC_E_TIMEOUT
     # (status 5) without faulting anything: the enqueued passes still run,
