@@ -36,6 +36,15 @@ constexpr float kC2 = -1.0f / 5.0f;
 constexpr float kC3 = 8.0f / 315.0f;
 constexpr float kC4 = -1.0f / 560.0f;
 
+// Source amplitudes of a wave plan kept on the device: step n adds w[n]
+// (n < nw) with n = *t + n_off, *t being the plan's time on the device.  With
+// w == nullptr the launch's own amplitude argument is used.
+struct WaveSrcTable {
+    const float *w = nullptr;
+    const int64_t *t = nullptr;
+    int64_t n_off = 0, nw = 0;
+};
+
 // Kernel launchers (stream-ordered, no synchronisation).  All return
 // cudaGetLastError() of the launch.
 cudaError_t launch_heat7(ConstRing in, Ring out, int64_t nx, int64_t ny, int64_t nz, int64_t z0, int64_t z1,
@@ -57,11 +66,14 @@ cudaError_t launch_heat7x2(ConstRing in, Ring out, int64_t nx, int64_t ny, int64
 cudaError_t launch_heat7_f64(const double *in, double *out, int64_t nx, int64_t ny, int64_t nz, double r,
                              cudaStream_t st);
 cudaError_t launch_wave25(ConstRing p, Ring pprev_out, ConstRing kappa, int64_t nx, int64_t ny, int64_t nz,
-                          int64_t z0, int64_t z1, int64_t sx, int64_t sy, int64_t sz, float w, cudaStream_t st);
+                          int64_t z0, int64_t z1, int64_t sx, int64_t sy, int64_t sz, float w, cudaStream_t st,
+                          WaveSrcTable tab = WaveSrcTable{});
 // Same step with p_prev read from `pprev` and p' written to `pnew` (may alias).
 cudaError_t launch_wave25_to(ConstRing p, ConstRing pprev, Ring pnew, ConstRing kappa, int64_t nx, int64_t ny,
                              int64_t nz, int64_t z0, int64_t z1, int64_t sx, int64_t sy, int64_t sz, float w,
-                             cudaStream_t st);
+                             cudaStream_t st, WaveSrcTable tab = WaveSrcTable{});
+// plan time on the device: *t += n (one thread)
+cudaError_t launch_add_time(int64_t *t, int64_t n, cudaStream_t st);
 // Codec over the 4-aligned plane range [z0, z1) of a ring; the stream part
 // for those planes is contiguous (2*rate words per block).
 cudaError_t launch_fr4_encode(ConstRing in, int64_t nx, int64_t ny, int64_t z0, int64_t z1, int rate,

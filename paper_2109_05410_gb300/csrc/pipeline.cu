@@ -37,6 +37,7 @@ using namespace ooc;
 namespace {
 
 constexpr int kEv = 4;  // event ring depth (waits look back at most 2 slabs)
+constexpr int64_t kSrcTable = 16384;  // source amplitudes kept on the device (graph replay)
 
 int64_t round4(int64_t v) { return (v + 3) / 4 * 4; }
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
@@ -64,6 +65,7 @@ struct ooc_plan {
     int nrw = 0, nfield = 0, nring = 0;
     int spl = 1;  // heat7 steps per stencil launch (1 or 2)
     size_t off_band = 0, band_bytes = 0;  // level-s bands of the fused launches
+    size_t off_src = 0;                   // wave source table (kSrcTable floats) and the device time
     int fmt[3] = {0, 0, 0}, rate[3] = {0, 0, 0};
     int64_t fplane[3] = {0, 0, 0};  // storage bytes per plane, per field
     int64_t plane_elems = 0;
@@ -92,6 +94,7 @@ struct ooc_plan {
     int64_t time = 0;
     int64_t sx = -1, sy = -1, sz = -1;
     std::vector<float> w;
+    bool src_uploaded = false;  // w is in the device table
     ooc_stats stats{};
 };
 
@@ -134,6 +137,9 @@ size_t layout(ooc_plan *p, int64_t T)
     p->off_band = off;
     p->band_bytes = p->spl == 2 ? (size_t)(2 * h) * p->plane_elems * sizeof(float) : 0;
     off += align256(p->band_bytes) * 2 * (size_t)(p->cfg.k / 2);
+    // the plan's time on the device, then the wave's source amplitudes
+    p->off_src = off;
+    off += 256 + (p->cfg.stencil == OOC_WAVE25 ? align256(kSrcTable * sizeof(float)) : 0);
     (void)any_staged;
     p->Z = Z;
     return off;
@@ -145,6 +151,9 @@ Ring ring_view(ooc_plan *p, int r, int64_t zbase)
 }
 
 ConstRing cring(const Ring &r) { return ConstRing{r.base, r.nslot, r.zbase}; }
+
+int64_t *dev_time(ooc_plan *p) { return (int64_t *)(p->dev + p->off_src); }
+float *dev_src(ooc_plan *p) { return (float *)(p->dev + p->off_src + 256); }
 
 // Band of pair j written by slabs of parity `parity`.
 float *band(ooc_plan *p, int64_t j, int64_t parity)
@@ -400,10 +409,17 @@ ooc_status enqueue_steps(ooc_plan *p, int64_t nsteps, ooc_stats *st, int64_t *sl
                                           nx, ny, nz, lo, hi, r, sC));
                 } else {
                     const int64_t n = t0 + s - 1;  // computing p^{n+1}
-                    const bool src = p->sx >= 0 && n < (int64_t)p->w.size() && p->sz >= lo && p->sz < hi;
+                    WaveSrcTable tab{};
+                    bool src;
+                    if (p->src_uploaded) {  // amplitude read on the device: the launch is time-invariant
+                        tab = WaveSrcTable{dev_src(p), dev_time(p), pass * k + s - 1, (int64_t)p->w.size()};
+                        src = p->sx >= 0 && p->sz >= lo && p->sz < hi;
+                    } else {
+                        src = p->sx >= 0 && n < (int64_t)p->w.size() && p->sz >= lo && p->sz < hi;
+                    }
                     OOC_CUDA(launch_wave25(cring(ring_view(p, (int)((s - 1) & 1), zb)), ring_view(p, (int)(s & 1), zb),
                                            cring(ring_view(p, 2, zb)), nx, ny, nz, lo, hi, src ? p->sx : -1, p->sy,
-                                           p->sz, src ? p->w[n] : 0.0f, sC));
+                                           p->sz, src && !p->src_uploaded ? p->w[n] : 0.0f, sC, tab));
                 }
                 st->kernel_launches++;
                 s += len;
@@ -451,6 +467,9 @@ ooc_status enqueue_steps(ooc_plan *p, int64_t nsteps, ooc_stats *st, int64_t *sl
         }
         st->passes++;
     }
+    // the plan's time on the device advances with the call (read by the
+    // table-driven source of the wave kernel)
+    OOC_CUDA(launch_add_time(dev_time(p), nsteps, sC));
     *slabs = g;
     return OOC_OK;
 }
@@ -660,6 +679,10 @@ ooc_status ooc_plan_bind(ooc_plan *p, void *device_arena, size_t device_bytes, v
     p->host = (char *)host_arena;
     for (int i = 0; i < 3; ++i)
         p->st[i] = (cudaStream_t)streams[i];
+    drop_graph(p);
+    p->src_uploaded = false;
+    if (cudaMemcpy(dev_time(p), &p->time, sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess)
+        return OOC_E_CUDA;
     p->bound = true;
     return OOC_OK;
 }
@@ -668,6 +691,8 @@ ooc_status ooc_set_source(ooc_plan *p, int64_t sx, int64_t sy, int64_t sz, const
 {
     if (!p || nw < 0 || (nw > 0 && !w))
         return OOC_E_INVALID;
+    drop_graph(p);
+    p->src_uploaded = false;
     if (nw == 0) {
         p->sx = p->sy = p->sz = -1;
         p->w.clear();
@@ -775,10 +800,18 @@ ooc_status ooc_step(ooc_plan *p, int64_t nsteps)
         return OOC_OK;
     const auto t_start = std::chrono::steady_clock::now();
     p->prof_used = 0;
-    // A call's launches depend only on nsteps for heat7 (the wave's source
-    // amplitudes follow the plan's time), so heat7 calls without per-launch
-    // profiling replay a captured graph.
-    const bool graphed = p->cfg.stencil == OOC_HEAT7 && !p->cfg.profile && p->cfg.graph_mode == 0;
+    // A call's launches depend only on nsteps (the wave's source amplitudes
+    // are read on the device from a table, at the device copy of the plan's
+    // time), so calls without per-launch profiling replay a captured graph.
+    const bool wave = p->cfg.stencil == OOC_WAVE25;
+    if (wave && p->sx >= 0 && !p->src_uploaded && (int64_t)p->w.size() <= kSrcTable) {
+        OOC_CUDA(cudaMemcpyAsync(dev_src(p), p->w.data(), p->w.size() * sizeof(float), cudaMemcpyHostToDevice,
+                                 p->st[1]));
+        OOC_CUDA(cudaStreamSynchronize(p->st[1]));
+        p->src_uploaded = true;
+        drop_graph(p);
+    }
+    const bool graphed = !p->cfg.profile && p->cfg.graph_mode == 0 && (!wave || p->sx < 0 || p->src_uploaded);
     if (graphed) {
         if (!p->graph || p->graph_nsteps != nsteps)
             OOC_TRY(capture_graph(p, nsteps));

@@ -418,7 +418,7 @@ template <int MODE>
 __global__ void __launch_bounds__(kTX *kWaveTY, 2)
     wave25_kernel(const float *__restrict__ pin, const float *pprev, float *pout, const float *__restrict__ kap, int nslot,
                   int64_t zbase, Grid3 g, int64_t z0, int64_t z1, int64_t zchunk, int64_t sx, int64_t sy, int64_t sz,
-                  float w, double *__restrict__ gsum)
+                  float w, double *__restrict__ gsum, WaveSrcTable tab)
 {
     constexpr int R = kWaveR;
     extern __shared__ __align__(16) unsigned char wave_smem[];
@@ -537,10 +537,15 @@ OOC_PRAGMA(unroll OOC_WAVE_UNROLL)
             for (int j = 0; j < 4; ++j)
                 o[j] = 2.0f * C[j] - PP[j] + KV[j] * lap[j];
             if (src_here && z == sz) {
+                float ws = w;
+                if (tab.w) {  // amplitude of step n = plan time + n_off, from the device table
+                    const int64_t n = *tab.t + tab.n_off;
+                    ws = n >= 0 && n < tab.nw ? tab.w[n] : 0.0f;
+                }
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
                     if (sx == x4 + j)
-                        o[j] += w;
+                        o[j] += ws;
             }
             if (inside)
                 *reinterpret_cast<float4 *>(pout + (int64_t)s * plane + off) = make_float4(o[0], o[1], o[2], o[3]);
@@ -598,6 +603,8 @@ int resident(const void *fn, int threads, size_t dyn_smem = 0)
         per_sm = 1;
     return per_sm * sms;
 }
+
+__global__ void add_time_kernel(int64_t *t, int64_t n) { *t += n; }
 
 __global__ void swap_kernel(float *a, float *b, int64_t n)
 {
@@ -668,7 +675,7 @@ cudaError_t launch_heat7_f64(const double *in, double *out, int64_t nx, int64_t 
 
 cudaError_t launch_wave25_to(ConstRing p, ConstRing pprev, Ring pnew, ConstRing kappa, int64_t nx, int64_t ny,
                              int64_t nz, int64_t z0, int64_t z1, int64_t sx, int64_t sy, int64_t sz, float w,
-                             cudaStream_t st)
+                             cudaStream_t st, WaveSrcTable tab)
 {
     if (z1 <= z0)
         return cudaSuccess;
@@ -687,7 +694,7 @@ cudaError_t launch_wave25_to(ConstRing p, ConstRing pprev, Ring pnew, ConstRing 
         return cudaErrorInvalidValue;
     wave25_kernel<0><<<dim3((unsigned)(gx * gy), (unsigned)gz), dim3(kTX, kWaveTY), sizeof(WaveSmem), st>>>(
         p.base, pprev.base, pnew.base, kappa.base, (int)p.nslot, p.zbase, Grid3{nx, ny, nz, nx * ny}, z0, z1, chunk,
-        sx, sy, sz, w, nullptr);
+        sx, sy, sz, w, nullptr, tab);
     return cudaGetLastError();
 }
 
@@ -707,15 +714,23 @@ cudaError_t launch_wave25_grad(const float *p, const float *mu, double *g, int64
     if (gx * gy > 0x7fffffffll || nz > (1ll << 30))
         return cudaErrorInvalidValue;
     wave25_kernel<1><<<dim3((unsigned)(gx * gy), (unsigned)gz), dim3(kTX, kWaveTY), sizeof(WaveSmem), st>>>(
-        p, mu, nullptr, nullptr, (int)nz, 0, Grid3{nx, ny, nz, nx * ny}, 0, nz, chunk, -1, -1, -1, 0.0f, g);
+        p, mu, nullptr, nullptr, (int)nz, 0, Grid3{nx, ny, nz, nx * ny}, 0, nz, chunk, -1, -1, -1, 0.0f, g,
+        WaveSrcTable{});
     return cudaGetLastError();
 }
 
 cudaError_t launch_wave25(ConstRing p, Ring pprev_out, ConstRing kappa, int64_t nx, int64_t ny, int64_t nz,
-                          int64_t z0, int64_t z1, int64_t sx, int64_t sy, int64_t sz, float w, cudaStream_t st)
+                          int64_t z0, int64_t z1, int64_t sx, int64_t sy, int64_t sz, float w, cudaStream_t st,
+                          WaveSrcTable tab)
 {
     return launch_wave25_to(p, ConstRing{pprev_out.base, pprev_out.nslot, pprev_out.zbase}, pprev_out, kappa, nx, ny,
-                            nz, z0, z1, sx, sy, sz, w, st);
+                            nz, z0, z1, sx, sy, sz, w, st, tab);
+}
+
+cudaError_t launch_add_time(int64_t *t, int64_t n, cudaStream_t st)
+{
+    add_time_kernel<<<1, 1, 0, st>>>(t, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_swap(float *a, float *b, int64_t n, cudaStream_t st)

@@ -357,3 +357,31 @@ def test_graph_replay_matches_direct_launches(ooc, fmt, rate):
     assert np.array_equal(out[0].view(np.uint32), out[1].view(np.uint32))
     ref = incore_heat(ooc, u0, [8, 8, 5, 8], 4, fmt, rate)
     assert np.array_equal(out[0].view(np.uint32), ref.view(np.uint32))
+
+
+def test_wave_graph_replay_with_source_matches_direct(ooc):
+    # wave plans replay graphs too: the source amplitude of each step is read
+    # on the device from a table at the device copy of the plan's time, so
+    # calls of 6, 6, 6, 4 steps (replays, then a recapture) inject the same
+    # amplitudes as direct launches and as the in-core reference
+    shape = (64, 20, 24)
+    kappa, p0, pm1, src, w = wave_inputs(shape, 22)
+    calls = [6, 6, 6, 4]
+    out = {}
+    for mode in (0, 1):
+        plan = ooc.Plan(nx=24, ny=20, nz=64, stencil="wave25", k=3, rw_format="fr4", rw_rate=16, ro_format="fp32",
+                        ro_rate=16, slab_planes=16, graph_mode=mode)
+        try:
+            plan.set_field(0, p0)
+            plan.set_field(1, pm1)
+            plan.set_field(2, kappa)
+            plan.set_source(*src, w)
+            for n in calls:
+                plan.step(n)
+            out[mode] = (plan.get_field(0), plan.get_field(1))
+        finally:
+            plan.close()
+    ref_p, ref_pp = incore_wave(ooc, p0, pm1, kappa, calls, 3, "fr4", 16, "fp32", 16, src, w)
+    for mode in (0, 1):
+        assert np.array_equal(out[mode][0].view(np.uint32), ref_p.view(np.uint32)), mode
+        assert np.array_equal(out[mode][1].view(np.uint32), ref_pp.view(np.uint32)), mode
