@@ -442,30 +442,49 @@ __device__ __forceinline__ void decode_block(const uint32_t *src, int nwords, in
         if (n < 64) {
             uint64_t X = 0ull;  // the plane's new ones
             for (;;) {
+                // The segments (group bit, scan) that end inside the next 32
+                // stream bits are parsed from one register, k bits in; the
+                // reader then advances once.  A segment that reaches past
+                // the window is parsed again from a fresh window, and from
+                // the long-scan path below when even that is too short.
                 const uint32_t wv = r.peek32();
-                if ((wv & 1u) == 0u) {  // group test: nothing more in this plane
-                    r.skip(1);
-                    break;
-                }
-                const int len = 63 - n;  // explicit scan bits at most (after the group bit)
-                const int m = len < 31 ? len : 31;
-                const uint32_t sc = (wv >> 1) & low_mask(m);
-                if (sc != 0u) {
-                    const int t = __ffs((int)sc) - 1;
-                    r.skip(t + 2);
-                    X |= 1ull << (n + t);
-                    n += t + 1;
-                    continue;
-                }
-                if (len <= 31) {  // whole scan zero: the last coefficient's one is implied
-                    if (r.pos + 1 + len <= budget) {
-                        X |= 1ull << 63;
-                        n = 64;
+                int k = 0;
+                int state = 0;  // 0: window used up; 1: plane done; 2: segment reaches past the window
+                while (k < 32) {
+                    const uint32_t w = wv >> k;
+                    if ((w & 1u) == 0u) {  // group test: nothing more in this plane
+                        ++k;
+                        state = 1;
+                        break;
                     }
-                    r.skip(1 + len);
+                    const int len = 63 - n;  // explicit scan bits at most (after the group bit)
+                    const uint32_t sc = w >> 1;  // the 31 - k scan bits inside the window
+                    const int t = __ffs((int)sc) - 1;
+                    if (sc != 0u && t < len) {
+                        X |= 1ull << (n + t);
+                        n += t + 1;
+                        k += t + 2;
+                        continue;
+                    }
+                    if (len <= 31 - k) {  // the len scan bits are zero: the last coefficient's one is implied
+                        if (r.pos + k + 1 + len <= budget) {
+                            X |= 1ull << 63;
+                            n = 64;
+                        }
+                        k += 1 + len;
+                        state = 1;
+                        break;
+                    }
+                    state = 2;
                     break;
                 }
-                // long scan whose first 31 bits are zero
+                r.skip(k);
+                if (state == 1)
+                    break;
+                if (state == 0 || k > 0)
+                    continue;
+                // long scan: group bit 1, then 31 zero bits of a scan of len > 31
+                const int len = 63 - n;
                 r.skip(32);
                 int done = 31;
                 bool found = false;
