@@ -21,6 +21,7 @@ method works on one GPU; there is no data-path collective).
 from __future__ import annotations
 
 import argparse
+import bisect
 import json
 import os
 import statistics
@@ -226,6 +227,43 @@ def timed_steps(torch, plan, nsteps, reps):
 SUB = slice(N // 2 - 64, N // 2 + 64)  # central 128^3 sub-box for the stated error
 
 
+def overlap_summary(tr):
+    """Per-operation breakdown of one profiled ooc_step call (Section VI-B,
+    Fig. 7) from its trace: the busy time of each stream, the overlap
+    efficiency (busiest stream / wall time of the call), and the compute
+    stream's idle time split by what it waited for: the H2D of the slab it
+    decodes next, or the D2H that frees the staging buffer it encodes into."""
+    if not tr:
+        return None
+    t0 = min(r["start_ms"] for r in tr)
+    wall = max(r["end_ms"] for r in tr) - t0
+    busy = {"h2d": 0.0, "d2h": 0.0, "compute": 0.0}
+    for r in tr:
+        busy["compute" if r["kind"] in ("decode", "stencil", "encode") else r["kind"]] += r["end_ms"] - r["start_ms"]
+    h2d_ends = sorted(r["end_ms"] for r in tr if r["kind"] == "h2d")
+    d2h_ends = sorted(r["end_ms"] for r in tr if r["kind"] == "d2h")
+
+    def near(ends, t, tol=0.02):
+        i = bisect.bisect_left(ends, t - tol)
+        return i < len(ends) and ends[i] <= t + tol
+
+    idle = {"waiting_h2d": 0.0, "waiting_d2h": 0.0, "other": 0.0}
+    prev = t0
+    for r in (r for r in tr if r["kind"] in ("decode", "stencil", "encode")):
+        gap = r["start_ms"] - prev
+        if gap > 0:
+            if r["kind"] == "decode" and near(h2d_ends, r["start_ms"]):
+                idle["waiting_h2d"] += gap
+            elif r["kind"] == "encode" and near(d2h_ends, r["start_ms"]):
+                idle["waiting_d2h"] += gap
+            else:
+                idle["other"] += gap
+        prev = r["end_ms"]
+    return {"call_ms": wall, "busy_ms": busy, "efficiency": max(busy.values()) / wall if wall > 0 else None,
+            "compute_idle_ms": idle,
+            "source": "ooc_plan_get_trace of the last profiled ooc_step call (one bench step, with CUDA events)"}
+
+
 def sub_box(field):
     return np.array(field[SUB, SUB, SUB], dtype=np.float64)
 
@@ -282,6 +320,7 @@ def run_gpu(args, world, rank, local):
         plan.set_profile(True)
         plan.reset_stats()
         ms_prof = timed_steps(torch, plan, NSTEPS, args.steps)
+        overlap = overlap_summary(plan.trace())
         plan.set_profile(False)
     torch.cuda.synchronize()
     barrier(world)
@@ -414,6 +453,7 @@ def run_gpu(args, world, rank, local):
                               "h2d_GBs_per_copy": h2d_GBs, "d2h_GBs_per_copy": d2h_GBs},
         "roofline": roofline,
         "kernels": kernels,
+        "overlap": overlap,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "Gpts/s", "h2d_bytes_per_step": int(h2d_step),
                 "d2h_bytes_per_step": int(d2h_step),

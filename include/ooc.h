@@ -325,6 +325,29 @@ ooc_status ooc_plan_set_profile(ooc_plan *plan, int profile);
 ooc_status ooc_get_stats(const ooc_plan *plan, ooc_stats *stats);
 ooc_status ooc_reset_stats(ooc_plan *plan);
 
+/* One timed interval of a profiled ooc_step call (the per-operation
+ * breakdown of Section VI-B, Fig. 7): a decode, a slab's group of stencil
+ * launches, an encode, or a slab's host-to-device or device-to-host copies. */
+#define OOC_TRACE_DECODE 0
+#define OOC_TRACE_STENCIL 1
+#define OOC_TRACE_ENCODE 2
+#define OOC_TRACE_H2D 3
+#define OOC_TRACE_D2H 4
+typedef struct {
+    int32_t kind;            /* OOC_TRACE_* */
+    int32_t count;           /* launches or copies inside the interval */
+    int64_t pass;            /* pass of the call, from 0 */
+    int64_t slab;            /* slab of the pass, from 0 */
+    double start_ms, end_ms; /* CUDA-event times from the start of the call's first interval */
+} ooc_trace_rec;
+
+/* Intervals of the last ooc_step call made with profile = 1, in the order
+ * they were enqueued (stream by stream they are in time order).  Copies
+ * min(*n, cap) records to out (out may be NULL when cap = 0) and sets *n to
+ * the number recorded; 0 when the last call was not profiled.  The plan
+ * owns the records until its next ooc_step. */
+ooc_status ooc_plan_get_trace(const ooc_plan *plan, ooc_trace_rec *out, int64_t cap, int64_t *n);
+
 /* Releases the plan's events and host bookkeeping (not the arenas). */
 void ooc_plan_destroy(ooc_plan *plan);
 

@@ -69,6 +69,14 @@ class OocPlanInfo(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class OocTraceRec(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("count", ctypes.c_int32), ("pass_", ctypes.c_int64),
+                ("slab", ctypes.c_int64), ("start_ms", ctypes.c_double), ("end_ms", ctypes.c_double)]
+
+
+TRACE_KINDS = ("decode", "stencil", "encode", "h2d", "d2h")
+
+
 class OocError(RuntimeError):
     def __init__(self, status, what):
         super().__init__(f"{what}: {ooc_status_string(status)} ({status})")
@@ -113,6 +121,8 @@ _SIGS = {
     "ooc_plan_set_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "ooc_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(OocStats)]),
     "ooc_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
+    "ooc_plan_get_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(OocTraceRec), ctypes.c_int64,
+                                          ctypes.POINTER(ctypes.c_int64)]),
     "ooc_plan_destroy": (None, [ctypes.c_void_p]),
     "ooc_heat7_steps_noalloc": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int64] * 3
                                 + [ctypes.c_double, ctypes.c_int64, ctypes.c_void_p]),
@@ -485,6 +495,16 @@ class Plan:
         s = OocStats()
         _check(lib().ooc_get_stats(self._h, ctypes.byref(s)), "ooc_get_stats")
         return s.as_dict()
+
+    def trace(self):
+        """Intervals of the last ooc_step made with profiling on: a list of
+        dicts (kind, count, pass, slab, start_ms, end_ms)."""
+        n = ctypes.c_int64()
+        _check(lib().ooc_plan_get_trace(self._h, None, 0, ctypes.byref(n)), "ooc_plan_get_trace")
+        recs = (OocTraceRec * max(n.value, 1))()
+        _check(lib().ooc_plan_get_trace(self._h, recs, n.value, ctypes.byref(n)), "ooc_plan_get_trace")
+        return [{"kind": TRACE_KINDS[r.kind], "count": r.count, "pass": r.pass_, "slab": r.slab,
+                 "start_ms": r.start_ms, "end_ms": r.end_ms} for r in recs[:n.value]]
 
     def reset_stats(self):
         _check(lib().ooc_reset_stats(self._h), "ooc_reset_stats")

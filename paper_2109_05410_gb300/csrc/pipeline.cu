@@ -55,6 +55,7 @@ struct ProfPair {
     cudaEvent_t a, b;
     int kind;   // 0 decode, 1 stencil, 2 encode, 3 h2d, 4 d2h
     int count;  // launches or copies between a and b
+    int64_t pass, slab;
 };
 
 }  // namespace
@@ -90,6 +91,8 @@ struct ooc_plan {
     cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr}, ev_done = nullptr;
     std::vector<ProfPair> prof;
     size_t prof_used = 0;
+    int64_t prof_pass = 0, prof_slab = 0;  // pass and slab being enqueued
+    std::vector<ooc_trace_rec> trace;      // intervals of the last profiled ooc_step
     // run state
     int64_t time = 0;
     int64_t sx = -1, sy = -1, sz = -1;
@@ -221,6 +224,8 @@ ooc_status prof_begin(ooc_plan *p, cudaStream_t st, int kind, size_t *idx)
     *idx = p->prof_used++;
     p->prof[*idx].kind = kind;
     p->prof[*idx].count = 1;
+    p->prof[*idx].pass = p->prof_pass;
+    p->prof[*idx].slab = p->prof_slab;
     return cudaEventRecord(p->prof[*idx].a, st) == cudaSuccess ? OOC_OK : OOC_E_CUDA;
 }
 
@@ -327,6 +332,8 @@ ooc_status enqueue_steps(ooc_plan *p, int64_t nsteps, ooc_stats *st, int64_t *sl
         for (int64_t i = 0; i < p->nslab; ++i, ++g) {
             const SlabGeom sg = slab_geom(p, i, Wp);
             const int e = (int)(g % kEv);
+            p->prof_pass = pass;
+            p->prof_slab = i;
             // ---- H2D: input units R_i and C_i (slab 0 also C_{-1}) -------------
             // FP32 fields land in the rings, whose slots slab g-2's D2H may
             // still read; staged fields land in staging buffer g&1, free
@@ -800,6 +807,7 @@ ooc_status ooc_step(ooc_plan *p, int64_t nsteps)
         return OOC_OK;
     const auto t_start = std::chrono::steady_clock::now();
     p->prof_used = 0;
+    p->trace.clear();
     // A call's launches depend only on nsteps (the wave's source amplitudes
     // are read on the device from a table, at the device copy of the plan's
     // time), so calls without per-launch profiling replay a captured graph.
@@ -829,9 +837,18 @@ ooc_status ooc_step(ooc_plan *p, int64_t nsteps)
     p->time += nsteps;
     p->stats.steps_done += nsteps;
     if (p->cfg.profile) {
+        try {
+            p->trace.reserve(p->prof_used);
+        } catch (...) {
+            return OOC_E_ALLOC;
+        }
         for (size_t j = 0; j < p->prof_used; ++j) {
-            float ms = 0.0f;
+            float ms = 0.0f, t0 = 0.0f, t1 = 0.0f;
             OOC_CUDA(cudaEventElapsedTime(&ms, p->prof[j].a, p->prof[j].b));
+            OOC_CUDA(cudaEventElapsedTime(&t0, p->prof[0].a, p->prof[j].a));
+            OOC_CUDA(cudaEventElapsedTime(&t1, p->prof[0].a, p->prof[j].b));
+            p->trace.push_back(ooc_trace_rec{p->prof[j].kind, p->prof[j].count, p->prof[j].pass, p->prof[j].slab,
+                                             (double)t0, (double)t1});
             switch (p->prof[j].kind) {
             case 0: p->stats.ms_decode += ms; p->stats.n_decode++; break;
             case 1: p->stats.ms_stencil += ms; p->stats.n_stencil += p->prof[j].count; break;
@@ -869,6 +886,17 @@ ooc_status ooc_plan_set_wait_timeout(ooc_plan *p, int64_t wait_timeout_ms)
     if (!p || wait_timeout_ms < 0)
         return OOC_E_INVALID;
     p->cfg.wait_timeout_ms = wait_timeout_ms;
+    return OOC_OK;
+}
+
+ooc_status ooc_plan_get_trace(const ooc_plan *p, ooc_trace_rec *out, int64_t cap, int64_t *n)
+{
+    if (!p || !n || cap < 0 || (cap > 0 && !out))
+        return OOC_E_INVALID;
+    const int64_t have = (int64_t)p->trace.size();
+    for (int64_t j = 0; j < have && j < cap; ++j)
+        out[j] = p->trace[(size_t)j];
+    *n = have;
     return OOC_OK;
 }
 

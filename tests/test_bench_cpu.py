@@ -71,3 +71,29 @@ def test_max_over_ranks_gloo_world2():
     res = sorted(q.get(timeout=10) for _ in range(2))
     assert res == [(0, 11.0), (1, 11.0)]
     assert all(p.exitcode == 0 for p in procs)
+
+
+def test_overlap_summary_attributes_compute_idle_time():
+    # Two slabs of a hand-made trace: the compute stream waits 1 ms for the
+    # first H2D, 0.5 ms for the D2H before the second encode, and 0.1 ms for
+    # nothing it can name; the compute stream is the busiest.
+    sys.path.insert(0, ROOT)
+    import bench
+    tr = [
+        {"kind": "h2d", "count": 1, "pass": 0, "slab": 0, "start_ms": 0.0, "end_ms": 1.0},
+        {"kind": "decode", "count": 1, "pass": 0, "slab": 0, "start_ms": 1.0, "end_ms": 1.5},
+        {"kind": "stencil", "count": 4, "pass": 0, "slab": 0, "start_ms": 1.6, "end_ms": 3.0},
+        {"kind": "encode", "count": 1, "pass": 0, "slab": 0, "start_ms": 3.0, "end_ms": 3.5},
+        {"kind": "d2h", "count": 1, "pass": 0, "slab": 0, "start_ms": 3.5, "end_ms": 6.5},
+        {"kind": "h2d", "count": 1, "pass": 0, "slab": 1, "start_ms": 1.0, "end_ms": 2.0},
+        {"kind": "decode", "count": 1, "pass": 0, "slab": 1, "start_ms": 3.5, "end_ms": 4.0},
+        {"kind": "stencil", "count": 4, "pass": 0, "slab": 1, "start_ms": 4.0, "end_ms": 6.0},
+        {"kind": "encode", "count": 1, "pass": 0, "slab": 1, "start_ms": 6.5, "end_ms": 7.0},
+        {"kind": "d2h", "count": 1, "pass": 0, "slab": 1, "start_ms": 7.0, "end_ms": 8.0},
+    ]
+    o = bench.overlap_summary(tr)
+    assert o["call_ms"] == pytest.approx(8.0)
+    assert o["busy_ms"] == pytest.approx({"h2d": 2.0, "d2h": 4.0, "compute": 5.4})
+    assert o["efficiency"] == pytest.approx(5.4 / 8.0)
+    assert o["compute_idle_ms"] == pytest.approx({"waiting_h2d": 1.0, "waiting_d2h": 0.5, "other": 0.1})
+    assert bench.overlap_summary([]) is None

@@ -385,3 +385,51 @@ def test_wave_graph_replay_with_source_matches_direct(ooc):
     for mode in (0, 1):
         assert np.array_equal(out[mode][0].view(np.uint32), ref_p.view(np.uint32)), mode
         assert np.array_equal(out[mode][1].view(np.uint32), ref_pp.view(np.uint32)), mode
+
+
+@pytest.mark.parametrize("fmt,rate", [("fr4", 16), ("fp32", 16), ("bf16", 16)])
+def test_profiled_trace_follows_each_slab_stages(ooc, fmt, rate):
+    # With profiling on, ooc_plan_get_trace returns the intervals of the last
+    # call: every slab's stages run in dependency order (H2D -> decode ->
+    # stencil launches -> encode -> D2H), each stream's intervals are in time
+    # order, the counts match ooc_get_stats, and the bits match direct runs.
+    shape = (48, 40, 36)
+    u0 = smooth_random_field(shape, 5.0, seed=33)
+    plan = ooc.Plan(nx=36, ny=40, nz=48, stencil="heat7", k=4, rw_format=fmt, rw_rate=rate, slab_planes=12,
+                    profile=1)
+    try:
+        plan.set_field(0, u0)
+        plan.step(8)
+        plan.reset_stats()
+        plan.step(6)
+        tr = plan.trace()
+        st = plan.stats()
+        got = plan.get_field(0)
+        plan.set_profile(False)
+        plan.step(4)
+        assert plan.trace() == []
+    finally:
+        plan.close()
+    assert tr and {r["pass"] for r in tr} == {0, 1} and {r["slab"] for r in tr} == {0, 1, 2, 3}
+    by = {}
+    for r in tr:
+        assert r["end_ms"] >= r["start_ms"] >= -1e-3
+        by.setdefault(r["kind"], []).append(r)
+    assert len(by.get("decode", [])) == st["n_decode"] and len(by.get("encode", [])) == st["n_encode"]
+    assert len(by["h2d"]) == st["n_h2d"] and len(by["d2h"]) == st["n_d2h"]
+    assert sum(r["count"] for r in by["stencil"]) == st["n_stencil"] == 4 * 4 + 4 * 2
+    staged = fmt != "fp32"
+    assert ("decode" in by) == staged and ("encode" in by) == staged
+    eps = 2e-3  # event timestamps are good to about a microsecond
+    for stream in (("h2d",), ("decode", "stencil", "encode"), ("d2h",)):
+        seq = [r for r in tr if r["kind"] in stream]
+        for a, b in zip(seq, seq[1:]):
+            assert b["start_ms"] >= a["end_ms"] - eps, (a, b)
+    order = ("h2d", "decode", "stencil", "encode", "d2h")
+    for ps in {(r["pass"], r["slab"]) for r in tr}:
+        stages = {r["kind"]: r for r in tr if (r["pass"], r["slab"]) == ps}
+        present = [k for k in order if k in stages]
+        for a, b in zip(present, present[1:]):
+            assert stages[b]["start_ms"] >= stages[a]["end_ms"] - eps, (ps, a, b)
+    ref = incore_heat(ooc, u0, [8, 6], 4, fmt, rate)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))

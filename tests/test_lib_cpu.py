@@ -138,3 +138,24 @@ def test_wave_plan_geometry(L):
     assert s == 0
     assert info["halo"] == 4 and info["common_planes"] == 40 and info["nrings"] == 3
     assert host == 3 * 128 ** 3 * 2
+
+
+def test_trace_of_an_unstepped_plan_is_empty(L):
+    # ooc_plan_get_trace: no profiled ooc_step yet, so no records; argument
+    # errors are refused without touching the plan.
+    c = make_cfg(slab_planes=8)
+    h = ctypes.c_void_p()
+    d, hb = ctypes.c_size_t(), ctypes.c_size_t()
+    assert L.ooc_plan_create(ctypes.byref(c), ctypes.byref(h), ctypes.byref(d), ctypes.byref(hb)) == 0
+    try:
+        n = ctypes.c_int64(-7)
+        assert L.ooc_plan_get_trace(h, None, 0, ctypes.byref(n)) == 0 and n.value == 0
+        recs = (ooc.OocTraceRec * 4)()
+        assert L.ooc_plan_get_trace(h, recs, 4, ctypes.byref(n)) == 0 and n.value == 0
+        assert L.ooc_plan_get_trace(h, None, 4, ctypes.byref(n)) == 1
+        assert L.ooc_plan_get_trace(h, recs, -1, ctypes.byref(n)) == 1
+        assert L.ooc_plan_get_trace(h, recs, 4, None) == 1
+        assert L.ooc_plan_get_trace(None, recs, 4, ctypes.byref(n)) == 1
+    finally:
+        L.ooc_plan_destroy(h)
+    assert ctypes.sizeof(ooc.OocTraceRec) == 40
