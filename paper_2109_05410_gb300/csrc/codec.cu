@@ -438,7 +438,7 @@ __device__ __forceinline__ void decode_block(const uint32_t *src, int nwords, in
     for (; p >= pmin && r.pos < budget; --p) {
         const int n1 = n < 32 ? n : 32;
         uint32_t xl = r.get(n1);
-        uint32_t xh = r.get(n - n1);
+        uint32_t xh = n > 32 ? r.get(n - 32) : 0u;
         if (n < 64) {
             uint64_t X = 0ull;  // the plane's new ones
             for (;;) {
@@ -579,6 +579,24 @@ __global__ void __launch_bounds__(kThreads) fr4_encode_kernel(ConstRing in, int6
     const int64_t left = nblk - first;
     const int nvalid = left < kThreads ? (int)left : kThreads;
     uint32_t *dst = out + first * words;
+    if ((words & 3) == 0 && ((uintptr_t)out & 15) == 0) {
+        // 16-byte stores: chunk c of the CTA's output is words 4 (c mod q) ..
+        // of block c / q, q = words / 4; c advances by kThreads
+        const int q = words >> 2;
+        int blk = threadIdx.x / q, ch = threadIdx.x - blk * q;
+        const int step_blk = kThreads / q, step_ch = kThreads - step_blk * q;
+        for (int c = threadIdx.x; c < nvalid * q; c += kThreads) {
+            const uint32_t *w = smem + blk * stride + 4 * ch;
+            reinterpret_cast<uint4 *>(dst)[c] = make_uint4(w[0], w[1], w[2], w[3]);
+            blk += step_blk;
+            ch += step_ch;
+            if (ch >= q) {
+                ch -= q;
+                ++blk;
+            }
+        }
+        return;
+    }
     // word o of the CTA's output is word (o mod words) of block (o / words);
     // o advances by kThreads, so block and word advance incrementally
     int blk = threadIdx.x / words, wd = threadIdx.x - blk * words;
