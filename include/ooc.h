@@ -42,7 +42,7 @@ typedef int ooc_status;
 #define OOC_E_ALLOC 3    /* host-side bookkeeping allocation failed */
 #define OOC_E_CUDA 4     /* a CUDA runtime call or kernel launch failed */
 #define OOC_E_TIMEOUT 5  /* a bounded wait on the GPU ran past its deadline */
-#define OOC_E_CORRUPT 6  /* inconsistent stored data (e.g. non-finite values) */
+#define OOC_E_CORRUPT 6  /* inconsistent stored data, or a failed debug check (debug_checks) */
 
 /* Stencils (Section III's neighbour average; Section VI's 25-point
  * acoustic propagator with HALO = 4, Table I). */
@@ -77,6 +77,10 @@ typedef struct {
                                       chip.  Results are bit-identical.  wave25: 0 or 1. */
     int32_t graph_mode;          /* 0 = heat7 calls without profiling are captured once per distinct
                                     nsteps as a CUDA graph and replayed; 1 = always launch directly */
+    int32_t debug_checks;        /* 1 = guard words after every region of the device arena, checked on
+                                    the device after each ooc_step / ooc_set_field / ooc_get_field,
+                                    and host checks of every launch's plane window and every copy's
+                                    byte range; a failure returns OOC_E_CORRUPT.  0 = off */
 } ooc_config;
 
 typedef struct ooc_plan ooc_plan;

@@ -42,6 +42,7 @@ class OocConfig(ctypes.Structure):
         ("device_budget_bytes", ctypes.c_int64), ("slab_planes", ctypes.c_int32),
         ("profile", ctypes.c_int32), ("wait_timeout_ms", ctypes.c_int64),
         ("heat_steps_per_launch", ctypes.c_int32), ("graph_mode", ctypes.c_int32),
+        ("debug_checks", ctypes.c_int32),
     ]
 
 
@@ -425,7 +426,7 @@ class Plan:
     streams (H2D, compute, D2H).  Configuration keys mirror ``ooc_config``:
     nx, ny, nz, stencil ('heat7'|'wave25'), k, r, rw_format, rw_rate,
     ro_format, ro_rate, device_budget_bytes, slab_planes, profile,
-    wait_timeout_ms, heat_steps_per_launch, graph_mode."""
+    wait_timeout_ms, heat_steps_per_launch, graph_mode, debug_checks."""
 
     def __init__(self, device=0, **kw):
         import torch
@@ -445,6 +446,7 @@ class Plan:
         c.wait_timeout_ms = kw.get("wait_timeout_ms", 0)
         c.heat_steps_per_launch = int(kw.get("heat_steps_per_launch", 0))
         c.graph_mode = int(kw.get("graph_mode", 0))
+        c.debug_checks = int(kw.get("debug_checks", 0))
         self.config = c
         self.shape = (c.nz, c.ny, c.nx)
         self._h = ctypes.c_void_p()

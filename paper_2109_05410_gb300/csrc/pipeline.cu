@@ -38,6 +38,25 @@ namespace {
 
 constexpr int kEv = 4;  // event ring depth (waits look back at most 2 slabs)
 constexpr int64_t kSrcTable = 16384;  // source amplitudes kept on the device (graph replay)
+constexpr size_t kGuard = 256;        // guard bytes after each arena region (debug_checks)
+constexpr int kMaxGuards = 32;
+constexpr unsigned char kGuardByte = 0xA5;
+
+struct GuardList {
+    uint64_t off[kMaxGuards];
+    int n;
+};
+
+// Sets *flag when a guard region no longer holds kGuardByte in every byte
+// (one CTA of 64 threads per region, one 32-bit word each).
+__global__ void check_guards_kernel(const unsigned char *base, GuardList g, int *flag)
+{
+    for (int i = blockIdx.x; i < g.n; i += gridDim.x) {
+        const uint32_t w = reinterpret_cast<const uint32_t *>(base + g.off[i])[threadIdx.x];
+        if (w != 0xA5A5A5A5u)
+            atomicOr(flag, 1);
+    }
+}
 
 int64_t round4(int64_t v) { return (v + 3) / 4 * 4; }
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
@@ -93,6 +112,9 @@ struct ooc_plan {
     size_t prof_used = 0;
     int64_t prof_pass = 0, prof_slab = 0;  // pass and slab being enqueued
     std::vector<ooc_trace_rec> trace;      // intervals of the last profiled ooc_step
+    // debug_checks: arena offsets of the guard regions, and of the device flag
+    std::vector<size_t> guards;
+    size_t off_flag = 0;
     // run state
     int64_t time = 0;
     int64_t sx = -1, sy = -1, sz = -1;
@@ -119,10 +141,19 @@ size_t layout(ooc_plan *p, int64_t T)
         direct |= !staged(p, f);
     const int64_t Z = round4((direct ? 2 * T : T) + W + 2 * h);
     size_t off = 0;
+    const bool dbg = p->cfg.debug_checks != 0;
+    p->guards.clear();
+    auto guard = [&]() {
+        if (dbg) {
+            p->guards.push_back(off);
+            off += kGuard;
+        }
+    };
     const size_t ring_bytes = (size_t)Z * p->plane_elems * sizeof(float);
     for (int r = 0; r < p->nring; ++r) {
         p->off_ring[r] = off;
         off += align256(ring_bytes);
+        guard();
     }
     for (int f = 0; f < p->nfield; ++f) {
         p->in_bytes_field[f] = staged(p, f) ? (size_t)(T + W) * p->fplane[f] : 0;
@@ -132,17 +163,28 @@ size_t layout(ooc_plan *p, int64_t T)
         for (int f = 0; f < p->nfield; ++f) {
             p->off_in[b][f] = off;
             off += align256(p->in_bytes_field[f]);
+            if (p->in_bytes_field[f] > 0)
+                guard();
             p->off_out[b][f] = off;
             off += align256(p->out_bytes_field[f]);
+            if (p->out_bytes_field[f] > 0)
+                guard();
         }
     // Fused heat7 pairs: the intermediate level's top 2h planes of each slab,
     // for the next slab; one band per pair of the pass and slab parity.
     p->off_band = off;
     p->band_bytes = p->spl == 2 ? (size_t)(2 * h) * p->plane_elems * sizeof(float) : 0;
     off += align256(p->band_bytes) * 2 * (size_t)(p->cfg.k / 2);
+    if (p->band_bytes > 0)
+        guard();
     // the plan's time on the device, then the wave's source amplitudes
     p->off_src = off;
     off += 256 + (p->cfg.stencil == OOC_WAVE25 ? align256(kSrcTable * sizeof(float)) : 0);
+    guard();
+    if (dbg) {
+        p->off_flag = off;  // the guard checks' flag
+        off += 256;
+    }
     (void)any_staged;
     p->Z = Z;
     return off;
@@ -203,6 +245,25 @@ ooc_status wait_event(ooc_plan *p, cudaEvent_t ev)
             return OOC_E_TIMEOUT;
         std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
+}
+
+// debug_checks: every guard region back to kGuardByte and the flag to 0.
+ooc_status arm_guards(ooc_plan *p)
+{
+    if (!p->cfg.debug_checks)
+        return OOC_OK;
+    for (size_t off : p->guards)
+        if (cudaMemset(p->dev + off, kGuardByte, kGuard) != cudaSuccess)
+            return OOC_E_CUDA;
+    return cudaMemset(p->dev + p->off_flag, 0, sizeof(int)) == cudaSuccess ? OOC_OK : OOC_E_CUDA;
+}
+
+ooc_status check_guards(ooc_plan *p);
+
+// Host-side debug check of an internal invariant.
+inline ooc_status expect(const ooc_plan *p, bool ok)
+{
+    return (!p->cfg.debug_checks || ok) ? OOC_OK : OOC_E_CORRUPT;
 }
 
 ooc_status prof_begin(ooc_plan *p, cudaStream_t st, int kind, size_t *idx)
@@ -360,6 +421,11 @@ ooc_status enqueue_steps(ooc_plan *p, int64_t nsteps, ooc_stats *st, int64_t *sl
                 for (int f = 0; f < p->nfield; ++f) {
                     char *src = p->host + p->off_host[f] + (size_t)sg.in_lo * p->fplane[f];
                     const size_t nb = (size_t)(sg.in_hi - sg.in_lo) * p->fplane[f];
+                    // the units lie in the field's host image, 4-aligned, and
+                    // fit the staging buffer (FP32: the ring)
+                    OOC_TRY(expect(p, sg.in_lo >= 0 && sg.in_hi <= nz && sg.in_lo % 4 == 0 && sg.in_hi % 4 == 0 &&
+                                          (staged(p, f) ? nb <= p->in_bytes_field[f]
+                                                        : sg.in_hi - sg.in_lo <= p->Z)));
                     if (staged(p, f))
                         OOC_CUDA(cudaMemcpyAsync(p->dev + p->off_in[g & 1][f], src, nb, cudaMemcpyHostToDevice, sH));
                     else
@@ -398,6 +464,9 @@ ooc_status enqueue_steps(ooc_plan *p, int64_t nsteps, ooc_stats *st, int64_t *sl
                     s += len;
                     continue;
                 }
+                // the planes a launch reads (h beyond its window on each side)
+                // and the 2h below it that the next level needs fit the ring
+                OOC_TRY(expect(p, lo >= 0 && hi <= nz && (hi - lo) + 2 * p->h <= p->Z));
                 if (nst++ == 0)
                     OOC_TRY(prof_begin(p, sC, 1, &pst));
                 if (!wave && len == 2) {
@@ -444,6 +513,8 @@ ooc_status enqueue_steps(ooc_plan *p, int64_t nsteps, ooc_stats *st, int64_t *sl
             for (int f = 0; f < p->nrw; ++f) {
                 if (!staged(p, f))
                     continue;
+                OOC_TRY(expect(p, sg.a % 4 == 0 && sg.b % 4 == 0 && sg.b <= nz &&
+                                      (size_t)(sg.b - sg.a) * p->fplane[f] <= p->out_bytes_field[f]));
                 size_t pi;
                 OOC_TRY(prof_begin(p, sC, 2, &pi));
                 OOC_TRY(encode_from(p, f, cring(ring_view(p, output_ring(p, f, kp), zb)),
@@ -491,6 +562,28 @@ ooc_status ensure_graph_events(ooc_plan *p)
         cudaEventCreateWithFlags(&p->ev_done, cudaEventDisableTiming) != cudaSuccess)
         return OOC_E_CUDA;
     return OOC_OK;
+}
+
+ooc_status check_guards(ooc_plan *p)
+{
+    if (!p->cfg.debug_checks)
+        return OOC_OK;
+    GuardList g{};
+    if (p->guards.size() > (size_t)kMaxGuards)
+        return OOC_E_INVALID;
+    g.n = (int)p->guards.size();
+    for (int i = 0; i < g.n; ++i)
+        g.off[i] = p->guards[(size_t)i];
+    OOC_TRY(ensure_graph_events(p));
+    cudaStream_t sC = p->st[1];
+    check_guards_kernel<<<g.n, (unsigned)(kGuard / 4), 0, sC>>>((const unsigned char *)p->dev, g,
+                                                                 (int *)(p->dev + p->off_flag));
+    OOC_CUDA(cudaGetLastError());
+    OOC_CUDA(cudaEventRecord(p->ev_done, sC));
+    OOC_TRY(wait_event(p, p->ev_done));
+    int flag = 0;
+    OOC_CUDA(cudaMemcpy(&flag, p->dev + p->off_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    return flag ? OOC_E_CORRUPT : OOC_OK;
 }
 
 void drop_graph(ooc_plan *p)
@@ -690,6 +783,7 @@ ooc_status ooc_plan_bind(ooc_plan *p, void *device_arena, size_t device_bytes, v
     p->src_uploaded = false;
     if (cudaMemcpy(dev_time(p), &p->time, sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess)
         return OOC_E_CUDA;
+    OOC_TRY(arm_guards(p));
     p->bound = true;
     return OOC_OK;
 }
@@ -757,7 +851,7 @@ ooc_status ooc_set_field(ooc_plan *p, int field, const float *host_src)
         OOC_CUDA(cudaEventRecord(p->ev_d2h[e], sD));
     }
     OOC_TRY(wait_event(p, p->ev_d2h[(j - 1) % kEv]));
-    return OOC_OK;
+    return check_guards(p);
 }
 
 ooc_status ooc_get_field(ooc_plan *p, int field, float *host_dst)
@@ -796,7 +890,7 @@ ooc_status ooc_get_field(ooc_plan *p, int field, float *host_dst)
         OOC_CUDA(cudaEventRecord(p->ev_d2h[e], sD));
     }
     OOC_TRY(wait_event(p, p->ev_d2h[(j - 1) % kEv]));
-    return OOC_OK;
+    return check_guards(p);
 }
 
 ooc_status ooc_step(ooc_plan *p, int64_t nsteps)
@@ -860,7 +954,7 @@ ooc_status ooc_step(ooc_plan *p, int64_t nsteps)
     }
     p->stats.ms_last_step =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
-    return OOC_OK;
+    return check_guards(p);
 }
 
 ooc_status ooc_get_stats(const ooc_plan *p, ooc_stats *s)

@@ -433,3 +433,69 @@ def test_profiled_trace_follows_each_slab_stages(ooc, fmt, rate):
             assert stages[b]["start_ms"] >= stages[a]["end_ms"] - eps, (ps, a, b)
     ref = incore_heat(ooc, u0, [8, 6], 4, fmt, rate)
     assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+
+
+@pytest.mark.parametrize("fmt,rate", [("fr4", 16), ("fp32", 16)])
+def test_debug_checks_pass_and_keep_the_bits(ooc, fmt, rate):
+    # debug_checks = 1: guard bytes after every arena region stay intact and
+    # every launch window and copy range passes its host check over ragged
+    # slabs, a short last pass and set/get; the bits are those of the in-core
+    # reference.
+    shape = (48, 40, 36)
+    u0 = smooth_random_field(shape, 5.0, seed=35)
+    plan = ooc.Plan(nx=36, ny=40, nz=48, stencil="heat7", k=4, rw_format=fmt, rw_rate=rate, slab_planes=12,
+                    debug_checks=1)
+    try:
+        plan.set_field(0, u0)
+        plan.step(8)
+        plan.step(6)
+        got = plan.get_field(0)
+    finally:
+        plan.close()
+    ref = incore_heat(ooc, u0, [8, 6], 4, fmt, rate)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+
+
+def test_debug_checks_wave_fields(ooc):
+    shape = (64, 20, 24)
+    kappa, p0, pm1, src, w = wave_inputs(shape, 12)
+    plan = ooc.Plan(nx=24, ny=20, nz=64, stencil="wave25", k=3, rw_format="fr4", rw_rate=16, ro_format="fr4",
+                    ro_rate=16, slab_planes=16, debug_checks=1)
+    try:
+        plan.set_field(0, p0)
+        plan.set_field(1, pm1)
+        plan.set_field(2, kappa)
+        plan.set_source(*src, w)
+        plan.step(6)
+        plan.step(4)
+        got = (plan.get_field(0), plan.get_field(1))
+    finally:
+        plan.close()
+    ref_p, ref_pp = incore_wave(ooc, p0, pm1, kappa, [6, 4], 3, "fr4", 16, "fr4", 16, src, w)
+    assert np.array_equal(got[0].view(np.uint32), ref_p.view(np.uint32))
+    assert np.array_equal(got[1].view(np.uint32), ref_pp.view(np.uint32))
+
+
+def test_debug_guard_overwrite_is_reported(ooc):
+    # A byte of the guard that follows ring 0, overwritten here on purpose
+    # from the host side (an in-bounds write to the caller's arena), makes
+    # the next call return OOC_E_CORRUPT.
+    nx, ny, nz = 36, 40, 48
+    u0 = smooth_random_field((nz, ny, nx), 5.0, seed=36)
+    plan = ooc.Plan(nx=nx, ny=ny, nz=nz, stencil="heat7", k=4, rw_format="fr4", rw_rate=16, slab_planes=12,
+                    debug_checks=1)
+    try:
+        plan.set_field(0, u0)
+        plan.step(4)
+        ring_bytes = plan.info()["ring_planes"] * nx * ny * 4
+        guard0 = (ring_bytes + 255) // 256 * 256
+        assert guard0 + 256 <= plan.dev_arena.numel()
+        with torch.cuda.stream(plan.streams[1]):
+            plan.dev_arena[guard0 + 17] = 0
+        torch.cuda.synchronize()
+        with pytest.raises(ooc.OocError) as e:
+            plan.step(4)
+        assert e.value.status == 6
+    finally:
+        torch.cuda.synchronize()
+        plan.close()

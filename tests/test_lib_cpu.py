@@ -62,6 +62,7 @@ def make_cfg(**kw):
     c.device_budget_bytes = kw.get("budget", 0)
     c.slab_planes = kw.get("slab_planes", 0)
     c.heat_steps_per_launch = kw.get("spl", 0)
+    c.debug_checks = kw.get("debug", 0)
     return c
 
 
@@ -159,3 +160,21 @@ def test_trace_of_an_unstepped_plan_is_empty(L):
     finally:
         L.ooc_plan_destroy(h)
     assert ctypes.sizeof(ooc.OocTraceRec) == 40
+
+
+def test_debug_checks_add_guard_regions(L):
+    # debug_checks = 1 puts 256 guard bytes after every arena region (each
+    # ring, each nonempty staging buffer, the fused-pair bands, the time and
+    # source slot) plus a 256-byte flag; the geometry is otherwise the same.
+    cases = [
+        (dict(slab_planes=16), 2 + 4 + 1),                                      # heat7 FR4
+        (dict(slab_planes=16, rw_format=ooc.OOC_FMT_FP32), 2 + 1),               # FP32: no staging
+        (dict(slab_planes=16, spl=2, k=4), 2 + 4 + 1 + 1),                       # fused pairs: bands
+        (dict(slab_planes=32, stencil=ooc.OOC_WAVE25, k=2, ro_format=ooc.OOC_FMT_FR4), 3 + 2 * (3 + 2) + 1),
+    ]
+    for kw, nguard in cases:
+        s0, d0, h0, i0 = plan_create(L, make_cfg(**kw))
+        s1, d1, h1, i1 = plan_create(L, make_cfg(debug=1, **kw))
+        assert s0 == 0 and s1 == 0, kw
+        assert d1 - d0 == 256 * (nguard + 1), (kw, d1 - d0)
+        assert h1 == h0 and i1["slab_planes"] == i0["slab_planes"] and i1["ring_planes"] == i0["ring_planes"]
