@@ -175,3 +175,57 @@ def test_storage_pipeline_error_ordering():
         errs[(fmt, rate)] = oracle.error_metrics(u, exact)["rel_l2"]
     assert errs[("fp32", 0)] < 1e-6
     assert errs[("fp32", 0)] < errs[("fr4", 24)] < errs[("fr4", 16)] < errs[("fr4", 8)]
+
+
+def _paper():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_setup.json")
+    return {k: v["value"] for k, v in json.load(open(path))["items"].items()}
+
+
+def test_wave25_footprint_is_table_I_stencil():
+    # Table I and Section VI: a 25-point stencil with HALO = 4.  One oracle
+    # step from a unit impulse (p^{n-1} = 0, kappa = 1) changes exactly the
+    # 1 + 6 HALO points on the three axes through it, none farther than HALO.
+    P = _paper()
+    h = P["table1_halo"]
+    n = 2 * h + 5
+    p = np.zeros((n, n, n))
+    c = n // 2
+    p[c, c, c] = 1.0
+    q, _ = oracle.wave25_run(p, np.zeros_like(p), np.ones_like(p), 1)
+    nzp = np.argwhere(q != 0.0) - c
+    assert len(nzp) == P["stencil_points"] == 1 + 6 * h
+    assert np.abs(nzp).max() == h
+    assert all(np.count_nonzero(o) <= 1 for o in nzp)  # on an axis through the impulse
+
+
+def test_table_I_sizes_and_schedule():
+    # Table I's 46 GB lies between 4 double datasets of the 1152^3 interior
+    # (45.6 GiB) and of the (1152 + 2 HALO)^3 padded grid (46.5 GiB); the
+    # steps 480..4320 are whole multiples of the temporal block 12, and the
+    # padded side splits into the 8 divisions.
+    P = _paper()
+    side = P["table1_interior_side"] + 2 * P["table1_halo"]
+    per_point = P["table1_datasets"] * P["table1_data_type_bytes"]
+    inner = per_point * P["table1_interior_side"] ** 3 / 2 ** 30
+    padded = per_point * side ** 3 / 2 ** 30
+    assert inner <= P["table1_entire_size_gb"] <= padded < P["table1_entire_size_gb"] + 1
+    steps = range(P["total_steps_first"], P["total_steps_last"] + 1, P["total_steps_increment"])
+    assert len(steps) == 9 and all(s % P["temporal_block_steps"] == 0 for s in steps)
+    assert side % P["divisions"] == 0  # 8 slabs of 145 planes
+
+
+def test_paper_rates_are_fr4_rates_for_float():
+    # The codes keep 32 or 24 of 64 bits per double (ratios 2 and 8/3); on
+    # 32-bit floats the same ratios are FR4 at R = 16 and R = 12, and the
+    # oracle's stream has exactly that size.
+    P = _paper()
+    shape = (8, 8, 8)
+    fp32 = 8 * 8 * 8 * 4
+    for bits in (P["code2_rw_bits_per_double"], P["code4_bits_per_double"]):
+        ratio = 64 / bits
+        rate = int(round(32 / ratio))
+        x = np.random.default_rng(bits).normal(size=shape).astype(np.float32)
+        assert oracle.fr4_encode(x, rate).nbytes * ratio == fp32
