@@ -612,9 +612,12 @@ __global__ void __launch_bounds__(kThreads) fr4_encode_kernel(ConstRing in, int6
     }
 }
 
-// 6 CTAs per SM (80 registers): measured faster than 5 CTAs at 96 registers
-// (R = 16 decode of 1024^3: 4.93 against 5.17 ms).
-__global__ void __launch_bounds__(kThreads, 6) fr4_decode_kernel(const uint32_t *__restrict__ in, int64_t nx, int64_t ny,
+// MINB CTAs per SM: 6 (80 registers) for rates up to 16, 5 (96 registers,
+// more L1 beside the plane masks) above.  1024^3 decode, 6 against 5:
+// R = 8 3.35 against 3.60 ms, R = 16 4.19 against 4.30, R = 24 4.90
+// against 4.59.
+template <int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) fr4_decode_kernel(const uint32_t *__restrict__ in, int64_t nx, int64_t ny,
                                                              int64_t z0, int64_t nblk, int rate, Ring out)
 {
     extern __shared__ uint32_t smem[];  // each thread's plane masks
@@ -865,7 +868,10 @@ cudaError_t ensure_smem_attr()
     cudaError_t e = cudaFuncSetAttribute(fr4_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_bytes(64, true));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fr4_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(fr4_decode_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_bytes(64, false));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fr4_decode_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem_bytes(64, false));
     if (e == cudaSuccess)
         done = true;
@@ -898,7 +904,10 @@ cudaError_t launch_fr4_decode(const uint32_t *in, int64_t nx, int64_t ny, int64_
     if (e != cudaSuccess)
         return e;
     const int64_t grid = (nblk + kThreads - 1) / kThreads;
-    fr4_decode_kernel<<<(unsigned)grid, kThreads, smem_bytes(rate, false), st>>>(in, nx, ny, z0, nblk, rate, out);
+    if (rate > 16)
+        fr4_decode_kernel<5><<<(unsigned)grid, kThreads, smem_bytes(rate, false), st>>>(in, nx, ny, z0, nblk, rate, out);
+    else
+        fr4_decode_kernel<6><<<(unsigned)grid, kThreads, smem_bytes(rate, false), st>>>(in, nx, ny, z0, nblk, rate, out);
     return cudaGetLastError();
 }
 
