@@ -40,10 +40,13 @@ constexpr int kWaveTY = 8;
 #define OOC_HEAT_UNROLL 8
 #endif
 #ifndef OOC_HEATX2_UNROLL
-#define OOC_HEATX2_UNROLL 4
+#define OOC_HEATX2_UNROLL 1
 #endif
 #ifndef OOC_WAVE_UNROLL
 #define OOC_WAVE_UNROLL 1
+#endif
+#ifndef OOC_HEATX2_MINB
+#define OOC_HEATX2_MINB 3  // heat7x2 CTAs per SM: 64 registers, no loop unrolling
 #endif
 #ifndef OOC_HEATX2_TY
 #define OOC_HEATX2_TY 8
@@ -267,7 +270,7 @@ __global__ void __launch_bounds__(kTX *kHeatTY)
 // of the pipeline), and the two planes [bout_lo, bout_lo+2) are saved to
 // band_out for the next slab.  Outside the grid every level is zero.
 template <int TYO>
-__global__ void __launch_bounds__(kTX *(TYO + 2))
+__global__ void __launch_bounds__(kTX *(TYO + 2), OOC_HEATX2_MINB)
     heat7x2_kernel(const float *__restrict__ in, float *__restrict__ out, int nslot, int64_t zbase, Grid3 g,
                    int64_t z0, int64_t z1, int64_t zchunk, int64_t lo, int64_t hi, const float *__restrict__ band_in,
                    int64_t bin_lo, float *__restrict__ band_out, int64_t bout_lo, float r)
