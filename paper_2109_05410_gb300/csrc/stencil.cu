@@ -46,10 +46,10 @@ constexpr int kWaveTY = 8;
 #define OOC_WAVE_UNROLL 1
 #endif
 #ifndef OOC_HEATX2_MINB
-#define OOC_HEATX2_MINB 3  // heat7x2 CTAs per SM: 64 registers, no loop unrolling
+#define OOC_HEATX2_MINB 2  // heat7x2 CTAs per SM (16 warps each): 64 registers, no loop unrolling
 #endif
 #ifndef OOC_HEATX2_TY
-#define OOC_HEATX2_TY 8
+#define OOC_HEATX2_TY 14
 #endif
 constexpr int kHeatX2TY = OOC_HEATX2_TY;  // level s+1 rows per CTA of the fused kernel
 constexpr int kSeg = 4 * kTX;
