@@ -51,7 +51,14 @@ constexpr int kWaveTY = 8;
 #ifndef OOC_HEATX2_TY
 #define OOC_HEATX2_TY 14
 #endif
-constexpr int kHeatX2TY = OOC_HEATX2_TY;  // level s+1 rows per CTA of the fused kernel
+[[maybe_unused]] constexpr int kHeatX2TY = OOC_HEATX2_TY;  // level s+1 rows per CTA of heat7x2_kernel
+#ifndef OOC_HEATX2_ROWS
+#define OOC_HEATX2_ROWS 2  // fused kernel: rows per thread (2: heat7x2r_kernel, 1: heat7x2_kernel)
+#endif
+#ifndef OOC_HEATX2_NW
+#define OOC_HEATX2_NW 8
+#endif
+constexpr int kHeatX2NW = OOC_HEATX2_NW;  // warps of heat7x2r_kernel (2 NW - 2 output rows)
 constexpr int kSeg = 4 * kTX;
 
 __device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
@@ -376,6 +383,157 @@ OOC_PRAGMA(unroll OOC_HEATX2_UNROLL)
     }
 }
 
+// Two heat7 steps per launch, two rows per thread.  Warp w of NW holds the
+// level-s rows a = y0 - 1 + 2w and b = y0 + 2w (rows y0-1 .. y0+TYO of the
+// tile, TYO = 2 NW - 2 outputs) over 128 x.  Each row's neighbour on the
+// warp's other row comes from registers and only the outer neighbour from
+// shared memory; the per-plane address, predicate and barrier work is shared
+// by 8 points per thread instead of 4.  Same planes, bands and arithmetic
+// (heat_pt4 with the operands in the same slots) as heat7x2_kernel.
+template <int NW>
+__global__ void __launch_bounds__(kTX *NW, 2)
+    heat7x2r_kernel(const float *__restrict__ in, float *__restrict__ out, int nslot, int64_t zbase, Grid3 g,
+                    int64_t z0, int64_t z1, int64_t zchunk, int64_t lo64, int64_t hi64,
+                    const float *__restrict__ band_in, int64_t bin_lo64, float *__restrict__ band_out,
+                    int64_t bout_lo64, float r)
+{
+    constexpr int TYO = 2 * NW - 2;
+    __shared__ float4 ta[2][2 * NW + 2][kTX];  // level s-1, row y at index y - y0 + 2
+    __shared__ float4 tb[2][2 * NW][kTX];      // level s, row y at index y - y0 + 1
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int64_t gx = (g.nx + kSeg - 9) / (kSeg - 8);  // x tiles; blockIdx.x = by * gx + bx
+    const int64_t xs = (int64_t)(blockIdx.x % gx) * (kSeg - 8) - 4;
+    const int64_t x4 = xs + 4 * lane;
+    const int64_t y0 = (int64_t)(blockIdx.x / gx) * TYO;
+    const int64_t ya = y0 - 1 + 2 * w, yb = ya + 1;
+    const int64_t zs = z0 + (int64_t)blockIdx.y * zchunk;
+    const int cnt = (int)(min(zs + zchunk, z1) - zs);
+    // plane indices fit 32 bits (nz <= 2^20)
+    const int nz = (int)g.nz, lo = (int)lo64, hi = (int)hi64, bin_lo = (int)bin_lo64, bout_lo = (int)bout_lo64;
+    const int64_t plane = g.plane;
+    const bool xin = x4 >= 0 && x4 < g.nx;
+    const bool ina = xin && ya >= 0 && ya < g.ny, inb = xin && yb >= 0 && yb < g.ny;
+    const int64_t offa = ina ? ya * g.nx + x4 : 0, offb = inb ? yb * g.nx + x4 : 0;
+    const int64_t yh = w == 0 ? y0 - 2 : y0 + TYO + 1;  // halo row of the edge warps
+    const bool hrow = (w == 0 || w == NW - 1) && yh >= 0 && yh < g.ny && xin;
+    const int64_t hoff = hrow ? yh * g.nx + x4 : 0;
+    const int64_t xh = lane == 0 ? xs - 1 : xs + kSeg;  // halo column of the edge lanes
+    const bool xhin = (lane == 0 || lane == kTX - 1) && xh >= 0 && xh < g.nx;
+    const bool hca = xhin && ya >= 0 && ya < g.ny, hcb = xhin && yb >= 0 && yb < g.ny;
+    const int64_t xoffa = hca ? ya * g.nx + xh : 0, xoffb = hcb ? yb * g.nx + xh : 0;
+    // level s+1 is stored on rows y0 .. y0+TYO-1 and the inner lanes
+    const bool lin = lane >= 1 && lane <= kTX - 2;
+    const bool owna = ina && lin && w >= 1, ownb = inb && lin && w <= NW - 2;
+    const float4 z4 = zero4();
+
+    int z = (int)zs - 1;  // plane of level s produced in the current iteration
+    int s = (int)ring_slot(z, zbase, nslot);
+    const float *pm = in + (int64_t)wrap_add(s, nslot - 1, nslot) * plane;
+    const float *p0 = in + (int64_t)s * plane;
+    const float *p1 = in + (int64_t)wrap_add(s, 1, nslot) * plane;
+    const float *p2 = in + (int64_t)wrap_add(s, 2, nslot) * plane;
+    // level s-1 queues z-1 .. z+2 of rows a and b, halos of planes z, z+1
+    float4 pa = (ina && z >= 1) ? ldg4(pm + offa) : z4, pb = (inb && z >= 1) ? ldg4(pm + offb) : z4;
+    float4 ca = (ina && z >= 0) ? ldg4(p0 + offa) : z4, cb = (inb && z >= 0) ? ldg4(p0 + offb) : z4;
+    float4 na = (ina && z + 1 < nz) ? ldg4(p1 + offa) : z4, nb = (inb && z + 1 < nz) ? ldg4(p1 + offb) : z4;
+    float4 nna = (ina && z + 2 < nz) ? ldg4(p2 + offa) : z4, nnb = (inb && z + 2 < nz) ? ldg4(p2 + offb) : z4;
+    float4 hyv = (hrow && z >= 0) ? ldg4(p0 + hoff) : z4;
+    float4 hyv1 = (hrow && z + 1 < nz) ? ldg4(p1 + hoff) : z4;
+    float hxa = (hca && z >= 0) ? __ldg(p0 + xoffa) : 0.f, hxb = (hcb && z >= 0) ? __ldg(p0 + xoffb) : 0.f;
+    float hxa1 = (hca && z + 1 < nz) ? __ldg(p1 + xoffa) : 0.f, hxb1 = (hcb && z + 1 < nz) ? __ldg(p1 + xoffb) : 0.f;
+    float4 s2a = z4, s1a = z4, s2b = z4, s1b = z4;  // level s at planes z-2, z-1
+OOC_PRAGMA(unroll OOC_HEATX2_UNROLL)
+    for (int i = 0; i < cnt + 2; ++i, ++z) {
+        const int s2 = wrap_add(s, 2, nslot), s3 = wrap_add(s, 3, nslot);
+        const float *q2 = in + (int64_t)s2 * plane;
+        const float *q3 = in + (int64_t)s3 * plane;
+        const bool v3 = z + 3 < nz, v2 = z + 2 < nz;  // z >= -1
+        const float4 pfa = (ina && v3) ? ldg4(q3 + offa) : z4;
+        const float4 pfb = (inb && v3) ? ldg4(q3 + offb) : z4;
+        const float4 hyv2 = (hrow && v2) ? ldg4(q2 + hoff) : z4;
+        const float hxa2 = (hca && v2) ? __ldg(q2 + xoffa) : 0.f;
+        const float hxb2 = (hcb && v2) ? __ldg(q2 + xoffb) : 0.f;
+
+        const int bb = i & 1;
+        ta[bb][2 * w + 1][lane] = ca;
+        ta[bb][2 * w + 2][lane] = cb;
+        if (w == 0)
+            ta[bb][0][lane] = hyv;
+        if (w == NW - 1)
+            ta[bb][2 * NW + 1][lane] = hyv;
+        float xla = __shfl_up_sync(0xffffffffu, ca.w, 1), xra = __shfl_down_sync(0xffffffffu, ca.x, 1);
+        float xlb = __shfl_up_sync(0xffffffffu, cb.w, 1), xrb = __shfl_down_sync(0xffffffffu, cb.x, 1);
+        if (lane == 0) {
+            xla = hxa;
+            xlb = hxb;
+        }
+        if (lane == kTX - 1) {
+            xra = hxa;
+            xrb = hxb;
+        }
+        __syncthreads();
+        // level s at plane z (z is uniform over the CTA)
+        float4 sva = z4, svb = z4;
+        if (z >= lo && z < hi) {
+            const float4 upa = ta[bb][2 * w][lane];
+            const float4 dnb = ta[bb][2 * w + 3][lane];
+            const float4 oa = heat_pt4(ca, xla, xra, upa, cb, pa, na, r);
+            const float4 ob = heat_pt4(cb, xlb, xrb, ca, dnb, pb, nb, r);
+            sva = ina ? oa : z4;
+            svb = inb ? ob : z4;
+        } else if (band_in != nullptr && z >= bin_lo && z < bin_lo + 2) {
+            const float *bp = band_in + (int64_t)(z - bin_lo) * plane;
+            if (ina)
+                sva = ldg4(bp + offa);
+            if (inb)
+                svb = ldg4(bp + offb);
+        }
+        if (band_out != nullptr && z >= bout_lo && z < bout_lo + 2) {
+            float *bp = band_out + (int64_t)(z - bout_lo) * plane;
+            if (owna)
+                *reinterpret_cast<float4 *>(bp + offa) = sva;
+            if (ownb)
+                *reinterpret_cast<float4 *>(bp + offb) = svb;
+        }
+        tb[bb][2 * w][lane] = sva;
+        tb[bb][2 * w + 1][lane] = svb;
+        // level s+1 at plane z-1 from level s at planes z-2, z-1 (registers and
+        // the neighbouring warps' rows, written in the previous iteration) and z
+        if (i >= 2) {
+            const float4 upa = w >= 1 ? tb[bb ^ 1][2 * w - 1][lane] : z4;
+            const float4 dnb = w <= NW - 2 ? tb[bb ^ 1][2 * w + 2][lane] : z4;
+            const float yla = __shfl_up_sync(0xffffffffu, s1a.w, 1), yra = __shfl_down_sync(0xffffffffu, s1a.x, 1);
+            const float ylb = __shfl_up_sync(0xffffffffu, s1b.w, 1), yrb = __shfl_down_sync(0xffffffffu, s1b.x, 1);
+            const float4 oa = heat_pt4(s1a, yla, yra, upa, s1b, s2a, sva, r);
+            const float4 ob = heat_pt4(s1b, ylb, yrb, s1a, dnb, s2b, svb, r);
+            float *op = out + (int64_t)wrap_add(s, nslot - 1, nslot) * plane;
+            if (owna)
+                *reinterpret_cast<float4 *>(op + offa) = oa;
+            if (ownb)
+                *reinterpret_cast<float4 *>(op + offb) = ob;
+        }
+        s2a = s1a;
+        s1a = sva;
+        s2b = s1b;
+        s1b = svb;
+        pa = ca;
+        ca = na;
+        na = nna;
+        nna = pfa;
+        pb = cb;
+        cb = nb;
+        nb = nnb;
+        nnb = pfb;
+        hyv = hyv1;
+        hyv1 = hyv2;
+        hxa = hxa1;
+        hxa1 = hxa2;
+        hxb = hxb1;
+        hxb1 = hxb2;
+        s = wrap_add(s, 1, nslot);
+    }
+}
+
 // x-neighbour at offset idx in [-4, 7] from the thread's first point, given
 // its own 4 points c and the 4-point groups to its left (l) and right (rr).
 __device__ __forceinline__ float pick(const float (&l)[4], const float (&c)[4], const float (&rr)[4], int idx)
@@ -644,19 +802,33 @@ cudaError_t launch_heat7x2(ConstRing in, Ring out, int64_t nx, int64_t ny, int64
 {
     if (z1 <= z0)
         return cudaSuccess;
+#if OOC_HEATX2_ROWS == 2
+    constexpr int NW = kHeatX2NW;
+    constexpr int TYO = 2 * NW - 2;
+    static int res = 0;
+    if (res == 0)
+        res = resident((const void *)heat7x2r_kernel<NW>, kTX * NW);
+#else
     constexpr int TYO = kHeatX2TY;
     static int res = 0;
     if (res == 0)
         res = resident((const void *)heat7x2_kernel<TYO>, kTX * (TYO + 2));
+#endif
     const int64_t gx = (nx + kSeg - 9) / (kSeg - 8), gy = (ny + TYO - 1) / TYO;
     const int64_t chunk = choose_chunk(gx * gy, z1 - z0, 8, 5, res);
     const int64_t gz = (z1 - z0 + chunk - 1) / chunk;
     if (in.nslot != out.nslot || in.zbase != out.zbase || in.nslot > (1ll << 30) || in.base == out.base ||
-        gx * gy > 0x7fffffffll)
+        gx * gy > 0x7fffffffll || nz > (1ll << 30))
         return cudaErrorInvalidValue;
+#if OOC_HEATX2_ROWS == 2
+    heat7x2r_kernel<NW><<<dim3((unsigned)(gx * gy), (unsigned)gz), dim3(kTX, NW), 0, st>>>(
+        in.base, out.base, (int)in.nslot, in.zbase, Grid3{nx, ny, nz, nx * ny}, z0, z1, chunk, lo, hi, band_in, bin_lo,
+        band_out, bout_lo, r);
+#else
     heat7x2_kernel<TYO><<<dim3((unsigned)(gx * gy), (unsigned)gz), dim3(kTX, TYO + 2), 0, st>>>(
         in.base, out.base, (int)in.nslot, in.zbase, Grid3{nx, ny, nz, nx * ny}, z0, z1, chunk, lo, hi, band_in, bin_lo,
         band_out, bout_lo, r);
+#endif
     return cudaGetLastError();
 }
 
