@@ -39,6 +39,10 @@ N = 1024
 NSTEPS = 64
 K = 4
 BUDGET = 1 << 30
+# heat7 steps per stencil launch: 2 = the k steps run as fused pairs with the
+# intermediate level on chip (the library's default for k >= 2), 1 = one step
+# per launch
+SPL = int(os.environ.get("OOC_BENCH_HEAT_STEPS_PER_LAUNCH", "2"))
 MAIN = ("fr4", 16)
 COMPARE = [("fp32", 0), ("bf16", 0), ("fr4", 8), ("fr4", 12), ("fr4", 24)]
 # DRAM traffic per point of one heat7 launch, from `ncu --set full` on the
@@ -213,7 +217,7 @@ def run_reference(args, world, rank):
 # --------------------------------------------------------------------------- GPU arm
 def make_plan(ooc, fmt, rate, profile=0):
     return ooc.Plan(nx=N, ny=N, nz=N, stencil="heat7", k=K, rw_format=fmt, rw_rate=rate or 16,
-                    device_budget_bytes=BUDGET, profile=profile)
+                    device_budget_bytes=BUDGET, profile=profile, heat_steps_per_launch=SPL)
 
 
 def timed_steps(torch, plan, nsteps, reps):
@@ -342,7 +346,11 @@ def run_gpu(args, world, rank, local):
     nsten = pts * NSTEPS * args.steps
     rate = MAIN[1]
     kernels = {
-        "heat7_stencil": {"ms": st["ms_stencil"], "launches": st["n_stencil"], "bytes": 8 * nsten},
+        # 8 B per point per launch: one step per launch reads and writes each
+        # point once per step; a fused pair once per two steps (the band of
+        # the intermediate level, about 3 % more, is not counted)
+        "heat7_stencil": {"ms": st["ms_stencil"], "launches": st["n_stencil"], "bytes": 8 * nsten / SPL,
+                          "steps_per_launch": SPL},
         "fr4_decode": {"ms": st["ms_decode"], "launches": st["n_decode"], "bytes": (4 + rate / 8) * pts * st["passes"]},
         "fr4_encode": {"ms": st["ms_encode"], "launches": st["n_encode"], "bytes": (4 + rate / 8) * pts * st["passes"]},
     }
@@ -353,7 +361,7 @@ def run_gpu(args, world, rank, local):
     dk = kernels[dom]
     launches = max(dk["launches"], 1)
     traffic = None
-    if dom == "heat7_stencil" and stencil_source_sha() == HEAT7_TRAFFIC_SRC_SHA:
+    if dom == "heat7_stencil" and SPL == 1 and stencil_source_sha() == HEAT7_TRAFFIC_SRC_SHA:
         traffic = HEAT7_TRAFFIC_PER_POINT * (dk["bytes"] / 8) / launches
     roofline = {"bound": "hbm", "kernel": dom, "achieved": dk["GBs"], "peak": hbm_peak, "unit": "GB/s",
                 "frac": dk["frac_hbm"], "traffic": traffic,
@@ -362,6 +370,11 @@ def run_gpu(args, world, rank, local):
                 "timing": "CUDA events on the compute stream around each slab's stencil launches (and each "
                           "codec launch) over a second timed region of the same steps; mean launch = bracketed "
                           "time / launches (whole-job rate with the events: %.1f Gpts/s)" % value_profiled}
+    if dom == "heat7_stencil" and SPL == 2:
+        roofline["kernel"] = "heat7x2r (two heat7 steps per launch)"
+        roofline["note"] = ("the fused kernel moves 4 B per point-step instead of 8 and is bound by instruction "
+                            "issue and latency, not HBM; traffic is null: its DRAM counters were taken on "
+                            "another grid split (profiles/kernels_512cube_full.md: 7.85 B per point per launch)")
     h2d_GBs = st["h2d_bytes"] / (st["ms_h2d"] / 1e3) / 1e9 if st["ms_h2d"] > 0 else None
     d2h_GBs = st["d2h_bytes"] / (st["ms_d2h"] / 1e3) / 1e9 if st["ms_d2h"] > 0 else None
     plan.close()
@@ -446,7 +459,7 @@ def run_gpu(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "storage": fmt_name(*MAIN), "grid": [N, N, N], "k": K,
-                   "time_steps_per_bench_step": NSTEPS, "device_budget_bytes": BUDGET,
+                   "heat_steps_per_launch": SPL, "time_steps_per_bench_step": NSTEPS, "device_budget_bytes": BUDGET,
                    "slab_planes": info["slab_planes"], "nslab": info["nslab"], "ring_planes": info["ring_planes"],
                    "device_bytes": info["device_bytes"], "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (4 GiB field streamed from pinned host memory each pass)"},

@@ -72,9 +72,10 @@ typedef struct {
     int32_t slab_planes;         /* slab thickness T (multiple of 4); 0 = largest that fits */
     int32_t profile;             /* 1 = time every launch and copy with CUDA events */
     int64_t wait_timeout_ms;     /* deadline for host waits on the GPU; 0 = 600000 */
-    int32_t heat_steps_per_launch; /* heat7: 1 = one step per launch (0 = default = 1); 2 = each pair
-                                      of the k steps in one launch with the intermediate level kept on
-                                      chip.  Results are bit-identical.  wave25: 0 or 1. */
+    int32_t heat_steps_per_launch; /* heat7: 2 = each pair of the k steps in one launch with the
+                                      intermediate level kept on chip; 1 = one step per launch; 0 =
+                                      default = 2 when k >= 2, else 1.  Results are bit-identical.
+                                      wave25: 0 or 1. */
     int32_t graph_mode;          /* 0 = heat7 calls without profiling are captured once per distinct
                                     nsteps as a CUDA graph and replayed; 1 = always launch directly */
     int32_t debug_checks;        /* 1 = guard words after every region of the device arena, checked on

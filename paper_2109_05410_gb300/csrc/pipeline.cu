@@ -676,7 +676,11 @@ ooc_status ooc_plan_create(const ooc_config *cfg, ooc_plan **out, size_t *device
         return OOC_E_ALLOC;
     p->cfg = c;
     p->h = c.stencil == OOC_HEAT7 ? 1 : 4;
-    p->spl = c.stencil == OOC_HEAT7 && c.heat_steps_per_launch == 2 ? 2 : 1;
+    // heat7 runs the k steps of a pass as fused pairs unless one step per
+    // launch is asked for (heat_steps_per_launch = 1) or k = 1
+    p->spl = c.stencil == OOC_HEAT7 && (c.heat_steps_per_launch == 2 || (c.heat_steps_per_launch == 0 && c.k >= 2))
+                 ? 2
+                 : 1;
     p->W = round4((int64_t)c.k * p->h);
     p->nrw = c.stencil == OOC_HEAT7 ? 1 : 2;
     p->nfield = c.stencil == OOC_HEAT7 ? 1 : 3;

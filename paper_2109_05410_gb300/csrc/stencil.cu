@@ -393,21 +393,35 @@ OOC_PRAGMA(unroll OOC_HEATX2_UNROLL)
 template <int NW>
 __global__ void __launch_bounds__(kTX *NW, 2)
     heat7x2r_kernel(const float *__restrict__ in, float *__restrict__ out, int nslot, int64_t zbase, Grid3 g,
-                    int64_t z0, int64_t z1, int64_t zchunk, int64_t lo64, int64_t hi64,
-                    const float *__restrict__ band_in, int64_t bin_lo64, float *__restrict__ band_out,
+                    int64_t z0, int64_t z1, int64_t ntiles, int64_t nfull, int64_t zchunk, int64_t lo64,
+                    int64_t hi64, const float *__restrict__ band_in, int64_t bin_lo64, float *__restrict__ band_out,
                     int64_t bout_lo64, float r)
 {
     constexpr int TYO = 2 * NW - 2;
     __shared__ float4 ta[2][2 * NW + 2][kTX];  // level s-1, row y at index y - y0 + 2
     __shared__ float4 tb[2][2 * NW][kTX];      // level s, row y at index y - y0 + 1
     const int lane = threadIdx.x, w = threadIdx.y;
-    const int64_t gx = (g.nx + kSeg - 9) / (kSeg - 8);  // x tiles; blockIdx.x = by * gx + bx
-    const int64_t xs = (int64_t)(blockIdx.x % gx) * (kSeg - 8) - 4;
+    // CTAs below nfull march tiles 0 .. nfull-1 over [z0, z1); the others
+    // march z-chunks of zchunk planes of the remaining tiles, chunk-major
+    // (the tiles of one chunk side by side, so neighbouring tiles run
+    // together and share their halo rows through L2).
+    int64_t tile, zs, ze;
+    if ((int64_t)blockIdx.x < nfull) {
+        tile = blockIdx.x;
+        zs = z0;
+        ze = z1;
+    } else {
+        const int64_t j = (int64_t)blockIdx.x - nfull, rest = ntiles - nfull;
+        tile = nfull + j % rest;
+        zs = z0 + (j / rest) * zchunk;
+        ze = min(zs + zchunk, z1);
+    }
+    const int cnt = (int)(ze - zs);
+    const int64_t gx = (g.nx + kSeg - 9) / (kSeg - 8);  // x tiles; tile = by * gx + bx
+    const int64_t xs = (tile % gx) * (kSeg - 8) - 4;
     const int64_t x4 = xs + 4 * lane;
-    const int64_t y0 = (int64_t)(blockIdx.x / gx) * TYO;
+    const int64_t y0 = (tile / gx) * TYO;
     const int64_t ya = y0 - 1 + 2 * w, yb = ya + 1;
-    const int64_t zs = z0 + (int64_t)blockIdx.y * zchunk;
-    const int cnt = (int)(min(zs + zchunk, z1) - zs);
     // plane indices fit 32 bits (nz <= 2^20)
     const int nz = (int)g.nz, lo = (int)lo64, hi = (int)hi64, bin_lo = (int)bin_lo64, bout_lo = (int)bout_lo64;
     const int64_t plane = g.plane;
@@ -821,9 +835,33 @@ cudaError_t launch_heat7x2(ConstRing in, Ring out, int64_t nx, int64_t ny, int64
         gx * gy > 0x7fffffffll || nz > (1ll << 30))
         return cudaErrorInvalidValue;
 #if OOC_HEATX2_ROWS == 2
-    heat7x2r_kernel<NW><<<dim3((unsigned)(gx * gy), (unsigned)gz), dim3(kTX, NW), 0, st>>>(
-        in.base, out.base, (int)in.nslot, in.zbase, Grid3{nx, ny, nz, nx * ny}, z0, z1, chunk, lo, hi, band_in, bin_lo,
-        band_out, bout_lo, r);
+    // Whole waves of whole tiles, then the remaining tiles cut into z-chunks
+    // that fill the last wave, when the model (waves x (planes + 5)) says it
+    // beats one chunk size for all tiles.
+    const int64_t ntiles = gx * gy, H = z1 - z0;
+    int64_t nfull = 0, zch = chunk, ncta = ntiles * gz;
+    double best = (double)((ncta + res - 1) / res) * (double)(chunk + 5);
+    const int64_t full = ntiles / res * res, rest = ntiles - full;
+    if (full > 0 && rest > 0) {
+        for (int64_t m = 1; m <= 16; ++m) {
+            const int64_t c = (H + m - 1) / m;
+            if (m > 1 && c < 8)
+                break;
+            const double cost = (double)(full / res) * (double)(H + 5) +
+                                (double)((rest * m + res - 1) / res) * (double)(c + 5);
+            if (cost < best * 0.999) {
+                best = cost;
+                nfull = full;
+                zch = c;
+                ncta = full + rest * ((H + c - 1) / c);
+            }
+        }
+    }
+    if (ncta > 0x7fffffffll)
+        return cudaErrorInvalidValue;
+    heat7x2r_kernel<NW><<<(unsigned)ncta, dim3(kTX, NW), 0, st>>>(in.base, out.base, (int)in.nslot, in.zbase,
+                                                                 Grid3{nx, ny, nz, nx * ny}, z0, z1, ntiles, nfull,
+                                                                 zch, lo, hi, band_in, bin_lo, band_out, bout_lo, r);
 #else
     heat7x2_kernel<TYO><<<dim3((unsigned)(gx * gy), (unsigned)gz), dim3(kTX, TYO + 2), 0, st>>>(
         in.base, out.base, (int)in.nslot, in.zbase, Grid3{nx, ny, nz, nx * ny}, z0, z1, chunk, lo, hi, band_in, bin_lo,

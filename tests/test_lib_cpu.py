@@ -101,8 +101,11 @@ def test_fused_pairs_reserve_bands(L):
     for k in (1, 2, 4, 5):
         s1, d1, _, _ = plan_create(L, make_cfg(k=k, slab_planes=16, spl=1))
         s2, d2, _, _ = plan_create(L, make_cfg(k=k, slab_planes=16, spl=2))
-        assert s1 == 0 and s2 == 0
+        s0, d0, _, _ = plan_create(L, make_cfg(k=k, slab_planes=16, spl=0))
+        assert s1 == 0 and s2 == 0 and s0 == 0
         assert d2 - d1 == 2 * (k // 2) * 2 * plane
+        # the default runs pairs whenever k >= 2
+        assert d0 == (d2 if k >= 2 else d1)
 
 
 def test_budget_derivation(L):
@@ -167,9 +170,10 @@ def test_debug_checks_add_guard_regions(L):
     # ring, each nonempty staging buffer, the fused-pair bands, the time and
     # source slot) plus a 256-byte flag; the geometry is otherwise the same.
     cases = [
-        (dict(slab_planes=16), 2 + 4 + 1),                                      # heat7 FR4
-        (dict(slab_planes=16, rw_format=ooc.OOC_FMT_FP32), 2 + 1),               # FP32: no staging
+        (dict(slab_planes=16, spl=1), 2 + 4 + 1),                                # heat7 FR4
+        (dict(slab_planes=16, spl=1, rw_format=ooc.OOC_FMT_FP32), 2 + 1),        # FP32: no staging
         (dict(slab_planes=16, spl=2, k=4), 2 + 4 + 1 + 1),                       # fused pairs: bands
+        (dict(slab_planes=16), 2 + 4 + 1 + 1),                                   # the default (k = 2): pairs
         (dict(slab_planes=32, stencil=ooc.OOC_WAVE25, k=2, ro_format=ooc.OOC_FMT_FR4), 3 + 2 * (3 + 2) + 1),
     ]
     for kw, nguard in cases:
