@@ -387,8 +387,8 @@ def test_wave_graph_replay_with_source_matches_direct(ooc):
         assert np.array_equal(out[mode][1].view(np.uint32), ref_pp.view(np.uint32)), mode
 
 
-@pytest.mark.parametrize("fmt,rate", [("fr4", 16), ("fp32", 16), ("bf16", 16)])
-def test_profiled_trace_follows_each_slab_stages(ooc, fmt, rate):
+@pytest.mark.parametrize("fmt,rate,spl", [("fr4", 16, 2), ("fr4", 16, 1), ("fp32", 16, 2), ("bf16", 16, 1)])
+def test_profiled_trace_follows_each_slab_stages(ooc, fmt, rate, spl):
     # With profiling on, ooc_plan_get_trace returns the intervals of the last
     # call: every slab's stages run in dependency order (H2D -> decode ->
     # stencil launches -> encode -> D2H), each stream's intervals are in time
@@ -396,7 +396,7 @@ def test_profiled_trace_follows_each_slab_stages(ooc, fmt, rate):
     shape = (48, 40, 36)
     u0 = smooth_random_field(shape, 5.0, seed=33)
     plan = ooc.Plan(nx=36, ny=40, nz=48, stencil="heat7", k=4, rw_format=fmt, rw_rate=rate, slab_planes=12,
-                    profile=1)
+                    profile=1, heat_steps_per_launch=spl)
     try:
         plan.set_field(0, u0)
         plan.step(8)
@@ -417,7 +417,8 @@ def test_profiled_trace_follows_each_slab_stages(ooc, fmt, rate):
         by.setdefault(r["kind"], []).append(r)
     assert len(by.get("decode", [])) == st["n_decode"] and len(by.get("encode", [])) == st["n_encode"]
     assert len(by["h2d"]) == st["n_h2d"] and len(by["d2h"]) == st["n_d2h"]
-    assert sum(r["count"] for r in by["stencil"]) == st["n_stencil"] == 4 * 4 + 4 * 2
+    # launches: 4 slabs x (4 steps, then 2), one step or a fused pair each
+    assert sum(r["count"] for r in by["stencil"]) == st["n_stencil"] == (4 * 4 + 4 * 2) // spl
     staged = fmt != "fp32"
     assert ("decode" in by) == staged and ("encode" in by) == staged
     eps = 2e-3  # event timestamps are good to about a microsecond
