@@ -447,12 +447,14 @@ def run_gpu(args, world, rank, local):
     link_dir = 170.0  # GB/s each way with both directions busy (measured H2D/D2H probe)
     link_roof = {f: link_dir * 1e9 * K / (bits / 8) / 1e9 for f, bits in
                  (("fp32", 32), ("bf16", 16), ("fr4-8", 8), ("fr4-12", 12), ("fr4-16", 16), ("fr4-24", 24))}
-    hbm_roof = hbm_peak * 1e9 / 8 / 1e9
+    # stencil bytes per point-step: 8 with one step per launch, 4 with fused pairs
+    sten_b = 8.0 / SPL
+    hbm_roof = hbm_peak / sten_b
     # HBM bound including the codec and DMA bytes of the storage format: per
-    # point-step 8 B of stencil, plus per pass (/k) decode R/8 + 4, encode
+    # point-step the stencil bytes, plus per pass (/k) decode R/8 + 4, encode
     # 4 + R/8 and the landing / sending of R/8 each way.
     fmt_bits = {"fp32": 32, "bf16": 16, "fr4-8": 8, "fr4-12": 12, "fr4-16": 16, "fr4-24": 24}
-    hbm_refined = {f: hbm_peak / (8 + ((8 + b / 4 if f != "fp32" else 0) + b / 4) / K)
+    hbm_refined = {f: hbm_peak / (sten_b + ((8 + b / 4 if f != "fp32" else 0) + b / 4) / K)
                    for f, b in fmt_bits.items()}
     line = {
         "metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": world, "steps": args.steps,
