@@ -131,9 +131,6 @@ bool staged(const ooc_plan *p, int f) { return p->fmt[f] != OOC_FMT_FP32; }
 size_t layout(ooc_plan *p, int64_t T)
 {
     const int64_t W = p->W, h = p->h;
-    bool any_staged = false;
-    for (int f = 0; f < p->nfield; ++f)
-        any_staged |= staged(p, f);
     // FP32 slabs land in the ring while the previous slab computes (2T);
     // staged slabs land in staging buffers and are decoded in stream order.
     bool direct = false;
@@ -185,7 +182,6 @@ size_t layout(ooc_plan *p, int64_t T)
         p->off_flag = off;  // the guard checks' flag
         off += 256;
     }
-    (void)any_staged;
     p->Z = Z;
     return off;
 }
