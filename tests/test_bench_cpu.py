@@ -97,3 +97,25 @@ def test_overlap_summary_attributes_compute_idle_time():
     assert o["efficiency"] == pytest.approx(5.4 / 8.0)
     assert o["compute_idle_ms"] == pytest.approx({"waiting_h2d": 1.0, "waiting_d2h": 0.5, "other": 0.1})
     assert bench.overlap_summary([]) is None
+
+
+def test_heat7_traffic_hash_tracks_heat7_code_only(tmp_path, monkeypatch):
+    # The bench ties its measured heat7 DRAM traffic to a hash of the heat7
+    # part of stencil.cu: comments, blank lines and the fused kernel's
+    # settings (OOC_HEATX2_* blocks) do not change it; code does.
+    sys.path.insert(0, ROOT)
+    import bench
+    src = open(os.path.join(ROOT, "paper_2109_05410_gb300", "csrc", "stencil.cu")).read()
+    d = tmp_path / "paper_2109_05410_gb300" / "csrc"
+    d.mkdir(parents=True)
+
+    def sha_of(text):
+        (d / "stencil.cu").write_text(text)
+        monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+        return bench.stencil_source_sha()
+
+    base = sha_of(src)
+    assert base == bench.HEAT7_TRAFFIC_SRC_SHA
+    assert sha_of(src.replace("namespace ooc {", "// a new comment\n\nnamespace ooc {", 1)) == base
+    assert sha_of(src.replace("#define OOC_HEATX2_NW 8", "#define OOC_HEATX2_NW 6", 1)) == base
+    assert sha_of(src.replace("constexpr int kHeatTY = 2;", "constexpr int kHeatTY = 4;", 1)) != base
