@@ -19,9 +19,12 @@
  * Conventions for every entry point:
  *   - Grids are [z][y][x], x fastest; nx, ny, nz are multiples of 4.
  *   - Pointers are plain host or device addresses as stated; the library
- *     never frees memory it did not allocate, and allocates no device
- *     memory at all: the caller passes a device arena (its size *is* the
- *     device budget) and a pinned host arena.
+ *     never frees memory it did not allocate, and no call allocates device
+ *     memory: the caller passes a device arena (its size *is* the device
+ *     budget) and a pinned host arena.  The one piece of device memory the
+ *     library holds itself is the fixed 16 MiB array of
+ *     ooc_heat7_steps_noalloc, part of the loaded library image on every
+ *     GPU that loads it, outside any plan's budget.
  *   - Every function returns an ooc_status and never aborts the process.
  *   - Streams are cudaStream_t passed as void* (0 = legacy default stream).
  */
@@ -166,7 +169,9 @@ size_t ooc_var_scratch_bytes(int64_t nx, int64_t ny, int64_t nz);
  * and returns when the size is known: *out_bytes (host) = 4 * total words.
  * Two passes: block sizes, a prefix sum into d_index, then the blocks.  If
  * the stream would exceed out_cap, returns OOC_E_INVALID after the first
- * pass without writing d_out (d_index then holds the offsets). */
+ * pass without writing d_out (d_index then holds the offsets).  The host
+ * waits for the first pass by polling an event against a 10-minute
+ * deadline: OOC_E_TIMEOUT past it, with the first pass still enqueued. */
 ooc_status ooc_compress_var(const float *d_in, int64_t nx, int64_t ny, int64_t nz, int mode, double param,
                             void *d_out, size_t out_cap, uint64_t *d_index, void *d_scratch,
                             size_t scratch_bytes, size_t *out_bytes, void *stream);
@@ -227,7 +232,11 @@ ooc_status ooc_heat7_steps_fused(float *d_u, float *d_tmp, int64_t nx, int64_t n
  * that loads the library until the process exits); no call allocates
  * anything.  Grids with more points return OOC_E_INVALID.  The first call
  * on a device looks up the array's device address for that device, so make
- * that first call before any stream capture begins.  All calls share the
+ * that first call before any stream capture begins.  The address is kept
+ * with the ID of the context it was looked up in; a call made in another
+ * context of the device (after a cudaDeviceReset, say) looks it up again,
+ * so make the first call after such a reset outside stream capture too.
+ * All calls share the
  * array: calls that overlap on the GPU race on it, so the caller must order
  * them.  Results are bit-identical to ooc_heat7_steps. */
 ooc_status ooc_heat7_steps_noalloc(float *d_u, int64_t nx, int64_t ny, int64_t nz, double r, int64_t nsteps,
@@ -313,7 +322,9 @@ ooc_status ooc_set_source(ooc_plan *plan, int64_t sx, int64_t sy, int64_t sz, co
  * or OOC_E_TIMEOUT if that takes longer than wait_timeout_ms.  After a
  * timeout the enqueued passes still run to completion on the plan's
  * streams: synchronise those streams before touching the arenas.  The
- * timed-out call is not counted in the plan's time or statistics. */
+ * call's steps are enqueued before the wait, so a timed-out call still
+ * advances the plan's time (host and device copies alike) and counts its
+ * steps, passes and launches in the statistics. */
 ooc_status ooc_step(ooc_plan *plan, int64_t nsteps);
 
 /* Change the plan's host-wait deadline (ms; 0 = 600000).  The waits of

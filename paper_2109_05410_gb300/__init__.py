@@ -462,6 +462,13 @@ class Plan:
         _check(lib().ooc_plan_bind(self._h, _ptr(self.dev_arena), self.dev_arena.numel(), _ptr(self.host_arena),
                                    self.host_arena.numel(), arr), "ooc_plan_bind")
 
+    def rebind(self):
+        """Bind the plan again to its own arenas and streams (ooc_plan_bind):
+        copies the plan's time to the device and drops any captured graph."""
+        arr = (ctypes.c_void_p * 3)(*[s.cuda_stream for s in self.streams])
+        _check(lib().ooc_plan_bind(self._h, _ptr(self.dev_arena), self.dev_arena.numel(), _ptr(self.host_arena),
+                                   self.host_arena.numel(), arr), "ooc_plan_bind")
+
     def info(self):
         i = OocPlanInfo()
         _check(lib().ooc_plan_get_info(self._h, ctypes.byref(i)), "ooc_plan_get_info")

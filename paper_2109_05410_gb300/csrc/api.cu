@@ -1,6 +1,8 @@
 // api.cu -- stand-alone entry points of the C ABI: codec, BF16, in-core
 // stencil runs and status strings.  See include/ooc.h for the contract.
+#include <chrono>
 #include <cmath>
+#include <thread>
 
 #include "common.cuh"
 
@@ -14,9 +16,36 @@ bool dims_ok(int64_t nx, int64_t ny, int64_t nz)
            ny <= (1ll << 30) && nz <= (1ll << 30);
 }
 
+// Deadline of the host waits inside stand-alone calls (ooc_compress_var).
+constexpr int64_t kCallWaitMs = 600000;
+
 bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p % a) == 0; }
 
 ooc_status cuda_status(cudaError_t e) { return e == cudaSuccess ? OOC_OK : OOC_E_CUDA; }
+
+// Waits until the work enqueued so far on `st` has run, polling an event
+// against a deadline (OOC_E_TIMEOUT past it; the work still runs).
+ooc_status wait_stream(cudaStream_t st, int64_t timeout_ms)
+{
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+        return OOC_E_CUDA;
+    ooc_status s = cudaEventRecord(ev, st) == cudaSuccess ? OOC_OK : OOC_E_CUDA;
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+    while (s == OOC_OK) {
+        const cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess)
+            break;
+        if (e != cudaErrorNotReady)
+            s = OOC_E_CUDA;
+        else if (std::chrono::steady_clock::now() > deadline)
+            s = OOC_E_TIMEOUT;
+        else
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    cudaEventDestroy(ev);
+    return s;
+}
 
 // Flat BF16 conversion.  Quads of 4 values move as 16-byte (FP32) and
 // 8-byte (BF16) accesses, four quads per thread per round so that several
@@ -199,12 +228,14 @@ ooc_status ooc_compress_var(const float *d_in, int64_t nx, int64_t ny, int64_t n
                                             d_index, st);
     if (e == cudaSuccess)
         e = launch_exclusive_scan(d_index, nblk, (uint64_t *)d_scratch, st);
-    uint64_t total = 0;
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&total, d_index + nblk, sizeof(total), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess)
-        e = cudaStreamSynchronize(st);
     if (e != cudaSuccess)
+        return OOC_E_CUDA;
+    // the total is read once the first pass has run; the wait is bounded
+    const ooc_status ws = wait_stream(st, kCallWaitMs);
+    if (ws != OOC_OK)
+        return ws;
+    uint64_t total = 0;
+    if (cudaMemcpy(&total, d_index + nblk, sizeof(total), cudaMemcpyDeviceToHost) != cudaSuccess)
         return OOC_E_CUDA;
     *out_bytes = (size_t)total * 4;
     if (*out_bytes > out_cap)

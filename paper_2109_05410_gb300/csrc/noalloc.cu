@@ -16,6 +16,8 @@
 // it and must be serialised by the caller.  A step writes every point of its
 // output before any point is read, so nothing left in the array by an
 // earlier call is ever used and nothing has to be cleared between calls.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "common.cuh"
@@ -29,10 +31,46 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) float g_heat_scratch[kNoAllocMaxPoints];
 
-// Device address of g_heat_scratch per device, looked up once per device
-// (with that device current) on the first call made on it.
-float *g_scratch_addr[kMaxDevices];
+// Device address of g_heat_scratch per device, with the unique ID of the
+// context it was looked up in.  The address belongs to the module loaded
+// in that context: if the context is destroyed and another one made (a
+// cudaDeviceReset, for one), the module is loaded again and the array may
+// move, so a call whose current context has another ID looks it up again.
+struct ScratchEntry {
+    unsigned long long ctx_id;
+    float *addr;
+};
+ScratchEntry g_scratch[kMaxDevices];
 std::mutex g_scratch_mutex;
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// Unique ID of the calling thread's current context (0 when there is none
+// yet).  The driver functions come through the runtime's entry-point query,
+// so the library does not link the driver library itself.
+ooc_status current_ctx_id(unsigned long long *id)
+{
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1{}, q2{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return OOC_E_CUDA;
+        g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+        g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS)
+        return OOC_E_CUDA;
+    *id = 0;
+    if (ctx && g_ctx_get_id(ctx, id) != CUDA_SUCCESS)
+        return OOC_E_CUDA;
+    return OOC_OK;
+}
 
 ooc_status scratch_for_current_device(float **out)
 {
@@ -40,13 +78,20 @@ ooc_status scratch_for_current_device(float **out)
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return OOC_E_CUDA;
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (g_scratch_addr[dev] == nullptr) {
+    unsigned long long id = 0;
+    if (current_ctx_id(&id) != OOC_OK)
+        return OOC_E_CUDA;
+    if (id == 0 || g_scratch[dev].addr == nullptr || g_scratch[dev].ctx_id != id) {
+        // the lookup also makes the device's primary context current when
+        // no context is yet
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_heat_scratch) != cudaSuccess || p == nullptr)
             return OOC_E_CUDA;
-        g_scratch_addr[dev] = static_cast<float *>(p);
+        if (current_ctx_id(&id) != OOC_OK || id == 0)
+            return OOC_E_CUDA;
+        g_scratch[dev] = ScratchEntry{id, static_cast<float *>(p)};
     }
-    *out = g_scratch_addr[dev];
+    *out = g_scratch[dev].addr;
     return OOC_OK;
 }
 

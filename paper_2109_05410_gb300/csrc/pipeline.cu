@@ -781,7 +781,9 @@ ooc_status ooc_plan_bind(ooc_plan *p, void *device_arena, size_t device_bytes, v
         p->st[i] = (cudaStream_t)streams[i];
     drop_graph(p);
     p->src_uploaded = false;
-    if (cudaMemcpy(dev_time(p), &p->time, sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess)
+    // stream-ordered on the compute stream: after the last kernel of any
+    // earlier call on it (which may still advance the device time)
+    if (cudaMemcpyAsync(dev_time(p), &p->time, sizeof(int64_t), cudaMemcpyHostToDevice, p->st[1]) != cudaSuccess)
         return OOC_E_CUDA;
     OOC_TRY(arm_guards(p));
     p->bound = true;
@@ -907,29 +909,39 @@ ooc_status ooc_step(ooc_plan *p, int64_t nsteps)
     // time), so calls without per-launch profiling replay a captured graph.
     const bool wave = p->cfg.stencil == OOC_WAVE25;
     if (wave && p->sx >= 0 && !p->src_uploaded && (int64_t)p->w.size() <= kSrcTable) {
+        // Stream-ordered on the compute stream: it lands after every kernel
+        // of earlier calls that reads the table (even of a call that timed
+        // out) and before every kernel of this one.  A copy from pageable
+        // memory has taken its source when it returns, so nothing waits.
         OOC_CUDA(cudaMemcpyAsync(dev_src(p), p->w.data(), p->w.size() * sizeof(float), cudaMemcpyHostToDevice,
                                  p->st[1]));
-        OOC_CUDA(cudaStreamSynchronize(p->st[1]));
         p->src_uploaded = true;
         drop_graph(p);
     }
     const bool graphed = !p->cfg.profile && p->cfg.graph_mode == 0 && (!wave || p->sx < 0 || p->src_uploaded);
+    cudaEvent_t last = nullptr;
     if (graphed) {
         if (!p->graph || p->graph_nsteps != nsteps)
             OOC_TRY(capture_graph(p, nsteps));
         OOC_CUDA(cudaGraphLaunch(p->graph, p->st[1]));
         OOC_CUDA(cudaEventRecord(p->ev_done, p->st[1]));
-        OOC_TRY(wait_event(p, p->ev_done));
         add_counters(&p->stats, p->graph_delta);
+        last = p->ev_done;
     } else {
         ooc_stats delta{};
         int64_t g = 0;
         OOC_TRY(enqueue_steps(p, nsteps, &delta, &g));
         add_counters(&p->stats, delta);
-        OOC_TRY(wait_event(p, p->ev_d2h[(g - 1) % kEv]));
+        last = p->ev_d2h[(g - 1) % kEv];
     }
+    // Every pass is enqueued, and the device copy of the time advances with
+    // the call's last kernel, so the host time and the step count advance
+    // now: a call whose wait below times out has still done its steps once
+    // the streams drain, and the next call (or a rebind, which copies the
+    // host time to the device) continues from the right time.
     p->time += nsteps;
     p->stats.steps_done += nsteps;
+    OOC_TRY(wait_event(p, last));
     if (p->cfg.profile) {
         try {
             p->trace.reserve(p->prof_used);

@@ -55,7 +55,7 @@ def test_gather_scatter(ooc):
     assert f[17].item() == 18.0 and f[1].item() == 1.0
 
 
-def problem(n, nsteps, seed=3):
+def problem(n, nsteps, seed=3, rec_stride=2):
     shape = (n, n, n)
     v_true = layered_velocity(shape, seed=seed)
     dx = 10.0
@@ -68,7 +68,8 @@ def problem(n, nsteps, seed=3):
     kap_src = float((v_true[src[2], src[1], src[0]] * c) ** 2)
     w = (ricker(nsteps, dt) * kap_src * 1e3).astype(np.float32)
     zr = 8
-    rec = np.array([(zr * n + y) * n + x for y in range(0, n, 2) for x in range(0, n, 2)], dtype=np.int64)
+    rec = np.array([(zr * n + y) * n + x for y in range(0, n, rec_stride) for x in range(0, n, rec_stride)],
+                   dtype=np.int64)
     kap_true = (v_true.astype(np.float32).astype(np.float64) * c) ** 2
     d = oracle.wave25_traces(kap_true, src_flat, w.astype(np.float64), nsteps, rec)
     return dict(v=v, c=c, dt=dt, dx=dx, src=src, src_flat=src_flat, w=w, rec=rec, d=d, shape=shape)
@@ -80,10 +81,14 @@ def kappa_of(v, c):
     return (s * s).astype(np.float32)
 
 
-@pytest.mark.parametrize("rate", [0, 16])
-def test_checkpointed_gradient_matches_oracle(ooc, rate):
-    n, N, every = 48, 120, 10
-    P = problem(n, N)
+@pytest.mark.parametrize("rate,n,N,stride", [(0, 48, 120, 2), (16, 48, 120, 2), (16, 64, 150, 1)])
+def test_checkpointed_gradient_matches_oracle(ooc, rate, n, N, stride):
+    # (16, 64, 150, 1) is the adjoint configuration's oracle check: 64^3, a
+    # 64 x 64 receiver plane at z = 8 (every cell), checkpoints every 10
+    # steps at 16 bits/value
+    every = 10
+    P = problem(n, N, rec_stride=stride)
+    assert P["rec"].size == (n // stride) ** 2
     kap = kappa_of(P["v"], P["c"])
     kap64 = kap.astype(np.float64)
     tr_ref = oracle.wave25_traces(kap64, P["src_flat"], P["w"].astype(np.float64), N, P["rec"])

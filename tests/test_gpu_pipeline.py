@@ -271,6 +271,111 @@ def test_full_size_wave_benchmark_configuration(ooc):
     assert np.array_equal(got_pp.view(np.uint32), ref_pp.view(np.uint32))
 
 
+@pytest.mark.parametrize("rw,rw_rate,ro,ro_rate", [("fr4", 16, "fr4", 16), ("fr4", 16, "fp32", 16),
+                                                   ("bf16", 16, "bf16", 16)])
+def test_wave25_compressed_pipeline_against_oracle(ooc, rw, rw_rate, ro, ro_rate):
+    # Section VI's codes 4 (read-write levels and kappa at 16 bits/value) and
+    # 2 (read-write levels only), and BF16 storage, against the oracle's FP64
+    # leapfrog with the same storage round trips (at load, kappa once, both
+    # levels after every pass).  4 slabs of 32 planes with k = 10 (the common
+    # region, 40 planes, is wider than a slab), the source on, two calls of
+    # 10 and 11 steps (passes of 10, 10 and 1 steps), planes spanning two
+    # 128-wide x tiles and six 8-row y tiles of the wave kernel.
+    #
+    # Tolerance: both sides round-trip identical formats at identical points,
+    # so they differ by the GPU's FP32 arithmetic (about 21 steps x 2^-24
+    # relative) carried through each codec round trip, where a value next to
+    # a truncation boundary can land on the other side (one unit of the last
+    # kept bit plane, about the codec's own error).  rel-L2 1e-4 admits such
+    # flips at a small fraction of the points; against the pure FP64 run the
+    # storage error itself (Section VI-C: grows with steps, below 1e-3 here)
+    # dominates.
+    nz, ny, nx = 128, 48, 136
+    shape = (nz, ny, nx)
+    v = layered_velocity(shape, seed=3)
+    dt = 0.4 * 10.0 / v.max()
+    kappa = ((v * dt / 10.0) ** 2).astype(np.float32)
+    p0 = (1e-3 * smooth_random_field(shape, 6.0, seed=41)).astype(np.float32)
+    pm1 = (0.95 * p0).astype(np.float32)
+    src = (nx // 2, ny // 2, nz // 2)
+    srcf = (src[2] * ny + src[1]) * nx + src[0]
+    w = (ricker(40, dt) * float(kappa[src[2], src[1], src[0]]) * 1e-2).astype(np.float32)
+    calls = [10, 11]
+    plan = ooc.Plan(nx=nx, ny=ny, nz=nz, stencil="wave25", k=10, rw_format=rw, rw_rate=rw_rate, ro_format=ro,
+                    ro_rate=ro_rate, slab_planes=32)
+    try:
+        assert plan.info()["nslab"] == 4 and plan.info()["common_planes"] == 40
+        plan.set_field(0, p0)
+        plan.set_field(1, pm1)
+        plan.set_field(2, kappa)
+        plan.set_source(*src, w)
+        for n in calls:
+            plan.step(n)
+        got_p, got_pp = plan.get_field(0), plan.get_field(1)
+        assert plan.stats()["passes"] == 3
+    finally:
+        plan.close()
+    want_p, want_pp = oracle.wave25_storage_pipeline(p0, pm1, kappa, sum(calls), 10, rw, rw_rate, ro_fmt=ro,
+                                                     ro_rate=ro_rate, src=srcf, w=w.astype(np.float64))
+    exact_p, _ = oracle.wave25_run(p0.astype(np.float64), pm1.astype(np.float64), kappa.astype(np.float64),
+                                   sum(calls), src=srcf, w=w.astype(np.float64))
+    for got, want in ((got_p, want_p), (got_pp, want_pp)):
+        m = oracle.error_metrics(got, want)
+        print(f"{rw}-{rw_rate}/{ro}-{ro_rate} vs oracle pipeline: {m}")
+        assert m["rel_l2"] < 1e-4, m
+        assert m["max_abs"] < 1e-3 * np.abs(want).max(), m
+    m = oracle.error_metrics(got_p, exact_p)
+    print(f"{rw}-{rw_rate}/{ro}-{ro_rate} vs FP64 run without storage: {m}")
+    assert m["rel_l2"] < 1e-3, m
+
+
+@pytest.mark.parametrize("table", [True, False])
+def test_wave_step_deadline_keeps_the_source_in_step(ooc, table):
+    # A wave plan with a source whose call times out: the call still advances
+    # the plan's time, so a rebind (which copies the host time to the device
+    # time that the table-driven source reads) and the next call inject the
+    # right amplitudes; with a series longer than the device table the
+    # amplitudes come from the host at the host time.  The bits equal a plan
+    # that waited normally.
+    n, k = 256, 10
+    shape = (n, n, n)
+    v = layered_velocity(shape, seed=3)
+    dt = 0.4 * 10.0 / v.max()
+    kappa = ((v * dt / 10.0) ** 2).astype(np.float32)
+    zero = np.zeros(shape, dtype=np.float32)
+    src = (n // 2, n // 2, n // 2)
+    nw = 100 if table else 20000  # the device table holds 16384 amplitudes
+    w = np.zeros(nw, dtype=np.float32)
+    w[:80] = ricker(80, dt) * float(kappa[src[2], src[1], src[0]])
+    out = []
+    for hurried in (True, False):
+        plan = ooc.Plan(nx=n, ny=n, nz=n, stencil="wave25", k=k, rw_format="fr4", rw_rate=16, ro_format="fr4",
+                        ro_rate=16, slab_planes=64)
+        try:
+            plan.set_field(0, zero)
+            plan.set_field(1, zero)
+            plan.set_field(2, kappa)
+            plan.set_source(*src, w)
+            if hurried:
+                plan.set_wait_timeout(1)
+                with pytest.raises(ooc.OocError) as err:
+                    plan.step(40)
+                assert err.value.status == 5
+                torch.cuda.synchronize()
+                plan.set_wait_timeout(0)
+                plan.rebind()
+            else:
+                plan.step(40)
+            assert plan.stats()["steps_done"] == 40
+            plan.step(30)
+            out.append((plan.get_field(0), plan.get_field(1)))
+        finally:
+            plan.close()
+    assert np.abs(out[1][0]).max() > 0
+    assert np.array_equal(out[0][0].view(np.uint32), out[1][0].view(np.uint32))
+    assert np.array_equal(out[0][1].view(np.uint32), out[1][1].view(np.uint32))
+
+
 def test_step_deadline_reports_timeout_and_work_completes(ooc):
     # A host wait that runs past the plan's deadline returns OOC_E_TIMEOUT
     # (status 5) without faulting anything: the enqueued passes still run,
@@ -289,7 +394,7 @@ def test_step_deadline_reports_timeout_and_work_completes(ooc):
         assert err.value.status == 5
         torch.cuda.synchronize()
         plan.set_wait_timeout(0)
-        assert plan.stats()["steps_done"] == 0  # the timed-out call is not counted
+        assert plan.stats()["steps_done"] == 64  # enqueued before the wait, so counted
         got = plan.get_field(0)
         ref.set_field(0, u0)
         ref.step(64)
