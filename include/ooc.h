@@ -218,6 +218,15 @@ ooc_status ooc_heat7_steps_f64(double *d_u, double *d_tmp, int64_t nx, int64_t n
 ooc_status ooc_heat7_steps_fused(float *d_u, float *d_tmp, int64_t nx, int64_t ny, int64_t nz, double r,
                                  int64_t nsteps, void *stream);
 
+/* Reads and clears the library's device fault word on the current device:
+ * *fault = 1 if a kernel launched since the last read gave up one of its
+ * bounded waits (a shared-memory copy that did not arrive within about a
+ * second) and returned without writing the rest of its planes, else 0.
+ * ooc_step checks it itself and returns OOC_E_TIMEOUT; callers of the
+ * in-core entry points read it after synchronising their stream.  Kernels
+ * never trap or spin without bound. */
+ooc_status ooc_take_device_fault(int *fault);
+
 /* Largest grid, in points, that ooc_heat7_steps_noalloc accepts: the size of
  * its fixed scratch array (4 Mi floats, 16 MiB). */
 #define OOC_NOALLOC_MAX_POINTS (4ll * 1024 * 1024)

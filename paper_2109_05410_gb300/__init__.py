@@ -19,7 +19,7 @@ from . import build as _build_mod
 __all__ = [
     "OOC_HEAT7", "OOC_WAVE25", "OOC_FMT_FP32", "OOC_FMT_BF16", "OOC_FMT_FR4",
     "OocConfig", "OocStats", "OocPlanInfo", "OocError", "lib", "build",
-    "ooc_status_string", "ooc_compressed_bytes", "ooc_compress", "ooc_decompress", "ooc_compress_var",
+    "ooc_status_string", "ooc_take_device_fault", "ooc_compressed_bytes", "ooc_compress", "ooc_decompress", "ooc_compress_var",
     "ooc_decompress_var", "ooc_compress_var_bound", "ooc_var_scratch_bytes", "OOC_FR4_PRECISION", "OOC_FR4_ACCURACY",
     "ooc_bf16_pack", "ooc_bf16_unpack", "ooc_heat7_steps", "ooc_heat7_steps_f64", "ooc_heat7_steps_fused", "ooc_heat7_steps_noalloc", "ooc_wave25_steps", "Plan",
     "ooc_gather", "ooc_scatter_add", "ooc_wave25_adjoint_step", "ooc_wave25_grad_accum", "ooc_kappa_from_velocity",
@@ -118,6 +118,7 @@ _SIGS = {
     "ooc_get_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "ooc_set_source": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int64] * 3 + [ctypes.c_void_p, ctypes.c_int64]),
     "ooc_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "ooc_take_device_fault": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]),
     "ooc_plan_set_wait_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "ooc_plan_set_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "ooc_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(OocStats)]),
@@ -187,6 +188,14 @@ def _stream(stream):
 
 def ooc_status_string(s):
     return lib().ooc_status_string(int(s)).decode()
+
+
+def ooc_take_device_fault():
+    """1 if a kernel gave up a bounded wait since the last call, else 0
+    (reads and clears the library's device fault word)."""
+    f = ctypes.c_int()
+    _check(lib().ooc_take_device_fault(ctypes.byref(f)), "ooc_take_device_fault")
+    return f.value
 
 
 def ooc_compressed_bytes(nx, ny, nz, rate):

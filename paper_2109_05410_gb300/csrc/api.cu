@@ -368,3 +368,14 @@ ooc_status ooc_wave25_steps(float *d_p, float *d_pprev, const float *d_kappa, in
 }
 
 }  // extern "C"
+
+extern "C" ooc_status ooc_take_device_fault(int *fault)
+{
+    if (!fault)
+        return OOC_E_INVALID;
+    unsigned v = 0u;
+    if (take_stencil_fault(&v) != cudaSuccess)
+        return OOC_E_CUDA;
+    *fault = v != 0u ? 1 : 0;
+    return OOC_OK;
+}

@@ -72,6 +72,9 @@ cudaError_t launch_wave25(ConstRing p, Ring pprev_out, ConstRing kappa, int64_t 
 cudaError_t launch_wave25_to(ConstRing p, ConstRing pprev, Ring pnew, ConstRing kappa, int64_t nx, int64_t ny,
                              int64_t nz, int64_t z0, int64_t z1, int64_t sx, int64_t sy, int64_t sz, float w,
                              cudaStream_t st, WaveSrcTable tab = WaveSrcTable{});
+// Reads and clears the device word that a stencil kernel sets when one of
+// its bounded waits gives up (nonzero: that launch left planes unwritten).
+cudaError_t take_stencil_fault(unsigned *fault);
 // plan time on the device: *t += n (one thread)
 cudaError_t launch_add_time(int64_t *t, int64_t n, cudaStream_t st);
 // Codec over the 4-aligned plane range [z0, z1) of a ring; the stream part

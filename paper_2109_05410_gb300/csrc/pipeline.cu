@@ -942,6 +942,11 @@ ooc_status ooc_step(ooc_plan *p, int64_t nsteps)
     p->time += nsteps;
     p->stats.steps_done += nsteps;
     OOC_TRY(wait_event(p, last));
+    // a kernel whose bounded wait gave up left planes unwritten
+    unsigned fault = 0u;
+    OOC_CUDA(take_stencil_fault(&fault));
+    if (fault)
+        return OOC_E_TIMEOUT;
     if (p->cfg.profile) {
         try {
             p->trace.reserve(p->prof_used);

@@ -28,9 +28,18 @@
 //   p' = 2p - p_prev + kappa * sum_axes[c0 p + sum_m c_m (p[+m] + p[-m])]
 // p' overwrites p_prev in place (or goes to a separate array): each point's
 // p_prev is read only by the thread that writes p' there.
+#include <cuda.h>
+
+#include <mutex>
+
 #include "common.cuh"
 
 namespace ooc {
+
+// Set by a kernel whose bounded wait gave up (see heat7x2t_kernel); read and
+// cleared by take_stencil_fault().
+__device__ unsigned g_stencil_fault = 0u;
+
 namespace {
 
 constexpr int kTX = 32;  // threads per row segment (4 points each: 128 x)
@@ -55,7 +64,7 @@ constexpr int kWaveTY = 8;
 #endif
 [[maybe_unused]] constexpr int kHeatX2TY = OOC_HEATX2_TY;  // level s+1 rows per CTA of heat7x2_kernel
 #ifndef OOC_HEATX2_ROWS
-#define OOC_HEATX2_ROWS 2  // fused kernel: rows per thread (2: heat7x2r_kernel, 1: heat7x2_kernel)
+#define OOC_HEATX2_ROWS 3  // fused kernel: 3: heat7x2t_kernel (TMA-staged), 2: heat7x2r_kernel, 1: heat7x2_kernel
 #endif
 #ifndef OOC_HEATX2_NW
 #define OOC_HEATX2_NW 8
@@ -550,6 +559,291 @@ OOC_PRAGMA(unroll OOC_HEATX2_UNROLL)
     }
 }
 
+// ---- fused heat7 pairs with TMA-staged planes ---------------------------------
+// Same tiles, planes, bands and per-point arithmetic as heat7x2r_kernel (so
+// the results are bit-identical), but level s-1 reaches the CTA as whole
+// planes of its tile: one thread issues a TMA tensor copy per plane
+// (cp.async.bulk.tensor, 136 x 18 floats: the 128 level-s columns with 4 on
+// each side, the 16 level-s rows with 1 above and below) into a ring of NS
+// shared-memory stages, each guarded by an mbarrier that the copy completes.
+// The tensor map's zero fill of out-of-range x and y is the zero ghost of
+// the boundary, so no thread tests or loads halos; the threads only read
+// shared memory, compute and store.  Level s goes to a 3-plane shared ring
+// for the y-neighbours of level s+1.  One CTA barrier per plane orders the
+// level-s ring and frees the stage the next copy lands in.
+//
+// Every wait on an mbarrier is bounded: after kMbarTries polls (each
+// suspending up to ~1 us) the CTA agrees, through the plane barrier, to stop;
+// thread 0 then waits (bounded again) for the copies it issued, sets
+// g_stencil_fault and the CTA returns without writing further planes.
+constexpr int kX2tNW = kHeatX2NW;                // warps (2 level-s rows each)
+constexpr int kX2tRows = 2 * kX2tNW;             // level-s rows of a tile
+constexpr int kX2tSRows = kX2tRows + 2;          // level s-1 rows staged
+constexpr int kX2tSCols = 4 * kTX + 8;           // level s-1 columns staged (136)
+constexpr int kX2tStageFloats = (kX2tSRows * kX2tSCols + 31) / 32 * 32;  // 128-byte aligned stages
+constexpr int kX2tCopyBytes = kX2tSRows * kX2tSCols * 4;
+constexpr int kX2tL1Float4 = kX2tRows * kTX;     // one level-s plane of the tile
+// 5 stages and 3 CTAs per SM (72 KB of shared memory and at most 85
+// registers each), loop unrolled 3 times (the z-queues rotate without
+// copies).  In the 1024^3 FR4-16 pipeline (56-plane windows), per launch:
+// 110.4 us; 112.4 us not unrolled; 6 stages and 2 CTAs per SM 128.6 us
+// (120.6 us unrolled); heat7x2r_kernel 146.2 us.
+#ifndef OOC_HEATX2T_NS
+#define OOC_HEATX2T_NS 5
+#endif
+#ifndef OOC_HEATX2T_MINB
+#define OOC_HEATX2T_MINB 3
+#endif
+#ifndef OOC_HEATX2T_UNROLL
+#define OOC_HEATX2T_UNROLL 3
+#endif
+constexpr int kX2tNS = OOC_HEATX2T_NS;
+constexpr int kMbarTries = 1 << 20;
+
+size_t heat7x2t_smem_bytes()
+{
+    return (size_t)kX2tNS * kX2tStageFloats * 4 + 3 * (size_t)kX2tL1Float4 * 16 + kX2tNS * 8;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// true once the phase with parity `parity` has completed; false after
+// kMbarTries polls
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
+{
+    const unsigned a = smem_u32(bar);
+    for (int it = 0; it < kMbarTries; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity), "r"(1000u)
+            : "memory");
+        if (done)
+            return true;
+    }
+    return false;
+}
+
+// TMA copy of the box at (x, y, slot) of the ring's tensor map into `dst`,
+// completing `bar`'s transaction count
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <int NS>
+__global__ void __launch_bounds__(kTX *kX2tNW, OOC_HEATX2T_MINB)
+    heat7x2t_kernel(const __grid_constant__ CUtensorMap tin, float *__restrict__ out, int nslot, int64_t zbase,
+                    Grid3 g, int64_t z0, int64_t z1, int64_t ntiles, int64_t nfull, int64_t zchunk, int64_t lo64,
+                    int64_t hi64, const float *__restrict__ band_in, int64_t bin_lo64, float *__restrict__ band_out,
+                    int64_t bout_lo64, float r)
+{
+    constexpr int NW = kX2tNW;
+    constexpr int TYO = 2 * NW - 2;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *stages = reinterpret_cast<float *>(smem_raw);
+    float4 *l1 = reinterpret_cast<float4 *>(smem_raw + (size_t)NS * kX2tStageFloats * 4);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + (size_t)NS * kX2tStageFloats * 4 +
+                                                 3 * (size_t)kX2tL1Float4 * 16);
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const bool leader = lane == 0 && w == 0;
+    int64_t tile, zs64, ze64;
+    if ((int64_t)blockIdx.x < nfull) {
+        tile = blockIdx.x;
+        zs64 = z0;
+        ze64 = z1;
+    } else {
+        const int64_t j = (int64_t)blockIdx.x - nfull, rest = ntiles - nfull;
+        tile = nfull + j % rest;
+        zs64 = z0 + (j / rest) * zchunk;
+        ze64 = min(zs64 + zchunk, z1);
+    }
+    const int64_t gx = (g.nx + kSeg - 9) / (kSeg - 8);  // x tiles; tile = by * gx + bx
+    const int64_t xs = (tile % gx) * (kSeg - 8) - 4;     // first level-s column
+    const int64_t x4 = xs + 4 * lane;
+    const int64_t y0 = (tile / gx) * TYO;
+    const int64_t ya = y0 - 1 + 2 * w, yb = ya + 1;
+    // plane indices fit 32 bits (nz <= 2^30)
+    const int nz = (int)g.nz, lo = (int)lo64, hi = (int)hi64, bin_lo = (int)bin_lo64, bout_lo = (int)bout_lo64;
+    const int zs = (int)zs64, ze = (int)ze64;
+    const int64_t plane = g.plane;
+    const bool xin = x4 >= 0 && x4 < g.nx;
+    const bool ina = xin && ya >= 0 && ya < g.ny, inb = xin && yb >= 0 && yb < g.ny;
+    const int64_t offa = ina ? ya * g.nx + x4 : 0, offb = inb ? yb * g.nx + x4 : 0;
+    const bool lin = lane >= 1 && lane <= kTX - 2;
+    const bool owna = ina && lin && w >= 1, ownb = inb && lin && w <= NW - 2;
+    const float4 z4 = zero4();
+
+    // staged planes zs-2 .. ze+1: stage index i holds plane zs - 2 + i in
+    // slot i mod NS, completing phase (i / NS) of that slot's mbarrier
+    const int zfirst = zs - 2, nplanes = ze - zs + 4;
+    const int tx = (int)(xs - 4), ty = (int)(y0 - 2);
+    // ring slot of the next plane the leader copies (advanced one plane per
+    // copy, so no division in the loop)
+    int islot = (int)ring_slot(zfirst, zbase, nslot);
+    auto issue = [&](int i) {  // copies plane zfirst + i; i advances by one per call
+        const int zp = zfirst + i, sl = i % NS;
+        if (zp >= 0 && zp < nz) {
+            mbar_arrive_tx(&bar[sl], (unsigned)kX2tCopyBytes);
+            tma_load_3d(stages + sl * kX2tStageFloats, &tin, tx, ty, islot, &bar[sl]);
+        } else {
+            mbar_arrive(&bar[sl]);  // a plane outside the grid: nothing to copy, the phase completes at once
+        }
+        islot = wrap_add(islot, 1, nslot);
+    };
+    if (leader) {
+        for (int j = 0; j < NS; ++j)
+            mbar_init(&bar[j], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
+    __syncthreads();
+    int issued = 0;  // stage indices issued so far (tracked by every thread)
+    if (leader)
+        for (int i = 0; i < NS && i < nplanes; ++i)
+            issue(i);
+    issued = NS < nplanes ? NS : nplanes;
+    // this thread's float4 of a staged row (column 4 lane + 4) and the
+    // halo floats of lanes 0 (column 3) and 31 (column 4 kTX + 4)
+    auto srow = [&](int sl, int row) -> const float * {
+        return stages + sl * kX2tStageFloats + row * kX2tSCols;
+    };
+    auto s4 = [&](int sl, int row) -> float4 { return reinterpret_cast<const float4 *>(srow(sl, row))[lane + 1]; };
+
+    unsigned fail = 0;
+    fail |= mbar_wait(&bar[0], 0) ? 0u : 1u;
+    fail |= mbar_wait(&bar[1 % NS], (1 / NS) & 1) ? 0u : 1u;
+    // level s-1 queue z-1, z, z+1 of rows a and b (zero outside the grid:
+    // the copies fill zeros there, and planes outside the grid are not read)
+    float4 pa = z4, pb = z4, ca = z4, cb = z4;
+    if (!fail) {
+        if (zfirst >= 0) {
+            pa = s4(0, 2 * w + 1);
+            pb = s4(0, 2 * w + 2);
+        }
+        if (zfirst + 1 >= 0 && zfirst + 1 < nz) {
+            ca = s4(1 % NS, 2 * w + 1);
+            cb = s4(1 % NS, 2 * w + 2);
+        }
+    }
+    float4 s2a = z4, s1a = z4, s2b = z4, s1b = z4;  // level s at planes z-2, z-1
+    int sc = 1 % NS, sn = 2 % NS;                    // stages of planes z and z+1
+    int l1c = 0;                                     // level-s ring plane of z
+    int oslot = (int)ring_slot(zs - 2, zbase, nslot);  // output ring slot of plane z-1
+OOC_PRAGMA(unroll OOC_HEATX2T_UNROLL)
+    for (int z = zs - 1, i = 1; z <= ze; ++z, ++i) {
+        // level s-1 plane z+1 (stage index i + 1)
+        if (!mbar_wait(&bar[sn], (unsigned)(((i + 1) / NS) & 1)))
+            fail = 1u;
+        float4 na = z4, nb = z4;
+        if (z + 1 < nz) {
+            na = s4(sn, 2 * w + 1);
+            nb = s4(sn, 2 * w + 2);
+        }
+        // level s at plane z (z is uniform over the CTA)
+        float4 sva = z4, svb = z4;
+        if (z >= lo && z < hi) {
+            const float4 upa = s4(sc, 2 * w);
+            const float4 dnb = s4(sc, 2 * w + 3);
+            float xla = __shfl_up_sync(0xffffffffu, ca.w, 1), xra = __shfl_down_sync(0xffffffffu, ca.x, 1);
+            float xlb = __shfl_up_sync(0xffffffffu, cb.w, 1), xrb = __shfl_down_sync(0xffffffffu, cb.x, 1);
+            if (lane == 0) {
+                xla = srow(sc, 2 * w + 1)[3];
+                xlb = srow(sc, 2 * w + 2)[3];
+            }
+            if (lane == kTX - 1) {
+                xra = srow(sc, 2 * w + 1)[4 * kTX + 4];
+                xrb = srow(sc, 2 * w + 2)[4 * kTX + 4];
+            }
+            const float4 oa = heat_pt4(ca, xla, xra, upa, cb, pa, na, r);
+            const float4 ob = heat_pt4(cb, xlb, xrb, ca, dnb, pb, nb, r);
+            sva = ina ? oa : z4;
+            svb = inb ? ob : z4;
+        } else if (band_in != nullptr && z >= bin_lo && z < bin_lo + 2) {
+            const float *bp = band_in + (int64_t)(z - bin_lo) * plane;
+            if (ina)
+                sva = ldg4(bp + offa);
+            if (inb)
+                svb = ldg4(bp + offb);
+        }
+        if (band_out != nullptr && z >= bout_lo && z < bout_lo + 2) {
+            float *bp = band_out + (int64_t)(z - bout_lo) * plane;
+            if (owna)
+                *reinterpret_cast<float4 *>(bp + offa) = sva;
+            if (ownb)
+                *reinterpret_cast<float4 *>(bp + offb) = svb;
+        }
+        l1[l1c * kX2tL1Float4 + (2 * w) * kTX + lane] = sva;
+        l1[l1c * kX2tL1Float4 + (2 * w + 1) * kTX + lane] = svb;
+        // all threads have read stage z-1 and written level s of plane z;
+        // the plane read next (level s of z-1) was written before this
+        // barrier in the previous iteration
+        if (__syncthreads_or((int)fail)) {
+            if (leader) {
+                // the last copy issued into each slot may still be in flight
+                for (int j = issued > NS ? issued - NS : 0; j < issued; ++j)
+                    mbar_wait(&bar[j % NS], (unsigned)((j / NS) & 1));
+                atomicOr(&g_stencil_fault, 1u);
+            }
+            return;
+        }
+        if (i - 1 + NS < nplanes) {
+            if (leader)
+                issue(i - 1 + NS);  // into the slot of plane z-1
+            ++issued;
+        }
+        // level s+1 at plane z-1 from level s at planes z-2, z-1, z
+        if (z - 1 >= zs) {
+            const int lp = l1c == 0 ? 2 : l1c - 1;
+            const float4 upa = w >= 1 ? l1[lp * kX2tL1Float4 + (2 * w - 1) * kTX + lane] : z4;
+            const float4 dnb = w <= NW - 2 ? l1[lp * kX2tL1Float4 + (2 * w + 2) * kTX + lane] : z4;
+            const float yla = __shfl_up_sync(0xffffffffu, s1a.w, 1), yra = __shfl_down_sync(0xffffffffu, s1a.x, 1);
+            const float ylb = __shfl_up_sync(0xffffffffu, s1b.w, 1), yrb = __shfl_down_sync(0xffffffffu, s1b.x, 1);
+            const float4 oa = heat_pt4(s1a, yla, yra, upa, s1b, s2a, sva, r);
+            const float4 ob = heat_pt4(s1b, ylb, yrb, s1a, dnb, s2b, svb, r);
+            float *op = out + (int64_t)oslot * plane;
+            if (owna)
+                *reinterpret_cast<float4 *>(op + offa) = oa;
+            if (ownb)
+                *reinterpret_cast<float4 *>(op + offb) = ob;
+        }
+        s2a = s1a;
+        s1a = sva;
+        s2b = s1b;
+        s1b = svb;
+        pa = ca;
+        ca = na;
+        pb = cb;
+        cb = nb;
+        sc = sn;
+        sn = sn + 1 == NS ? 0 : sn + 1;
+        l1c = l1c == 2 ? 0 : l1c + 1;
+        oslot = wrap_add(oslot, 1, nslot);
+    }
+}
+
 // x-neighbour at offset idx in [-4, 7] from the thread's first point, given
 // its own 4 points c and the 4-point groups to its left (l) and right (rr).
 __device__ __forceinline__ float pick(const float (&l)[4], const float (&c)[4], const float (&rr)[4], int idx)
@@ -812,13 +1106,102 @@ cudaError_t launch_heat7(ConstRing in, Ring out, int64_t nx, int64_t ny, int64_t
     return cudaGetLastError();
 }
 
+namespace {
+
+// Tensor maps of the rings the TMA kernel reads, keyed by (base, nx, ny,
+// slots); the pipeline alternates between two rings, so a few entries
+// cover it and a map is encoded once per ring.
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+struct MapEntry {
+    const void *base;
+    int64_t nx, ny, nslot;
+    int dev;
+    CUtensorMap map;
+};
+constexpr int kMapCache = 8;
+MapEntry g_maps[kMapCache];
+int g_maps_used = 0, g_maps_next = 0;
+std::mutex g_maps_mutex;
+
+cudaError_t ring_tensor_map(const float *base, int64_t nx, int64_t ny, int64_t nslot, CUtensorMap *out)
+{
+    static EncodeTiledFn encode = nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_maps_mutex);
+    for (int i = 0; i < g_maps_used; ++i)
+        if (g_maps[i].base == base && g_maps[i].nx == nx && g_maps[i].ny == ny && g_maps[i].nslot == nslot &&
+            g_maps[i].dev == dev) {
+            *out = g_maps[i].map;
+            return cudaSuccess;
+        }
+    if (!encode) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !f)
+            return cudaErrorNotSupported;
+        encode = reinterpret_cast<EncodeTiledFn>(f);
+    }
+    // dims x, y, slot; the box is the 136 x 18 staged rows of one plane;
+    // out-of-range x and y read as zero (the boundary's zero ghosts)
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nslot};
+    const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)(nx * ny) * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)kX2tSCols, (cuuint32_t)kX2tSRows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    MapEntry e{base, nx, ny, nslot, dev, {}};
+    if (encode(&e.map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    if (g_maps_used < kMapCache)
+        g_maps[g_maps_used++] = e;
+    else {
+        g_maps[g_maps_next] = e;
+        g_maps_next = (g_maps_next + 1) % kMapCache;
+    }
+    *out = e.map;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t take_stencil_fault(unsigned *fault)
+{
+    unsigned v = 0u;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_stencil_fault, sizeof(v));
+    if (e == cudaSuccess && v != 0u) {
+        const unsigned zero = 0u;
+        e = cudaMemcpyToSymbol(g_stencil_fault, &zero, sizeof(zero));
+    }
+    *fault = v;
+    return e;
+}
+
 cudaError_t launch_heat7x2(ConstRing in, Ring out, int64_t nx, int64_t ny, int64_t nz, int64_t z0, int64_t z1,
                            int64_t lo, int64_t hi, const float *band_in, int64_t bin_lo, float *band_out,
                            int64_t bout_lo, float r, cudaStream_t st)
 {
     if (z1 <= z0)
         return cudaSuccess;
-#if OOC_HEATX2_ROWS == 2
+#if OOC_HEATX2_ROWS == 3
+    // TMA-staged kernel: same tiles and split as heat7x2r_kernel
+    constexpr int NW = kX2tNW;
+    constexpr int TYO = 2 * NW - 2;
+    static int res = 0;
+    const size_t smem = heat7x2t_smem_bytes();
+    if (res == 0) {
+        const cudaError_t e = cudaFuncSetAttribute(heat7x2t_kernel<kX2tNS>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        res = resident((const void *)heat7x2t_kernel<kX2tNS>, kTX * NW, smem);
+    }
+#elif OOC_HEATX2_ROWS == 2
     constexpr int NW = kHeatX2NW;
     constexpr int TYO = 2 * NW - 2;
     static int res = 0;
@@ -836,7 +1219,7 @@ cudaError_t launch_heat7x2(ConstRing in, Ring out, int64_t nx, int64_t ny, int64
     if (in.nslot != out.nslot || in.zbase != out.zbase || in.nslot > (1ll << 30) || in.base == out.base ||
         gx * gy > 0x7fffffffll || nz > (1ll << 30))
         return cudaErrorInvalidValue;
-#if OOC_HEATX2_ROWS == 2
+#if OOC_HEATX2_ROWS >= 2
     // Whole waves of whole tiles, then the remaining tiles cut into z-chunks
     // that fill the last wave, when the model (waves x (planes + 5)) says it
     // beats one chunk size for all tiles.
@@ -861,9 +1244,23 @@ cudaError_t launch_heat7x2(ConstRing in, Ring out, int64_t nx, int64_t ny, int64
     }
     if (ncta > 0x7fffffffll)
         return cudaErrorInvalidValue;
+#if OOC_HEATX2_ROWS == 3
+    // the TMA x coordinate (first column - 8) is a multiple of 4 floats:
+    // tiles start at multiples of 120; ring strides are multiples of 16 bytes
+    if (nx % 4 || ((uintptr_t)in.base % 16) || nx > 0x7fffffffll || ny > 0x7fffffffll)
+        return cudaErrorInvalidValue;
+    CUtensorMap map;
+    cudaError_t e = ring_tensor_map(in.base, nx, ny, in.nslot, &map);
+    if (e != cudaSuccess)
+        return e;
+    heat7x2t_kernel<kX2tNS><<<(unsigned)ncta, dim3(kTX, NW), smem, st>>>(
+        map, out.base, (int)in.nslot, in.zbase, Grid3{nx, ny, nz, nx * ny}, z0, z1, ntiles, nfull, zch, lo, hi, band_in,
+        bin_lo, band_out, bout_lo, r);
+#else
     heat7x2r_kernel<NW><<<(unsigned)ncta, dim3(kTX, NW), 0, st>>>(in.base, out.base, (int)in.nslot, in.zbase,
                                                                  Grid3{nx, ny, nz, nx * ny}, z0, z1, ntiles, nfull,
                                                                  zch, lo, hi, band_in, bin_lo, band_out, bout_lo, r);
+#endif
 #else
     heat7x2_kernel<TYO><<<dim3((unsigned)(gx * gy), (unsigned)gz), dim3(kTX, TYO + 2), 0, st>>>(
         in.base, out.base, (int)in.nslot, in.zbase, Grid3{nx, ny, nz, nx * ny}, z0, z1, chunk, lo, hi, band_in, bin_lo,

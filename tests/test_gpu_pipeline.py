@@ -283,13 +283,17 @@ def test_wave25_compressed_pipeline_against_oracle(ooc, rw, rw_rate, ro, ro_rate
     # 128-wide x tiles and six 8-row y tiles of the wave kernel.
     #
     # Tolerance: both sides round-trip identical formats at identical points,
-    # so they differ by the GPU's FP32 arithmetic (about 21 steps x 2^-24
-    # relative) carried through each codec round trip, where a value next to
-    # a truncation boundary can land on the other side (one unit of the last
-    # kept bit plane, about the codec's own error).  rel-L2 1e-4 admits such
-    # flips at a small fraction of the points; against the pure FP64 run the
-    # storage error itself (Section VI-C: grows with steps, below 1e-3 here)
-    # dominates.
+    # so they differ by the GPU's FP32 arithmetic (about 10 steps x 2^-24
+    # relative between round trips) carried through each round trip, where a
+    # value next to a rounding or truncation boundary lands on the other side
+    # and moves by one unit of what the format keeps: one BF16 ulp (2^-8
+    # relative), or one unit of the last FR4 bit plane kept (about the codec's
+    # own error, 1e-5 relative here at 16 bits/value).  Such flips hit a
+    # fraction of the points (the FP32 error over the quantum, ~1e-4 for BF16)
+    # and spread with the wave: rel-L2 below 2e-3 (BF16) and 5e-5 (FR4-16),
+    # max-abs below two units (2^-7 of the largest value for BF16).  Against
+    # the FP64 run without storage, the storage error itself (Section VI-C)
+    # adds on top.
     nz, ny, nx = 128, 48, 136
     shape = (nz, ny, nx)
     v = layered_velocity(shape, seed=3)
@@ -319,14 +323,15 @@ def test_wave25_compressed_pipeline_against_oracle(ooc, rw, rw_rate, ro, ro_rate
                                                      ro_rate=ro_rate, src=srcf, w=w.astype(np.float64))
     exact_p, _ = oracle.wave25_run(p0.astype(np.float64), pm1.astype(np.float64), kappa.astype(np.float64),
                                    sum(calls), src=srcf, w=w.astype(np.float64))
+    bf16 = rw == "bf16"
     for got, want in ((got_p, want_p), (got_pp, want_pp)):
         m = oracle.error_metrics(got, want)
         print(f"{rw}-{rw_rate}/{ro}-{ro_rate} vs oracle pipeline: {m}")
-        assert m["rel_l2"] < 1e-4, m
-        assert m["max_abs"] < 1e-3 * np.abs(want).max(), m
+        assert m["rel_l2"] < (2e-3 if bf16 else 5e-5), m
+        assert m["max_abs"] < (2.0 ** -7 if bf16 else 1e-3) * np.abs(want).max(), m
     m = oracle.error_metrics(got_p, exact_p)
     print(f"{rw}-{rw_rate}/{ro}-{ro_rate} vs FP64 run without storage: {m}")
-    assert m["rel_l2"] < 1e-3, m
+    assert m["rel_l2"] < (2e-2 if bf16 else 1e-4), m
 
 
 @pytest.mark.parametrize("table", [True, False])
