@@ -9,11 +9,12 @@ compressed-vs-uncompressed comparison.  Error is stated against the FP64
 oracle on a sampled central 128^3 sub-box (exact dependency cone).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload heat1024|kernels512|wave1024|precision|precision192|adjoint512]
+                  [--workload heat1024|kernels512|window56|wave1024|precision|precision192|adjoint512]
 
 Prints one JSON line (rank 0).  The default workload is the headline; the
 others measure the remaining configurations: one launch of each kernel on a
-512^3 field (kernels512, the ncu capture case), the 1024^3 wave with the
+512^3 field (kernels512), the headline's kernels on one 56-plane 1024^2
+window (window56, the ncu capture case of the headline), the 1024^3 wave with the
 paper's four storage codes (wave1024), the long-horizon precision study
 (precision at 384^3 with an FP64-oracle prefix; precision192 with the oracle
 over all 4320 steps) and the checkpointed adjoint at 512^3 (adjoint512).  N > 1 runs N independent replicas (the
@@ -46,14 +47,24 @@ BUDGET = 1 << 30
 SPL = int(os.environ.get("OOC_BENCH_HEAT_STEPS_PER_LAUNCH", "2"))
 MAIN = ("fr4", 16)
 COMPARE = [("fp32", 0), ("bf16", 0), ("fr4", 8), ("fr4", 12), ("fr4", 24)]
-# DRAM traffic per point of one heat7 launch, from `ncu --set full` on the
-# 512^3 case of `--workload kernels512` (dram__bytes_read.sum +
-# dram__bytes_write.sum over 134.2 M points).  Traffic is proportional to the
-# points a launch processes, so the bench scales it to its own launches.  It
-# is only valid for the heat7 code it was measured on (sha256 prefix of that
-# source without comments).
-HEAT7_TRAFFIC_PER_POINT = 7.81
-HEAT7_TRAFFIC_SRC_SHA = "3b74f465d61db6f3"
+# ncu counters of the headline's three kernels, per launch, on one 56-plane
+# window of 1024^2 planes (58,720,256 points or values; FR4 at 16 bits per
+# value): `python bench.py --workload window56 --steps 1 --warmup 0` under
+# `ncu --set full --clock-control none -k regex:"heat7x2t|fr4_encode_kernel|
+# fr4_decode_kernel" -c 4`.  DRAM bytes (read + write) and executed warp
+# instructions scale with the points a launch processes, so the bench scales
+# them to its own launches.  They hold only for the kernel source they were
+# taken on: `sha` is the hash of that .cu file without comments and blank
+# lines, and a changed file gives null.
+NCU_UNITS = 56 * 1024 * 1024
+NCU_COUNTERS = {
+    "heat7_stencil": {"src": "stencil.cu", "sha": "8c9f47f5c55ef3bc", "dram_bytes": 428.7e6, "warp_inst": 87.00e6},
+    "fr4_encode": {"src": "codec.cu", "sha": "8e2c300bc5f510bb", "dram_bytes": 319.2e6, "warp_inst": 182.16e6},
+    "fr4_decode": {"src": "codec.cu", "sha": "8e2c300bc5f510bb", "dram_bytes": 296.9e6, "warp_inst": 180.98e6},
+}
+# issue peak: 152 SMs x 4 schedulers x one warp instruction per clock at the
+# maximum SM clock of 2070 MHz
+ISSUE_PEAK_WARP_INST = 152 * 4 * 2070e6
 METRIC = "Gpts/s out-of-core (compressed vs uncompressed, same GB300) at stated L2 error; % roofline"
 WORKLOAD = "heat7 1024^3 FP32, device budget 1 GiB, k=4, 64 steps/bench step"
 
@@ -62,26 +73,24 @@ def fmt_name(fmt, rate):
     return f"fr4-{rate}" if fmt == "fr4" else fmt
 
 
-def stencil_source_sha():
-    """sha256 prefix of the heat7 kernel's source: stencil.cu up to the
-    kernel that follows heat7_kernel, with comments and blank lines removed
-    and without the settings of the fused heat7x2 kernel that share the
-    file's preamble (the traffic measurement is tied to the heat7 code)."""
+def source_sha(name):
+    """sha256 prefix of csrc/<name> with comments and blank lines removed."""
     import hashlib
     import re
-    with open(os.path.join(ROOT, "paper_2109_05410_gb300", "csrc", "stencil.cu")) as f:
+    with open(os.path.join(ROOT, "paper_2109_05410_gb300", "csrc", name)) as f:
         text = f.read()
-    end = text.find("// Two heat7 steps per launch")
-    text = text[:end if end >= 0 else len(text)]
-    code = [re.sub(r"//.*$", "", line).rstrip() for line in text.split("\n")]
-    kept, skipped = [], False
-    for line in (l for l in code if l):
-        if "HEATX2" in line or "kHeatX2TY" in line or (skipped and line.strip() == "#endif"):
-            skipped = "HEATX2" in line or "kHeatX2TY" in line
-            continue
-        skipped = False
-        kept.append(line)
-    return hashlib.sha256("\n".join(kept).encode()).hexdigest()[:16]
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    code = [" ".join(re.sub(r"//.*$", "", line).split()) for line in text.split("\n")]
+    return hashlib.sha256("\n".join(l for l in code if l).encode()).hexdigest()[:16]
+
+
+def ncu_counters(kernel):
+    """The window56 ncu counters of `kernel`, or None when its source has
+    changed since they were taken."""
+    c = NCU_COUNTERS.get(kernel)
+    if c is None or source_sha(c["src"]) != c["sha"]:
+        return None
+    return c
 
 
 def load_peaks():
@@ -355,26 +364,41 @@ def run_gpu(args, world, rank, local):
         "fr4_decode": {"ms": st["ms_decode"], "launches": st["n_decode"], "bytes": (4 + rate / 8) * pts * st["passes"]},
         "fr4_encode": {"ms": st["ms_encode"], "launches": st["n_encode"], "bytes": (4 + rate / 8) * pts * st["passes"]},
     }
-    for kv in kernels.values():
+    # units (points or values) of each kernel class over the timed region
+    units = {"heat7_stencil": nsten / SPL, "fr4_decode": pts * st["passes"], "fr4_encode": pts * st["passes"]}
+    for name, kv in kernels.items():
         kv["GBs"] = kv["bytes"] / (kv["ms"] / 1e3) / 1e9 if kv["ms"] > 0 else None
         kv["frac_hbm"] = kv["GBs"] / hbm_peak if kv["GBs"] else None
+        c = ncu_counters(name) if SPL == 2 or name != "heat7_stencil" else None
+        per_launch = units[name] / max(kv["launches"], 1)
+        kv["dram_bytes_per_launch_ncu"] = c["dram_bytes"] / NCU_UNITS * per_launch if c else None
+        kv["issue_frac"] = (c["warp_inst"] / NCU_UNITS * units[name] / (kv["ms"] / 1e3) / ISSUE_PEAK_WARP_INST
+                            if c and kv["ms"] > 0 else None)
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     dk = kernels[dom]
     launches = max(dk["launches"], 1)
-    traffic = None
-    if dom == "heat7_stencil" and SPL == 1 and stencil_source_sha() == HEAT7_TRAFFIC_SRC_SHA:
-        traffic = HEAT7_TRAFFIC_PER_POINT * (dk["bytes"] / 8) / launches
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": dk["GBs"], "peak": hbm_peak, "unit": "GB/s",
-                "frac": dk["frac_hbm"], "traffic": traffic,
-                "bytes_per_launch": dk["bytes"] / launches, "ms_per_launch": dk["ms"] / launches,
-                "peak_source": peak_src,
-                "timing": "CUDA events on the compute stream around each slab's stencil launches (and each "
-                          "codec launch) over a second timed region of the same steps; mean launch = bracketed "
-                          "time / launches (whole-job rate with the events: %.1f Gpts/s)" % value_profiled}
-    if dom == "heat7_stencil" and SPL == 2:
-        roofline["kernel"] = "heat7x2r (two heat7 steps per launch)"
-        roofline["note"] = ("the fused kernel moves 4 B per point-step instead of 8; traffic is null when its "
-                            "DRAM counters were not taken on this kernel source")
+    timing = ("CUDA events on the compute stream around each slab's stencil launches and each codec launch, "
+              "over a second timed region of the same steps; mean launch = bracketed time / launches (whole-job "
+              "rate with the events: %.1f Gpts/s)" % value_profiled)
+    if dom == "heat7_stencil":
+        roofline = {"bound": "hbm", "kernel": "heat7x2t (two heat7 steps per launch)" if SPL == 2 else "heat7",
+                    "achieved": dk["GBs"], "peak": hbm_peak, "unit": "GB/s", "frac": dk["frac_hbm"],
+                    "traffic": dk["dram_bytes_per_launch_ncu"], "bytes_per_launch": dk["bytes"] / launches,
+                    "ms_per_launch": dk["ms"] / launches, "peak_source": peak_src, "timing": timing}
+    else:
+        # the codec is bound by instruction issue (integer and shared-memory
+        # work per block), not by HBM: its roofline is the issue rate, with
+        # its HBM fraction beside it
+        c = ncu_counters(dom)
+        ach = c["warp_inst"] / NCU_UNITS * units[dom] / (dk["ms"] / 1e3) / 1e9 if c and dk["ms"] > 0 else None
+        roofline = {"bound": "alu", "kernel": dom + "_kernel", "achieved": ach, "peak": ISSUE_PEAK_WARP_INST / 1e9,
+                    "unit": "G warp-instructions/s", "frac": ach * 1e9 / ISSUE_PEAK_WARP_INST if ach else None,
+                    "traffic": dk["dram_bytes_per_launch_ncu"], "bytes_per_launch": dk["bytes"] / launches,
+                    "ms_per_launch": dk["ms"] / launches, "hbm_achieved_GBs": dk["GBs"], "hbm_frac": dk["frac_hbm"],
+                    "peak_source": "152 SMs x 4 schedulers x 1 warp instruction per clock x 2070 MHz",
+                    "achieved_source": "executed warp instructions per value from ncu on the window56 case "
+                                       "(same kernel source), scaled to the values of the timed launches",
+                    "timing": timing}
     h2d_GBs = st["h2d_bytes"] / (st["ms_h2d"] / 1e3) / 1e9 if st["ms_h2d"] > 0 else None
     d2h_GBs = st["d2h_bytes"] / (st["ms_d2h"] / 1e3) / 1e9 if st["ms_d2h"] > 0 else None
     plan.close()
@@ -586,6 +610,52 @@ def run_kernels512(args, world, rank, local):
     if rank == 0:
         print(json.dumps({"workload": "kernels512", "kernels": res, "codec_variants": var, "n_gpus": world,
                           "steps": args.steps, "warmup": args.warmup}), flush=True)
+    return 0
+
+
+def run_window56(args, world, rank, local):
+    """The headline pipeline's kernels on one of its windows, in-core: a
+    56-plane window of 1024^2 planes (the slab thickness the 1 GiB budget
+    gives at k = 4), a smooth field; per step one fused heat7 pair launch
+    (two launches per call: levels 0 -> 2 -> 4, no copy back), one FR4-16
+    encode and one decode of the window.  CUDA-event times per launch.  This
+    is the small ncu capture case of the 1024^3 workload's kernels."""
+    import torch
+
+    import paper_2109_05410_gb300 as ooc
+    from synth import smooth_random_field
+    torch.cuda.set_device(local)
+    ooc.build()
+    ooc.lib()
+    shape = (56, 1024, 1024)
+    pts = 56 * 1024 * 1024
+    d = torch.from_numpy(smooth_random_field(shape, 32.0, seed=2)).cuda()
+    tmp = torch.empty_like(d)
+    out = torch.empty_like(d)
+    w = torch.empty(ooc.ooc_compressed_bytes(1024, 1024, 56, 16), dtype=torch.uint8, device="cuda")
+    ops = {
+        # name: (call, launches per call, algorithmic bytes per launch)
+        "heat7x2_pair": (lambda: ooc.ooc_heat7_steps_fused(d, tmp, 4), 2, 8 * pts),
+        "fr4_encode": (lambda: ooc.ooc_compress(d, 16, d_out=w), 1, (4 + 2) * pts),
+        "fr4_decode": (lambda: ooc.ooc_decompress(w, shape, 16, d_out=out), 1, (4 + 2) * pts),
+    }
+    res = {}
+    for name, (fn, nl, by) in ops.items():
+        for _ in range(args.warmup):
+            fn()
+        e0, e1 = _cuda_events(torch)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(max(args.steps, 1)):
+            fn()
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / max(args.steps, 1) / nl
+        res[name] = {"us_per_launch": 1e3 * ms, "GBs": by / (ms / 1e3) / 1e9, "bytes_per_launch": by}
+    if rank == 0:
+        print(json.dumps({"workload": "window56", "window": list(shape), "kernels": res,
+                          "device_fault": ooc.ooc_take_device_fault(), "steps": args.steps,
+                          "warmup": args.warmup}), flush=True)
     return 0
 
 
@@ -846,13 +916,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="heat1024",
-                    choices=["heat1024", "kernels512", "wave1024", "precision", "precision192", "adjoint512"])
+                    choices=["heat1024", "kernels512", "window56", "wave1024", "precision", "precision192",
+                             "adjoint512"])
     args = ap.parse_args()
     world, rank, local = dist_init(args)
     try:
         if args.impl == "reference":
             return run_reference(args, world, rank)
-        runner = {"heat1024": run_gpu, "kernels512": run_kernels512, "wave1024": run_wave1024,
+        runner = {"heat1024": run_gpu, "kernels512": run_kernels512, "window56": run_window56,
+                  "wave1024": run_wave1024,
                   "precision": run_precision,
                   "precision192": lambda a, w, r, l: run_precision(a, w, r, l, n=192, oracle_budget_s=1e9),
                   "adjoint512": run_adjoint512}[args.workload]

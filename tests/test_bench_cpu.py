@@ -99,23 +99,27 @@ def test_overlap_summary_attributes_compute_idle_time():
     assert bench.overlap_summary([]) is None
 
 
-def test_heat7_traffic_hash_tracks_heat7_code_only(tmp_path, monkeypatch):
-    # The bench ties its measured heat7 DRAM traffic to a hash of the heat7
-    # part of stencil.cu: comments, blank lines and the fused kernel's
-    # settings (OOC_HEATX2_* blocks) do not change it; code does.
+def test_ncu_counters_follow_the_kernel_source(tmp_path, monkeypatch):
+    # The bench ties its ncu DRAM and instruction counts to a hash of each
+    # kernel's source file: comments and blank lines do not change it, code
+    # does, and a changed source gives no counters (null traffic).
     sys.path.insert(0, ROOT)
     import bench
-    src = open(os.path.join(ROOT, "paper_2109_05410_gb300", "csrc", "stencil.cu")).read()
     d = tmp_path / "paper_2109_05410_gb300" / "csrc"
     d.mkdir(parents=True)
+    srcs = {n: open(os.path.join(ROOT, "paper_2109_05410_gb300", "csrc", n)).read()
+            for n in ("stencil.cu", "codec.cu")}
 
-    def sha_of(text):
-        (d / "stencil.cu").write_text(text)
+    def write(name, text):
+        for n, t in srcs.items():
+            (d / n).write_text(text if n == name else t)
         monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-        return bench.stencil_source_sha()
 
-    base = sha_of(src)
-    assert base == bench.HEAT7_TRAFFIC_SRC_SHA
-    assert sha_of(src.replace("namespace ooc {", "// a new comment\n\nnamespace ooc {", 1)) == base
-    assert sha_of(src.replace("#define OOC_HEATX2_NW 8", "#define OOC_HEATX2_NW 6", 1)) == base
-    assert sha_of(src.replace("constexpr int kHeatTY = 2;", "constexpr int kHeatTY = 4;", 1)) != base
+    for kernel, c in bench.NCU_COUNTERS.items():
+        write(c["src"], srcs[c["src"]])
+        assert bench.source_sha(c["src"]) == c["sha"], kernel
+        assert bench.ncu_counters(kernel) is c
+        write(c["src"], "// a new comment\n\n" + srcs[c["src"]].replace("namespace ooc {", "/* note */ namespace ooc {", 1))
+        assert bench.ncu_counters(kernel) is c
+        write(c["src"], srcs[c["src"]].replace("namespace ooc {", "namespace ooc { constexpr int kChanged = 1;", 1))
+        assert bench.ncu_counters(kernel) is None
