@@ -541,6 +541,7 @@ def run_kernels512(args, world, rank, local):
     n = 512
     pts = n ** 3
     d = torch.from_numpy(smooth_random_field((n, n, n), 32.0, seed=2)).cuda()
+    d_codec = d.clone()  # the stencil ops below advance d in place; the codec variants get the field itself
     w = torch.empty(ooc.ooc_compressed_bytes(n, n, n, 16), dtype=torch.uint8, device="cuda")
     out = torch.empty_like(d)
     tmp = torch.empty_like(d)
@@ -583,6 +584,7 @@ def run_kernels512(args, world, rank, local):
     # codec variants: variable-size blocks (two encode passes with a prefix
     # sum and a host read of the size in between; one decode pass)
     var = {}
+    d = d_codec
     for name, mode, param in (("precision16", ooc.OOC_FR4_PRECISION, 16), ("accuracy1e-4", ooc.OOC_FR4_ACCURACY, 1e-4)):
         stream, index = ooc.ooc_compress_var(d, mode, param)
         times = {}

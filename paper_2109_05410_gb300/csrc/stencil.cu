@@ -576,13 +576,27 @@ OOC_PRAGMA(unroll OOC_HEATX2_UNROLL)
 // suspending up to ~1 us) the CTA agrees, through the plane barrier, to stop;
 // thread 0 then waits (bounded again) for the copies it issued, sets
 // g_stencil_fault and the CTA returns without writing further planes.
-constexpr int kX2tNW = kHeatX2NW;                // warps (2 level-s rows each)
-constexpr int kX2tRows = 2 * kX2tNW;             // level-s rows of a tile
-constexpr int kX2tSRows = kX2tRows + 2;          // level s-1 rows staged
-constexpr int kX2tSCols = 4 * kTX + 8;           // level s-1 columns staged (136)
-constexpr int kX2tStageFloats = (kX2tSRows * kX2tSCols + 31) / 32 * 32;  // 128-byte aligned stages
-constexpr int kX2tCopyBytes = kX2tSRows * kX2tSCols * 4;
-constexpr int kX2tL1Float4 = kX2tRows * kTX;     // one level-s plane of the tile
+// Tile shape: NW warps, R level-s rows per warp (R = 2: the tiles of
+// heat7x2r_kernel), so R NW level-s rows and R NW - 2 output rows.
+#ifndef OOC_HEATX2T_R
+#define OOC_HEATX2T_R 2
+#endif
+#ifndef OOC_HEATX2T_NW
+#define OOC_HEATX2T_NW 8
+#endif
+template <int R, int NW>
+struct X2tShape {
+    static constexpr int rows = R * NW;                                  // level-s rows of a tile
+    static constexpr int tyo = rows - 2;                                 // level s+1 (output) rows
+    static constexpr int srows = rows + 2;                               // level s-1 rows staged
+    static constexpr int scols = 4 * kTX + 8;                            // level s-1 columns staged (136)
+    static constexpr int stage_floats = (srows * scols + 31) / 32 * 32;  // 128-byte aligned stages
+    static constexpr int copy_bytes = srows * scols * 4;
+    static constexpr int l1_float4 = rows * kTX;                         // one level-s plane of the tile
+};
+constexpr int kX2tR = OOC_HEATX2T_R;
+constexpr int kX2tNW = OOC_HEATX2T_NW;
+using X2t = X2tShape<kX2tR, kX2tNW>;
 // 5 stages and 3 CTAs per SM (72 KB of shared memory and at most 85
 // registers each), loop unrolled 3 times (the z-queues rotate without
 // copies).  In the 1024^3 FR4-16 pipeline (56-plane windows), per launch:
@@ -602,7 +616,7 @@ constexpr int kMbarTries = 1 << 20;
 
 size_t heat7x2t_smem_bytes()
 {
-    return (size_t)kX2tNS * kX2tStageFloats * 4 + 3 * (size_t)kX2tL1Float4 * 16 + kX2tNS * 8;
+    return (size_t)kX2tNS * X2t::stage_floats * 4 + 3 * (size_t)X2t::l1_float4 * 16 + kX2tNS * 8;
 }
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -653,20 +667,20 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
-template <int NS>
-__global__ void __launch_bounds__(kTX *kX2tNW, OOC_HEATX2T_MINB)
+template <int NS, int R, int NW>
+__global__ void __launch_bounds__(kTX *NW, OOC_HEATX2T_MINB)
     heat7x2t_kernel(const __grid_constant__ CUtensorMap tin, float *__restrict__ out, int nslot, int64_t zbase,
                     Grid3 g, int64_t z0, int64_t z1, int64_t ntiles, int64_t nfull, int64_t zchunk, int64_t lo64,
                     int64_t hi64, const float *__restrict__ band_in, int64_t bin_lo64, float *__restrict__ band_out,
                     int64_t bout_lo64, float r)
 {
-    constexpr int NW = kX2tNW;
-    constexpr int TYO = 2 * NW - 2;
+    using S = X2tShape<R, NW>;
+    constexpr int TYO = S::tyo;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *stages = reinterpret_cast<float *>(smem_raw);
-    float4 *l1 = reinterpret_cast<float4 *>(smem_raw + (size_t)NS * kX2tStageFloats * 4);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + (size_t)NS * kX2tStageFloats * 4 +
-                                                 3 * (size_t)kX2tL1Float4 * 16);
+    float4 *l1 = reinterpret_cast<float4 *>(smem_raw + (size_t)NS * S::stage_floats * 4);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + (size_t)NS * S::stage_floats * 4 +
+                                                 3 * (size_t)S::l1_float4 * 16);
     const int lane = threadIdx.x, w = threadIdx.y;
     const bool leader = lane == 0 && w == 0;
     int64_t tile, zs64, ze64;
@@ -684,16 +698,22 @@ __global__ void __launch_bounds__(kTX *kX2tNW, OOC_HEATX2T_MINB)
     const int64_t xs = (tile % gx) * (kSeg - 8) - 4;     // first level-s column
     const int64_t x4 = xs + 4 * lane;
     const int64_t y0 = (tile / gx) * TYO;
-    const int64_t ya = y0 - 1 + 2 * w, yb = ya + 1;
+    const int L0 = R * w;  // this warp's first level-s row in the tile (row y0 - 1 + L0)
     // plane indices fit 32 bits (nz <= 2^30)
     const int nz = (int)g.nz, lo = (int)lo64, hi = (int)hi64, bin_lo = (int)bin_lo64, bout_lo = (int)bout_lo64;
     const int zs = (int)zs64, ze = (int)ze64;
     const int64_t plane = g.plane;
     const bool xin = x4 >= 0 && x4 < g.nx;
-    const bool ina = xin && ya >= 0 && ya < g.ny, inb = xin && yb >= 0 && yb < g.ny;
-    const int64_t offa = ina ? ya * g.nx + x4 : 0, offb = inb ? yb * g.nx + x4 : 0;
     const bool lin = lane >= 1 && lane <= kTX - 2;
-    const bool owna = ina && lin && w >= 1, ownb = inb && lin && w <= NW - 2;
+    bool in[R], own[R];
+    int64_t off[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const int64_t y = y0 - 1 + L0 + j;
+        in[j] = xin && y >= 0 && y < g.ny;
+        off[j] = in[j] ? y * g.nx + x4 : 0;
+        own[j] = in[j] && lin && L0 + j >= 1 && L0 + j <= S::rows - 2;  // level s+1 stored here
+    }
     const float4 z4 = zero4();
 
     // staged planes zs-2 .. ze+1: stage index i holds plane zs - 2 + i in
@@ -706,8 +726,8 @@ __global__ void __launch_bounds__(kTX *kX2tNW, OOC_HEATX2T_MINB)
     auto issue = [&](int i) {  // copies plane zfirst + i; i advances by one per call
         const int zp = zfirst + i, sl = i % NS;
         if (zp >= 0 && zp < nz) {
-            mbar_arrive_tx(&bar[sl], (unsigned)kX2tCopyBytes);
-            tma_load_3d(stages + sl * kX2tStageFloats, &tin, tx, ty, islot, &bar[sl]);
+            mbar_arrive_tx(&bar[sl], (unsigned)S::copy_bytes);
+            tma_load_3d(stages + sl * S::stage_floats, &tin, tx, ty, islot, &bar[sl]);
         } else {
             mbar_arrive(&bar[sl]);  // a plane outside the grid: nothing to copy, the phase completes at once
         }
@@ -725,78 +745,71 @@ __global__ void __launch_bounds__(kTX *kX2tNW, OOC_HEATX2T_MINB)
         for (int i = 0; i < NS && i < nplanes; ++i)
             issue(i);
     issued = NS < nplanes ? NS : nplanes;
-    // this thread's float4 of a staged row (column 4 lane + 4) and the
-    // halo floats of lanes 0 (column 3) and 31 (column 4 kTX + 4)
-    auto srow = [&](int sl, int row) -> const float * {
-        return stages + sl * kX2tStageFloats + row * kX2tSCols;
-    };
+    // staged row `row` (row 0 = y0 - 2); this thread's float4 is at column
+    // 4 lane + 4, the halo floats of lanes 0 and 31 at columns 3 and 4 kTX + 4
+    auto srow = [&](int sl, int row) -> const float * { return stages + sl * S::stage_floats + row * S::scols; };
     auto s4 = [&](int sl, int row) -> float4 { return reinterpret_cast<const float4 *>(srow(sl, row))[lane + 1]; };
 
     unsigned fail = 0;
     fail |= mbar_wait(&bar[0], 0) ? 0u : 1u;
     fail |= mbar_wait(&bar[1 % NS], (1 / NS) & 1) ? 0u : 1u;
-    // level s-1 queue z-1, z, z+1 of rows a and b (zero outside the grid:
-    // the copies fill zeros there, and planes outside the grid are not read)
-    float4 pa = z4, pb = z4, ca = z4, cb = z4;
-    if (!fail) {
-        if (zfirst >= 0) {
-            pa = s4(0, 2 * w + 1);
-            pb = s4(0, 2 * w + 2);
-        }
-        if (zfirst + 1 >= 0 && zfirst + 1 < nz) {
-            ca = s4(1 % NS, 2 * w + 1);
-            cb = s4(1 % NS, 2 * w + 2);
-        }
+    // level s-1 queue z-1, z, z+1 of the thread's rows (zero outside the
+    // grid: the copies fill zeros there, and planes outside are not read)
+    float4 pq[R], cq[R], s2[R], s1[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        pq[j] = (!fail && zfirst >= 0) ? s4(0, L0 + j + 1) : z4;
+        cq[j] = (!fail && zfirst + 1 >= 0 && zfirst + 1 < nz) ? s4(1 % NS, L0 + j + 1) : z4;
+        s2[j] = z4;  // level s at planes z-2, z-1
+        s1[j] = z4;
     }
-    float4 s2a = z4, s1a = z4, s2b = z4, s1b = z4;  // level s at planes z-2, z-1
-    int sc = 1 % NS, sn = 2 % NS;                    // stages of planes z and z+1
-    int l1c = 0;                                     // level-s ring plane of z
+    int sc = 1 % NS, sn = 2 % NS;                      // stages of planes z and z+1
+    int l1c = 0;                                       // level-s ring plane of z
     int oslot = (int)ring_slot(zs - 2, zbase, nslot);  // output ring slot of plane z-1
 OOC_PRAGMA(unroll OOC_HEATX2T_UNROLL)
     for (int z = zs - 1, i = 1; z <= ze; ++z, ++i) {
         // level s-1 plane z+1 (stage index i + 1)
         if (!mbar_wait(&bar[sn], (unsigned)(((i + 1) / NS) & 1)))
             fail = 1u;
-        float4 na = z4, nb = z4;
-        if (z + 1 < nz) {
-            na = s4(sn, 2 * w + 1);
-            nb = s4(sn, 2 * w + 2);
+        float4 nq[R], sv[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            nq[j] = z + 1 < nz ? s4(sn, L0 + j + 1) : z4;
+            sv[j] = z4;
         }
-        // level s at plane z (z is uniform over the CTA)
-        float4 sva = z4, svb = z4;
+        // level s at plane z (z is uniform over the CTA); a row's neighbours
+        // on the thread's other rows come from registers
         if (z >= lo && z < hi) {
-            const float4 upa = s4(sc, 2 * w);
-            const float4 dnb = s4(sc, 2 * w + 3);
-            float xla = __shfl_up_sync(0xffffffffu, ca.w, 1), xra = __shfl_down_sync(0xffffffffu, ca.x, 1);
-            float xlb = __shfl_up_sync(0xffffffffu, cb.w, 1), xrb = __shfl_down_sync(0xffffffffu, cb.x, 1);
-            if (lane == 0) {
-                xla = srow(sc, 2 * w + 1)[3];
-                xlb = srow(sc, 2 * w + 2)[3];
+            const float4 upo = s4(sc, L0);          // the row above the thread's first
+            const float4 dno = s4(sc, L0 + R + 1);  // the row below its last
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                float xl = __shfl_up_sync(0xffffffffu, cq[j].w, 1), xr = __shfl_down_sync(0xffffffffu, cq[j].x, 1);
+                if (lane == 0)
+                    xl = srow(sc, L0 + j + 1)[3];
+                if (lane == kTX - 1)
+                    xr = srow(sc, L0 + j + 1)[4 * kTX + 4];
+                const float4 o = heat_pt4(cq[j], xl, xr, j == 0 ? upo : cq[j - 1], j == R - 1 ? dno : cq[j + 1],
+                                          pq[j], nq[j], r);
+                sv[j] = in[j] ? o : z4;
             }
-            if (lane == kTX - 1) {
-                xra = srow(sc, 2 * w + 1)[4 * kTX + 4];
-                xrb = srow(sc, 2 * w + 2)[4 * kTX + 4];
-            }
-            const float4 oa = heat_pt4(ca, xla, xra, upa, cb, pa, na, r);
-            const float4 ob = heat_pt4(cb, xlb, xrb, ca, dnb, pb, nb, r);
-            sva = ina ? oa : z4;
-            svb = inb ? ob : z4;
         } else if (band_in != nullptr && z >= bin_lo && z < bin_lo + 2) {
             const float *bp = band_in + (int64_t)(z - bin_lo) * plane;
-            if (ina)
-                sva = ldg4(bp + offa);
-            if (inb)
-                svb = ldg4(bp + offb);
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                if (in[j])
+                    sv[j] = ldg4(bp + off[j]);
         }
         if (band_out != nullptr && z >= bout_lo && z < bout_lo + 2) {
             float *bp = band_out + (int64_t)(z - bout_lo) * plane;
-            if (owna)
-                *reinterpret_cast<float4 *>(bp + offa) = sva;
-            if (ownb)
-                *reinterpret_cast<float4 *>(bp + offb) = svb;
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                if (own[j])
+                    *reinterpret_cast<float4 *>(bp + off[j]) = sv[j];
         }
-        l1[l1c * kX2tL1Float4 + (2 * w) * kTX + lane] = sva;
-        l1[l1c * kX2tL1Float4 + (2 * w + 1) * kTX + lane] = svb;
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+            l1[l1c * S::l1_float4 + (L0 + j) * kTX + lane] = sv[j];
         // all threads have read stage z-1 and written level s of plane z;
         // the plane read next (level s of z-1) was written before this
         // barrier in the previous iteration
@@ -817,26 +830,26 @@ OOC_PRAGMA(unroll OOC_HEATX2T_UNROLL)
         // level s+1 at plane z-1 from level s at planes z-2, z-1, z
         if (z - 1 >= zs) {
             const int lp = l1c == 0 ? 2 : l1c - 1;
-            const float4 upa = w >= 1 ? l1[lp * kX2tL1Float4 + (2 * w - 1) * kTX + lane] : z4;
-            const float4 dnb = w <= NW - 2 ? l1[lp * kX2tL1Float4 + (2 * w + 2) * kTX + lane] : z4;
-            const float yla = __shfl_up_sync(0xffffffffu, s1a.w, 1), yra = __shfl_down_sync(0xffffffffu, s1a.x, 1);
-            const float ylb = __shfl_up_sync(0xffffffffu, s1b.w, 1), yrb = __shfl_down_sync(0xffffffffu, s1b.x, 1);
-            const float4 oa = heat_pt4(s1a, yla, yra, upa, s1b, s2a, sva, r);
-            const float4 ob = heat_pt4(s1b, ylb, yrb, s1a, dnb, s2b, svb, r);
+            const float4 upo = w >= 1 ? l1[lp * S::l1_float4 + (L0 - 1) * kTX + lane] : z4;
+            const float4 dno = w <= NW - 2 ? l1[lp * S::l1_float4 + (L0 + R) * kTX + lane] : z4;
             float *op = out + (int64_t)oslot * plane;
-            if (owna)
-                *reinterpret_cast<float4 *>(op + offa) = oa;
-            if (ownb)
-                *reinterpret_cast<float4 *>(op + offb) = ob;
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const float yl = __shfl_up_sync(0xffffffffu, s1[j].w, 1);
+                const float yr = __shfl_down_sync(0xffffffffu, s1[j].x, 1);
+                const float4 o = heat_pt4(s1[j], yl, yr, j == 0 ? upo : s1[j - 1], j == R - 1 ? dno : s1[j + 1],
+                                          s2[j], sv[j], r);
+                if (own[j])
+                    *reinterpret_cast<float4 *>(op + off[j]) = o;
+            }
         }
-        s2a = s1a;
-        s1a = sva;
-        s2b = s1b;
-        s1b = svb;
-        pa = ca;
-        ca = na;
-        pb = cb;
-        cb = nb;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            s2[j] = s1[j];
+            s1[j] = sv[j];
+            pq[j] = cq[j];
+            cq[j] = nq[j];
+        }
         sc = sn;
         sn = sn + 1 == NS ? 0 : sn + 1;
         l1c = l1c == 2 ? 0 : l1c + 1;
@@ -1151,7 +1164,7 @@ cudaError_t ring_tensor_map(const float *base, int64_t nx, int64_t ny, int64_t n
     // out-of-range x and y read as zero (the boundary's zero ghosts)
     const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nslot};
     const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)(nx * ny) * 4};
-    const cuuint32_t box[3] = {(cuuint32_t)kX2tSCols, (cuuint32_t)kX2tSRows, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)X2t::scols, (cuuint32_t)X2t::srows, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     MapEntry e{base, nx, ny, nslot, dev, {}};
     if (encode(&e.map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
@@ -1191,15 +1204,15 @@ cudaError_t launch_heat7x2(ConstRing in, Ring out, int64_t nx, int64_t ny, int64
 #if OOC_HEATX2_ROWS == 3
     // TMA-staged kernel: same tiles and split as heat7x2r_kernel
     constexpr int NW = kX2tNW;
-    constexpr int TYO = 2 * NW - 2;
+    constexpr int TYO = X2t::tyo;
     static int res = 0;
     const size_t smem = heat7x2t_smem_bytes();
     if (res == 0) {
-        const cudaError_t e = cudaFuncSetAttribute(heat7x2t_kernel<kX2tNS>,
+        const cudaError_t e = cudaFuncSetAttribute(heat7x2t_kernel<kX2tNS, kX2tR, kX2tNW>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
-        res = resident((const void *)heat7x2t_kernel<kX2tNS>, kTX * NW, smem);
+        res = resident((const void *)heat7x2t_kernel<kX2tNS, kX2tR, kX2tNW>, kTX * NW, smem);
     }
 #elif OOC_HEATX2_ROWS == 2
     constexpr int NW = kHeatX2NW;
@@ -1253,7 +1266,7 @@ cudaError_t launch_heat7x2(ConstRing in, Ring out, int64_t nx, int64_t ny, int64
     cudaError_t e = ring_tensor_map(in.base, nx, ny, in.nslot, &map);
     if (e != cudaSuccess)
         return e;
-    heat7x2t_kernel<kX2tNS><<<(unsigned)ncta, dim3(kTX, NW), smem, st>>>(
+    heat7x2t_kernel<kX2tNS, kX2tR, kX2tNW><<<(unsigned)ncta, dim3(kTX, NW), smem, st>>>(
         map, out.base, (int)in.nslot, in.zbase, Grid3{nx, ny, nz, nx * ny}, z0, z1, ntiles, nfull, zch, lo, hi, band_in,
         bin_lo, band_out, bout_lo, r);
 #else
