@@ -58,7 +58,8 @@ COMPARE = [("fp32", 0), ("bf16", 0), ("fr4", 8), ("fr4", 12), ("fr4", 24)]
 # lines, and a changed file gives null.
 NCU_UNITS = 56 * 1024 * 1024
 NCU_COUNTERS = {
-    "heat7_stencil": {"src": "stencil.cu", "sha": "8c9f47f5c55ef3bc", "dram_bytes": 428.7e6, "warp_inst": 87.00e6},
+    "heat7_stencil": {"src": ["heat_tma.cu", "stencil_common.cuh"], "sha": "", "dram_bytes": 428.7e6,
+                      "warp_inst": 90.66e6},
     "fr4_encode": {"src": "codec.cu", "sha": "8e2c300bc5f510bb", "dram_bytes": 319.2e6, "warp_inst": 182.16e6},
     "fr4_decode": {"src": "codec.cu", "sha": "8e2c300bc5f510bb", "dram_bytes": 296.9e6, "warp_inst": 180.98e6},
 }
@@ -73,12 +74,15 @@ def fmt_name(fmt, rate):
     return f"fr4-{rate}" if fmt == "fr4" else fmt
 
 
-def source_sha(name):
-    """sha256 prefix of csrc/<name> with comments and blank lines removed."""
+def source_sha(names):
+    """sha256 prefix of the csrc/ files `names` (one name or a list), with
+    comments and blank lines removed."""
     import hashlib
     import re
-    with open(os.path.join(ROOT, "paper_2109_05410_gb300", "csrc", name)) as f:
-        text = f.read()
+    text = ""
+    for name in [names] if isinstance(names, str) else names:
+        with open(os.path.join(ROOT, "paper_2109_05410_gb300", "csrc", name)) as f:
+            text += f.read() + "\n"
     text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
     code = [" ".join(re.sub(r"//.*$", "", line).split()) for line in text.split("\n")]
     return hashlib.sha256("\n".join(l for l in code if l).encode()).hexdigest()[:16]
@@ -841,8 +845,8 @@ def run_precision(args, world, rank, local, n=384, oracle_budget_s=120.0):
 def run_adjoint512(args, world, rank, local):
     """Adjoint at 512^3: forward 1500 steps with FR4-16 checkpoints every 10
     steps in pinned host memory, backward replay + discrete adjoint, gradient
-    w.r.t. kappa; checked against a central difference of the misfit along a
-    smooth random direction (GPU FP32 forward, FP64 misfit)."""
+    w.r.t. kappa; checked against central differences of the misfit along four
+    smooth random directions (GPU FP32 forward, FP64 misfit)."""
     import torch
 
     import paper_2109_05410_gb300 as ooc
@@ -893,11 +897,16 @@ def run_adjoint512(args, world, rank, local):
         ooc.ooc_wave25_forward_ckpt(kk, N, rec, t, every, rate, h_ckpt, work, streams, src=src, w=w)
         return 0.5 * float(((t.double() - d.double()) ** 2).sum())
 
-    delta = torch.from_numpy(np.clip(smooth_random_field(shape, 8.0, seed=21, dtype=np.float64), -1, 1)
-                             .astype(np.float32)).cuda() * kap
     eps = 1e-3
-    fd = (misfit(kap + eps * delta) - misfit(kap - eps * delta)) / (2 * eps)
-    an = float((g * delta.double()).sum())
+    fds, ans = [], []
+    for seed in (21, 22, 23, 24):  # four seeded smooth kappa-relative directions
+        delta = torch.from_numpy(np.clip(smooth_random_field(shape, 8.0, seed=seed, dtype=np.float64), -1, 1)
+                                 .astype(np.float32)).cuda() * kap
+        fds.append((misfit(kap + eps * delta) - misfit(kap - eps * delta)) / (2 * eps))
+        ans.append(float((g * delta.double()).sum()))
+        del delta
+    fd, an = fds[0], ans[0]
+    rel = [abs(f - a) / abs(f) if f else None for f, a in zip(fds, ans)]
     if rank == 0:
         print(json.dumps({"workload": "adjoint512", "grid": list(shape), "steps": N, "ckpt_every": every,
                           "ckpt_rate": rate, "ckpt_bytes_pinned": h_ckpt.numel(), "pin_seconds": t_pin,
@@ -906,6 +915,7 @@ def run_adjoint512(args, world, rank, local):
                           "Gpts_backward": n ** 3 * N / (ms_bwd / 1e3) / 1e9,
                           "fd_directional": fd, "adjoint_directional": an,
                           "rel_diff": abs(fd - an) / abs(fd) if fd else None,
+                          "fd_directions": fds, "adjoint_directions": ans, "rel_diff_directions": rel,
                           "fd_note": "central difference, eps 1e-3 of a smooth kappa-relative direction, GPU FP32 "
                                      "forward with FP64 misfit sums"}), flush=True)
     return 0

@@ -276,7 +276,7 @@ ooc_status ooc_velocity_grad(const double *d_grad_kappa, const float *d_v, float
                              double dt_over_dx, void *stream);
 /* Pinned host bytes for checkpoints every `every` steps at `rate` bits/value
  * (0 = FP32): ceil(N/every) checkpoints of (p^{kK}, p^{kK-1}).  Device work
- * bytes for the forward and backward runs (K + 5 fields at most). */
+ * bytes for the forward and backward runs (K + 6 fields at most). */
 size_t ooc_wave25_ckpt_bytes(int64_t nx, int64_t ny, int64_t nz, int64_t nsteps, int64_t every, int rate);
 size_t ooc_wave25_adjoint_work_bytes(int64_t nx, int64_t ny, int64_t nz, int64_t every, int rate);
 /* Forward run from rest writing d_traces[nsteps][nrec] and the checkpoints
@@ -288,6 +288,8 @@ ooc_status ooc_wave25_forward_ckpt(const float *d_kappa, int64_t nx, int64_t ny,
                                    void *d_work, size_t work_bytes, void *const streams[2]);
 /* Backward run: d_grad = dJ/dkappa (FP64, device, overwritten) for the
  * residual d_res[nsteps][nrec], replaying each segment from its checkpoint.
+ * Within a segment of `every` steps the gradient terms are summed in FP32;
+ * each segment's sum is added to the FP64 total.
  * The adjoint state is carried as kappa * mu (the forward propagator's
  * form) and the gradient divided by kappa at the end, so kappa must be
  * positive everywhere (as (v dt/dx)^2 of a positive velocity is). */

@@ -14,7 +14,7 @@
 // Checkpoints hold (p^{kK}, p^{k K - 1}) every K steps in pinned host memory,
 // FR4-compressed at `rate` bits/value (or FP32 with rate 0).  The backward
 // pass replays K steps from a checkpoint into a device history, so its
-// device footprint is K + 5 fields whatever the number of steps.
+// device footprint is K + 6 fields whatever the number of steps.
 //
 // The backward pass carries w = kappa mu instead of mu.  Multiplying the
 // adjoint recurrence by kappa gives
@@ -22,6 +22,10 @@
 // the forward propagator's own form, so the adjoint step runs on the
 // forward wave25 kernel; and dJ/dkappa = (sum_n w^{n+1} L(p^n)) / kappa,
 // the sum accumulated in FP64 and divided once at the end (kappa > 0).
+// Within a K-step segment the products and their sum are FP32 (at most K
+// terms, in a device field); each segment's sum is then added to the FP64
+// total.  GB300's FP64 pipe made a per-step FP64 update (two conversions, a
+// multiply and an add per point) the slowest kernel of the backward pass.
 #include <chrono>
 #include <cstring>
 #include <thread>
@@ -169,6 +173,16 @@ __global__ void scatter_add_scaled_kernel(float *f, const int64_t *__restrict__ 
     }
 }
 
+// g[i] += (double) a[i]; a[i] = 0: a segment's FP32 gradient sum into the
+// FP64 total.
+__global__ void flush_segment_kernel(double *__restrict__ g, float *__restrict__ a, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        g[i] += (double)a[i];
+        a[i] = 0.0f;
+    }
+}
+
 __global__ void divide_by_kappa_kernel(double *g, const float *__restrict__ kap, int64_t n)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -221,8 +235,8 @@ size_t field_bytes(int64_t n, int rate) { return rate > 0 ? (size_t)n * rate / 8
 size_t a256(size_t v) { return (v + 255) / 256 * 256; }
 
 struct Layout {
-    size_t p, pp, stage[2][2];  // forward
-    size_t mu1, mu2, hist0;     // backward (hist: K + 1 fields from hist0)
+    size_t p, pp, stage[2][2];   // forward
+    size_t mu1, mu2, gacc, hist0;  // backward (hist: K + 1 fields from hist0)
     size_t total;
 };
 
@@ -242,7 +256,8 @@ Layout make_layout(int64_t n, int64_t every, int rate)
     const size_t fwd_end = common + 2 * fb;
     L.mu1 = common;
     L.mu2 = common + fb;
-    L.hist0 = common + 2 * fb;
+    L.gacc = common + 2 * fb;
+    L.hist0 = common + 3 * fb;
     const size_t bwd_end = L.hist0 + (size_t)(every + 1) * fb;
     L.total = fwd_end > bwd_end ? fwd_end : bwd_end;
     return L;
@@ -443,13 +458,14 @@ ooc_status ooc_wave25_backward_ckpt(const float *d_kappa, int64_t nx, int64_t ny
     const Layout L = make_layout(n, every, rate);
     char *w = (char *)d_work;
     const size_t fb = a256((size_t)n * 4), cb = a256(field_bytes(n, rate));
-    float *mu1 = (float *)(w + L.mu1), *mu2 = (float *)(w + L.mu2);
+    float *mu1 = (float *)(w + L.mu1), *mu2 = (float *)(w + L.mu2), *gacc = (float *)(w + L.gacc);
     auto hist = [&](int64_t j) { return (float *)(w + L.hist0 + (size_t)j * fb); };
     Events ev;
     TRY_CUDA(ev.make());  // e[0..1]: staging loaded (sD), e[2..3]: staging consumed (sC)
     TRY_CUDA(cudaMemsetAsync(mu1, 0, sizeof(float) * n, sC));
     TRY_CUDA(cudaMemsetAsync(mu2, 0, sizeof(float) * n, sC));
     TRY_CUDA(cudaMemsetAsync(d_grad, 0, sizeof(double) * n, sC));
+    TRY_CUDA(cudaMemsetAsync(gacc, 0, sizeof(float) * n, sC));
     const bool src = sx >= 0 && h_w != nullptr;
     const int64_t nseg = (nsteps + every - 1) / every;
     auto load = [&](int64_t k) -> cudaError_t {  // checkpoint k -> staging (k & 1), on sD
@@ -497,11 +513,15 @@ ooc_status ooc_wave25_backward_ckpt(const float *d_kappa, int64_t nx, int64_t ny
                     mu2, d_rec, nrec, d_res + (m - 1) * nrec, d_kappa);
                 TRY_CUDA(cudaGetLastError());
             }
-            TRY_CUDA(launch_wave25_grad(hist(m - n0), mu2, d_grad, nx, ny, nz, sC));  // += w^m L(p^{m-1})
+            // += w^m L(p^{m-1}), in FP32 within the segment
+            TRY_CUDA(launch_wave25_grad32(hist(m - n0), mu2, gacc, nx, ny, nz, sC));
             float *t = mu1;
             mu1 = mu2;
             mu2 = t;
         }
+        // the segment's sum (at most `every` terms) into the FP64 total
+        flush_segment_kernel<<<grid1d(n, 256), 256, 0, sC>>>(d_grad, gacc, n);
+        TRY_CUDA(cudaGetLastError());
     }
     divide_by_kappa_kernel<<<grid1d(n, 256), 256, 0, sC>>>(d_grad, d_kappa, n);
     TRY_CUDA(cudaGetLastError());

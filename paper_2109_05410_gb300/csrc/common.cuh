@@ -53,6 +53,10 @@ cudaError_t launch_heat7(ConstRing in, Ring out, int64_t nx, int64_t ny, int64_t
 // 25-point Laplacian without kappa); g 32-byte aligned.
 cudaError_t launch_wave25_grad(const float *p, const float *mu, double *g, int64_t nx, int64_t ny, int64_t nz,
                                cudaStream_t st);
+// gacc[i] = fma(mu[i], L(p)[i], gacc[i]) in FP32 over whole dense fields
+// (gacc 16-byte aligned): the adjoint run's in-segment gradient sums.
+cudaError_t launch_wave25_grad32(const float *p, const float *mu, float *gacc, int64_t nx, int64_t ny, int64_t nz,
+                                 cudaStream_t st);
 // Two heat7 steps in one launch: level s on [lo, hi) computed on chip from
 // ring `in` (level s-1), level s+1 written to ring `out` on [z0, z1).  The
 // two level-s planes below lo are read from band_in (planes bin_lo,

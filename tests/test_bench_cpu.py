@@ -107,8 +107,9 @@ def test_ncu_counters_follow_the_kernel_source(tmp_path, monkeypatch):
     import bench
     d = tmp_path / "paper_2109_05410_gb300" / "csrc"
     d.mkdir(parents=True)
-    srcs = {n: open(os.path.join(ROOT, "paper_2109_05410_gb300", "csrc", n)).read()
-            for n in ("stencil.cu", "codec.cu")}
+    names = sorted({n for c in bench.NCU_COUNTERS.values() for n in ([c["src"]] if isinstance(c["src"], str)
+                                                                       else c["src"])})
+    srcs = {n: open(os.path.join(ROOT, "paper_2109_05410_gb300", "csrc", n)).read() for n in names}
 
     def write(name, text):
         for n, t in srcs.items():
@@ -116,12 +117,13 @@ def test_ncu_counters_follow_the_kernel_source(tmp_path, monkeypatch):
         monkeypatch.setattr(bench, "ROOT", str(tmp_path))
 
     for kernel, c0 in bench.NCU_COUNTERS.items():
-        write(c0["src"], srcs[c0["src"]])
+        first = c0["src"] if isinstance(c0["src"], str) else c0["src"][0]
+        write(first, srcs[first])
         # counters taken on the current source
         c = dict(c0, sha=bench.source_sha(c0["src"]))
         monkeypatch.setitem(bench.NCU_COUNTERS, kernel, c)
         assert bench.ncu_counters(kernel) is c
-        write(c["src"], "// a new comment\n\n" + srcs[c["src"]].replace("namespace ooc {", "/* note */ namespace ooc {", 1))
+        write(first, "// a new comment\n\n" + srcs[first].replace("namespace ooc {", "/* note */ namespace ooc {", 1))
         assert bench.ncu_counters(kernel) is c
-        write(c["src"], srcs[c["src"]].replace("namespace ooc {", "namespace ooc { constexpr int kChanged = 1;", 1))
+        write(first, srcs[first].replace("namespace ooc {", "namespace ooc { constexpr int kChanged = 1;", 1))
         assert bench.ncu_counters(kernel) is None
