@@ -269,6 +269,27 @@ def test_full_size_wave_benchmark_configuration(ooc):
     ref_p, ref_pp = incore_wave(ooc, p0, pm1, kappa, [nsteps], k, "fr4", 16, "fr4", 16, src, w)
     assert np.array_equal(got_p.view(np.uint32), ref_p.view(np.uint32))
     assert np.array_equal(got_pp.view(np.uint32), ref_pp.view(np.uint32))
+    del ref_p, ref_pp
+    # Against the FP64 oracle on sampled outputs: the central 32^3 box after
+    # 20 steps depends only on inputs within 4 x 20 = 80 planes of it, so the
+    # oracle runs on a 208^3 sub-box (88 planes of margin, 4-aligned so that
+    # its codec blocks are the full grid's blocks) with the same storage
+    # round trips.  Errors entering from the sub-box's edges travel 4 planes
+    # per step and cross at most one block per round trip: 80 + 6 < 88.
+    c0, c1, m = n // 2 - 16, n // 2 + 16, 88
+    lo, hi = c0 - m, c1 + m
+    sub = (slice(lo, hi),) * 3
+    srcf = ((src[2] - lo) * (hi - lo) + (src[1] - lo)) * (hi - lo) + (src[0] - lo)
+    want_p, _ = oracle.wave25_storage_pipeline(p0[sub], pm1[sub], kappa[sub], nsteps, k, "fr4", 16, ro_fmt="fr4",
+                                               ro_rate=16, src=srcf, w=w.astype(np.float64))
+    exact_p, _ = oracle.wave25_run(p0[sub].astype(np.float64), pm1[sub].astype(np.float64),
+                                   kappa[sub].astype(np.float64), nsteps, src=srcf, w=w.astype(np.float64))
+    cen = (slice(m, m + 32),) * 3
+    mp = oracle.error_metrics(got_p[c0:c1, c0:c1, c0:c1], want_p[cen])
+    me = oracle.error_metrics(got_p[c0:c1, c0:c1, c0:c1], exact_p[cen])
+    print(f"1024^3 wave code 4, central 32^3 after {nsteps} steps: vs oracle pipeline {mp}, vs FP64 run {me}")
+    assert mp["rel_l2"] < 1e-3, mp
+    assert me["rel_l2"] < 2e-2, me
 
 
 @pytest.mark.parametrize("rw,rw_rate,ro,ro_rate", [("fr4", 16, "fr4", 16), ("fr4", 16, "fp32", 16),
