@@ -2,11 +2,9 @@
 // launch, Section III's neighbour average with temporal blocking inside the
 // kernel), with each plane of level s-1 staged in shared memory by a TMA
 // tensor copy.
-#include <cuda.h>
-
 #include <mutex>
 
-#include "stencil_common.cuh"
+#include "tma.cuh"
 
 namespace ooc {
 
@@ -74,59 +72,9 @@ using X2t = X2tShape<kX2tR, kX2tNW>;
 #define OOC_HEATX2T_UNROLL 3
 #endif
 constexpr int kX2tNS = OOC_HEATX2T_NS;
-constexpr int kMbarTries = 1 << 20;
-
 size_t heat7x2t_smem_bytes()
 {
     return (size_t)kX2tNS * X2t::stage_floats * 4 + 3 * (size_t)X2t::l1_float4 * 16 + kX2tNS * 8;
-}
-
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// true once the phase with parity `parity` has completed; false after
-// kMbarTries polls
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
-{
-    const unsigned a = smem_u32(bar);
-    for (int it = 0; it < kMbarTries; ++it) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity), "r"(1000u)
-            : "memory");
-        if (done)
-            return true;
-    }
-    return false;
-}
-
-// TMA copy of the box at (x, y, slot) of the ring's tensor map into `dst`,
-// completing `bar`'s transaction count
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];\n" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-        : "memory");
 }
 
 template <int NS, int R, int NW>
@@ -319,24 +267,27 @@ OOC_PRAGMA(unroll OOC_HEATX2T_UNROLL)
     }
 }
 
-// Tensor maps of the rings the TMA kernel reads, keyed by (base, nx, ny,
-// slots); the pipeline alternates between two rings, so a few entries
-// cover it and a map is encoded once per ring.
+// Tensor maps of the rings the TMA kernels read, keyed by (base, nx, ny,
+// slots, box); the pipelines use a few rings, so a few entries cover them
+// and a map is encoded once per ring and box.
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 struct MapEntry {
     const void *base;
     int64_t nx, ny, nslot;
-    int dev;
+    int box_x, box_y, dev;
     CUtensorMap map;
 };
-constexpr int kMapCache = 8;
+constexpr int kMapCache = 16;
 MapEntry g_maps[kMapCache];
 int g_maps_used = 0, g_maps_next = 0;
 std::mutex g_maps_mutex;
 
-cudaError_t ring_tensor_map(const float *base, int64_t nx, int64_t ny, int64_t nslot, CUtensorMap *out)
+}  // namespace
+
+cudaError_t ring_tensor_map(const float *base, int64_t nx, int64_t ny, int64_t nslot, int box_x, int box_y,
+                            CUtensorMap *out)
 {
     static EncodeTiledFn encode = nullptr;
     int dev = 0;
@@ -345,7 +296,7 @@ cudaError_t ring_tensor_map(const float *base, int64_t nx, int64_t ny, int64_t n
     std::lock_guard<std::mutex> lock(g_maps_mutex);
     for (int i = 0; i < g_maps_used; ++i)
         if (g_maps[i].base == base && g_maps[i].nx == nx && g_maps[i].ny == ny && g_maps[i].nslot == nslot &&
-            g_maps[i].dev == dev) {
+            g_maps[i].box_x == box_x && g_maps[i].box_y == box_y && g_maps[i].dev == dev) {
             *out = g_maps[i].map;
             return cudaSuccess;
         }
@@ -358,13 +309,13 @@ cudaError_t ring_tensor_map(const float *base, int64_t nx, int64_t ny, int64_t n
             return cudaErrorNotSupported;
         encode = reinterpret_cast<EncodeTiledFn>(f);
     }
-    // dims x, y, slot; the box is the 136 x 18 staged rows of one plane;
-    // out-of-range x and y read as zero (the boundary's zero ghosts)
+    // dims x, y, slot; out-of-range x and y read as zero (the boundary's
+    // zero ghosts)
     const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nslot};
     const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)(nx * ny) * 4};
-    const cuuint32_t box[3] = {(cuuint32_t)X2t::scols, (cuuint32_t)X2t::srows, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
-    MapEntry e{base, nx, ny, nslot, dev, {}};
+    MapEntry e{base, nx, ny, nslot, box_x, box_y, dev, {}};
     if (encode(&e.map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
@@ -379,8 +330,6 @@ cudaError_t ring_tensor_map(const float *base, int64_t nx, int64_t ny, int64_t n
     return cudaSuccess;
 }
 
-}  // namespace
-
 cudaError_t take_stencil_fault(unsigned *fault)
 {
     unsigned v = 0u;
@@ -389,7 +338,10 @@ cudaError_t take_stencil_fault(unsigned *fault)
         const unsigned zero = 0u;
         e = cudaMemcpyToSymbol(g_stencil_fault, &zero, sizeof(zero));
     }
-    *fault = v;
+    unsigned vw = 0u;
+    if (e == cudaSuccess)
+        e = take_wave_fault(&vw);
+    *fault = v | vw;
     return e;
 }
 
@@ -426,7 +378,7 @@ cudaError_t launch_heat7x2(ConstRing in, Ring out, int64_t nx, int64_t ny, int64
     if (nx % 4 || ((uintptr_t)in.base % 16) || nx > 0x7fffffffll || ny > 0x7fffffffll)
         return cudaErrorInvalidValue;
     CUtensorMap map;
-    cudaError_t e = ring_tensor_map(in.base, nx, ny, in.nslot, &map);
+    cudaError_t e = ring_tensor_map(in.base, nx, ny, in.nslot, X2t::scols, X2t::srows, &map);
     if (e != cudaSuccess)
         return e;
     heat7x2t_kernel<kX2tNS, kX2tR, kX2tNW><<<(unsigned)fg.ncta, dim3(kTX, NW), smem, st>>>(

@@ -37,7 +37,7 @@ using namespace sten;
 namespace {
 
 constexpr int kHeatTY = 2;  // rows per CTA: small CTAs balance the waves of short windows
-constexpr int kWaveTY = 8;
+[[maybe_unused]] constexpr int kWaveTY = 8;  // rows per CTA of the cp.async wave kernel
 #ifndef OOC_HEAT_UNROLL
 #define OOC_HEAT_UNROLL 8
 #endif
@@ -505,6 +505,7 @@ OOC_PRAGMA(unroll OOC_HEATX2_UNROLL)
     }
 }
 
+#if !OOC_WAVE_TMA
 // x-neighbour at offset idx in [-4, 7] from the thread's first point, given
 // its own 4 points c and the 4-point groups to its left (l) and right (rr).
 __device__ __forceinline__ float pick(const float (&l)[4], const float (&c)[4], const float (&rr)[4], int idx)
@@ -709,6 +710,8 @@ OOC_PRAGMA(unroll OOC_WAVE_UNROLL)
     cp_async_wait<0>();  // no copy may outlive the CTA's shared memory
 }
 
+#endif
+
 __global__ void add_time_kernel(int64_t *t, int64_t n) { *t += n; }
 
 __global__ void swap_kernel(float *a, float *b, int64_t n)
@@ -763,7 +766,6 @@ cudaError_t launch_heat7x2_regs(ConstRing in, Ring out, int64_t nx, int64_t ny, 
 #endif
     const int64_t gx = (nx + kSeg - 9) / (kSeg - 8), gy = (ny + TYO - 1) / TYO;
     const int64_t chunk = choose_chunk(gx * gy, z1 - z0, 8, 5, res);
-    const int64_t gz = (z1 - z0 + chunk - 1) / chunk;
     if (in.nslot != out.nslot || in.zbase != out.zbase || in.nslot > (1ll << 30) || in.base == out.base ||
         gx * gy > 0x7fffffffll || nz > (1ll << 30))
         return cudaErrorInvalidValue;
@@ -775,6 +777,7 @@ cudaError_t launch_heat7x2_regs(ConstRing in, Ring out, int64_t nx, int64_t ny, 
         in.base, out.base, (int)in.nslot, in.zbase, Grid3{nx, ny, nz, nx * ny}, z0, z1, gx * gy, fg.nfull, fg.zch, lo,
         hi, band_in, bin_lo, band_out, bout_lo, r);
 #else
+    const int64_t gz = (z1 - z0 + chunk - 1) / chunk;
     heat7x2_kernel<TYO><<<dim3((unsigned)(gx * gy), (unsigned)gz), dim3(kTX, TYO + 2), 0, st>>>(
         in.base, out.base, (int)in.nslot, in.zbase, Grid3{nx, ny, nz, nx * ny}, z0, z1, chunk, lo, hi, band_in, bin_lo,
         band_out, bout_lo, r);
@@ -798,6 +801,7 @@ cudaError_t launch_heat7_f64(const double *in, double *out, int64_t nx, int64_t 
     return cudaGetLastError();
 }
 
+#if !OOC_WAVE_TMA
 cudaError_t launch_wave25_to(ConstRing p, ConstRing pprev, Ring pnew, ConstRing kappa, int64_t nx, int64_t ny,
                              int64_t nz, int64_t z0, int64_t z1, int64_t sx, int64_t sy, int64_t sz, float w,
                              cudaStream_t st, WaveSrcTable tab)
@@ -872,6 +876,8 @@ cudaError_t launch_wave25(ConstRing p, Ring pprev_out, ConstRing kappa, int64_t 
     return launch_wave25_to(p, ConstRing{pprev_out.base, pprev_out.nslot, pprev_out.zbase}, pprev_out, kappa, nx, ny,
                             nz, z0, z1, sx, sy, sz, w, st, tab);
 }
+
+#endif
 
 cudaError_t launch_add_time(int64_t *t, int64_t n, cudaStream_t st)
 {

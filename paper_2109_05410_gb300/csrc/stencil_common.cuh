@@ -11,6 +11,10 @@
 #ifndef OOC_HEATX2_ROWS
 #define OOC_HEATX2_ROWS 3
 #endif
+// wave25: 1 = TMA-staged kernel (wave_tma.cu), 0 = cp.async-staged kernel
+#ifndef OOC_WAVE_TMA
+#define OOC_WAVE_TMA 1
+#endif
 
 namespace ooc {
 namespace sten {
