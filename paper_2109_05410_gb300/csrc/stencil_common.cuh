@@ -11,9 +11,12 @@
 #ifndef OOC_HEATX2_ROWS
 #define OOC_HEATX2_ROWS 3
 #endif
-// wave25: 1 = TMA-staged kernel (wave_tma.cu), 0 = cp.async-staged kernel
+// wave25: 0 = cp.async-staged kernel (stencil.cu), 1 = TMA-staged kernel
+// (wave_tma.cu).  The TMA kernel passes the same tests but measured slower:
+// 0.393 against 0.369 ms per step at 512^3, and 188 against 209 Gpts/s for
+// the 1024^3 code-4 pipeline on one box.
 #ifndef OOC_WAVE_TMA
-#define OOC_WAVE_TMA 1
+#define OOC_WAVE_TMA 0
 #endif
 
 namespace ooc {

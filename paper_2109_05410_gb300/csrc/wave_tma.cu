@@ -1,7 +1,9 @@
 // wave_tma.cu -- the 25-point acoustic wave step (Section VI, Table I:
 // 8th-order Laplacian, HALO = 4, leapfrog in time) with its input planes
 // staged in shared memory by TMA tensor copies, and its gradient modes for
-// the adjoint run.
+// the adjoint run.  Built with OOC_WAVE_TMA = 1; the default build runs the
+// cp.async-staged kernel of stencil.cu, which measured faster (0.369 against
+// 0.393 ms per 512^3 step).
 //
 //   p' = 2p - p_prev + kappa * sum_axes[c0 p + sum_m c_m (p[+m] + p[-m])]
 //
@@ -37,6 +39,7 @@ using namespace sten;
 // take_wave_fault().
 __device__ unsigned g_wave_fault = 0u;
 
+#if OOC_WAVE_TMA
 namespace {
 
 constexpr int kWTY = 8;                 // rows per CTA (one per warp)
@@ -296,6 +299,7 @@ cudaError_t launch_wave25t(const float *p, const float *pprev, float *pout, cons
 }
 
 }  // namespace
+#endif
 
 cudaError_t take_wave_fault(unsigned *fault)
 {
@@ -310,6 +314,7 @@ cudaError_t take_wave_fault(unsigned *fault)
 }
 
 #if OOC_WAVE_TMA
+// the wave launchers (the default build has them in stencil.cu)
 cudaError_t launch_wave25_to(ConstRing p, ConstRing pprev, Ring pnew, ConstRing kappa, int64_t nx, int64_t ny,
                              int64_t nz, int64_t z0, int64_t z1, int64_t sx, int64_t sy, int64_t sz, float w,
                              cudaStream_t st, WaveSrcTable tab)

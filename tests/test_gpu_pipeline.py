@@ -288,8 +288,10 @@ def test_full_size_wave_benchmark_configuration(ooc):
     mp = oracle.error_metrics(got_p[c0:c1, c0:c1, c0:c1], want_p[cen])
     me = oracle.error_metrics(got_p[c0:c1, c0:c1, c0:c1], exact_p[cen])
     print(f"1024^3 wave code 4, central 32^3 after {nsteps} steps: vs oracle pipeline {mp}, vs FP64 run {me}")
-    assert mp["rel_l2"] < 1e-3, mp
-    assert me["rel_l2"] < 2e-2, me
+    # measured 7.6e-5 and 1.5e-3: the codec flips of the other wave tests at
+    # white-noise data, and FR4-16's storage error on white noise
+    assert mp["rel_l2"] < 3e-4, mp
+    assert me["rel_l2"] < 5e-3, me
 
 
 @pytest.mark.parametrize("rw,rw_rate,ro,ro_rate", [("fr4", 16, "fr4", 16), ("fr4", 16, "fp32", 16),
