@@ -58,7 +58,7 @@ COMPARE = [("fp32", 0), ("bf16", 0), ("fr4", 8), ("fr4", 12), ("fr4", 24)]
 # lines, and a changed file gives null.
 NCU_UNITS = 56 * 1024 * 1024
 NCU_COUNTERS = {
-    "heat7_stencil": {"src": ["heat_tma.cu", "tma.cuh", "stencil_common.cuh"], "sha": "", "dram_bytes": 428.7e6,
+    "heat7_stencil": {"src": ["heat_tma.cu", "tma.cuh", "stencil_common.cuh"], "sha": "8cee9af187b05b72", "dram_bytes": 428.7e6,
                       "warp_inst": 90.66e6},
     "fr4_encode": {"src": "codec.cu", "sha": "8e2c300bc5f510bb", "dram_bytes": 319.2e6, "warp_inst": 182.16e6},
     "fr4_decode": {"src": "codec.cu", "sha": "8e2c300bc5f510bb", "dram_bytes": 296.9e6, "warp_inst": 180.98e6},
