@@ -17,10 +17,11 @@
 //     9-plane queue from there.
 // Each CTA marches a chunk of z; the chunk count is chosen from the
 // occupancy so that the grid fills whole waves of the 152 SMs.
-// Also here: fused heat7 pairs (two steps per launch, the intermediate level
-// on chip): heat7x2r_kernel, two rows per thread, runs the pipeline's heat7
-// steps by default; heat7x2_kernel is the earlier one-row version.  And an
-// FP64 heat7 for whole fields.
+// Also here: the register-loading fused heat7 pairs (two steps per launch,
+// the intermediate level on chip), heat7x2r_kernel (two rows per thread)
+// and heat7x2_kernel (one row), built in with OOC_HEATX2_ROWS = 2 or 1 (the
+// default build runs the TMA-staged pairs of heat_tma.cu); and an FP64
+// heat7 for whole fields.
 //
 // heat7 (Section III's neighbour average, 3D):
 //   u' = u + r (u[x-1] + u[x+1] + u[y-1] + u[y+1] + u[z-1] + u[z+1] - 6u)
