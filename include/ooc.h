@@ -195,7 +195,8 @@ ooc_status ooc_bf16_unpack(const uint16_t *d_in, float *d_out, int64_t n, void *
  * of u (device) with scratch d_tmp (device, same size); result in d_u.
  * wave25: from (d_p, d_pprev) = (p^t, p^{t-1}) to (p^{t+n}, p^{t+n-1}),
  * adding h_w[t + s] (host array, may be NULL) at (sx, sy, sz) in step s
- * (0-based); pass sx < 0 for no source. */
+ * (0-based); pass sx < 0 for no source.  Device buffers 16-byte aligned and
+ * distinct; OOC_E_INVALID otherwise. */
 ooc_status ooc_heat7_steps(float *d_u, float *d_tmp, int64_t nx, int64_t ny, int64_t nz, double r,
                            int64_t nsteps, void *stream);
 ooc_status ooc_wave25_steps(float *d_p, float *d_pprev, const float *d_kappa, int64_t nx, int64_t ny,

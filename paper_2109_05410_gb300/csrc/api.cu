@@ -283,7 +283,8 @@ ooc_status ooc_bf16_unpack(const uint16_t *d_in, float *d_out, int64_t n, void *
 ooc_status ooc_heat7_steps(float *d_u, float *d_tmp, int64_t nx, int64_t ny, int64_t nz, double r, int64_t nsteps,
                            void *stream)
 {
-    if (!d_u || !d_tmp || !dims_ok(nx, ny, nz) || nsteps < 0)
+    if (!d_u || !d_tmp || d_u == d_tmp || !dims_ok(nx, ny, nz) || nsteps < 0 || !aligned(d_u, 16) ||
+        !aligned(d_tmp, 16))
         return OOC_E_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
     float *a = d_u, *b = d_tmp;
@@ -323,7 +324,8 @@ ooc_status ooc_heat7_steps_f64(double *d_u, double *d_tmp, int64_t nx, int64_t n
 ooc_status ooc_heat7_steps_fused(float *d_u, float *d_tmp, int64_t nx, int64_t ny, int64_t nz, double r,
                                  int64_t nsteps, void *stream)
 {
-    if (!d_u || !d_tmp || !dims_ok(nx, ny, nz) || nsteps < 0 || d_u == d_tmp)
+    if (!d_u || !d_tmp || !dims_ok(nx, ny, nz) || nsteps < 0 || d_u == d_tmp || !aligned(d_u, 16) ||
+        !aligned(d_tmp, 16))
         return OOC_E_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
     float *a = d_u, *b = d_tmp;
@@ -347,7 +349,8 @@ ooc_status ooc_wave25_steps(float *d_p, float *d_pprev, const float *d_kappa, in
                             int64_t sx, int64_t sy, int64_t sz, const float *h_w, int64_t t, int64_t nsteps,
                             void *stream)
 {
-    if (!d_p || !d_pprev || !d_kappa || !dims_ok(nx, ny, nz) || nsteps < 0 || t < 0)
+    if (!d_p || !d_pprev || !d_kappa || d_p == d_pprev || !dims_ok(nx, ny, nz) || nsteps < 0 || t < 0 ||
+        !aligned(d_p, 16) || !aligned(d_pprev, 16) || !aligned(d_kappa, 16))
         return OOC_E_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
     float *a = d_p, *b = d_pprev;  // a holds p^n, b holds p^{n-1}

@@ -182,3 +182,22 @@ def test_debug_checks_add_guard_regions(L):
         assert s0 == 0 and s1 == 0, kw
         assert d1 - d0 == 256 * (nguard + 1), (kw, d1 - d0)
         assert h1 == h0 and i1["slab_planes"] == i0["slab_planes"] and i1["ring_planes"] == i0["ring_planes"]
+
+
+def test_in_core_entry_points_reject_misaligned_or_aliased_buffers(L):
+    # The argument checks run before any CUDA call, so fake device addresses
+    # are enough: a buffer that is not 16-byte aligned, or the same buffer
+    # passed twice, is refused with OOC_E_INVALID (1) and nothing launches.
+    vp = ctypes.c_void_p
+    a, b, c, odd = vp(1 << 20), vp(2 << 20), vp(3 << 20), vp((4 << 20) + 4)
+    n = (ctypes.c_int64(8),) * 3
+    for fn in (L.ooc_heat7_steps, L.ooc_heat7_steps_fused):
+        assert fn(odd, b, *n, ctypes.c_double(1 / 6), ctypes.c_int64(2), None) == 1
+        assert fn(a, odd, *n, ctypes.c_double(1 / 6), ctypes.c_int64(2), None) == 1
+        assert fn(a, a, *n, ctypes.c_double(1 / 6), ctypes.c_int64(2), None) == 1
+    w = L.ooc_wave25_steps
+    src = (ctypes.c_int64(-1),) * 3
+    assert w(odd, b, c, *n, *src, None, ctypes.c_int64(0), ctypes.c_int64(2), None) == 1
+    assert w(a, b, odd, *n, *src, None, ctypes.c_int64(0), ctypes.c_int64(2), None) == 1
+    assert w(a, a, c, *n, *src, None, ctypes.c_int64(0), ctypes.c_int64(2), None) == 1
+    assert L.ooc_heat7_steps_noalloc(odd, *n, ctypes.c_double(1 / 6), ctypes.c_int64(2), None) == 1
