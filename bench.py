@@ -309,6 +309,38 @@ def cpu_oracle_leg(u0):
     return exact, cpu, oracle.error_metrics
 
 
+def wave1024_summary(torch, ooc, nsteps=100, reps=2):
+    """The paper's workload in brief, for the default line: the 1024^3 wave
+    (4 GiB budget, k = 10, source at the centre, from rest) with FP32 storage
+    (code 1) and with the read-write levels and kappa at FR4-16 (code 4),
+    one untimed call and `reps` timed calls of `nsteps` steps each."""
+    n, k = 1024, 10
+    kappa, src, dt = wave_inputs(n)
+    from synth import ricker
+    w = (ricker(nsteps * (reps + 1), dt) * float(kappa[src[2], src[1], src[0]])).astype(np.float32)
+    zero = np.zeros((n, n, n), dtype=np.float32)
+    out = {}
+    for name, (rw, ro) in (("code1_fp32", ("fp32", "fp32")), ("code4_rw_ro_fr4-16", ("fr4", "fr4"))):
+        plan = ooc.Plan(nx=n, ny=n, nz=n, stencil="wave25", k=k, rw_format=rw, rw_rate=16, ro_format=ro, ro_rate=16,
+                        device_budget_bytes=4 << 30)
+        try:
+            plan.set_field(0, zero)
+            plan.set_field(1, zero)
+            plan.set_field(2, kappa)
+            plan.set_source(*src, w)
+            plan.step(nsteps)
+            ms = timed_steps(torch, plan, nsteps, reps)
+            out[name] = n ** 3 * nsteps / (statistics.mean(ms) / 1e3) / 1e9
+        finally:
+            plan.close()
+        del plan
+        torch.cuda.empty_cache()
+    out["speedup_code4_vs_code1"] = out["code4_rw_ro_fr4-16"] / out["code1_fp32"]
+    out["what"] = (f"wave25 1024^3, 4 GiB budget, k = {k}, {reps} timed calls of {nsteps} steps after one untimed; "
+                   "bench.py --workload wave1024 has the full study")
+    return out
+
+
 def run_gpu(args, world, rank, local):
     import torch
 
@@ -458,6 +490,13 @@ def run_gpu(args, world, rank, local):
         torch.cuda.empty_cache()
     formats[fmt_name(*MAIN)] = {"Gpts": value / world, "slab_planes": info["slab_planes"], "nslab": info["nslab"]}
 
+    # ---- the paper's own workload (25-point wave, Section VI) in brief ---------
+    try:
+        wave = wave1024_summary(torch, ooc)
+    except Exception as exc:  # reported, never fatal to the headline
+        wave = {"error": f"{type(exc).__name__}: {exc}"}
+        torch.cuda.empty_cache()
+
     if rank != 0:
         return 0
 
@@ -511,6 +550,7 @@ def run_gpu(args, world, rank, local):
                               "link_GBs_each_way_assumed": link_dir,
                               "h2d_GBs_per_copy": h2d_GBs, "d2h_GBs_per_copy": d2h_GBs},
         "roofline": roofline,
+        "paper_workload_wave1024": wave,
         "kernels": kernels,
         "overlap": overlap,
         "cpu_baseline": cpu,
