@@ -130,8 +130,8 @@ static int value_exponent(float x)
  * bound guarantees that nothing wraps; `fr4_forward_wrapped` records any
  * wrap in the forward direction so that tests can check that claim.  The
  * inverse may wrap only on streams that no finite input produces. */
-static int fr4_forward_wrapped;
-static int fr4_inverse_wrapped;
+static _Thread_local int fr4_forward_wrapped;  /* per thread: the dense loops run blocks in parallel */
+static _Thread_local int fr4_inverse_wrapped;
 
 static int32_t wrap32(int64_t v, int *flag)
 {
@@ -435,17 +435,25 @@ int fr4_encode(const float *field, int64_t nx, int64_t ny, int64_t nz, int rate,
         return -1;
     if (!order_ready)
         build_order();
-    fr4_forward_wrapped = 0;
     int64_t nbx = nblocks(nx), nby = nblocks(ny), nbz = nblocks(nz);
-    float x[64];
-    for (int64_t bz = 0; bz < nbz; bz++)
-        for (int64_t by = 0; by < nby; by++)
-            for (int64_t bx = 0; bx < nbx; bx++) {
-                int64_t b = bx + nbx * (by + nby * bz);
-                gather_block(field, nx, ny, nz, bx, by, bz, x);
-                encode_block(x, rate, out + b * 2 * rate);
-            }
-    return fr4_forward_wrapped ? -2 : 0;
+    int wrapped = 0;
+    /* blocks are independent: one block per iteration, any order */
+#pragma omp parallel reduction(| : wrapped)
+    {
+        fr4_forward_wrapped = 0;
+#pragma omp for collapse(3) schedule(static)
+        for (int64_t bz = 0; bz < nbz; bz++)
+            for (int64_t by = 0; by < nby; by++)
+                for (int64_t bx = 0; bx < nbx; bx++) {
+                    float x[64];
+                    int64_t b = bx + nbx * (by + nby * bz);
+                    gather_block(field, nx, ny, nz, bx, by, bz, x);
+                    encode_block(x, rate, out + b * 2 * rate);
+                }
+        wrapped |= fr4_forward_wrapped;
+    }
+    fr4_forward_wrapped = wrapped;
+    return wrapped ? -2 : 0;
 }
 
 /* Decode a dense field.  Returns 0, -1 on bad arguments, or 1 when the
@@ -456,17 +464,25 @@ int fr4_decode(const uint32_t *in, int64_t nx, int64_t ny, int64_t nz, int rate,
         return -1;
     if (!order_ready)
         build_order();
-    fr4_inverse_wrapped = 0;
     int64_t nbx = nblocks(nx), nby = nblocks(ny), nbz = nblocks(nz);
-    float x[64];
-    for (int64_t bz = 0; bz < nbz; bz++)
-        for (int64_t by = 0; by < nby; by++)
-            for (int64_t bx = 0; bx < nbx; bx++) {
-                int64_t b = bx + nbx * (by + nby * bz);
-                decode_block(in + b * 2 * rate, rate, x);
-                scatter_block(field, nx, ny, nz, bx, by, bz, x);
-            }
-    return fr4_inverse_wrapped ? 1 : 0;
+    int wrapped = 0;
+    /* blocks are independent: one block per iteration, any order */
+#pragma omp parallel reduction(| : wrapped)
+    {
+        fr4_inverse_wrapped = 0;
+#pragma omp for collapse(3) schedule(static)
+        for (int64_t bz = 0; bz < nbz; bz++)
+            for (int64_t by = 0; by < nby; by++)
+                for (int64_t bx = 0; bx < nbx; bx++) {
+                    float x[64];
+                    int64_t b = bx + nbx * (by + nby * bz);
+                    decode_block(in + b * 2 * rate, rate, x);
+                    scatter_block(field, nx, ny, nz, bx, by, bz, x);
+                }
+        wrapped |= fr4_inverse_wrapped;
+    }
+    fr4_inverse_wrapped = wrapped;
+    return wrapped ? 1 : 0;
 }
 
 static int var_mode_ok(int mode, double param)

@@ -404,6 +404,45 @@ def test_wave_step_deadline_keeps_the_source_in_step(ooc, table):
     assert np.array_equal(out[0][1].view(np.uint32), out[1][1].view(np.uint32))
 
 
+def test_precision_configuration_against_oracle(ooc):
+    # The long-horizon precision configuration at its stated size: wave25 at
+    # 384^3, 6 slabs of 64 planes, k = 10, both levels and kappa at FR4-16,
+    # the source at the centre, from rest; after 100 steps (10 passes) the
+    # whole field against the FP64 oracle with the same storage round trips,
+    # and against the FP64 run without them.  Tolerances as in the other
+    # compressed wave tests (flips at truncation boundaries under FP32
+    # arithmetic); measured values are printed.
+    n, k, nsteps = 384, 10, 100
+    v = layered_velocity((n, n, n), seed=3)
+    dt = 0.4 * 10.0 / v.max()
+    kappa = ((v * dt / 10.0) ** 2).astype(np.float32)
+    src = (n // 2, n // 2, n // 2)
+    srcf = (src[2] * n + src[1]) * n + src[0]
+    w = (ricker(nsteps, dt) * float(kappa[src[2], src[1], src[0]])).astype(np.float32)
+    zero = np.zeros((n, n, n), dtype=np.float32)
+    plan = ooc.Plan(nx=n, ny=n, nz=n, stencil="wave25", k=k, rw_format="fr4", rw_rate=16, ro_format="fr4",
+                    ro_rate=16, slab_planes=64)
+    try:
+        assert plan.info()["nslab"] == 6
+        plan.set_field(0, zero)
+        plan.set_field(1, zero)
+        plan.set_field(2, kappa)
+        plan.set_source(*src, w)
+        plan.step(nsteps)
+        got = plan.get_field(0)
+    finally:
+        plan.close()
+    want, _ = oracle.wave25_storage_pipeline(zero, zero, kappa, nsteps, k, "fr4", 16, ro_fmt="fr4", ro_rate=16,
+                                             src=srcf, w=w.astype(np.float64))
+    exact, _ = oracle.wave25_run(np.zeros((n, n, n)), np.zeros((n, n, n)), kappa.astype(np.float64), nsteps,
+                                 src=srcf, w=w.astype(np.float64))
+    mp = oracle.error_metrics(got, want)
+    me = oracle.error_metrics(got, exact)
+    print(f"384^3 wave FR4-16 after {nsteps} steps: vs oracle pipeline {mp}, vs FP64 run {me}")
+    assert mp["rel_l2"] < 5e-5, mp
+    assert me["rel_l2"] < 5e-4, me
+
+
 def test_step_deadline_reports_timeout_and_work_completes(ooc):
     # A host wait that runs past the plan's deadline returns OOC_E_TIMEOUT
     # (status 5) without faulting anything: the enqueued passes still run,
