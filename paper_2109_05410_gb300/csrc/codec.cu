@@ -13,9 +13,11 @@
 // GPU design: one thread per 4^3 block.  The 64 values stay in registers
 // (16 coalesced 128-bit loads: neighbouring threads own neighbouring blocks
 // along x).  The bit-plane stage turns the 64 negabinary words into 32
-// 64-bit plane masks with two in-register 32x32 bit transposes; each plane
-// is then written in O(1) chunks per newly significant coefficient
-// (find-first-set over the plane mask) instead of bit by bit.  The encoder
+// 64-bit plane masks with two in-register 32x32 bit transposes; the encoder
+// then writes each plane with at most three 64-bit ORs (its significance
+// part from a 256-entry table of "doubled ones", whatever its number of new
+// coefficients), and the decoder parses all group-test segments inside a
+// 32-bit stream window from one register.  The encoder
 // stages its CTA's compressed words in shared memory and writes them with
 // coalesced 32-bit stores; the decoder reads each block's words straight
 // from the stream through L1, one word ahead of their use.
@@ -274,7 +276,34 @@ __device__ __forceinline__ void or_bits(uint32_t *w, int off, uint64_t v)
     w[i + 2] |= __funnelshift_l(b, 0u, sh);
 }
 
-__device__ __forceinline__ void set_bit(uint32_t *w, int pos) { w[pos >> 5] |= 1u << (pos & 31); }
+// Significance parts are written with "doubled ones": the bits of x with
+// every one followed by an extra one.  In a plane's significance part each
+// new one is followed by the group bit 1 of the next segment, so the part
+// after its first group bit is the doubled bits before the last new one,
+// then that one.  dtab[b] holds the doubled bits of byte b (8 + popc(b) <= 16
+// bits); a CTA fills it once.
+__device__ __forceinline__ void init_dup_table(uint16_t *dtab)
+{
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) {
+        uint32_t d = 0u;
+        int k = 0;
+        for (int i = 0; i < 8; ++i)
+            if ((b >> i) & 1) {
+                d |= 3u << (i + k);
+                ++k;
+            }
+        dtab[b] = (uint16_t)d;
+    }
+}
+
+// Doubled ones of a 32-bit word: 32 + popc(x) <= 64 bits.
+__device__ __forceinline__ uint64_t dup_ones(uint32_t x, const uint16_t *dtab)
+{
+    const uint32_t b0 = x & 0xFFu, b2 = (x >> 16) & 0xFFu;
+    const uint32_t lo = (uint32_t)dtab[b0] | ((uint32_t)dtab[(x >> 8) & 0xFFu] << (8 + __popc(b0)));
+    const uint32_t hi = (uint32_t)dtab[b2] | ((uint32_t)dtab[x >> 24] << (8 + __popc(b2)));
+    return (uint64_t)lo | ((uint64_t)hi << (16 + __popc(x & 0xFFFFu)));
+}
 
 // ---- one block ----------------------------------------------------------------
 // Lowest coded bit plane: 0 at a fixed rate; 32 - P at fixed precision P;
@@ -297,7 +326,7 @@ __device__ __forceinline__ int plane_floor(int mode, int mparam, int emax)
 // length in bits (exact for the variable-size modes, whose budget never
 // binds).
 __device__ __forceinline__ int encode_block(uint32_t (&v)[64], int words, int mode, int mparam, uint32_t *dst,
-                                            uint32_t *pm)
+                                            uint32_t *pm, const uint16_t *dtab)
 {
     uint32_t mx = 0;
 #pragma unroll
@@ -343,74 +372,49 @@ __device__ __forceinline__ int encode_block(uint32_t (&v)[64], int words, int mo
     // group bit 0 if coefficients remain.  When a new one is the last
     // coefficient its one is implied and not written.
     //
-    // Pass 1 walks the planes: each plane's length follows in O(1) from its
-    // mask (popcount, highest bit), so its offset is known and its
-    // refinement bits are written in place.  Planes with new ones record
-    // where their significance part starts.  Pass 2 then writes the ones of
-    // the significance parts, one new coefficient per iteration, so the
-    // lanes of a warp stay in step whatever their planes look like.
+    // With rest = the plane's bits past n and tl its highest one, the part
+    // after the refinement bits is the group bit 1, the doubled bits of rest
+    // below tl, and the one at tl: the one of segment j lands at t_j + j past
+    // the first group bit, and the next segment's group bit right after it.
+    // Each plane is written with at most three 64-bit ORs, whatever its
+    // number of new ones.
     int off = 9, n = 0;
-    uint32_t newmask = 0u;  // planes whose significance part has ones
 #pragma unroll 1
     for (int p = 31; p >= pmin && off < budget; --p) {
         const uint64_t X = ((uint64_t)pm[32 + p] << 32) | pm[p];
-        if (n > 0)
-            or_bits(dst, off, n >= 64 ? X : (X & ((1ull << n) - 1ull)));
         if (n >= 64) {
+            or_bits(dst, off, X);
             off += 64;
             continue;
         }
+        const uint64_t refine = X & ((1ull << n) - 1ull);
         const uint64_t rest = X >> n;
         if (rest == 0ull) {
+            if (n > 0)
+                or_bits(dst, off, refine);
             off += n + 1;  // refinement bits and the closing group bit 0
             continue;
         }
+        or_bits(dst, off, refine | (1ull << n));  // ... and the first group bit
         const int m = __popcll((long long)rest);
         const int tl = 63 - __clzll((long long)rest);  // offset of the last new one
         const int n_new = n + tl + 1;
-        newmask |= 1u << p;
+        const int at = off + n + 1;  // first bit past the first group bit
+        const uint64_t before = rest ^ (1ull << tl);
+        const uint64_t last = n_new == 64 ? 0ull : 1ull;  // the last coefficient's one is implied
+        const int rel = tl + m - 1;                        // the last one's position past `at`
+        if (tl < 32) {
+            or_bits(dst, at, dup_ones((uint32_t)before, dtab) | (last << rel));
+        } else {
+            const uint32_t lo = (uint32_t)before;
+            const int hs = 32 + __popc(lo);
+            or_bits(dst, at, dup_ones(lo, dtab));
+            or_bits(dst, at + hs, dup_ones((uint32_t)(before >> 32), dtab) | (last << (rel - hs)));
+        }
         // n refinement bits, m group bits 1, tl + 1 scanned bits (the last
         // one implied when it is coefficient 63), a closing 0 if n_new < 64
         off += n + m + tl + 1 - (n_new == 64 ? 1 : 0) + (n_new < 64 ? 1 : 0);
         n = n_new;
-    }
-    // Pass 2: significance ones.  Segment j (1-based) of a plane starts with
-    // its group bit at base + t_{j-1} + j (t_0 = -1) and ends with its one at
-    // base + t_j + j.  Planes are visited from the top, as in pass 1, so a
-    // plane's n is the previous visited plane's n plus its last offset + 1,
-    // and its offset follows in O(1): the planes skipped in between have no
-    // new ones and take n + 1 bits each (n < 64 while planes remain).
-    int base = 0, nq = 0, nnext = 0, j = 0, prev_end = 0;
-    int off2 = 9, pprev = 32;  // start of the plane below the last visited one
-    uint64_t rest = 0ull;
-#pragma unroll 1
-    for (;;) {
-        if (rest == 0ull) {
-            if (newmask == 0u)
-                break;
-            const int pl = 31 - __clz((int)newmask);
-            newmask ^= 1u << pl;
-            nq = nnext;
-            off2 += (pprev - pl - 1) * (nq + 1);
-            base = off2 + nq;
-            rest = (((uint64_t)pm[32 + pl] << 32) | pm[pl]) >> nq;
-            const int m = __popcll((long long)rest);
-            const int tl = 63 - __clzll((long long)rest);
-            const int nn = nq + tl + 1;
-            off2 += nq + m + tl + 1 - (nn == 64 ? 1 : 0) + (nn < 64 ? 1 : 0);
-            pprev = pl;
-            j = 0;
-            prev_end = base - 1;  // position of the previous segment's one
-        }
-        const int t = __ffsll((long long)rest) - 1;
-        rest &= rest - 1ull;
-        ++j;
-        set_bit(dst, prev_end + 1);  // group bit of this segment
-        const int d = base + t + j;
-        if (nq + t != 63)            // the last coefficient's one is implied
-            set_bit(dst, d);
-        prev_end = d;
-        nnext = nq + t + 1;
     }
     return off;
 }
@@ -553,6 +557,9 @@ __global__ void __launch_bounds__(kThreads) fr4_encode_kernel(ConstRing in, int6
                                                              int64_t nblk, int rate, uint32_t *__restrict__ out)
 {
     extern __shared__ uint32_t smem[];
+    __shared__ uint16_t dtab[256];
+    init_dup_table(dtab);
+    __syncthreads();
     const int words = 2 * rate, stride = words + kSlack + 1;
     const int64_t first = (int64_t)blockIdx.x * kThreads;
     const int64_t b = first + threadIdx.x;
@@ -573,7 +580,7 @@ __global__ void __launch_bounds__(kThreads) fr4_encode_kernel(ConstRing in, int6
                 v[16 * k + 4 * j + 3] = __float_as_uint(f.w);
             }
         encode_block(v, words, OOC_FR4_RATE, 0, smem + threadIdx.x * stride,
-                     smem + kThreads * stride + threadIdx.x * kPlaneStride);
+                     smem + kThreads * stride + threadIdx.x * kPlaneStride, dtab);
     }
     __syncthreads();
     const int64_t left = nblk - first;
@@ -668,6 +675,9 @@ __global__ void __launch_bounds__(kThreads)
                             int mode, int mparam, int phase, uint32_t *__restrict__ out, uint64_t *__restrict__ index)
 {
     extern __shared__ uint32_t smem[];
+    __shared__ uint16_t dtab[256];
+    init_dup_table(dtab);
+    __syncthreads();
     const int stride = words + kSlack + 1;
     const int64_t first = (int64_t)blockIdx.x * kThreads;
     const int64_t b = first + threadIdx.x;
@@ -678,7 +688,8 @@ __global__ void __launch_bounds__(kThreads)
         const int64_t bx = b % nbx, t2 = b / nbx, by = t2 % nby, bz = t2 / nby;
         uint32_t v[64];
         gather_clamped(in, nx, ny, nz, bx, by, bz, v);
-        bits = encode_block(v, words, mode, mparam, mine, smem + kThreads * stride + threadIdx.x * kPlaneStride);
+        bits = encode_block(v, words, mode, mparam, mine, smem + kThreads * stride + threadIdx.x * kPlaneStride,
+                            dtab);
     }
     if (mode != OOC_FR4_RATE) {  // uniform over the grid: no barrier on this path
         if (b >= nblk)
