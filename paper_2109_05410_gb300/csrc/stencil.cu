@@ -13,8 +13,9 @@
 //     the edge warps;
 //   - z-neighbours live in a register queue.  heat7 loads the planes two
 //     ahead of their use; wave25 stages each plane (tile, halos, p_prev,
-//     kappa) in shared memory with cp.async six planes ahead and fills its
-//     9-plane queue from there.
+//     kappa) in shared memory with cp.async eight planes ahead and fills
+//     its 9-plane queue from there; its z-loop runs in rounds of 9 planes,
+//     so that the queue and the stage rings are indexed by constants.
 // Each CTA marches a chunk of z; the chunk count is chosen from the
 // occupancy so that the grid fills whole waves of the 152 SMs.
 // Also here: the register-loading fused heat7 pairs (two steps per launch,
@@ -29,6 +30,8 @@
 //   p' = 2p - p_prev + kappa * sum_axes[c0 p + sum_m c_m (p[+m] + p[-m])]
 // p' overwrites p_prev in place (or goes to a separate array): each point's
 // p_prev is read only by the thread that writes p' there.
+#include <type_traits>
+
 #include "stencil_common.cuh"
 
 namespace ooc {
@@ -529,27 +532,36 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// wave25 staging: p tiles of kWaveStages planes (8 own rows and 4 halo rows
-// on each side, plus the 4-point groups beyond each row end), and p_prev /
-// kappa rows of kWavePD + 1 planes.  Plane g's p tile travels with p_prev
-// and kappa of plane g - 4, in one copy group issued kWavePD + 4 planes
-// ahead of its use as the centre.
+// wave25 staging: the p tile of every plane (8 own rows and 4 halo rows on
+// each side, plus the 4-point groups beyond the own rows' ends) in kWavePS
+// stages, and p_prev / kappa of the own rows in kWaveKS stages.  The copy
+// group of plane g, issued kWaveLead planes before g is the centre, carries
+// the p tile of g and p_prev / kappa of plane g - kWaveLead + 2.  The z-loop
+// runs in rounds of 9 planes, so that the 9-plane z-queue and both stage
+// rings are indexed by constants: the queue rotates by renaming, not by
+// register copies.
 constexpr int kWaveR = 4;
-constexpr int kWavePD = 2;                       // planes of copies in flight beyond the queue
-constexpr int kWaveStages = 2 * kWaveR - 3 + kWavePD;  // planes z .. z + 4 + kWavePD
-constexpr int kWaveKStages = kWavePD + 1;
+constexpr int kWavePS = 9;
+constexpr int kWaveKS = 3;
+constexpr int kWaveLead = 8;
 struct WaveSmem {
-    float4 p[kWaveStages][kWaveTY + 2 * kWaveR][kTX];
-    float4 xh[kWaveStages][kWaveTY][2];
-    float4 pp[kWaveKStages][kWaveTY][kTX];
-    float4 kk[kWaveKStages][kWaveTY][kTX];
+    float4 p[kWavePS][kWaveTY + 2 * kWaveR][kTX];
+    float4 xh[kWavePS][kWaveTY][2];
+    float4 pp[kWaveKS][kWaveTY][kTX];
+    float4 kk[kWaveKS][kWaveTY][kTX];
 };
+
+template <int V>
+using IC = std::integral_constant<int, V>;
 
 // MODE 0: the leapfrog step above.  MODE 1 (gradient of the adjoint run):
 // gsum[own] += (double) pprev * (double) L(pin) in FP64, with `pprev` the
 // adjoint field and kappa, pout and the source unused.  MODE 2: the same
 // term accumulated in FP32, gacc[own] = fma(pprev, L(pin), gacc[own]) (the
 // adjoint run's short in-segment sums, added to an FP64 total per segment).
+// The arithmetic is written with rounding intrinsics in a fixed order:
+//   L = 3 c0 p + sum_m c_m (((x-m + x+m) + (y-m + y+m)) + (z-m + z+m))
+//   p' = kappa L + (2 p - p_prev)
 template <int MODE>
 __global__ void __launch_bounds__(kTX *kWaveTY, 2)
     wave25_kernel(const float *__restrict__ pin, const float *pprev, float *pout, const float *__restrict__ kap, int nslot,
@@ -557,6 +569,7 @@ __global__ void __launch_bounds__(kTX *kWaveTY, 2)
                   float w, double *__restrict__ gsum, WaveSrcTable tab, float *__restrict__ gacc = nullptr)
 {
     constexpr int R = kWaveR;
+    static_assert(kWavePS == 2 * R + 1 && kWavePS % kWaveKS == 0 && kWaveLead == kWavePS - 1, "stage geometry");
     extern __shared__ __align__(16) unsigned char wave_smem[];
     WaveSmem &sm = *reinterpret_cast<WaveSmem *>(wave_smem);
     const int lane = threadIdx.x, ty = threadIdx.y;
@@ -567,12 +580,15 @@ __global__ void __launch_bounds__(kTX *kWaveTY, 2)
     const int64_t y = y0 + ty;
     const int64_t za = z0 + (int64_t)blockIdx.y * zchunk;
     const int cnt = (int)(min(za + zchunk, z1) - za);
+    const int64_t zend = za + cnt;
     const int64_t nz = g.nz, plane = g.plane;
     const bool xin = x4 < g.nx;
     const bool inside = xin && y < g.ny;
     const int64_t off = inside ? y * g.nx + x4 : 0;
     // copies of this thread: tile rows ty and ty + 8 (y0 - 4 + row), its own
-    // p_prev / kappa group, and (lanes 0, 31) the group beyond its row end
+    // p_prev / kappa group, and (lanes 0, 31) the group beyond its row end;
+    // an invalid copy reads nothing and fills zeros (its address stays in
+    // the ring)
     const int64_t ya = y0 - R + ty, yb = y0 - R + ty + kWaveTY;
     const bool va = xin && ya >= 0 && ya < g.ny, vb = xin && yb >= 0 && yb < g.ny;
     const int64_t offa = va ? ya * g.nx + x4 : 0, offb = vb ? yb * g.nx + x4 : 0;
@@ -582,52 +598,65 @@ __global__ void __launch_bounds__(kTX *kWaveTY, 2)
     const bool src_here = inside && y == sy && sx >= x4 && sx < x4 + 4;
     const float4 z4 = zero4();
 
-    // Copy group for plane gz = za + gi: its p tile from ring slot gslot, and
-    // p_prev / kappa of plane gz - 4 from slot kslot once that plane is in
-    // the chunk.  Both slots advance by one plane per group.
-    int gslot = (int)ring_slot(za, zbase, nslot), kslot = gslot;
-    auto issue = [&](int64_t gz, int gi) {
-        const bool vz = gz < nz;
-        const int st = gi % kWaveStages;
-        const float *pl = pin + (int64_t)gslot * plane;
-        cp_async16(&sm.p[st][ty][lane], vz && va ? pl + offa : pin, vz && va);
-        cp_async16(&sm.p[st][ty + kWaveTY][lane], vz && vb ? pl + offb : pin, vz && vb);
-        if (lane == 0 || lane == kTX - 1)
-            cp_async16(&sm.xh[st][ty][lane == 0 ? 0 : 1], vz && hcol ? pl + xoff : pin, vz && hcol);
-        gslot = wrap_add(gslot, 1, nslot);
-        if (gi >= R) {
-            const int ks = (gi - R) % kWaveKStages;
-            const int64_t kb = (int64_t)kslot * plane;
-            const bool vk = inside && gz - R < nz;
-            cp_async16(&sm.pp[ks][ty][lane], vk ? pprev + kb + off : pin, vk);
-            if (MODE == 0)
-                cp_async16(&sm.kk[ks][ty][lane], vk ? kap + kb + off : pin, vk);
-            kslot = wrap_add(kslot, 1, nslot);
+    // Copy group of plane gz into p stage ST and, with K, p_prev / kappa of
+    // plane gz - kWaveLead + 2 into stage KST.  Copies past the chunk's last
+    // use are skipped (the group stays, empty, so that the counts hold).
+    // The p slot advances with every group, the p_prev / kappa slot with
+    // every group that carries them.
+    int ps = (int)ring_slot(za, zbase, nslot), ks = ps, os = ps;
+    auto issue = [&](auto st_c, auto kst_c, int64_t gz, bool with_k) {
+        constexpr int ST = decltype(st_c)::value, KST = decltype(kst_c)::value;
+        if (gz < zend + R) {
+            const bool vz = gz < nz;
+            const float *pl = pin + (int64_t)ps * plane;
+            cp_async16(&sm.p[ST][ty][lane], pl + offa, vz && va);
+            cp_async16(&sm.p[ST][ty + kWaveTY][lane], pl + offb, vz && vb);
+            if (lane == 0 || lane == kTX - 1)
+                cp_async16(&sm.xh[ST][ty][lane == 0 ? 0 : 1], pl + xoff, vz && hcol);
+        }
+        ps = wrap_add(ps, 1, nslot);
+        if (with_k) {
+            if (gz - kWaveLead + 2 < zend) {
+                const int64_t kb = (int64_t)ks * plane;
+                cp_async16(&sm.pp[KST][ty][lane], pprev + kb + off, inside);
+                if (MODE == 0)
+                    cp_async16(&sm.kk[KST][ty][lane], kap + kb + off, inside);
+            }
+            ks = wrap_add(ks, 1, nslot);
         }
         cp_async_commit();
     };
 
-    int s = (int)ring_slot(za, zbase, nslot);  // slot of plane z
-    // q[j] = p at plane z - 4 + j of this thread's 4 points; planes za - 4 ..
-    // za + 3 are read directly, later ones come from the staged tiles
+    // q[(phase + j) mod 9] = p at plane z - 4 + j of this thread's 4 points;
+    // planes za - 4 .. za + 3 are read directly, later ones come from the
+    // staged tiles
     float4 q[2 * R + 1];
 #pragma unroll
     for (int j = 0; j < 2 * R; ++j) {
         const int64_t zj = za - R + j;
-        const float *pj = pin + (int64_t)wrap_add(s, nslot - R + j >= nslot ? j - R : nslot - R + j, nslot) * plane;
+        const float *pj = pin + (int64_t)wrap_add(os, nslot - R + j >= nslot ? j - R : nslot - R + j, nslot) * plane;
         q[j] = (inside && zj >= 0 && zj < nz) ? ldg4(pj + off) : z4;
     }
-    for (int gi = 0; gi < R + kWavePD; ++gi)
-        issue(za + gi, gi);
+    issue(IC<0>{}, IC<0>{}, za + 0, false);
+    issue(IC<1>{}, IC<0>{}, za + 1, false);
+    issue(IC<2>{}, IC<0>{}, za + 2, false);
+    issue(IC<3>{}, IC<0>{}, za + 3, false);
+    issue(IC<4>{}, IC<0>{}, za + 4, false);
+    issue(IC<5>{}, IC<0>{}, za + 5, false);
+    issue(IC<6>{}, IC<0>{}, za + 6, true);
+    issue(IC<7>{}, IC<1>{}, za + 7, true);
+
     int64_t z = za;
-OOC_PRAGMA(unroll OOC_WAVE_UNROLL)
-    for (int i = 0; i < cnt; ++i, ++z) {
-        cp_async_wait<kWavePD - 1>();  // the group of plane z + 4 has landed
-        __syncthreads();               // ... for every thread; stage of z - 1 is free
-        issue(z + R + kWavePD, i + R + kWavePD);
-        const int st = i % kWaveStages, st4 = (i + R) % kWaveStages, ks = i % kWaveKStages;
-        q[2 * R] = sm.p[st4][ty + R][lane];
-        const float4 c = q[R];
+    int base = 0;  // first iteration of the current round
+    auto step = [&](auto ph_c) {
+        constexpr int PH = decltype(ph_c)::value;  // iteration mod 9: stage of plane z
+        if (base + PH >= cnt)
+            return;
+        cp_async_wait<1>();  // groups up to plane z + 6 have landed (p tile of z + 4, p_prev / kappa of z)
+        __syncthreads();     // ... for every thread; the stages of plane z - 1 are free
+        issue(IC<(PH + kWaveLead) % kWavePS>{}, IC<(PH + 2) % kWaveKS>{}, z + kWaveLead, true);
+        q[(PH + 2 * R) % kWavePS] = sm.p[(PH + R) % kWavePS][ty + R][lane];
+        const float4 c = q[(PH + R) % kWavePS];
         float4 lf, rt;
         lf.x = __shfl_up_sync(0xffffffffu, c.x, 1);
         lf.y = __shfl_up_sync(0xffffffffu, c.y, 1);
@@ -638,11 +667,11 @@ OOC_PRAGMA(unroll OOC_WAVE_UNROLL)
         rt.z = __shfl_down_sync(0xffffffffu, c.z, 1);
         rt.w = __shfl_down_sync(0xffffffffu, c.w, 1);
         if (lane == 0)
-            lf = sm.xh[st][ty][0];
+            lf = sm.xh[PH][ty][0];
         if (lane == kTX - 1)
-            rt = sm.xh[st][ty][1];
-        const float4 ppv = sm.pp[ks][ty][lane];
-        const float4 kv = MODE == 0 ? sm.kk[ks][ty][lane] : z4;
+            rt = sm.xh[PH][ty][1];
+        const float4 ppv = sm.pp[PH % kWaveKS][ty][lane];
+        const float4 kv = MODE == 0 ? sm.kk[PH % kWaveKS][ty][lane] : z4;
         const float L[4] = {lf.x, lf.y, lf.z, lf.w};
         const float C[4] = {c.x, c.y, c.z, c.w};
         const float Rt[4] = {rt.x, rt.y, rt.z, rt.w};
@@ -652,26 +681,29 @@ OOC_PRAGMA(unroll OOC_WAVE_UNROLL)
         float lap[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            lap[j] = (3.0f * kC0) * C[j];
+            lap[j] = __fmul_rn(3.0f * kC0, C[j]);
 #pragma unroll
         for (int m = 1; m <= R; ++m) {
-            const float4 ym = sm.p[st][ty + R - m][lane];
-            const float4 yp = sm.p[st][ty + R + m][lane];
+            const float4 ym = sm.p[PH][ty + R - m][lane];
+            const float4 yp = sm.p[PH][ty + R + m][lane];
+            const float4 zm = q[(PH + R - m) % kWavePS];
+            const float4 zp = q[(PH + R + m) % kWavePS];
             const float YM[4] = {ym.x, ym.y, ym.z, ym.w};
             const float YP[4] = {yp.x, yp.y, yp.z, yp.w};
-            const float ZM[4] = {q[R - m].x, q[R - m].y, q[R - m].z, q[R - m].w};
-            const float ZP[4] = {q[R + m].x, q[R + m].y, q[R + m].z, q[R + m].w};
+            const float ZM[4] = {zm.x, zm.y, zm.z, zm.w};
+            const float ZP[4] = {zp.x, zp.y, zp.z, zp.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const float xsum = pick(L, C, Rt, j - m) + pick(L, C, Rt, j + m);
-                lap[j] += cf[m - 1] * ((xsum + (YM[j] + YP[j])) + (ZM[j] + ZP[j]));
+                const float xsum = __fadd_rn(pick(L, C, Rt, j - m), pick(L, C, Rt, j + m));
+                const float s = __fadd_rn(__fadd_rn(xsum, __fadd_rn(YM[j], YP[j])), __fadd_rn(ZM[j], ZP[j]));
+                lap[j] = __fmaf_rn(cf[m - 1], s, lap[j]);
             }
         }
         if (MODE == 0) {
             float o[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-                o[j] = 2.0f * C[j] - PP[j] + KV[j] * lap[j];
+                o[j] = __fmaf_rn(KV[j], lap[j], __fmaf_rn(2.0f, C[j], -PP[j]));
             if (src_here && z == sz) {
                 float ws = w;
                 if (tab.w) {  // amplitude of step n = plan time + n_off, from the device table
@@ -684,9 +716,9 @@ OOC_PRAGMA(unroll OOC_WAVE_UNROLL)
                         o[j] += ws;
             }
             if (inside)
-                *reinterpret_cast<float4 *>(pout + (int64_t)s * plane + off) = make_float4(o[0], o[1], o[2], o[3]);
+                *reinterpret_cast<float4 *>(pout + (int64_t)os * plane + off) = make_float4(o[0], o[1], o[2], o[3]);
         } else if (MODE == 2 && inside) {
-            float4 *ap = reinterpret_cast<float4 *>(gacc + (int64_t)s * plane + off);
+            float4 *ap = reinterpret_cast<float4 *>(gacc + (int64_t)os * plane + off);
             float4 a = *ap;
             a.x = __fmaf_rn(PP[0], lap[0], a.x);
             a.y = __fmaf_rn(PP[1], lap[1], a.y);
@@ -694,7 +726,7 @@ OOC_PRAGMA(unroll OOC_WAVE_UNROLL)
             a.w = __fmaf_rn(PP[3], lap[3], a.w);
             *ap = a;
         } else if (MODE == 1 && inside) {
-            double2 *gp = reinterpret_cast<double2 *>(gsum + (int64_t)s * plane + off);
+            double2 *gp = reinterpret_cast<double2 *>(gsum + (int64_t)os * plane + off);
             double2 g0 = gp[0], g1 = gp[1];
             g0.x += (double)PP[0] * (double)lap[0];
             g0.y += (double)PP[1] * (double)lap[1];
@@ -703,10 +735,20 @@ OOC_PRAGMA(unroll OOC_WAVE_UNROLL)
             gp[0] = g0;
             gp[1] = g1;
         }
-#pragma unroll
-        for (int j = 0; j < 2 * R; ++j)
-            q[j] = q[j + 1];
-        s = wrap_add(s, 1, nslot);
+        os = wrap_add(os, 1, nslot);
+        ++z;
+    };
+#pragma unroll 1
+    for (; base < cnt; base += kWavePS) {
+        step(IC<0>{});
+        step(IC<1>{});
+        step(IC<2>{});
+        step(IC<3>{});
+        step(IC<4>{});
+        step(IC<5>{});
+        step(IC<6>{});
+        step(IC<7>{});
+        step(IC<8>{});
     }
     cp_async_wait<0>();  // no copy may outlive the CTA's shared memory
 }
