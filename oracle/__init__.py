@@ -1,7 +1,8 @@
 """CPU oracle -- TEST INFRASTRUCTURE ONLY.
 
 Plain, slow, obviously correct CPU implementations of everything the GPU
-path computes: the FR4 fixed-rate block codec (serial definition, C), the
+path computes: the FR4 fixed-rate block codec and its FP64 form FR4D
+(serial definitions, C), the
 FP64 heat7 and wave25 stencils (C, OpenMP over z), BF16 storage rounding
 (numpy bit manipulation) and the storage round trips that the out-of-core
 pipeline applies at pass boundaries.
@@ -25,7 +26,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
-_SOURCES = ["codec.c", "stencil.c", "adjoint.c", "util.c"]
+_SOURCES = ["codec.c", "codec64.c", "stencil.c", "adjoint.c", "util.c"]
 _lock = threading.Lock()
 _lib = None
 
@@ -68,6 +69,12 @@ def lib():
                 "fr4_decode_var": (i32, [vp, vp, i64, i64, i64, i32, dbl, vp]),
                 "fr4_var_max_words_per_block": (i64, []),
                 "fr4_decode_planes": (i64, [vp, i64, vp]),
+                "fr4d_encode": (i32, [vp, i64, i64, i64, i32, vp]),
+                "fr4d_decode": (i32, [vp, i64, i64, i64, i32, vp]),
+                "fr4d_transform_forward": (i32, [vp]),
+                "fr4d_transform_inverse": (i32, [vp]),
+                "fr4d_encode_planes": (i64, [vp, i64, vp]),
+                "fr4d_decode_planes": (i64, [vp, i64, vp]),
                 "oracle_heat7_step": (None, [vp, vp, i64, i64, i64, dbl]),
                 "oracle_heat7_run": (None, [vp, vp, i64, i64, i64, dbl, i64]),
                 "oracle_laplacian8": (None, [vp, vp, i64, i64, i64]),
@@ -213,6 +220,67 @@ def decode_planes(words, budget_bits):
     w = np.ascontiguousarray(words, dtype=np.uint32)
     u = np.zeros(64, dtype=np.uint32)
     n = lib().fr4_decode_planes(_p(w), budget_bits, _p(u))
+    return u, int(n)
+
+
+# --------------------------------------------------------------------------- FP64 codec
+def fr4d_encode(field, rate):
+    """Encode a float64 [nz, ny, nx] field with FR4D at ``rate`` bits per
+    value (2*rate uint32 words per 4^3 block).  Rates above 64 are for the
+    full-precision checks only."""
+    f = np.ascontiguousarray(field, dtype=np.float64)
+    nz, ny, nx = f.shape
+    out = np.zeros(_nblocks(f.shape) * 2 * rate, dtype=np.uint32)
+    rc = lib().fr4d_encode(_p(f), nx, ny, nz, rate, _p(out))
+    if rc != 0:
+        raise RuntimeError(f"fr4d_encode failed ({rc})")
+    return out
+
+
+def fr4d_decode(words, shape, rate):
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    nz, ny, nx = shape
+    if w.size != _nblocks(shape) * 2 * rate:
+        raise ValueError("stream size does not match shape and rate")
+    out = np.empty(shape, dtype=np.float64)
+    rc = lib().fr4d_decode(_p(w), nx, ny, nz, rate, _p(out))
+    if rc < 0:
+        raise RuntimeError(f"fr4d_decode failed ({rc})")
+    return out
+
+
+def fr4d_roundtrip(field, rate):
+    f = np.ascontiguousarray(field, dtype=np.float64)
+    return fr4d_decode(fr4d_encode(f, rate), f.shape, rate)
+
+
+def fr4d_transform_forward(block):
+    """FR4D's 3D forward lifting of one block (64 int64); returns
+    (coefficients, wrapped)."""
+    v = np.ascontiguousarray(block, dtype=np.int64).reshape(64).copy()
+    rc = lib().fr4d_transform_forward(_p(v))
+    return v, rc != 0
+
+
+def fr4d_transform_inverse(coef):
+    v = np.ascontiguousarray(coef, dtype=np.int64).reshape(64).copy()
+    rc = lib().fr4d_transform_inverse(_p(v))
+    return v, rc != 0
+
+
+def fr4d_encode_planes(u, budget_bits):
+    """Only FR4D's 64-plane coder on 64 negabinary uint64 words; returns
+    (words, bits_written)."""
+    uu = np.ascontiguousarray(u, dtype=np.uint64)
+    words = np.zeros((budget_bits + 31) // 32 + 1, dtype=np.uint32)
+    n = lib().fr4d_encode_planes(_p(uu), budget_bits, _p(words))
+    return words, int(n)
+
+
+def fr4d_decode_planes(words, budget_bits):
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    u = np.zeros(64, dtype=np.uint64)
+    n = lib().fr4d_decode_planes(_p(w), budget_bits, _p(u))
     return u, int(n)
 
 

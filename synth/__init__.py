@@ -161,3 +161,38 @@ def random_blocks(kind, nblocks, seed):
     else:
         raise ValueError(kind)
     return np.asarray(v, dtype=np.float32).reshape(nblocks * 4, 4, 4)
+
+
+def random_blocks64(kind, nblocks, seed):
+    """float64 arrays of shape (nblocks*4, 4, 4) for the FP64 codec's tests;
+    the kinds of ``random_blocks`` over the double range ('wide': exponents
+    over the full finite double range; 'denormal': double subnormals; 'bits':
+    random finite 64-bit patterns).  'normal', 'smooth', 'constant' and
+    'sparse' take ``random_blocks``' values and give them full double
+    significands (one factor per block for 'constant'); 'zero' keeps its
+    signed zeros."""
+    rng = np.random.default_rng(seed)
+    n = nblocks * 64
+    if kind == "wide":
+        v = rng.choice([-1.0, 1.0], size=n) * np.ldexp(rng.uniform(1.0, 2.0, size=n), rng.integers(-1022, 1023, size=n))
+    elif kind == "denormal":
+        m = rng.integers(0, 1 << 52, size=n, dtype=np.int64)
+        v = np.ldexp(m.astype(np.float64), -1074) * rng.choice([-1.0, 1.0], size=n)
+        v[rng.random(n) < 0.2] = 0.0
+    elif kind == "bits":
+        bits = rng.integers(0, np.iinfo(np.uint64).max, size=n, dtype=np.uint64, endpoint=True)
+        expo = (bits >> np.uint64(52)) & np.uint64(0x7FF)
+        bits = np.where(expo == 0x7FF, bits & ~np.uint64(1 << 62), bits)  # keep finite
+        v = bits.view(np.float64)
+    elif kind == "zero":
+        v = random_blocks(kind, nblocks, seed).astype(np.float64).ravel()
+    elif kind in ("normal", "smooth", "constant", "sparse"):
+        v = random_blocks(kind, nblocks, seed).astype(np.float64).ravel()
+        if kind == "constant":
+            f = np.repeat(1.0 + rng.uniform(-1e-9, 1e-9, size=nblocks), 64)
+        else:
+            f = 1.0 + rng.uniform(-1e-9, 1e-9, size=n)
+        v = v * f
+    else:
+        raise ValueError(kind)
+    return np.asarray(v, dtype=np.float64).reshape(nblocks * 4, 4, 4)
