@@ -142,6 +142,24 @@ ooc_status ooc_compress(const float *d_in, int64_t nx, int64_t ny, int64_t nz, i
 ooc_status ooc_decompress(const void *d_in, size_t in_bytes, int64_t nx, int64_t ny, int64_t nz,
                           int rate, float *d_out, void *stream);
 
+/* FR4D: the fixed-rate codec for FP64 fields (Section VI ran its double
+ * fields at 32 and 24 of every 64 bits).  The same 4^3 blocks, stream layout
+ * and bit-plane coder as FR4, with 58-bit block floating point (emax
+ * clamped at -1022, 11 header bits), the lifting in 64-bit integers and 64
+ * bit planes.  Compresses d_in[nz][ny][nx] (device FP64, 16-byte aligned,
+ * finite values; nx, ny, nz multiples of 4) into d_out (device, 4-byte
+ * aligned, ooc_compressed_bytes(nx, ny, nz, rate) bytes: R bits per value
+ * as for FR4) on `stream`, asynchronously; rate 1..64.  Returns
+ * OOC_E_INVALID on bad shapes, rates, alignment or out_cap < required;
+ * OOC_E_CUDA if the launch fails. */
+ooc_status ooc_compress64(const double *d_in, int64_t nx, int64_t ny, int64_t nz, int rate,
+                          void *d_out, size_t out_cap, void *stream);
+
+/* Inverse of ooc_compress64 into d_out (device FP64, 16-byte aligned).  Any
+ * word content decodes without faulting. */
+ooc_status ooc_decompress64(const void *d_in, size_t in_bytes, int64_t nx, int64_t ny, int64_t nz,
+                            int rate, double *d_out, void *stream);
+
 /* ---- Codec variants with variable-size blocks ------------------------------
  * Not used by the paper, which needs a size known in advance (Section IV);
  * it names comparing other compressors as future work.  The same block

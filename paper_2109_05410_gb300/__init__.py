@@ -19,7 +19,7 @@ from . import build as _build_mod
 __all__ = [
     "OOC_HEAT7", "OOC_WAVE25", "OOC_FMT_FP32", "OOC_FMT_BF16", "OOC_FMT_FR4",
     "OocConfig", "OocStats", "OocPlanInfo", "OocError", "lib", "build",
-    "ooc_status_string", "ooc_take_device_fault", "ooc_compressed_bytes", "ooc_compress", "ooc_decompress", "ooc_compress_var",
+    "ooc_status_string", "ooc_take_device_fault", "ooc_compressed_bytes", "ooc_compress", "ooc_decompress", "ooc_compress64", "ooc_decompress64", "ooc_compress_var",
     "ooc_decompress_var", "ooc_compress_var_bound", "ooc_var_scratch_bytes", "OOC_FR4_PRECISION", "OOC_FR4_ACCURACY",
     "ooc_bf16_pack", "ooc_bf16_unpack", "ooc_heat7_steps", "ooc_heat7_steps_f64", "ooc_heat7_steps_fused", "ooc_heat7_steps_noalloc", "ooc_wave25_steps", "Plan",
     "ooc_gather", "ooc_scatter_add", "ooc_wave25_adjoint_step", "ooc_wave25_grad_accum", "ooc_kappa_from_velocity",
@@ -92,6 +92,10 @@ _SIGS = {
                                                                               ctypes.c_size_t, ctypes.c_void_p]),
     "ooc_decompress": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t] + [ctypes.c_int64] * 3
                        + [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "ooc_compress64": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int64] * 3 + [ctypes.c_int, ctypes.c_void_p,
+                                                                                ctypes.c_size_t, ctypes.c_void_p]),
+    "ooc_decompress64": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t] + [ctypes.c_int64] * 3
+                         + [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "ooc_compress_var_bound": (ctypes.c_size_t, [ctypes.c_int64] * 3),
     "ooc_var_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int64] * 3),
     "ooc_compress_var": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int64] * 3
@@ -222,6 +226,30 @@ def ooc_decompress(d_in, shape, rate, d_out=None, stream=None):
         d_out = torch.empty(shape, dtype=torch.float32, device=d_in.device)
     _check(lib().ooc_decompress(_ptr(d_in), d_in.numel() * d_in.element_size(), nx, ny, nz, rate, _ptr(d_out),
                                 _stream(stream)), "ooc_decompress")
+    return d_out
+
+
+def ooc_compress64(d_in, rate, d_out=None, stream=None):
+    """FR4D: encode a float64 CUDA tensor [nz, ny, nx] (sides multiples of 4)
+    at ``rate`` bits/value into ``d_out`` (uint8 CUDA tensor, allocated if
+    None); returns d_out."""
+    import torch
+    nz, ny, nx = d_in.shape
+    nbytes = ooc_compressed_bytes(nx, ny, nz, rate)
+    if d_out is None:
+        d_out = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=d_in.device)
+    _check(lib().ooc_compress64(_ptr(d_in), nx, ny, nz, rate, _ptr(d_out), d_out.numel() * d_out.element_size(),
+                                _stream(stream)), "ooc_compress64")
+    return d_out
+
+
+def ooc_decompress64(d_in, shape, rate, d_out=None, stream=None):
+    import torch
+    nz, ny, nx = shape
+    if d_out is None:
+        d_out = torch.empty(shape, dtype=torch.float64, device=d_in.device)
+    _check(lib().ooc_decompress64(_ptr(d_in), d_in.numel() * d_in.element_size(), nx, ny, nz, rate, _ptr(d_out),
+                                  _stream(stream)), "ooc_decompress64")
     return d_out
 
 

@@ -169,6 +169,28 @@ ooc_status ooc_decompress(const void *d_in, size_t in_bytes, int64_t nx, int64_t
                                                2 * rate, OOC_FR4_RATE, 0, d_out, st));
 }
 
+ooc_status ooc_compress64(const double *d_in, int64_t nx, int64_t ny, int64_t nz, int rate, void *d_out,
+                          size_t out_cap, void *stream)
+{
+    const size_t need = ooc_compressed_bytes(nx, ny, nz, rate);
+    if (!d_in || !d_out || need == 0 || !dims_ok(nx, ny, nz) || !aligned(d_in, 16) || !aligned(d_out, 4) ||
+        out_cap < need)
+        return OOC_E_INVALID;
+    return cuda_status(launch_fr4d_encode(DConstRing{d_in, nz, 0}, nx, ny, 0, nz, rate, (uint32_t *)d_out,
+                                          (cudaStream_t)stream));
+}
+
+ooc_status ooc_decompress64(const void *d_in, size_t in_bytes, int64_t nx, int64_t ny, int64_t nz, int rate,
+                            double *d_out, void *stream)
+{
+    const size_t need = ooc_compressed_bytes(nx, ny, nz, rate);
+    if (!d_in || !d_out || need == 0 || !dims_ok(nx, ny, nz) || !aligned(d_in, 4) || !aligned(d_out, 16) ||
+        in_bytes < need)
+        return OOC_E_INVALID;
+    return cuda_status(launch_fr4d_decode((const uint32_t *)d_in, nx, ny, 0, nz, rate, DRing{d_out, nz, 0},
+                                          (cudaStream_t)stream));
+}
+
 namespace {
 
 constexpr int64_t kVarBlockWords = 130;

@@ -321,6 +321,68 @@ __device__ __forceinline__ int plane_floor(int mode, int mparam, int emax)
     return 0;
 }
 
+// The bit-plane coder shared by FR4 (NP = 32 planes) and FR4D (NP = 64):
+// pm[p] and pm[NP + p] hold bit p of coefficients 0..31 and 32..63; the
+// planes NP-1 .. pmin are written from bit `off` of the zeroed words dst
+// until the budget is spent.  Returns the coded length in bits.
+//
+// Plane p (NP-1 .. 0) is written as: the refinement bits of the n
+// significant coefficients; then, for each new one at offset t past n,
+// a group bit 1, the zeros before it and the one itself; then a closing
+// group bit 0 if coefficients remain.  When a new one is the last
+// coefficient its one is implied and not written.
+//
+// With rest = the plane's bits past n and tl its highest one, the part
+// after the refinement bits is the group bit 1, the doubled bits of rest
+// below tl, and the one at tl: the one of segment j lands at t_j + j past
+// the first group bit, and the next segment's group bit right after it.
+// Each plane is written with at most three 64-bit ORs, whatever its
+// number of new ones.
+template <int NP>
+__device__ __forceinline__ int code_planes(const uint32_t *pm, uint32_t *dst, int off, int budget, int pmin,
+                                           const uint16_t *dtab)
+{
+    int n = 0;
+#pragma unroll 1
+    for (int p = NP - 1; p >= pmin && off < budget; --p) {
+        const uint64_t X = ((uint64_t)pm[NP + p] << 32) | pm[p];
+        if (n >= 64) {
+            or_bits(dst, off, X);
+            off += 64;
+            continue;
+        }
+        const uint64_t refine = X & ((1ull << n) - 1ull);
+        const uint64_t rest = X >> n;
+        if (rest == 0ull) {
+            if (n > 0)
+                or_bits(dst, off, refine);
+            off += n + 1;  // refinement bits and the closing group bit 0
+            continue;
+        }
+        or_bits(dst, off, refine | (1ull << n));  // ... and the first group bit
+        const int m = __popcll((long long)rest);
+        const int tl = 63 - __clzll((long long)rest);  // offset of the last new one
+        const int n_new = n + tl + 1;
+        const int at = off + n + 1;  // first bit past the first group bit
+        const uint64_t before = rest ^ (1ull << tl);
+        const uint64_t last = n_new == 64 ? 0ull : 1ull;  // the last coefficient's one is implied
+        const int rel = tl + m - 1;                        // the last one's position past `at`
+        if (tl < 32) {
+            or_bits(dst, at, dup_ones((uint32_t)before, dtab) | (last << rel));
+        } else {
+            const uint32_t lo = (uint32_t)before;
+            const int hs = 32 + __popc(lo);
+            or_bits(dst, at, dup_ones(lo, dtab));
+            or_bits(dst, at + hs, dup_ones((uint32_t)(before >> 32), dtab) | (last << (rel - hs)));
+        }
+        // n refinement bits, m group bits 1, tl + 1 scanned bits (the last
+        // one implied when it is coefficient 63), a closing 0 if n_new < 64
+        off += n + m + tl + 1 - (n_new == 64 ? 1 : 0) + (n_new < 64 ? 1 : 0);
+        n = n_new;
+    }
+    return off;
+}
+
 // Encode one block into dst[0 .. words) (a bit budget of 32 words; words =
 // 2R at a fixed rate) with the plane range of `mode`.  Returns the coded
 // length in bits (exact for the variable-size modes, whose budget never
@@ -360,84 +422,24 @@ __device__ __forceinline__ int encode_block(uint32_t (&v)[64], int words, int mo
     to_coding_order(v, q, std::make_integer_sequence<int, 64>{});
     transpose32<0>(v);   // v[p]      = bits p of coefficients 0..31
     transpose32<32>(v);  // v[32 + p] = bits p of coefficients 32..63
-    // The plane loop below stays a compact loop (no unrolling) and reads the
+    // The plane coder stays a compact loop (no unrolling) and reads the
     // plane masks from this thread's shared-memory slot.
 #pragma unroll
     for (int i = 0; i < 64; ++i)
         pm[i] = v[i];
 
-    // Plane p (31 .. 0) is written as: the refinement bits of the n
-    // significant coefficients; then, for each new one at offset t past n,
-    // a group bit 1, the zeros before it and the one itself; then a closing
-    // group bit 0 if coefficients remain.  When a new one is the last
-    // coefficient its one is implied and not written.
-    //
-    // With rest = the plane's bits past n and tl its highest one, the part
-    // after the refinement bits is the group bit 1, the doubled bits of rest
-    // below tl, and the one at tl: the one of segment j lands at t_j + j past
-    // the first group bit, and the next segment's group bit right after it.
-    // Each plane is written with at most three 64-bit ORs, whatever its
-    // number of new ones.
-    int off = 9, n = 0;
-#pragma unroll 1
-    for (int p = 31; p >= pmin && off < budget; --p) {
-        const uint64_t X = ((uint64_t)pm[32 + p] << 32) | pm[p];
-        if (n >= 64) {
-            or_bits(dst, off, X);
-            off += 64;
-            continue;
-        }
-        const uint64_t refine = X & ((1ull << n) - 1ull);
-        const uint64_t rest = X >> n;
-        if (rest == 0ull) {
-            if (n > 0)
-                or_bits(dst, off, refine);
-            off += n + 1;  // refinement bits and the closing group bit 0
-            continue;
-        }
-        or_bits(dst, off, refine | (1ull << n));  // ... and the first group bit
-        const int m = __popcll((long long)rest);
-        const int tl = 63 - __clzll((long long)rest);  // offset of the last new one
-        const int n_new = n + tl + 1;
-        const int at = off + n + 1;  // first bit past the first group bit
-        const uint64_t before = rest ^ (1ull << tl);
-        const uint64_t last = n_new == 64 ? 0ull : 1ull;  // the last coefficient's one is implied
-        const int rel = tl + m - 1;                        // the last one's position past `at`
-        if (tl < 32) {
-            or_bits(dst, at, dup_ones((uint32_t)before, dtab) | (last << rel));
-        } else {
-            const uint32_t lo = (uint32_t)before;
-            const int hs = 32 + __popc(lo);
-            or_bits(dst, at, dup_ones(lo, dtab));
-            or_bits(dst, at + hs, dup_ones((uint32_t)(before >> 32), dtab) | (last << (rel - hs)));
-        }
-        // n refinement bits, m group bits 1, tl + 1 scanned bits (the last
-        // one implied when it is coefficient 63), a closing 0 if n_new < 64
-        off += n + m + tl + 1 - (n_new == 64 ? 1 : 0) + (n_new < 64 ? 1 : 0);
-        n = n_new;
-    }
-    return off;
+    return code_planes<32>(pm, dst, 9, budget, pmin, dtab);
 }
 
-// Decode one block of `nwords` words (2R at a fixed rate) with the plane
-// range of `mode`.
-__device__ __forceinline__ void decode_block(const uint32_t *src, int nwords, int mode, int mparam,
-                                             float (&out)[64], uint32_t *pm)
+// The plane parser shared by FR4 (NP = 32 planes) and FR4D (NP = 64): reads
+// planes NP-1 .. pmin from r (positioned past the header) within `budget`
+// bits into pm[p] (bit p of coefficients 0..31) and pm[NP + p] (32..63);
+// planes not received are zero.
+template <int NP>
+__device__ __forceinline__ void parse_planes(BitReader &r, int budget, int pmin, uint32_t *pm)
 {
-    const int budget = 32 * nwords;
-    const uint32_t w0 = nwords > 0 ? __ldg(src) : 0u;
-    if ((w0 & 1u) == 0u) {
-#pragma unroll
-        for (int i = 0; i < 64; ++i)
-            out[i] = 0.0f;
-        return;
-    }
-    const int emax = (int)((w0 >> 1) & 0xFFu) - 127;
-    const int pmin = plane_floor(mode, mparam, emax);
-    BitReader r;
-    r.init(src, 9, nwords);
     int n = 0;
-    int p = 31;
+    int p = NP - 1;
 #pragma unroll 1
     for (; p >= pmin && r.pos < budget; --p) {
         const int n1 = n < 32 ? n : 32;
@@ -523,12 +525,32 @@ __device__ __forceinline__ void decode_block(const uint32_t *src, int nwords, in
             xh |= (uint32_t)(X >> 32);
         }
         pm[p] = xl;
-        pm[32 + p] = xh;
+        pm[NP + p] = xh;
     }
     for (; p >= 0; --p) {  // planes past the budget or below the coded range
         pm[p] = 0u;
-        pm[32 + p] = 0u;
+        pm[NP + p] = 0u;
     }
+}
+
+// Decode one block of `nwords` words (2R at a fixed rate) with the plane
+// range of `mode`.
+__device__ __forceinline__ void decode_block(const uint32_t *src, int nwords, int mode, int mparam,
+                                             float (&out)[64], uint32_t *pm)
+{
+    const int budget = 32 * nwords;
+    const uint32_t w0 = nwords > 0 ? __ldg(src) : 0u;
+    if ((w0 & 1u) == 0u) {
+#pragma unroll
+        for (int i = 0; i < 64; ++i)
+            out[i] = 0.0f;
+        return;
+    }
+    const int emax = (int)((w0 >> 1) & 0xFFu) - 127;
+    const int pmin = plane_floor(mode, mparam, emax);
+    BitReader r;
+    r.init(src, 9, nwords);
+    parse_planes<32>(r, budget, pmin, pm);
     uint32_t u[64];
 #pragma unroll
     for (int i = 0; i < 64; ++i)
@@ -643,6 +665,311 @@ __global__ void __launch_bounds__(kThreads, MINB) fr4_decode_kernel(const uint32
         for (int j = 0; j < 4; ++j)
             *reinterpret_cast<float4 *>(p + ((int64_t)k * ny + j) * nx) =
                 make_float4(f[16 * k + 4 * j], f[16 * k + 4 * j + 1], f[16 * k + 4 * j + 2], f[16 * k + 4 * j + 3]);
+}
+
+// ---- FR4D: the same codec for FP64 fields -------------------------------------
+// 58-bit block floating point (emax clamped at -1022, 11 header bits), the
+// FR4 lifting in wrapping int64, the same coding order, 64-bit negabinary
+// and 64 bit planes through the shared plane coder and parser.  One thread
+// owns one block; a CTA of 64 threads keeps each thread's 128 plane words
+// (and, encoding, its staged output) in shared memory.
+constexpr int kPrec64 = 58;
+constexpr int kThreads64 = 64;
+constexpr int kPlaneStride64 = 129;  // 128 plane words, odd stride
+constexpr uint64_t kNB64 = 0xAAAAAAAAAAAAAAAAull;
+
+__device__ __forceinline__ int64_t wadd64(int64_t a, int64_t b) { return (int64_t)((uint64_t)a + (uint64_t)b); }
+__device__ __forceinline__ int64_t wsub64(int64_t a, int64_t b) { return (int64_t)((uint64_t)a - (uint64_t)b); }
+
+__device__ __forceinline__ void lift_fwd64(int64_t &a0, int64_t &a1, int64_t &a2, int64_t &a3)
+{
+    int64_t d0 = wsub64(a0, a1);
+    const int64_t s0 = wadd64(a1, d0 >> 1);
+    int64_t d1 = wsub64(a2, a3);
+    const int64_t s1 = wadd64(a3, d1 >> 1);
+    const int64_t D = wsub64(s0, s1);
+    const int64_t S = wadd64(s1, D >> 1);
+    d0 = wsub64(d0, D >> 1);
+    d1 = wsub64(d1, D >> 1);
+    a0 = S;
+    a1 = D;
+    a2 = d0;
+    a3 = d1;
+}
+
+__device__ __forceinline__ void lift_inv64(int64_t &a0, int64_t &a1, int64_t &a2, int64_t &a3)
+{
+    const int64_t S = a0, D = a1;
+    const int64_t d0 = wadd64(a2, D >> 1);
+    const int64_t d1 = wadd64(a3, D >> 1);
+    const int64_t s1 = wsub64(S, D >> 1);
+    const int64_t s0 = wadd64(s1, D);
+    const int64_t x3 = wsub64(s1, d1 >> 1);
+    const int64_t x2 = wadd64(x3, d1);
+    const int64_t x1 = wsub64(s0, d0 >> 1);
+    const int64_t x0 = wadd64(x1, d0);
+    a0 = x0;
+    a1 = x1;
+    a2 = x2;
+    a3 = x3;
+}
+
+__device__ __forceinline__ void transform_fwd64(int64_t (&c)[64])
+{
+#pragma unroll
+    for (int z = 0; z < 4; ++z)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            const int b = 4 * y + 16 * z;
+            lift_fwd64(c[b], c[b + 1], c[b + 2], c[b + 3]);
+        }
+#pragma unroll
+    for (int z = 0; z < 4; ++z)
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const int b = x + 16 * z;
+            lift_fwd64(c[b], c[b + 4], c[b + 8], c[b + 12]);
+        }
+#pragma unroll
+    for (int y = 0; y < 4; ++y)
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const int b = x + 4 * y;
+            lift_fwd64(c[b], c[b + 16], c[b + 32], c[b + 48]);
+        }
+}
+
+__device__ __forceinline__ void transform_inv64(int64_t (&c)[64])
+{
+#pragma unroll
+    for (int y = 0; y < 4; ++y)
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const int b = x + 4 * y;
+            lift_inv64(c[b], c[b + 16], c[b + 32], c[b + 48]);
+        }
+#pragma unroll
+    for (int z = 0; z < 4; ++z)
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const int b = x + 16 * z;
+            lift_inv64(c[b], c[b + 4], c[b + 8], c[b + 12]);
+        }
+#pragma unroll
+    for (int z = 0; z < 4; ++z)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            const int b = 4 * y + 16 * z;
+            lift_inv64(c[b], c[b + 1], c[b + 2], c[b + 3]);
+        }
+}
+
+// coefficient order_at(r) as 64-bit negabinary, split into its low and high
+// words
+template <int... R>
+__device__ __forceinline__ void to_coding_order64(uint32_t (&lo)[64], uint32_t (&hi)[64], const int64_t (&q)[64],
+                                                  std::integer_sequence<int, R...>)
+{
+    ((lo[R] = (uint32_t)(((uint64_t)q[std::integral_constant<int, order_at(R)>::value] + kNB64) ^ kNB64),
+      hi[R] = (uint32_t)((((uint64_t)q[std::integral_constant<int, order_at(R)>::value] + kNB64) ^ kNB64) >> 32)),
+     ...);
+}
+
+template <int... R>
+__device__ __forceinline__ void from_coding_order64(int64_t (&q)[64], const uint32_t (&lo)[64],
+                                                    const uint32_t (&hi)[64], std::integer_sequence<int, R...>)
+{
+    ((q[std::integral_constant<int, order_at(R)>::value] =
+          (int64_t)(((((uint64_t)hi[R] << 32) | lo[R]) ^ kNB64) - kNB64)),
+     ...);
+}
+
+// 64 coefficients' low and high words -> pm[p] (bit p of coefficients
+// 0..31) and pm[64 + p] (32..63) for p = 0..63, and back.
+__device__ __forceinline__ void words_to_planes64(uint32_t (&lo)[64], uint32_t (&hi)[64], uint32_t *pm)
+{
+    transpose32<0>(lo);
+    transpose32<32>(lo);
+    transpose32<0>(hi);
+    transpose32<32>(hi);
+#pragma unroll
+    for (int p = 0; p < 32; ++p) {
+        pm[p] = lo[p];
+        pm[32 + p] = hi[p];
+        pm[64 + p] = lo[32 + p];
+        pm[96 + p] = hi[32 + p];
+    }
+}
+
+__device__ __forceinline__ void planes_to_words64(const uint32_t *pm, uint32_t (&lo)[64], uint32_t (&hi)[64])
+{
+#pragma unroll
+    for (int p = 0; p < 32; ++p) {
+        lo[p] = pm[p];
+        hi[p] = pm[32 + p];
+        lo[32 + p] = pm[64 + p];
+        hi[32 + p] = pm[96 + p];
+    }
+    transpose32<0>(lo);
+    transpose32<32>(lo);
+    transpose32<0>(hi);
+    transpose32<32>(hi);
+}
+
+__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
+
+__device__ __forceinline__ double pow2d(int k)  // k in [-1022, 1023]
+{
+    return __longlong_as_double((long long)(k + 1023) << 52);
+}
+
+// Encode one FP64 block (bit patterns v) into dst[0 .. words) at a fixed
+// rate: words = 2R, a budget of 64R bits.
+__device__ __forceinline__ void encode_block64(const uint64_t (&v)[64], int words, uint32_t *dst, uint32_t *pm,
+                                               const uint16_t *dtab)
+{
+    uint64_t mx = 0;
+#pragma unroll
+    for (int i = 0; i < 64; ++i)
+        mx = umax64(mx, v[i] & 0x7FFFFFFFFFFFFFFFull);
+    for (int i = 0; i < words + kSlack; ++i)
+        dst[i] = 0u;
+    if (mx == 0ull)
+        return;
+    // largest frexp exponent (biased exponent - 1022; subnormals clamp to -1022)
+    const int emax = (int)(mx >> 52) - 1022;
+    dst[0] = 1u | ((uint32_t)(emax + 1023) << 1);
+    // q = trunc(x * 2^(58 - emax)) through two normal powers of two: the
+    // first product is exact whenever the result can be nonzero, the second
+    // exact or already below 1
+    const int kk = kPrec64 - emax;
+    const int k1 = kk >> 1, k2 = kk - k1;
+    const double s1 = pow2d(k1), s2 = pow2d(k2);
+    int64_t q[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i)
+        q[i] = __double2ll_rz(__dmul_rn(__dmul_rn(__longlong_as_double((long long)v[i]), s1), s2));
+    transform_fwd64(q);
+    uint32_t lo[64], hi[64];
+    to_coding_order64(lo, hi, q, std::make_integer_sequence<int, 64>{});
+    words_to_planes64(lo, hi, pm);
+    code_planes<64>(pm, dst, 12, 32 * words, 0, dtab);
+}
+
+__device__ __forceinline__ void decode_block64(const uint32_t *src, int nwords, double (&out)[64], uint32_t *pm)
+{
+    const uint32_t w0 = nwords > 0 ? __ldg(src) : 0u;
+    if ((w0 & 1u) == 0u) {
+#pragma unroll
+        for (int i = 0; i < 64; ++i)
+            out[i] = 0.0;
+        return;
+    }
+    const int emax = (int)((w0 >> 1) & 0x7FFu) - 1023;
+    BitReader r;
+    r.init(src, 12, nwords);
+    parse_planes<64>(r, 32 * nwords, 0, pm);
+    uint32_t lo[64], hi[64];
+    planes_to_words64(pm, lo, hi);
+    int64_t q[64];
+    from_coding_order64(q, lo, hi, std::make_integer_sequence<int, 64>{});
+    transform_inv64(q);
+    // x = RN(RN(q) * 2^(emax - 58)): one exact or correctly rounded scaling
+    const int k = emax - kPrec64;
+    const bool split = k < -1022;
+    const double sa = pow2d(split ? k + 64 : k), sb = pow2d(-64);
+#pragma unroll
+    for (int i = 0; i < 64; ++i) {
+        double f = __dmul_rn(__ll2double_rn((long long)q[i]), sa);
+        if (split)
+            f = __dmul_rn(f, sb);
+        out[i] = f;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads64) fr4d_encode_kernel(DConstRing in, int64_t nx, int64_t ny, int64_t z0,
+                                                                 int64_t nblk, int rate, uint32_t *__restrict__ out)
+{
+    extern __shared__ uint32_t smem[];
+    __shared__ uint16_t dtab[256];
+    init_dup_table(dtab);
+    __syncthreads();
+    const int words = 2 * rate, stride = words + kSlack + 1;
+    const int64_t first = (int64_t)blockIdx.x * kThreads64;
+    const int64_t b = first + threadIdx.x;
+    if (b < nblk) {
+        const int64_t nbx = nx >> 2, nby = ny >> 2;
+        const int64_t bx = b % nbx, t2 = b / nbx, by = t2 % nby, bz = t2 / nby;
+        const int64_t slot = ring_slot(z0 + 4 * bz, in.zbase, in.nslot);
+        const double *p = in.base + (slot * ny + 4 * by) * nx + 4 * bx;
+        uint64_t v[64];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const double2 *row = reinterpret_cast<const double2 *>(p + ((int64_t)k * ny + j) * nx);
+                const double2 a = __ldg(row), c = __ldg(row + 1);
+                v[16 * k + 4 * j + 0] = (uint64_t)__double_as_longlong(a.x);
+                v[16 * k + 4 * j + 1] = (uint64_t)__double_as_longlong(a.y);
+                v[16 * k + 4 * j + 2] = (uint64_t)__double_as_longlong(c.x);
+                v[16 * k + 4 * j + 3] = (uint64_t)__double_as_longlong(c.y);
+            }
+        encode_block64(v, words, smem + threadIdx.x * stride, smem + kThreads64 * stride + threadIdx.x * kPlaneStride64,
+                       dtab);
+    }
+    __syncthreads();
+    const int64_t left = nblk - first;
+    const int nvalid = left < kThreads64 ? (int)left : kThreads64;
+    uint32_t *dst = out + first * words;
+    // word o of the CTA's output is word (o mod words) of block (o / words)
+    for (int o = threadIdx.x; o < nvalid * words; o += kThreads64)
+        dst[o] = smem[(o / words) * stride + (o % words)];
+}
+
+__global__ void __launch_bounds__(kThreads64) fr4d_decode_kernel(const uint32_t *__restrict__ in, int64_t nx,
+                                                                 int64_t ny, int64_t z0, int64_t nblk, int rate,
+                                                                 DRing out)
+{
+    extern __shared__ uint32_t smem[];  // each thread's plane words
+    const int64_t b = (int64_t)blockIdx.x * kThreads64 + threadIdx.x;
+    if (b >= nblk)
+        return;
+    double f[64];
+    decode_block64(in + b * (2 * rate), 2 * rate, f, smem + threadIdx.x * kPlaneStride64);
+    const int64_t nbx = nx >> 2, nby = ny >> 2;
+    const int64_t bx = b % nbx, t2 = b / nbx, by = t2 % nby, bz = t2 / nby;
+    const int64_t slot = ring_slot(z0 + 4 * bz, out.zbase, out.nslot);
+    double *p = out.base + (slot * ny + 4 * by) * nx + 4 * bx;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            double2 *row = reinterpret_cast<double2 *>(p + ((int64_t)k * ny + j) * nx);
+            row[0] = make_double2(f[16 * k + 4 * j], f[16 * k + 4 * j + 1]);
+            row[1] = make_double2(f[16 * k + 4 * j + 2], f[16 * k + 4 * j + 3]);
+        }
+}
+
+size_t smem_bytes64(int rate, bool encoder)
+{
+    if (!encoder)
+        return (size_t)kThreads64 * kPlaneStride64 * sizeof(uint32_t);
+    return ((size_t)kThreads64 * (2 * rate + kSlack + 1) + (size_t)kThreads64 * kPlaneStride64) * sizeof(uint32_t);
+}
+
+cudaError_t ensure_smem_attr64()
+{
+    static bool done = false;
+    if (done)
+        return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(fr4d_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes64(64, true));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fr4d_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_bytes64(64, false));
+    if (e == cudaSuccess)
+        done = true;
+    return e;
 }
 
 // ---- dense fields of any shape, fixed rate and variable-size modes -------------
@@ -922,6 +1249,37 @@ cudaError_t launch_fr4_decode(const uint32_t *in, int64_t nx, int64_t ny, int64_
     return cudaGetLastError();
 }
 
+cudaError_t launch_fr4d_encode(DConstRing in, int64_t nx, int64_t ny, int64_t z0, int64_t z1, int rate,
+                               uint32_t *out, cudaStream_t st)
+{
+    const int64_t nblk = (nx / 4) * (ny / 4) * ((z1 - z0) / 4);
+    if (nblk <= 0)
+        return cudaSuccess;
+    if (rate < 1 || rate > 64)
+        return cudaErrorInvalidValue;
+    cudaError_t e = ensure_smem_attr64();
+    if (e != cudaSuccess)
+        return e;
+    const int64_t grid = (nblk + kThreads64 - 1) / kThreads64;
+    fr4d_encode_kernel<<<(unsigned)grid, kThreads64, smem_bytes64(rate, true), st>>>(in, nx, ny, z0, nblk, rate, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fr4d_decode(const uint32_t *in, int64_t nx, int64_t ny, int64_t z0, int64_t z1, int rate,
+                               DRing out, cudaStream_t st)
+{
+    const int64_t nblk = (nx / 4) * (ny / 4) * ((z1 - z0) / 4);
+    if (nblk <= 0)
+        return cudaSuccess;
+    if (rate < 1 || rate > 64)
+        return cudaErrorInvalidValue;
+    cudaError_t e = ensure_smem_attr64();
+    if (e != cudaSuccess)
+        return e;
+    const int64_t grid = (nblk + kThreads64 - 1) / kThreads64;
+    fr4d_decode_kernel<<<(unsigned)grid, kThreads64, smem_bytes64(rate, false), st>>>(in, nx, ny, z0, nblk, rate, out);
+    return cudaGetLastError();
+}
 
 int64_t fr4_blocks(int64_t nx, int64_t ny, int64_t nz) { return ((nx + 3) / 4) * ((ny + 3) / 4) * ((nz + 3) / 4); }
 

@@ -22,6 +22,19 @@ struct ConstRing {
     int64_t zbase;
 };
 
+// The same window of an FP64 field.
+struct DRing {
+    double *base;
+    int64_t nslot;
+    int64_t zbase;
+};
+
+struct DConstRing {
+    const double *base;
+    int64_t nslot;
+    int64_t zbase;
+};
+
 __host__ __device__ inline int64_t ring_slot(int64_t z, int64_t zbase, int64_t nslot)
 {
     int64_t s = z + zbase;
@@ -87,6 +100,12 @@ cudaError_t launch_fr4_encode(ConstRing in, int64_t nx, int64_t ny, int64_t z0, 
                               uint32_t *out, cudaStream_t st);
 cudaError_t launch_fr4_decode(const uint32_t *in, int64_t nx, int64_t ny, int64_t z0, int64_t z1, int rate,
                               Ring out, cudaStream_t st);
+// FR4D (FP64 fields, rate 1..64): planes [z0, z1) of an FP64 ring, whole
+// 4^3 blocks (nx, ny, z1 - z0 multiples of 4), the stream of plane z0 first.
+cudaError_t launch_fr4d_encode(DConstRing in, int64_t nx, int64_t ny, int64_t z0, int64_t z1, int rate,
+                               uint32_t *out, cudaStream_t st);
+cudaError_t launch_fr4d_decode(const uint32_t *in, int64_t nx, int64_t ny, int64_t z0, int64_t z1, int rate,
+                               DRing out, cudaStream_t st);
 // Dense fields of any shape (partial blocks edge-padded).  Fixed rate:
 // mode OOC_FR4_RATE, `words` = 2R per block.  Variable-size modes
 // (OOC_FR4_PRECISION / OOC_FR4_ACCURACY, mparam = P or floor(log2 tol)):
