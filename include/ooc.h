@@ -52,10 +52,21 @@ typedef int ooc_status;
 #define OOC_HEAT7 1
 #define OOC_WAVE25 2
 
-/* Storage formats of a field in host memory and on the wire. */
+/* Storage formats of a field in host memory and on the wire.  FP32 plans
+ * take FP32, BF16 or FR4; FP64 plans take FP64 or FR4 (which is then the
+ * FP64 codec FR4D, ooc_compress64). */
 #define OOC_FMT_FP32 0  /* 4 bytes per value, uncompressed */
 #define OOC_FMT_BF16 1  /* 2 bytes per value, round to nearest even */
 #define OOC_FMT_FR4 2   /* fixed-rate 4^3-block codec, `rate` bits per value */
+#define OOC_FMT_FP64 3  /* 8 bytes per value, uncompressed (FP64 plans) */
+
+/* Precision of a plan's fields and arithmetic.  The paper's runs are in
+ * double precision (Section VI); FP64 plans compute in FP64 on the GPU,
+ * run heat7 one step per launch, and exchange whole fields with
+ * ooc_set_field64 / ooc_get_field64.  Wave source amplitudes stay FP32
+ * values (ooc_set_source) in both precisions. */
+#define OOC_PREC_FP32 0
+#define OOC_PREC_FP64 1
 
 /* Field indices.  HEAT7: 0 = u.  WAVE25: 0 = p^t, 1 = p^{t-1} (both
  * read-write, Section VI), 2 = kappa = (v dt / dx)^2 (read-only). */
@@ -85,6 +96,7 @@ typedef struct {
                                     the device after each ooc_step / ooc_set_field / ooc_get_field,
                                     and host checks of every launch's plane window and every copy's
                                     byte range; a failure returns OOC_E_CORRUPT.  0 = off */
+    int32_t precision;           /* OOC_PREC_FP32 (0) or OOC_PREC_FP64 */
 } ooc_config;
 
 typedef struct ooc_plan ooc_plan;
@@ -228,6 +240,12 @@ ooc_status ooc_wave25_steps(float *d_p, float *d_pprev, const float *d_kappa, in
 ooc_status ooc_heat7_steps_f64(double *d_u, double *d_tmp, int64_t nx, int64_t ny, int64_t nz, double r,
                                int64_t nsteps, void *stream);
 
+/* wave25 in double precision: as ooc_wave25_steps with FP64 device fields
+ * (16-byte aligned) and an FP64 source series h_w (host). */
+ooc_status ooc_wave25_steps_f64(double *d_p, double *d_pprev, const double *d_kappa, int64_t nx, int64_t ny,
+                                int64_t nz, int64_t sx, int64_t sy, int64_t sz, const double *h_w, int64_t t,
+                                int64_t nsteps, void *stream);
+
 /* The nsteps heat7 steps of ooc_heat7_steps with each pair of steps in one
  * kernel launch (temporal blocking inside the kernel, Section III: the
  * intermediate level stays in shared memory and registers, so HBM carries
@@ -339,9 +357,14 @@ ooc_status ooc_plan_bind(ooc_plan *plan, void *device_arena, size_t device_bytes
 
 /* Store / fetch a whole FP32 field (host pointers, nx*ny*nz floats) into /
  * out of the plan's host storage, encoding / decoding on the GPU.  Blocks
- * until done.  Must not overlap an ooc_step on the same plan. */
+ * until done.  Must not overlap an ooc_step on the same plan.  FP32 plans
+ * only (OOC_E_INVALID otherwise). */
 ooc_status ooc_set_field(ooc_plan *plan, int field, const float *host_src);
 ooc_status ooc_get_field(ooc_plan *plan, int field, float *host_dst);
+
+/* The same for FP64 plans, with nx*ny*nz doubles. */
+ooc_status ooc_set_field64(ooc_plan *plan, int field, const double *host_src);
+ooc_status ooc_get_field64(ooc_plan *plan, int field, double *host_dst);
 
 /* Point source of the wave stencil: p^{n+1}(sx,sy,sz) += w[n] for n < nw
  * (host array, copied).  nw = 0 removes it. */

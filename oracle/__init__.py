@@ -303,9 +303,18 @@ def bf16_roundtrip(x):
     return bf16_to_f32(bf16_bits(x)).reshape(np.shape(x))
 
 
-def storage_roundtrip(field, fmt, rate=16):
-    """What a field looks like after being stored in ``fmt``: cast to float32
-    and, for bf16/fr4, rounded/encoded and decoded.  Returns float64."""
+def storage_roundtrip(field, fmt, rate=16, precision="fp32"):
+    """What a field looks like after being stored in ``fmt``.  FP32 plans:
+    cast to float32 and, for bf16/fr4, rounded/encoded and decoded.  FP64
+    plans (precision='fp64'): 'fp64' keeps the value, 'fr4' is the FR4D
+    round trip.  Returns float64."""
+    if precision == "fp64":
+        d = np.array(field, dtype=np.float64)
+        if fmt == "fp64":
+            return d
+        if fmt == "fr4":
+            return fr4d_roundtrip(d, rate)
+        raise ValueError(fmt)
     f = np.ascontiguousarray(field, dtype=np.float32)
     if fmt == "fp32":
         g = f
@@ -419,35 +428,37 @@ def misfit(traces, d):
 
 
 # --------------------------------------------------------------------------- pipelines
-def heat7_storage_pipeline(u0, nsteps, k, fmt, rate=16, r=1.0 / 6.0):
+def heat7_storage_pipeline(u0, nsteps, k, fmt, rate=16, r=1.0 / 6.0, precision="fp32"):
     """FP64 heat7 with the storage round trip the out-of-core pipeline
     applies: once at load, then after every pass of ``k`` steps (the last
     pass may be shorter).  With fmt='fp32' this is FP64 compute on the
-    FP32-rounded state at pass boundaries."""
-    u = storage_roundtrip(u0, fmt, rate)
+    FP32-rounded state at pass boundaries; precision='fp64' stores in the
+    FP64 plan's formats ('fp64', or 'fr4' = FR4D)."""
+    u = storage_roundtrip(u0, fmt, rate, precision)
     done = 0
     while done < nsteps:
         s = min(k, nsteps - done)
         u = heat7_run(u, s, r)
-        u = storage_roundtrip(u, fmt, rate)
+        u = storage_roundtrip(u, fmt, rate, precision)
         done += s
     return u
 
 
 def wave25_storage_pipeline(p0, pm1, kappa, nsteps, k, fmt, rate=16, ro_fmt=None, ro_rate=None,
-                            src=-1, w=None):
+                            src=-1, w=None, precision="fp32"):
     """FP64 leapfrog with storage round trips of both time levels at load
     and after every pass of ``k`` steps; kappa (read-only) is stored once in
-    ``ro_fmt`` (default fp32)."""
-    kap = storage_roundtrip(kappa, ro_fmt or "fp32", ro_rate or rate)
-    p = storage_roundtrip(p0, fmt, rate)
-    q = storage_roundtrip(pm1, fmt, rate)
+    ``ro_fmt`` (default: the plan's uncompressed format)."""
+    raw = "fp64" if precision == "fp64" else "fp32"
+    kap = storage_roundtrip(kappa, ro_fmt or raw, ro_rate or rate, precision)
+    p = storage_roundtrip(p0, fmt, rate, precision)
+    q = storage_roundtrip(pm1, fmt, rate, precision)
     done = 0
     while done < nsteps:
         s = min(k, nsteps - done)
         p, q = wave25_run(p, q, kap, s, src=src, w=w, t0=done)
-        p = storage_roundtrip(p, fmt, rate)
-        q = storage_roundtrip(q, fmt, rate)
+        p = storage_roundtrip(p, fmt, rate, precision)
+        q = storage_roundtrip(q, fmt, rate, precision)
         done += s
     return p, q
 

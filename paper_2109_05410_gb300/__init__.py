@@ -21,15 +21,17 @@ __all__ = [
     "OocConfig", "OocStats", "OocPlanInfo", "OocError", "lib", "build",
     "ooc_status_string", "ooc_take_device_fault", "ooc_compressed_bytes", "ooc_compress", "ooc_decompress", "ooc_compress64", "ooc_decompress64", "ooc_compress_var",
     "ooc_decompress_var", "ooc_compress_var_bound", "ooc_var_scratch_bytes", "OOC_FR4_PRECISION", "OOC_FR4_ACCURACY",
-    "ooc_bf16_pack", "ooc_bf16_unpack", "ooc_heat7_steps", "ooc_heat7_steps_f64", "ooc_heat7_steps_fused", "ooc_heat7_steps_noalloc", "ooc_wave25_steps", "Plan",
+    "ooc_bf16_pack", "ooc_bf16_unpack", "ooc_heat7_steps", "ooc_heat7_steps_f64", "ooc_heat7_steps_fused", "ooc_heat7_steps_noalloc", "ooc_wave25_steps", "ooc_wave25_steps_f64", "Plan",
     "ooc_gather", "ooc_scatter_add", "ooc_wave25_adjoint_step", "ooc_wave25_grad_accum", "ooc_kappa_from_velocity",
     "ooc_velocity_grad", "ooc_wave25_ckpt_bytes", "ooc_wave25_adjoint_work_bytes", "ooc_wave25_forward_ckpt",
     "ooc_wave25_backward_ckpt", "WaveFn", "wave_forward",
 ]
 
 OOC_HEAT7, OOC_WAVE25 = 1, 2
-OOC_FMT_FP32, OOC_FMT_BF16, OOC_FMT_FR4 = 0, 1, 2
-FORMATS = {"fp32": OOC_FMT_FP32, "bf16": OOC_FMT_BF16, "fr4": OOC_FMT_FR4}
+OOC_FMT_FP32, OOC_FMT_BF16, OOC_FMT_FR4, OOC_FMT_FP64 = 0, 1, 2, 3
+FORMATS = {"fp32": OOC_FMT_FP32, "bf16": OOC_FMT_BF16, "fr4": OOC_FMT_FR4, "fp64": OOC_FMT_FP64}
+OOC_PREC_FP32, OOC_PREC_FP64 = 0, 1
+PRECISIONS = {"fp32": OOC_PREC_FP32, "fp64": OOC_PREC_FP64}
 STENCILS = {"heat7": OOC_HEAT7, "wave25": OOC_WAVE25}
 
 
@@ -42,7 +44,7 @@ class OocConfig(ctypes.Structure):
         ("device_budget_bytes", ctypes.c_int64), ("slab_planes", ctypes.c_int32),
         ("profile", ctypes.c_int32), ("wait_timeout_ms", ctypes.c_int64),
         ("heat_steps_per_launch", ctypes.c_int32), ("graph_mode", ctypes.c_int32),
-        ("debug_checks", ctypes.c_int32),
+        ("debug_checks", ctypes.c_int32), ("precision", ctypes.c_int32),
     ]
 
 
@@ -113,6 +115,8 @@ _SIGS = {
                               + [ctypes.c_double, ctypes.c_int64, ctypes.c_void_p]),
     "ooc_wave25_steps": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int64] * 6
                          + [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]),
+    "ooc_wave25_steps_f64": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int64] * 6
+                             + [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]),
     "ooc_plan_create": (ctypes.c_int, [ctypes.POINTER(OocConfig), ctypes.POINTER(ctypes.c_void_p),
                                        ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
     "ooc_plan_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(OocPlanInfo)]),
@@ -120,6 +124,8 @@ _SIGS = {
                                      ctypes.c_size_t, ctypes.c_void_p * 3]),
     "ooc_set_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "ooc_get_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "ooc_set_field64": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "ooc_get_field64": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "ooc_set_source": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int64] * 3 + [ctypes.c_void_p, ctypes.c_int64]),
     "ooc_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "ooc_take_device_fault": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]),
@@ -363,6 +369,23 @@ def ooc_wave25_steps(d_p, d_pprev, d_kappa, nsteps, src=None, w=None, t=0, strea
     return d_p, d_pprev
 
 
+def ooc_wave25_steps_f64(d_p, d_pprev, d_kappa, nsteps, src=None, w=None, t=0, stream=None):
+    """FP64 leapfrog in place on float64 CUDA tensors; ``w`` a float64 numpy
+    series indexed by absolute step."""
+    nz, ny, nx = d_p.shape
+    if src is None or w is None:
+        sx, sy, sz, wp = -1, -1, -1, None
+    else:
+        sx, sy, sz = src
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        if len(w) < t + nsteps:
+            raise ValueError("source series shorter than t + nsteps")
+        wp = w.ctypes.data_as(ctypes.c_void_p)
+    _check(lib().ooc_wave25_steps_f64(_ptr(d_p), _ptr(d_pprev), _ptr(d_kappa), nx, ny, nz, sx, sy, sz, wp, int(t),
+                                      int(nsteps), _stream(stream)), "ooc_wave25_steps_f64")
+    return d_p, d_pprev
+
+
 def ooc_gather(d_field, d_idx, d_out=None, stream=None):
     import torch
     if d_out is None:
@@ -463,7 +486,9 @@ class Plan:
     streams (H2D, compute, D2H).  Configuration keys mirror ``ooc_config``:
     nx, ny, nz, stencil ('heat7'|'wave25'), k, r, rw_format, rw_rate,
     ro_format, ro_rate, device_budget_bytes, slab_planes, profile,
-    wait_timeout_ms, heat_steps_per_launch, graph_mode, debug_checks."""
+    wait_timeout_ms, heat_steps_per_launch, graph_mode, debug_checks,
+    precision ('fp32'|'fp64'; FP64 plans store 'fp64' or 'fr4' fields and
+    exchange float64 arrays)."""
 
     def __init__(self, device=0, **kw):
         import torch
@@ -484,6 +509,9 @@ class Plan:
         c.heat_steps_per_launch = int(kw.get("heat_steps_per_launch", 0))
         c.graph_mode = int(kw.get("graph_mode", 0))
         c.debug_checks = int(kw.get("debug_checks", 0))
+        prec = kw.get("precision", "fp32")
+        c.precision = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+        self.dtype = np.float64 if c.precision == OOC_PREC_FP64 else np.float32
         self.config = c
         self.shape = (c.nz, c.ny, c.nx)
         self._h = ctypes.c_void_p()
@@ -512,15 +540,19 @@ class Plan:
         return i.as_dict()
 
     def set_field(self, field, host_src):
-        a = np.ascontiguousarray(host_src, dtype=np.float32)
+        a = np.ascontiguousarray(host_src, dtype=self.dtype)
         if a.shape != self.shape:
             raise ValueError(f"field shape {a.shape} != {self.shape}")
-        _check(lib().ooc_set_field(self._h, int(field), a.ctypes.data_as(ctypes.c_void_p)), "ooc_set_field")
+        fn = "ooc_set_field64" if self.dtype == np.float64 else "ooc_set_field"
+        _check(getattr(lib(), fn)(self._h, int(field), a.ctypes.data_as(ctypes.c_void_p)), fn)
 
     def get_field(self, field, out=None):
         if out is None:
-            out = np.empty(self.shape, dtype=np.float32)
-        _check(lib().ooc_get_field(self._h, int(field), out.ctypes.data_as(ctypes.c_void_p)), "ooc_get_field")
+            out = np.empty(self.shape, dtype=self.dtype)
+        if out.dtype != self.dtype or out.shape != self.shape or not out.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous array of the plan's shape and precision")
+        fn = "ooc_get_field64" if self.dtype == np.float64 else "ooc_get_field"
+        _check(getattr(lib(), fn)(self._h, int(field), out.ctypes.data_as(ctypes.c_void_p)), fn)
         return out
 
     def set_source(self, sx, sy, sz, w):

@@ -392,6 +392,31 @@ ooc_status ooc_wave25_steps(float *d_p, float *d_pprev, const float *d_kappa, in
     return OOC_OK;
 }
 
+ooc_status ooc_wave25_steps_f64(double *d_p, double *d_pprev, const double *d_kappa, int64_t nx, int64_t ny,
+                                int64_t nz, int64_t sx, int64_t sy, int64_t sz, const double *h_w, int64_t t,
+                                int64_t nsteps, void *stream)
+{
+    if (!d_p || !d_pprev || !d_kappa || d_p == d_pprev || !dims_ok(nx, ny, nz) || nsteps < 0 || t < 0 ||
+        !aligned(d_p, 16) || !aligned(d_pprev, 16) || !aligned(d_kappa, 16))
+        return OOC_E_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *a = d_p, *b = d_pprev;  // a holds p^n, b holds p^{n-1}
+    for (int64_t s = 0; s < nsteps; ++s) {
+        const bool src = sx >= 0 && h_w != nullptr;
+        const double w = src ? h_w[t + s] : 0.0;
+        cudaError_t e = launch_wave25_f64(DConstRing{a, nz, 0}, DRing{b, nz, 0}, DConstRing{d_kappa, nz, 0}, nx, ny,
+                                          nz, 0, nz, src ? sx : -1, sy, sz, w, st);
+        if (e != cudaSuccess)
+            return OOC_E_CUDA;
+        double *tmp = a;  // b now holds p^{n+1}
+        a = b;
+        b = tmp;
+    }
+    if (a != d_p)  // swap the two buffers' contents (as 32-bit words)
+        return cuda_status(launch_swap((float *)d_p, (float *)d_pprev, 2 * nx * ny * nz, st));
+    return OOC_OK;
+}
+
 }  // extern "C"
 
 extern "C" ooc_status ooc_take_device_fault(int *fault)

@@ -82,6 +82,13 @@ cudaError_t launch_heat7x2(ConstRing in, Ring out, int64_t nx, int64_t ny, int64
 // FP64 heat7 step over a whole dense field (nx even, in != out).
 cudaError_t launch_heat7_f64(const double *in, double *out, int64_t nx, int64_t ny, int64_t nz, double r,
                              cudaStream_t st);
+// FP64 rings (stencil64.cu): heat7 one step on [z0, z1) from `in` into
+// `out`; wave25 one leapfrog step with p_prev overwritten in place.
+cudaError_t launch_heat7_f64_ring(DConstRing in, DRing out, int64_t nx, int64_t ny, int64_t nz, int64_t z0, int64_t z1,
+                                  double r, cudaStream_t st);
+cudaError_t launch_wave25_f64(DConstRing p, DRing pprev_out, DConstRing kappa, int64_t nx, int64_t ny, int64_t nz,
+                              int64_t z0, int64_t z1, int64_t sx, int64_t sy, int64_t sz, double w, cudaStream_t st,
+                              WaveSrcTable tab = WaveSrcTable{});
 cudaError_t launch_wave25(ConstRing p, Ring pprev_out, ConstRing kappa, int64_t nx, int64_t ny, int64_t nz,
                           int64_t z0, int64_t z1, int64_t sx, int64_t sy, int64_t sz, float w, cudaStream_t st,
                           WaveSrcTable tab = WaveSrcTable{});

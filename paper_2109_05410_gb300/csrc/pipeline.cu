@@ -65,6 +65,8 @@ int fmt_bits(int fmt, int rate)
 {
     if (fmt == OOC_FMT_FP32)
         return 32;
+    if (fmt == OOC_FMT_FP64)
+        return 64;
     if (fmt == OOC_FMT_BF16)
         return 16;
     return rate;
@@ -84,6 +86,7 @@ struct ooc_plan {
     int64_t T = 0, nslab = 0, W = 0, h = 0, Z = 0;
     int nrw = 0, nfield = 0, nring = 0;
     int spl = 1;  // heat7 steps per stencil launch (1 or 2)
+    int esize = 4;  // bytes per value in the rings: 4 (FP32 plans) or 8 (FP64)
     size_t off_band = 0, band_bytes = 0;  // level-s bands of the fused launches
     size_t off_src = 0;                   // wave source table (kSrcTable floats) and the device time
     int fmt[3] = {0, 0, 0}, rate[3] = {0, 0, 0};
@@ -125,7 +128,7 @@ struct ooc_plan {
 
 namespace {
 
-bool staged(const ooc_plan *p, int f) { return p->fmt[f] != OOC_FMT_FP32; }
+bool staged(const ooc_plan *p, int f) { return p->fmt[f] != OOC_FMT_FP32 && p->fmt[f] != OOC_FMT_FP64; }
 
 // Layout of the device arena for slab thickness T; returns total bytes.
 size_t layout(ooc_plan *p, int64_t T)
@@ -146,7 +149,7 @@ size_t layout(ooc_plan *p, int64_t T)
             off += kGuard;
         }
     };
-    const size_t ring_bytes = (size_t)Z * p->plane_elems * sizeof(float);
+    const size_t ring_bytes = (size_t)Z * p->plane_elems * p->esize;
     for (int r = 0; r < p->nring; ++r) {
         p->off_ring[r] = off;
         off += align256(ring_bytes);
@@ -170,7 +173,7 @@ size_t layout(ooc_plan *p, int64_t T)
     // Fused heat7 pairs: the intermediate level's top 2h planes of each slab,
     // for the next slab; one band per pair of the pass and slab parity.
     p->off_band = off;
-    p->band_bytes = p->spl == 2 ? (size_t)(2 * h) * p->plane_elems * sizeof(float) : 0;
+    p->band_bytes = p->spl == 2 ? (size_t)(2 * h) * p->plane_elems * p->esize : 0;
     off += align256(p->band_bytes) * 2 * (size_t)(p->cfg.k / 2);
     if (p->band_bytes > 0)
         guard();
@@ -193,6 +196,14 @@ Ring ring_view(ooc_plan *p, int r, int64_t zbase)
 
 ConstRing cring(const Ring &r) { return ConstRing{r.base, r.nslot, r.zbase}; }
 
+// The same rings of an FP64 plan.
+DRing dring_view(ooc_plan *p, int r, int64_t zbase)
+{
+    return DRing{(double *)(p->dev + p->off_ring[r]), p->Z, zbase};
+}
+
+DConstRing dcring(const DRing &r) { return DConstRing{r.base, r.nslot, r.zbase}; }
+
 int64_t *dev_time(ooc_plan *p) { return (int64_t *)(p->dev + p->off_src); }
 float *dev_src(ooc_plan *p) { return (float *)(p->dev + p->off_src + 256); }
 
@@ -209,7 +220,7 @@ int64_t stencil_launches(const ooc_plan *p, int64_t kp) { return p->spl == 2 ? k
 cudaError_t copy_ring(ooc_plan *p, int r, int64_t zbase, int64_t z0, int64_t z1, char *hostp, bool to_device,
                       cudaStream_t st)
 {
-    const size_t pb = (size_t)p->plane_elems * sizeof(float);
+    const size_t pb = (size_t)p->plane_elems * p->esize;
     int64_t z = z0;
     while (z < z1) {
         const int64_t slot = ring_slot(z, zbase, p->Z);
@@ -305,24 +316,30 @@ ooc_status prof_end(ooc_plan *p, cudaStream_t st, size_t idx)
             return OOC_E_CUDA;       \
     } while (0)
 
-// Decode planes [z0, z1) of field f from `src` (storage format) into ring r.
-ooc_status decode_into(ooc_plan *p, int f, const char *src, Ring dst, int64_t z0, int64_t z1, cudaStream_t st)
+// Decode planes [z0, z1) of field f from `src` (storage format) into ring r
+// (FR4D on FP64 plans).
+ooc_status decode_into(ooc_plan *p, int f, const char *src, int r, int64_t zb, int64_t z0, int64_t z1,
+                       cudaStream_t st)
 {
     const int64_t nx = p->cfg.nx, ny = p->cfg.ny;
-    if (p->fmt[f] == OOC_FMT_FR4)
-        OOC_CUDA(launch_fr4_decode((const uint32_t *)src, nx, ny, z0, z1, p->rate[f], dst, st));
+    if (p->esize == 8)
+        OOC_CUDA(launch_fr4d_decode((const uint32_t *)src, nx, ny, z0, z1, p->rate[f], dring_view(p, r, zb), st));
+    else if (p->fmt[f] == OOC_FMT_FR4)
+        OOC_CUDA(launch_fr4_decode((const uint32_t *)src, nx, ny, z0, z1, p->rate[f], ring_view(p, r, zb), st));
     else
-        OOC_CUDA(launch_bf16_unpack_ring((const uint16_t *)src, nx, ny, z0, z1, dst, st));
+        OOC_CUDA(launch_bf16_unpack_ring((const uint16_t *)src, nx, ny, z0, z1, ring_view(p, r, zb), st));
     return OOC_OK;
 }
 
-ooc_status encode_from(ooc_plan *p, int f, ConstRing srcr, char *dst, int64_t z0, int64_t z1, cudaStream_t st)
+ooc_status encode_from(ooc_plan *p, int f, int r, int64_t zb, char *dst, int64_t z0, int64_t z1, cudaStream_t st)
 {
     const int64_t nx = p->cfg.nx, ny = p->cfg.ny;
-    if (p->fmt[f] == OOC_FMT_FR4)
-        OOC_CUDA(launch_fr4_encode(srcr, nx, ny, z0, z1, p->rate[f], (uint32_t *)dst, st));
+    if (p->esize == 8)
+        OOC_CUDA(launch_fr4d_encode(dcring(dring_view(p, r, zb)), nx, ny, z0, z1, p->rate[f], (uint32_t *)dst, st));
+    else if (p->fmt[f] == OOC_FMT_FR4)
+        OOC_CUDA(launch_fr4_encode(cring(ring_view(p, r, zb)), nx, ny, z0, z1, p->rate[f], (uint32_t *)dst, st));
     else
-        OOC_CUDA(launch_bf16_pack_ring(srcr, nx, ny, z0, z1, (uint16_t *)dst, st));
+        OOC_CUDA(launch_bf16_pack_ring(cring(ring_view(p, r, zb)), nx, ny, z0, z1, (uint16_t *)dst, st));
     return OOC_OK;
 }
 
@@ -440,8 +457,8 @@ ooc_status enqueue_steps(ooc_plan *p, int64_t nsteps, ooc_stats *st, int64_t *sl
                         continue;
                     size_t pi;
                     OOC_TRY(prof_begin(p, sC, 0, &pi));
-                    OOC_TRY(decode_into(p, f, p->dev + p->off_in[g & 1][f], ring_view(p, input_ring(p, f), zb),
-                                        sg.in_lo, sg.in_hi, sC));
+                    OOC_TRY(decode_into(p, f, p->dev + p->off_in[g & 1][f], input_ring(p, f), zb, sg.in_lo,
+                                        sg.in_hi, sC));
                     OOC_TRY(prof_end(p, sC, pi));
                     st->kernel_launches++;
                 }
@@ -465,7 +482,11 @@ ooc_status enqueue_steps(ooc_plan *p, int64_t nsteps, ooc_stats *st, int64_t *sl
                 OOC_TRY(expect(p, lo >= 0 && hi <= nz && (hi - lo) + 2 * p->h <= p->Z));
                 if (nst++ == 0)
                     OOC_TRY(prof_begin(p, sC, 1, &pst));
-                if (!wave && len == 2) {
+                if (p->esize == 8 && !wave) {
+                    OOC_CUDA(launch_heat7_f64_ring(dcring(dring_view(p, (int)(j & 1), zb)),
+                                                   dring_view(p, (int)((j + 1) & 1), zb), nx, ny, nz, lo, hi, p->cfg.r,
+                                                   sC));
+                } else if (!wave && len == 2) {
                     // level s on [lo_s, hi_s) stays on chip; its 2h planes
                     // below lo_s come from slab i-1's band, its top 2h
                     // planes go to this slab's band
@@ -489,9 +510,16 @@ ooc_status enqueue_steps(ooc_plan *p, int64_t nsteps, ooc_stats *st, int64_t *sl
                     } else {
                         src = p->sx >= 0 && n < (int64_t)p->w.size() && p->sz >= lo && p->sz < hi;
                     }
-                    OOC_CUDA(launch_wave25(cring(ring_view(p, (int)((s - 1) & 1), zb)), ring_view(p, (int)(s & 1), zb),
-                                           cring(ring_view(p, 2, zb)), nx, ny, nz, lo, hi, src ? p->sx : -1, p->sy,
-                                           p->sz, src && !p->src_uploaded ? p->w[n] : 0.0f, sC, tab));
+                    if (p->esize == 8)
+                        OOC_CUDA(launch_wave25_f64(dcring(dring_view(p, (int)((s - 1) & 1), zb)),
+                                                   dring_view(p, (int)(s & 1), zb), dcring(dring_view(p, 2, zb)), nx,
+                                                   ny, nz, lo, hi, src ? p->sx : -1, p->sy, p->sz,
+                                                   src && !p->src_uploaded ? (double)p->w[n] : 0.0, sC, tab));
+                    else
+                        OOC_CUDA(launch_wave25(cring(ring_view(p, (int)((s - 1) & 1), zb)),
+                                               ring_view(p, (int)(s & 1), zb), cring(ring_view(p, 2, zb)), nx, ny, nz,
+                                               lo, hi, src ? p->sx : -1, p->sy, p->sz,
+                                               src && !p->src_uploaded ? p->w[n] : 0.0f, sC, tab));
                 }
                 st->kernel_launches++;
                 s += len;
@@ -513,8 +541,8 @@ ooc_status enqueue_steps(ooc_plan *p, int64_t nsteps, ooc_stats *st, int64_t *sl
                                       (size_t)(sg.b - sg.a) * p->fplane[f] <= p->out_bytes_field[f]));
                 size_t pi;
                 OOC_TRY(prof_begin(p, sC, 2, &pi));
-                OOC_TRY(encode_from(p, f, cring(ring_view(p, output_ring(p, f, kp), zb)),
-                                    p->dev + p->off_out[g & 1][f], sg.a, sg.b, sC));
+                OOC_TRY(encode_from(p, f, output_ring(p, f, kp), zb, p->dev + p->off_out[g & 1][f], sg.a, sg.b,
+                                    sC));
                 OOC_TRY(prof_end(p, sC, pi));
                 st->kernel_launches++;
             }
@@ -655,8 +683,13 @@ ooc_status ooc_plan_create(const ooc_config *cfg, ooc_plan **out, size_t *device
         return OOC_E_INVALID;
     if (c.stencil != OOC_HEAT7 && c.stencil != OOC_WAVE25)
         return OOC_E_INVALID;
-    auto fmt_ok = [](int f, int r) {
-        return f == OOC_FMT_FP32 || f == OOC_FMT_BF16 || (f == OOC_FMT_FR4 && r >= 1 && r <= 64);
+    if (c.precision != OOC_PREC_FP32 && c.precision != OOC_PREC_FP64)
+        return OOC_E_INVALID;
+    const bool f64 = c.precision == OOC_PREC_FP64;
+    auto fmt_ok = [f64](int f, int r) {
+        if (f == OOC_FMT_FR4)
+            return r >= 1 && r <= 64;
+        return f64 ? f == OOC_FMT_FP64 : (f == OOC_FMT_FP32 || f == OOC_FMT_BF16);
     };
     if (!fmt_ok(c.rw_format, c.rw_rate) || (c.stencil == OOC_WAVE25 && !fmt_ok(c.ro_format, c.ro_rate)))
         return OOC_E_INVALID;
@@ -665,7 +698,7 @@ ooc_status ooc_plan_create(const ooc_config *cfg, ooc_plan **out, size_t *device
     if (c.graph_mode < 0 || c.graph_mode > 1)
         return OOC_E_INVALID;
     if (c.heat_steps_per_launch < 0 || c.heat_steps_per_launch > 2 ||
-        (c.stencil == OOC_WAVE25 && c.heat_steps_per_launch > 1))
+        ((c.stencil == OOC_WAVE25 || f64) && c.heat_steps_per_launch > 1))
         return OOC_E_INVALID;
     ooc_plan *p = new (std::nothrow) ooc_plan();
     if (!p)
@@ -674,9 +707,11 @@ ooc_status ooc_plan_create(const ooc_config *cfg, ooc_plan **out, size_t *device
     p->h = c.stencil == OOC_HEAT7 ? 1 : 4;
     // heat7 runs the k steps of a pass as fused pairs unless one step per
     // launch is asked for (heat_steps_per_launch = 1) or k = 1
-    p->spl = c.stencil == OOC_HEAT7 && (c.heat_steps_per_launch == 2 || (c.heat_steps_per_launch == 0 && c.k >= 2))
+    p->spl = !f64 && c.stencil == OOC_HEAT7 &&
+                     (c.heat_steps_per_launch == 2 || (c.heat_steps_per_launch == 0 && c.k >= 2))
                  ? 2
                  : 1;
+    p->esize = f64 ? 8 : 4;
     p->W = round4((int64_t)c.k * p->h);
     p->nrw = c.stencil == OOC_HEAT7 ? 1 : 2;
     p->nfield = c.stencil == OOC_HEAT7 ? 1 : 3;
@@ -815,12 +850,18 @@ ooc_status ooc_set_source(ooc_plan *p, int64_t sx, int64_t sy, int64_t sz, const
     return OOC_OK;
 }
 
-ooc_status ooc_set_field(ooc_plan *p, int field, const float *host_src)
+}  // extern "C"
+
+namespace {
+
+// ooc_set_field / ooc_set_field64: host_src holds nx*ny*nz values of the
+// plan's precision.
+ooc_status set_field_impl(ooc_plan *p, int field, const void *host_src)
 {
     if (!p || !p->bound || !host_src || field < 0 || field >= p->nfield)
         return OOC_E_INVALID;
     const int64_t nz = p->cfg.nz;
-    const size_t pb = (size_t)p->plane_elems * sizeof(float);
+    const size_t pb = (size_t)p->plane_elems * p->esize;
     char *img = p->host + p->off_host[field];
     if (!staged(p, field)) {
         std::memcpy(img, host_src, pb * nz);
@@ -839,13 +880,13 @@ ooc_status ooc_set_field(ooc_plan *p, int field, const float *host_src)
         const int e = (int)(j % kEv), e2 = (int)((j + kEv - 2) % kEv);
         if (j >= 2)
             OOC_CUDA(cudaStreamWaitEvent(sH, p->ev_comp[e2], 0));
-        OOC_CUDA(copy_ring(p, b, zb, z0, z1, (char *)(host_src + (size_t)z0 * p->plane_elems), true, sH));
+        OOC_CUDA(copy_ring(p, b, zb, z0, z1, (char *)host_src + (size_t)z0 * pb, true, sH));
         OOC_CUDA(cudaEventRecord(p->ev_h2d[e], sH));
         OOC_CUDA(cudaStreamWaitEvent(sC, p->ev_h2d[e], 0));
         if (j >= 2)
             OOC_CUDA(cudaStreamWaitEvent(sC, p->ev_d2h[e2], 0));
         char *stage = p->dev + p->off_in[b][field];
-        OOC_TRY(encode_from(p, field, cring(ring_view(p, b, zb)), stage, z0, z1, sC));
+        OOC_TRY(encode_from(p, field, b, zb, stage, z0, z1, sC));
         OOC_CUDA(cudaEventRecord(p->ev_comp[e], sC));
         OOC_CUDA(cudaStreamWaitEvent(sD, p->ev_comp[e], 0));
         OOC_CUDA(cudaMemcpyAsync(img + (size_t)z0 * p->fplane[field], stage, (size_t)(z1 - z0) * p->fplane[field],
@@ -856,12 +897,12 @@ ooc_status ooc_set_field(ooc_plan *p, int field, const float *host_src)
     return check_guards(p);
 }
 
-ooc_status ooc_get_field(ooc_plan *p, int field, float *host_dst)
+ooc_status get_field_impl(ooc_plan *p, int field, void *host_dst)
 {
     if (!p || !p->bound || !host_dst || field < 0 || field >= p->nfield)
         return OOC_E_INVALID;
     const int64_t nz = p->cfg.nz;
-    const size_t pb = (size_t)p->plane_elems * sizeof(float);
+    const size_t pb = (size_t)p->plane_elems * p->esize;
     char *img = p->host + p->off_host[field];
     if (!staged(p, field)) {
         std::memcpy(host_dst, img, pb * nz);
@@ -885,14 +926,46 @@ ooc_status ooc_get_field(ooc_plan *p, int field, float *host_dst)
         OOC_CUDA(cudaStreamWaitEvent(sC, p->ev_h2d[e], 0));
         if (j >= 2)
             OOC_CUDA(cudaStreamWaitEvent(sC, p->ev_d2h[e2], 0));
-        OOC_TRY(decode_into(p, field, stage, ring_view(p, b, zb), z0, z1, sC));
+        OOC_TRY(decode_into(p, field, stage, b, zb, z0, z1, sC));
         OOC_CUDA(cudaEventRecord(p->ev_dec[e], sC));
         OOC_CUDA(cudaStreamWaitEvent(sD, p->ev_dec[e], 0));
-        OOC_CUDA(copy_ring(p, b, zb, z0, z1, (char *)(host_dst + (size_t)z0 * p->plane_elems), false, sD));
+        OOC_CUDA(copy_ring(p, b, zb, z0, z1, (char *)host_dst + (size_t)z0 * pb, false, sD));
         OOC_CUDA(cudaEventRecord(p->ev_d2h[e], sD));
     }
     OOC_TRY(wait_event(p, p->ev_d2h[(j - 1) % kEv]));
     return check_guards(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+ooc_status ooc_set_field(ooc_plan *p, int field, const float *host_src)
+{
+    if (!p || p->esize != 4)
+        return OOC_E_INVALID;
+    return set_field_impl(p, field, host_src);
+}
+
+ooc_status ooc_get_field(ooc_plan *p, int field, float *host_dst)
+{
+    if (!p || p->esize != 4)
+        return OOC_E_INVALID;
+    return get_field_impl(p, field, host_dst);
+}
+
+ooc_status ooc_set_field64(ooc_plan *p, int field, const double *host_src)
+{
+    if (!p || p->esize != 8)
+        return OOC_E_INVALID;
+    return set_field_impl(p, field, host_src);
+}
+
+ooc_status ooc_get_field64(ooc_plan *p, int field, double *host_dst)
+{
+    if (!p || p->esize != 8)
+        return OOC_E_INVALID;
+    return get_field_impl(p, field, host_dst);
 }
 
 ooc_status ooc_step(ooc_plan *p, int64_t nsteps)

@@ -21,8 +21,8 @@
 // Also here: the register-loading fused heat7 pairs (two steps per launch,
 // the intermediate level on chip), heat7x2r_kernel (two rows per thread)
 // and heat7x2_kernel (one row), built in with OOC_HEATX2_ROWS = 2 or 1 (the
-// default build runs the TMA-staged pairs of heat_tma.cu); and an FP64
-// heat7 for whole fields.
+// default build runs the TMA-staged pairs of heat_tma.cu).  The FP64
+// kernels are in stencil64.cu.
 //
 // heat7 (Section III's neighbour average, 3D):
 //   u' = u + r (u[x-1] + u[x+1] + u[y-1] + u[y+1] + u[z-1] + u[z+1] - 6u)
@@ -144,82 +144,6 @@ OOC_PRAGMA(unroll OOC_HEAT_UNROLL)
     }
 }
 
-// FP64 heat7 (the paper's runs are in double precision, Section VI), whole
-// field, one step per launch.  Same design as heat7_kernel with two points
-// per thread (16-byte double2 accesses, 64-point row segments per warp).
-// The update is written with rounding intrinsics in the order of heat_pt.
-constexpr int kSeg64 = 2 * kTX;
-
-__device__ __forceinline__ double heat_pt64(double c, double xl, double xr, double up, double dn, double zm,
-                                            double zp, double r)
-{
-    const double t = __dadd_rn(__dadd_rn(__dadd_rn(xl, xr), __dadd_rn(up, dn)), __dadd_rn(zm, zp));
-    return __fma_rn(r, __fma_rn(-6.0, c, t), c);
-}
-
-__device__ __forceinline__ double2 ldg2(const double *p) { return __ldg(reinterpret_cast<const double2 *>(p)); }
-
-__global__ void __launch_bounds__(kTX *kHeatTY)
-    heat7_f64_kernel(const double *__restrict__ in, double *__restrict__ out, Grid3 g, int64_t zchunk, double r)
-{
-    __shared__ double2 tile[2][kHeatTY + 2][kTX];
-    const int lane = threadIdx.x, ty = threadIdx.y;
-    const int64_t gx = (g.nx + kSeg64 - 1) / kSeg64;
-    const int64_t xs = (int64_t)(blockIdx.x % gx) * kSeg64;
-    const int64_t x2 = xs + 2 * lane;
-    const int64_t y0 = (int64_t)(blockIdx.x / gx) * kHeatTY;
-    const int64_t y = y0 + ty;
-    const int64_t za = (int64_t)blockIdx.y * zchunk;
-    const int cnt = (int)(min(za + zchunk, g.nz) - za);
-    const int64_t nz = g.nz, plane = g.plane;
-    const bool inside = x2 < g.nx && y < g.ny;
-    const int64_t off = inside ? y * g.nx + x2 : 0;
-    const int64_t yh = ty == 0 ? y0 - 1 : y0 + kHeatTY;
-    const bool hrow = (ty == 0 || ty == kHeatTY - 1) && yh >= 0 && yh < g.ny && x2 < g.nx;
-    const int64_t hoff = hrow ? yh * g.nx + x2 : 0;
-    const int64_t xh = lane == 0 ? xs - 1 : xs + kSeg64;
-    const bool hcol = (lane == 0 || lane == kTX - 1) && xh >= 0 && xh < g.nx && y < g.ny;
-    const int64_t xoff = hcol ? y * g.nx + xh : 0;
-    const double2 z2 = make_double2(0.0, 0.0);
-    const double *p = in + za * plane;
-    double2 prev = (inside && za >= 1) ? ldg2(p - plane + off) : z2;
-    double2 cur = inside ? ldg2(p + off) : z2;
-    double2 nxt = (inside && za + 1 < nz) ? ldg2(p + plane + off) : z2;
-    double2 hyv = hrow ? ldg2(p + hoff) : z2;
-    double hx = hcol ? __ldg(p + xoff) : 0.0;
-    for (int i = 0; i < cnt; ++i, p += plane) {
-        const int64_t z = za + i;
-        const bool v1 = z + 1 < nz, v2 = z + 2 < nz;
-        const double2 pfv = (inside && v2) ? ldg2(p + 2 * plane + off) : z2;
-        const double2 hyv1 = (hrow && v1) ? ldg2(p + plane + hoff) : z2;
-        const double hx1 = (hcol && v1) ? __ldg(p + plane + xoff) : 0.0;
-        const int b = i & 1;
-        tile[b][ty + 1][lane] = cur;
-        if (ty == 0)
-            tile[b][0][lane] = hyv;
-        if (ty == kHeatTY - 1)
-            tile[b][kHeatTY + 1][lane] = hyv;
-        double xl = __shfl_up_sync(0xffffffffu, cur.y, 1);
-        double xr = __shfl_down_sync(0xffffffffu, cur.x, 1);
-        if (lane == 0)
-            xl = hx;
-        if (lane == kTX - 1)
-            xr = hx;
-        __syncthreads();
-        const double2 up = tile[b][ty][lane];
-        const double2 dn = tile[b][ty + 2][lane];
-        double2 o;
-        o.x = heat_pt64(cur.x, xl, cur.y, up.x, dn.x, prev.x, nxt.x, r);
-        o.y = heat_pt64(cur.y, cur.x, xr, up.y, dn.y, prev.y, nxt.y, r);
-        if (inside)
-            *reinterpret_cast<double2 *>(out + z * plane + off) = o;
-        prev = cur;
-        cur = nxt;
-        nxt = pfv;
-        hyv = hyv1;
-        hx = hx1;
-    }
-}
 
 // Two heat7 steps per launch: levels s and s+1 of a pair, with level s kept
 // on chip (temporal blocking inside the kernel, so HBM carries 8 bytes per
@@ -828,21 +752,6 @@ cudaError_t launch_heat7x2_regs(ConstRing in, Ring out, int64_t nx, int64_t ny, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_heat7_f64(const double *in, double *out, int64_t nx, int64_t ny, int64_t nz, double r,
-                             cudaStream_t st)
-{
-    static int res = 0;
-    if (res == 0)
-        res = resident((const void *)heat7_f64_kernel, kTX * kHeatTY);
-    const int64_t gx = (nx + kSeg64 - 1) / kSeg64, gy = (ny + kHeatTY - 1) / kHeatTY;
-    const int64_t chunk = choose_chunk(gx * gy, nz, 8, 2, res);
-    const int64_t gz = (nz + chunk - 1) / chunk;
-    if (gx * gy > 0x7fffffffll || in == out)
-        return cudaErrorInvalidValue;
-    heat7_f64_kernel<<<dim3((unsigned)(gx * gy), (unsigned)gz), dim3(kTX, kHeatTY), 0, st>>>(
-        in, out, Grid3{nx, ny, nz, nx * ny}, chunk, r);
-    return cudaGetLastError();
-}
 
 #if !OOC_WAVE_TMA
 cudaError_t launch_wave25_to(ConstRing p, ConstRing pprev, Ring pnew, ConstRing kappa, int64_t nx, int64_t ny,

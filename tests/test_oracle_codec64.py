@@ -275,3 +275,23 @@ def test_paper_rates_accuracy_on_a_smooth_field():
     x = smooth_random_field((32, 32, 32), corr_len=8.0, seed=2, dtype=np.float64)
     e = {r: np.linalg.norm(oracle.fr4d_roundtrip(x, r) - x) / np.linalg.norm(x) for r in (24, 32)}
     assert e[32] < 1e-8 and e[24] < 1e-5 and e[32] < e[24] / 50, e
+
+
+def test_fp64_storage_pipeline_reduces_to_plain_runs():
+    # With FP64 storage the FP64 plan's oracle pipeline is the plain FP64
+    # run, exactly: no rounding happens at the pass boundaries.
+    from synth import sine_modes_field
+    u0, _ = sine_modes_field((16, 12, 20), seed=1)
+    u0 = np.asarray(u0, dtype=np.float64)
+    a = oracle.heat7_storage_pipeline(u0, 9, 4, "fp64", precision="fp64")
+    assert np.array_equal(a, oracle.heat7_run(u0, 9))
+    rng = np.random.default_rng(3)
+    p0 = rng.normal(size=(16, 12, 20)) * 1e-3
+    kap = 0.05 + 0.01 * rng.random((16, 12, 20))
+    p, q = oracle.wave25_storage_pipeline(p0, 0.9 * p0, kap, 7, 3, "fp64", precision="fp64")
+    pr, qr = oracle.wave25_run(p0, 0.9 * p0, kap, 7)
+    assert np.array_equal(p, pr) and np.array_equal(q, qr)
+    # and FR4D storage applies exactly the codec's round trip at each boundary
+    b = oracle.heat7_storage_pipeline(u0, 4, 4, "fr4", rate=24, precision="fp64")
+    ref = oracle.fr4d_roundtrip(oracle.heat7_run(oracle.fr4d_roundtrip(u0, 24), 4), 24)
+    assert np.array_equal(b, ref)
