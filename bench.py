@@ -9,7 +9,7 @@ compressed-vs-uncompressed comparison.  Error is stated against the FP64
 oracle on a sampled central 128^3 sub-box (exact dependency cone).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload heat1024|kernels512|window56|wave1024|precision|precision192|adjoint512]
+                  [--workload heat1024|kernels512|window56|wave1024|precision|precision192|adjoint512|fp64]
 
 Prints one JSON line (rank 0).  The default workload is the headline; the
 others measure the remaining configurations: one launch of each kernel on a
@@ -961,6 +961,136 @@ def run_adjoint512(args, world, rank, local):
     return 0
 
 
+def run_fp64(args, world, rank, local):
+    """FP64 fields, as the paper ran them (Section VI: double-precision
+    fields stored at 32 and 24 of every 64 bits): heat7 and wave25 at 1024^3
+    with FP64 compute, each with raw FP64 storage (the uncompressed
+    pipeline, code 1) and FR4D at 32 and 24 bits per value (both read-write
+    levels and kappa for the wave: code 4).  heat7: 2 GiB budget, k = 4, 32
+    steps per call; wave25: 8 GiB budget (the FP32 wave's 4 GiB in doubles),
+    k = 10, 20 steps per call, the layered velocity and the Ricker source of
+    the wave1024 workload.  One untimed call, then timed calls.  Errors
+    against the raw-FP64 pipeline on the central 64 planes (self-
+    consistency; the FP64 oracle checks are GPU tests at smaller sizes).
+    Also the FR4D kernels' CUDA-event times on one 56-plane window of 1024^2
+    planes."""
+    import torch
+
+    import paper_2109_05410_gb300 as ooc
+    from synth import ricker, smooth_random_field
+    torch.cuda.set_device(local)
+    ooc.build()
+    ooc.lib()
+    n = 1024
+    reps = max(args.steps, 1)
+    out = {"workload": "fp64", "grid": [n, n, n]}
+    # FR4D kernels on one window
+    shape = (56, n, n)
+    d = torch.from_numpy(smooth_random_field(shape, 32.0, seed=2, dtype=np.float64)).cuda()
+    dec = torch.empty_like(d)
+    kern = {}
+    for rate in (32, 24):
+        w = torch.empty(ooc.ooc_compressed_bytes(n, n, 56, rate), dtype=torch.uint8, device="cuda")
+        for name, fn in (("encode", lambda: ooc.ooc_compress64(d, rate, d_out=w)),
+                         ("decode", lambda: ooc.ooc_decompress64(w, shape, rate, d_out=dec))):
+            for _ in range(3):
+                fn()
+            e0, e1 = _cuda_events(torch)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(10):
+                fn()
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / 10
+            kern[f"fr4d_{name}_R{rate}"] = {"us_per_launch": 1e3 * ms,
+                                           "Gvalues_per_s": 56 * n * n / (ms / 1e3) / 1e9,
+                                           "GBs": (8 + rate / 8) * 56 * n * n / (ms / 1e3) / 1e9}
+    # the FP64 stencil kernels on the same window: heat7 and wave25 steps
+    tmp = torch.empty_like(d)
+    kap = torch.full_like(d, 0.05)
+    for name, fn, per in (("heat7_f64", lambda: ooc.ooc_heat7_steps_f64(d, tmp, 2), 2),
+                          ("wave25_f64", lambda: ooc.ooc_wave25_steps_f64(d, dec, kap, 2), 2)):
+        fn()
+        e0, e1 = _cuda_events(torch)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(5):
+            fn()
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / (5 * per)
+        kern[name] = {"us_per_step": 1e3 * ms, "Gpts_steps_per_s": 56 * n * n / (ms / 1e3) / 1e9}
+    out["kernels_window56"] = kern
+    del d, dec, tmp, kap
+    torch.cuda.empty_cache()
+    mid = slice(n // 2 - 32, n // 2 + 32)
+    fmts = {"fp64": ("fp64", 64), "fr4d-32": ("fr4", 32), "fr4d-24": ("fr4", 24)}
+    # heat7
+    u0 = smooth_random_field((n, n, n), 32.0, seed=2, dtype=np.float64)
+    heat = {}
+    ref = None
+    for name, (fmt, rate) in fmts.items():
+        plan = ooc.Plan(nx=n, ny=n, nz=n, stencil="heat7", k=4, rw_format=fmt, rw_rate=rate,
+                        device_budget_bytes=2 << 30, precision="fp64")
+        plan.set_field(0, u0)
+        plan.step(32)
+        ms = timed_steps(torch, plan, 32, reps)
+        t = sum(ms) / len(ms)
+        got = plan.get_field(0)[mid].copy()
+        heat[name] = {"Gpts": n ** 3 * 32 / (t / 1e3) / 1e9, "ms_per_call": t, "slab_planes": plan.info()["slab_planes"]}
+        if name == "fp64":
+            ref = got
+        else:
+            heat[name]["rel_l2_vs_fp64_storage"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        plan.close()
+        del plan
+        torch.cuda.empty_cache()
+    del u0
+    heat["speedup_fr4d32_vs_fp64"] = heat["fr4d-32"]["Gpts"] / heat["fp64"]["Gpts"]
+    out["heat7"] = heat
+    # wave25
+    from synth import layered_velocity
+    v = layered_velocity((n, n, n), seed=3)
+    dt = 0.4 * 10.0 / float(v.max())
+    kappa = (np.asarray(v, dtype=np.float64) * (dt / 10.0)) ** 2
+    del v
+    src = (n // 2, n // 2, n // 2)
+    nsteps = 20
+    w = (ricker(nsteps * (reps + 1), dt) * float(kappa[src[2], src[1], src[0]])).astype(np.float32)
+    zero = np.zeros((n, n, n), dtype=np.float64)
+    wave = {}
+    ref = None
+    for name, (fmt, rate) in fmts.items():
+        plan = ooc.Plan(nx=n, ny=n, nz=n, stencil="wave25", k=10, rw_format=fmt, rw_rate=rate, ro_format=fmt,
+                        ro_rate=rate, device_budget_bytes=8 << 30, precision="fp64")
+        plan.set_field(0, zero)
+        plan.set_field(1, zero)
+        plan.set_field(2, kappa)
+        plan.set_source(*src, w)
+        plan.step(nsteps)
+        ms = timed_steps(torch, plan, nsteps, reps)
+        t = sum(ms) / len(ms)
+        got = plan.get_field(0)[mid].copy()
+        wave[name] = {"Gpts": n ** 3 * nsteps / (t / 1e3) / 1e9, "ms_per_call": t,
+                      "slab_planes": plan.info()["slab_planes"]}
+        if name == "fp64":
+            ref = got
+        else:
+            wave[name]["rel_l2_vs_fp64_storage"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        plan.close()
+        del plan
+        torch.cuda.empty_cache()
+    wave["speedup_fr4d32_vs_fp64"] = wave["fr4d-32"]["Gpts"] / wave["fp64"]["Gpts"]
+    out["wave25"] = wave
+    out["steps"] = reps
+    out["error_note"] = ("rel-L2 of the central 64 planes against the same pipeline with raw FP64 storage "
+                         "(self-consistency, not oracle error)")
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -969,7 +1099,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="heat1024",
                     choices=["heat1024", "kernels512", "window56", "wave1024", "precision", "precision192",
-                             "adjoint512"])
+                             "adjoint512", "fp64"])
     args = ap.parse_args()
     world, rank, local = dist_init(args)
     try:
@@ -979,7 +1109,7 @@ def main():
                   "wave1024": run_wave1024,
                   "precision": run_precision,
                   "precision192": lambda a, w, r, l: run_precision(a, w, r, l, n=192, oracle_budget_s=1e9),
-                  "adjoint512": run_adjoint512}[args.workload]
+                  "adjoint512": run_adjoint512, "fp64": run_fp64}[args.workload]
         return runner(args, world, rank, local)
     finally:
         if world > 1:
