@@ -213,3 +213,56 @@ def test_precision_and_format_combinations_are_checked(ooc):
         assert ooc.lib().ooc_get_field(plan._h, 0, buf.ctypes.data) != 0
     finally:
         plan.close()
+
+
+@pytest.mark.parametrize("fmt,rate", [("fp64", 64), ("fr4", 32)])
+def test_fp64_plans_with_debug_checks_budget_and_graph_replay(ooc, fmt, rate):
+    # The FP64 plans go through the same scheduler machinery as the FP32
+    # ones: with debug checks (guard bytes and window/copy checks) on, with
+    # the slab thickness derived from a budget that forces streaming, and
+    # with calls replayed as CUDA graphs or launched directly, the bits stay
+    # those of a single-slab plan launched directly.
+    shape = (96, 32, 36)
+    u0 = smooth_random_field(shape, 5.0, seed=41, dtype=np.float64)
+    outs = {}
+    for name, kw in (("ref", dict(slab_planes=96, graph_mode=1)),
+                     ("debug", dict(slab_planes=12, debug_checks=1)),
+                     ("budget", dict(device_budget_bytes=1_200_000)),
+                     ("graph", dict(slab_planes=24, graph_mode=0))):
+        plan = ooc.Plan(nx=36, ny=32, nz=96, stencil="heat7", k=3, rw_format=fmt, rw_rate=rate, precision="fp64",
+                        **kw)
+        try:
+            plan.set_field(0, u0)
+            for n in (6, 6, 4, 6):
+                plan.step(n)
+            outs[name] = (plan.info()["nslab"], plan.get_field(0))
+            assert plan.stats()["steps_done"] == 22
+        finally:
+            plan.close()
+    assert outs["ref"][0] == 1 and outs["budget"][0] > 3
+    for name in ("debug", "budget", "graph"):
+        assert np.array_equal(outs[name][1].view(np.uint64), outs["ref"][1].view(np.uint64)), name
+
+
+def test_fp64_wave_graph_replay_with_the_source_table(ooc):
+    # graph replay reads the source amplitude from the device table at the
+    # plan's device time: replayed calls give the bits of direct launches
+    shape = (64, 24, 72)
+    kappa, src, w = wave_case(shape, 40)
+    p0 = 1e-3 * smooth_random_field(shape, 4.0, seed=13, dtype=np.float64)
+    outs = {}
+    for mode in (0, 1):
+        plan = ooc.Plan(nx=72, ny=24, nz=64, stencil="wave25", k=5, rw_format="fr4", rw_rate=32, ro_format="fp64",
+                        ro_rate=64, slab_planes=16, graph_mode=mode, precision="fp64")
+        try:
+            plan.set_field(0, p0)
+            plan.set_field(1, 0.9 * p0)
+            plan.set_field(2, kappa)
+            plan.set_source(*src, w.astype(np.float32))
+            for n in (10, 10, 10, 7):
+                plan.step(n)
+            outs[mode] = plan.get_field(0)
+        finally:
+            plan.close()
+    assert np.abs(outs[1]).max() > 0
+    assert np.array_equal(outs[0].view(np.uint64), outs[1].view(np.uint64))
