@@ -127,8 +127,9 @@ typedef struct {
 /* Static string for a status code. */
 const char *ooc_status_string(ooc_status s);
 
-/* Bytes of an nx*ny*nz FP32 field stored by the fixed-rate codec at `rate`
- * bits per value (Section IV: R bits per value, a size fixed in advance):
+/* Bytes of an nx*ny*nz field stored by the fixed-rate codec at `rate` bits
+ * per value, FR4 (FP32) or FR4D (FP64) alike (Section IV: R bits per value,
+ * a size fixed in advance):
  * ceil(nx/4)*ceil(ny/4)*ceil(nz/4) blocks of 8*rate bytes, i.e.
  * nx*ny*nz*rate/8 when the sides are multiples of 4.  Returns 0 for invalid
  * arguments. */
