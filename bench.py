@@ -9,7 +9,8 @@ compressed-vs-uncompressed comparison.  Error is stated against the FP64
 oracle on a sampled central 128^3 sub-box (exact dependency cone).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload heat1024|kernels512|window56|wave1024|precision|precision192|adjoint512|fp64]
+                  [--workload heat1024|kernels512|window56|wave1024|precision|precision192|adjoint512|fp64|
+                   window56_fp64]
 
 Prints one JSON line (rank 0).  The default workload is the headline; the
 others measure the remaining configurations: one launch of each kernel on a
@@ -961,30 +962,11 @@ def run_adjoint512(args, world, rank, local):
     return 0
 
 
-def run_fp64(args, world, rank, local):
-    """FP64 fields, as the paper ran them (Section VI: double-precision
-    fields stored at 32 and 24 of every 64 bits): heat7 and wave25 at 1024^3
-    with FP64 compute, each with raw FP64 storage (the uncompressed
-    pipeline, code 1) and FR4D at 32 and 24 bits per value (both read-write
-    levels and kappa for the wave: code 4).  heat7: 2 GiB budget, k = 4, 32
-    steps per call; wave25: 8 GiB budget (the FP32 wave's 4 GiB in doubles),
-    k = 10, 20 steps per call, the layered velocity and the Ricker source of
-    the wave1024 workload.  One untimed call, then timed calls.  Errors
-    against the raw-FP64 pipeline on the central 64 planes (self-
-    consistency; the FP64 oracle checks are GPU tests at smaller sizes).
-    Also the FR4D kernels' CUDA-event times on one 56-plane window of 1024^2
-    planes."""
-    import torch
-
-    import paper_2109_05410_gb300 as ooc
-    from synth import ricker, smooth_random_field
-    torch.cuda.set_device(local)
-    ooc.build()
-    ooc.lib()
-    n = 1024
-    reps = max(args.steps, 1)
-    out = {"workload": "fp64", "grid": [n, n, n]}
-    # FR4D kernels on one window
+def fp64_window_kernels(ooc, torch, n=1024):
+    """CUDA-event times of the FP64 path's kernels on one 56-plane window of
+    n^2 planes (a smooth double field): FR4D encode and decode at 32 and 24
+    bits per value, and one FP64 heat7 and wave25 step."""
+    from synth import smooth_random_field
     shape = (56, n, n)
     d = torch.from_numpy(smooth_random_field(shape, 32.0, seed=2, dtype=np.float64)).cuda()
     dec = torch.empty_like(d)
@@ -1021,9 +1003,51 @@ def run_fp64(args, world, rank, local):
         e1.synchronize()
         ms = e0.elapsed_time(e1) / (5 * per)
         kern[name] = {"us_per_step": 1e3 * ms, "Gpts_steps_per_s": 56 * n * n / (ms / 1e3) / 1e9}
-    out["kernels_window56"] = kern
     del d, dec, tmp, kap
     torch.cuda.empty_cache()
+    return kern
+
+
+def run_window56_fp64(args, world, rank, local):
+    """The FP64 path's kernels on one 56-plane window of 1024^2 planes (the
+    small ncu capture case of the fp64 workload)."""
+    import torch
+
+    import paper_2109_05410_gb300 as ooc
+    torch.cuda.set_device(local)
+    ooc.build()
+    ooc.lib()
+    kern = fp64_window_kernels(ooc, torch)
+    if rank == 0:
+        print(json.dumps({"workload": "window56_fp64", "window": [56, 1024, 1024], "kernels": kern,
+                          "device_fault": ooc.ooc_take_device_fault()}), flush=True)
+    return 0
+
+
+def run_fp64(args, world, rank, local):
+    """FP64 fields, as the paper ran them (Section VI: double-precision
+    fields stored at 32 and 24 of every 64 bits): heat7 and wave25 at 1024^3
+    with FP64 compute, each with raw FP64 storage (the uncompressed
+    pipeline, code 1) and FR4D at 32 and 24 bits per value (both read-write
+    levels and kappa for the wave: code 4).  heat7: 2 GiB budget, k = 4, 32
+    steps per call; wave25: 8 GiB budget (the FP32 wave's 4 GiB in doubles),
+    k = 10, 20 steps per call, the layered velocity and the Ricker source of
+    the wave1024 workload.  One untimed call, then timed calls.  Errors
+    against the raw-FP64 pipeline on the central 64 planes (self-
+    consistency; the FP64 oracle checks are GPU tests at smaller sizes).
+    Also the FR4D kernels' CUDA-event times on one 56-plane window of 1024^2
+    planes."""
+    import torch
+
+    import paper_2109_05410_gb300 as ooc
+    from synth import ricker, smooth_random_field
+    torch.cuda.set_device(local)
+    ooc.build()
+    ooc.lib()
+    n = 1024
+    reps = max(args.steps, 1)
+    out = {"workload": "fp64", "grid": [n, n, n]}
+    out["kernels_window56"] = fp64_window_kernels(ooc, torch, n)
     mid = slice(n // 2 - 32, n // 2 + 32)
     fmts = {"fp64": ("fp64", 64), "fr4d-32": ("fr4", 32), "fr4d-24": ("fr4", 24)}
     # heat7
@@ -1099,7 +1123,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="heat1024",
                     choices=["heat1024", "kernels512", "window56", "wave1024", "precision", "precision192",
-                             "adjoint512", "fp64"])
+                             "adjoint512", "fp64", "window56_fp64"])
     args = ap.parse_args()
     world, rank, local = dist_init(args)
     try:
@@ -1109,7 +1133,8 @@ def main():
                   "wave1024": run_wave1024,
                   "precision": run_precision,
                   "precision192": lambda a, w, r, l: run_precision(a, w, r, l, n=192, oracle_budget_s=1e9),
-                  "adjoint512": run_adjoint512, "fp64": run_fp64}[args.workload]
+                  "adjoint512": run_adjoint512, "fp64": run_fp64,
+                  "window56_fp64": run_window56_fp64}[args.workload]
         return runner(args, world, rank, local)
     finally:
         if world > 1:
