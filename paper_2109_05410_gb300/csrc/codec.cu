@@ -839,16 +839,21 @@ __device__ __forceinline__ void encode_block64(const uint64_t (&v)[64], int word
     // largest frexp exponent (biased exponent - 1022; subnormals clamp to -1022)
     const int emax = (int)(mx >> 52) - 1022;
     dst[0] = 1u | ((uint32_t)(emax + 1023) << 1);
-    // q = trunc(x * 2^(58 - emax)) through two normal powers of two: the
-    // first product is exact whenever the result can be nonzero, the second
-    // exact or already below 1
+    // q = trunc(x * 2^(58 - emax)) in integer arithmetic on the bits (the
+    // FP64 pipe is scarce on this GPU): x = m 2^e with the 53-bit significand
+    // m, so |q| = m shifted by e + 58 - emax (left by at most 5, since |x| <
+    // 2^emax; right past 63 is 0), then the sign
     const int kk = kPrec64 - emax;
-    const int k1 = kk >> 1, k2 = kk - k1;
-    const double s1 = pow2d(k1), s2 = pow2d(k2);
     int64_t q[64];
 #pragma unroll
-    for (int i = 0; i < 64; ++i)
-        q[i] = __double2ll_rz(__dmul_rn(__dmul_rn(__longlong_as_double((long long)v[i]), s1), s2));
+    for (int i = 0; i < 64; ++i) {
+        const uint64_t b = v[i];
+        const int eb = (int)((b >> 52) & 0x7FFu);
+        const uint64_t m = (b & 0xFFFFFFFFFFFFFull) | (eb != 0 ? (1ull << 52) : 0ull);
+        const int sh = (eb != 0 ? eb - 1075 : -1074) + kk;
+        const uint64_t a = sh >= 0 ? m << sh : (sh > -64 ? m >> -sh : 0ull);
+        q[i] = (b >> 63) ? -(int64_t)a : (int64_t)a;
+    }
     transform_fwd64(q);
     uint32_t lo[64], hi[64];
     to_coding_order64(lo, hi, q, std::make_integer_sequence<int, 64>{});
@@ -875,6 +880,7 @@ __device__ __forceinline__ void decode_block64(const uint32_t *src, int nwords, 
     from_coding_order64(q, lo, hi, std::make_integer_sequence<int, 64>{});
     transform_inv64(q);
     // x = RN(RN(q) * 2^(emax - 58)): one exact or correctly rounded scaling
+    // (on the FP64 pipe: the same in integer arithmetic measured slower)
     const int k = emax - kPrec64;
     const bool split = k < -1022;
     const double sa = pow2d(split ? k + 64 : k), sb = pow2d(-64);
