@@ -61,8 +61,8 @@ NCU_UNITS = 56 * 1024 * 1024
 NCU_COUNTERS = {
     "heat7_stencil": {"src": ["heat_tma.cu", "tma.cuh", "stencil_common.cuh"], "sha": "8cee9af187b05b72", "dram_bytes": 428.7e6,
                       "warp_inst": 90.66e6},
-    "fr4_encode": {"src": "codec.cu", "sha": "e822aeec28fbe774", "dram_bytes": 320.6e6, "warp_inst": 180.37e6},
-    "fr4_decode": {"src": "codec.cu", "sha": "e822aeec28fbe774", "dram_bytes": 296.7e6, "warp_inst": 180.98e6},
+    "fr4_encode": {"src": "codec.cu", "sha": "3d031d5fc8adc782", "dram_bytes": 320.7e6, "warp_inst": 180.37e6},
+    "fr4_decode": {"src": "codec.cu", "sha": "3d031d5fc8adc782", "dram_bytes": 296.2e6, "warp_inst": 180.98e6},
 }
 # issue peak: 152 SMs x 4 schedulers x one warp instruction per clock at the
 # maximum SM clock of 2070 MHz
