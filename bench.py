@@ -342,6 +342,38 @@ def wave1024_summary(torch, ooc, nsteps=100, reps=2):
     return out
 
 
+def fp64_summary(torch, ooc, n=512, nsteps=16, reps=2):
+    """FP64 fields in brief, for the default line: heat7 at n^3 in FP64 with
+    a 256 MiB budget (streaming), k = 4, raw FP64 storage against FR4D at 32
+    bits per value (the paper's 2:1 for doubles), one untimed call and
+    `reps` timed calls of `nsteps` steps each, with the FR4D result's rel-L2
+    against the raw-FP64 run."""
+    from synth import smooth_random_field
+    u0 = smooth_random_field((n, n, n), 16.0, seed=5, dtype=np.float64)
+    out, ref = {}, None
+    for name, (fmt, rate) in (("fp64", ("fp64", 64)), ("fr4d-32", ("fr4", 32))):
+        plan = ooc.Plan(nx=n, ny=n, nz=n, stencil="heat7", k=4, rw_format=fmt, rw_rate=rate,
+                        device_budget_bytes=256 << 20, precision="fp64")
+        try:
+            plan.set_field(0, u0)
+            plan.step(nsteps)
+            ms = timed_steps(torch, plan, nsteps, reps)
+            out[name] = n ** 3 * nsteps / (statistics.mean(ms) / 1e3) / 1e9
+            got = plan.get_field(0)
+        finally:
+            plan.close()
+        del plan
+        torch.cuda.empty_cache()
+        if ref is None:
+            ref = got
+        else:
+            out["fr4d-32_rel_l2_vs_fp64_storage"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    out["speedup_fr4d32_vs_fp64"] = out["fr4d-32"] / out["fp64"]
+    out["what"] = (f"heat7 {n}^3 in FP64, 256 MiB budget, k = 4, {reps} timed calls of {nsteps} steps after one "
+                   "untimed; bench.py --workload fp64 has the 1024^3 heat7 and wave25 study")
+    return out
+
+
 def run_gpu(args, world, rank, local):
     import torch
 
@@ -497,6 +529,12 @@ def run_gpu(args, world, rank, local):
     except Exception as exc:  # reported, never fatal to the headline
         wave = {"error": f"{type(exc).__name__}: {exc}"}
         torch.cuda.empty_cache()
+    # ---- FP64 fields, as the paper ran them, in brief ---------------------------
+    try:
+        f64 = fp64_summary(torch, ooc)
+    except Exception as exc:  # reported, never fatal to the headline
+        f64 = {"error": f"{type(exc).__name__}: {exc}"}
+        torch.cuda.empty_cache()
 
     if rank != 0:
         return 0
@@ -552,6 +590,7 @@ def run_gpu(args, world, rank, local):
                               "h2d_GBs_per_copy": h2d_GBs, "d2h_GBs_per_copy": d2h_GBs},
         "roofline": roofline,
         "paper_workload_wave1024": wave,
+        "fp64_fields_heat512": f64,
         "kernels": kernels,
         "overlap": overlap,
         "cpu_baseline": cpu,
