@@ -612,9 +612,9 @@ def _cuda_events(torch):
 def run_kernels512(args, world, rank, local):
     """Each kernel once per step on a 512^3 smooth field (the ncu capture case):
     FR4 encode and decode at R = 16, two in-core heat7 steps, two fused heat7
-    pairs (two steps per launch), two in-core wave25 steps, two FP64 heat7
-    steps, BF16 pack and unpack, one adjoint step and one gradient update;
-    CUDA-event times per kernel class."""
+    pairs (two steps per launch), two in-core wave25 steps, two fused wave25
+    pairs, two FP64 heat7 steps, BF16 pack and unpack, one adjoint step and
+    one gradient update; CUDA-event times per kernel class."""
     import torch
 
     import paper_2109_05410_gb300 as ooc
@@ -634,12 +634,16 @@ def run_kernels512(args, world, rank, local):
     d64 = d.double()
     t64 = torch.empty_like(d64)
     b16 = torch.empty(d.shape, dtype=torch.int16, device="cuda")
+    w1, w2 = torch.empty_like(d), torch.empty_like(d)  # scratch of the fused wave pairs
     ops = {
         "fr4_encode": (lambda: ooc.ooc_compress(d, 16, d_out=w), 1, (4 + 2) * pts, 0),
         "fr4_decode": (lambda: ooc.ooc_decompress(w, (n, n, n), 16, d_out=out), 1, (4 + 2) * pts, 0),
         "heat7": (lambda: ooc.ooc_heat7_steps(d, tmp, 2), 2, 8 * pts, 1),
         "heat7_fused_pair": (lambda: ooc.ooc_heat7_steps_fused(d, tmp, 4), 2, 8 * pts, 2),
         "wave25": (lambda: ooc.ooc_wave25_steps(d, pp, kap, 2), 2, 16 * pts, 1),
+        # two pairs land in place (no copy); p^n, p^{n-1}, kappa in and
+        # p^{n+1}, p^{n+2} out: 20 B per point per launch
+        "wave25_fused_pair": (lambda: ooc.ooc_wave25_steps_fused(d, pp, kap, 4, d_t1=w1, d_t2=w2), 2, 20 * pts, 2),
         "heat7_f64": (lambda: ooc.ooc_heat7_steps_f64(d64, t64, 2), 2, 16 * pts, 1),
         "bf16_pack": (lambda: ooc.ooc_bf16_pack(d, d_out=b16), 1, 6 * pts, 0),
         "bf16_unpack": (lambda: ooc.ooc_bf16_unpack(b16, d_out=out), 1, 6 * pts, 0),
@@ -756,6 +760,46 @@ def wave_inputs(n, seed=3):
     return kappa, src, dt
 
 
+def incore_wave_fusion(torch, ooc, kappa, src, w, nsteps=20, reps=2):
+    """In-core 1024^3 wave25 from rest with the source on: nsteps single
+    steps (16 B per point-step from HBM) against nsteps/2 fused pairs (two
+    steps per launch, level n+1 on chip: 10 B per point-step), CUDA-event
+    time per step, and whether the two give the same bits."""
+    d_k = torch.from_numpy(kappa).cuda()
+    res, fields = {}, {}
+    for name in ("single", "fused_pair"):
+        p, pp = torch.zeros_like(d_k), torch.zeros_like(d_k)
+        t1, t2 = (torch.empty_like(d_k), torch.empty_like(d_k)) if name == "fused_pair" else (None, None)
+
+        def run(t0):
+            if name == "fused_pair":
+                ooc.ooc_wave25_steps_fused(p, pp, d_k, nsteps, src=src, w=w, t=t0, d_t1=t1, d_t2=t2)
+            else:
+                ooc.ooc_wave25_steps(p, pp, d_k, nsteps, src=src, w=w, t=t0)
+        run(0)  # warm-up; its steps are part of the compared history
+        times = []
+        for r in range(reps):
+            e0, e1 = _cuda_events(torch)
+            torch.cuda.synchronize()
+            e0.record()
+            run(nsteps * (r + 1))
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / nsteps)
+        ms = min(times)
+        res[name] = {"ms_per_step": ms, "Gpts_steps_per_s": kappa.size / (ms / 1e3) / 1e9,
+                     "algorithmic_bytes_per_point_step": 16 if name == "single" else 10}
+        fields[name] = (p, pp)
+        del t1, t2
+    a, b = fields["single"], fields["fused_pair"]
+    res["bit_identical"] = bool(torch.equal(a[0].view(torch.int32), b[0].view(torch.int32)) and
+                                torch.equal(a[1].view(torch.int32), b[1].view(torch.int32)))
+    res["fused_over_single_time"] = res["fused_pair"]["ms_per_step"] / res["single"]["ms_per_step"]
+    del fields, a, b, d_k
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_wave1024(args, world, rank, local):
     """3D acoustic wave, 25-point, 1024^3, device budget 4 GiB, k = 10: the
     paper's four codes (FP32; read-write fields at 16 bits/value; read-only
@@ -814,13 +858,17 @@ def run_wave1024(args, world, rank, local):
         if name != "code1_fp32":
             out[name]["rel_l2_vs_fp32_storage_every_100"] = series[name]
     del series_ref
+    # the two-steps-per-launch kernel in-core at the same size (the pipeline
+    # keeps single steps: the pair is slower per step on GB300)
+    fusion = incore_wave_fusion(torch, ooc, kappa, src, w)
     if rank == 0:
         steps_done = nsteps * (args.warmup + args.steps + 1)
         print(json.dumps({"workload": "wave1024", "metric": "Gpts/s", "value": out["code4_rw_ro_fr4-16"]["Gpts"],
                           "unit": "Gpts/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                           "time_steps_per_bench_step": nsteps, "k": k, "device_budget_bytes": 4 << 30,
                           "speedup_code4_vs_code1": out["code4_rw_ro_fr4-16"]["Gpts"] / out["code1_fp32"]["Gpts"],
-                          "codes": out, "error_note": f"self-consistency, not oracle error: rel-L2 of the central "
+                          "codes": out, "incore_fusion_1024": fusion,
+                          "error_note": f"self-consistency, not oracle error: rel-L2 of the central "
                           f"128 planes against the same pipeline with FP32 storage, every 100 steps of the warm-up "
                           f"and after {steps_done} steps (an FP64 oracle at 1024^3 x 2000 steps is out of reach of "
                           "the host cores; the precision workload measures storage error against the FP64 oracle)"}),

@@ -241,6 +241,17 @@ ooc_status ooc_wave25_steps(float *d_p, float *d_pprev, const float *d_kappa, in
 ooc_status ooc_heat7_steps_f64(double *d_u, double *d_tmp, int64_t nx, int64_t ny, int64_t nz, double r,
                                int64_t nsteps, void *stream);
 
+/* The nsteps wave25 steps of ooc_wave25_steps with each pair of steps in
+ * one kernel launch (temporal blocking inside the kernel: level n+1 of the
+ * pair stays in shared memory, so HBM carries p^n, p^{n-1} and kappa once
+ * and p^{n+1}, p^{n+2} once per two steps).  d_t1, d_t2: scratch fields of
+ * the same size; all four fields distinct and 16-byte aligned.  Results,
+ * in d_p and d_pprev, are bit-identical to ooc_wave25_steps.  An odd last
+ * step runs alone. */
+ooc_status ooc_wave25_steps_fused(float *d_p, float *d_pprev, const float *d_kappa, float *d_t1, float *d_t2,
+                                  int64_t nx, int64_t ny, int64_t nz, int64_t sx, int64_t sy, int64_t sz,
+                                  const float *h_w, int64_t t, int64_t nsteps, void *stream);
+
 /* wave25 in double precision: as ooc_wave25_steps with FP64 device fields
  * (16-byte aligned) and an FP64 source series h_w (host). */
 ooc_status ooc_wave25_steps_f64(double *d_p, double *d_pprev, const double *d_kappa, int64_t nx, int64_t ny,

@@ -21,7 +21,7 @@ __all__ = [
     "OocConfig", "OocStats", "OocPlanInfo", "OocError", "lib", "build",
     "ooc_status_string", "ooc_take_device_fault", "ooc_compressed_bytes", "ooc_compress", "ooc_decompress", "ooc_compress64", "ooc_decompress64", "ooc_compress_var",
     "ooc_decompress_var", "ooc_compress_var_bound", "ooc_var_scratch_bytes", "OOC_FR4_PRECISION", "OOC_FR4_ACCURACY",
-    "ooc_bf16_pack", "ooc_bf16_unpack", "ooc_heat7_steps", "ooc_heat7_steps_f64", "ooc_heat7_steps_fused", "ooc_heat7_steps_noalloc", "ooc_wave25_steps", "ooc_wave25_steps_f64", "Plan",
+    "ooc_bf16_pack", "ooc_bf16_unpack", "ooc_heat7_steps", "ooc_heat7_steps_f64", "ooc_heat7_steps_fused", "ooc_heat7_steps_noalloc", "ooc_wave25_steps", "ooc_wave25_steps_f64", "ooc_wave25_steps_fused", "Plan",
     "ooc_gather", "ooc_scatter_add", "ooc_wave25_adjoint_step", "ooc_wave25_grad_accum", "ooc_kappa_from_velocity",
     "ooc_velocity_grad", "ooc_wave25_ckpt_bytes", "ooc_wave25_adjoint_work_bytes", "ooc_wave25_forward_ckpt",
     "ooc_wave25_backward_ckpt", "WaveFn", "wave_forward",
@@ -115,6 +115,8 @@ _SIGS = {
                               + [ctypes.c_double, ctypes.c_int64, ctypes.c_void_p]),
     "ooc_wave25_steps": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int64] * 6
                          + [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]),
+    "ooc_wave25_steps_fused": (ctypes.c_int, [ctypes.c_void_p] * 5 + [ctypes.c_int64] * 6
+                               + [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]),
     "ooc_wave25_steps_f64": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int64] * 6
                              + [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]),
     "ooc_plan_create": (ctypes.c_int, [ctypes.POINTER(OocConfig), ctypes.POINTER(ctypes.c_void_p),
@@ -366,6 +368,27 @@ def ooc_wave25_steps(d_p, d_pprev, d_kappa, nsteps, src=None, w=None, t=0, strea
         wp = w.ctypes.data_as(ctypes.c_void_p)
     _check(lib().ooc_wave25_steps(_ptr(d_p), _ptr(d_pprev), _ptr(d_kappa), nx, ny, nz, sx, sy, sz, wp, int(t),
                                   int(nsteps), _stream(stream)), "ooc_wave25_steps")
+    return d_p, d_pprev
+
+
+def ooc_wave25_steps_fused(d_p, d_pprev, d_kappa, nsteps, src=None, w=None, t=0, d_t1=None, d_t2=None,
+                           stream=None):
+    """ooc_wave25_steps with each pair of steps in one launch; d_t1, d_t2 are
+    scratch fields (allocated if None)."""
+    import torch
+    nz, ny, nx = d_p.shape
+    t1 = torch.empty_like(d_p) if d_t1 is None else d_t1
+    t2 = torch.empty_like(d_p) if d_t2 is None else d_t2
+    if src is None or w is None:
+        sx, sy, sz, wp = -1, -1, -1, None
+    else:
+        sx, sy, sz = src
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        if len(w) < t + nsteps:
+            raise ValueError("source series shorter than t + nsteps")
+        wp = w.ctypes.data_as(ctypes.c_void_p)
+    _check(lib().ooc_wave25_steps_fused(_ptr(d_p), _ptr(d_pprev), _ptr(d_kappa), _ptr(t1), _ptr(t2), nx, ny, nz, sx,
+                                        sy, sz, wp, int(t), int(nsteps), _stream(stream)), "ooc_wave25_steps_fused")
     return d_p, d_pprev
 
 

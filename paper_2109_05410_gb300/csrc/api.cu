@@ -392,6 +392,58 @@ ooc_status ooc_wave25_steps(float *d_p, float *d_pprev, const float *d_kappa, in
     return OOC_OK;
 }
 
+ooc_status ooc_wave25_steps_fused(float *d_p, float *d_pprev, const float *d_kappa, float *d_t1, float *d_t2,
+                                  int64_t nx, int64_t ny, int64_t nz, int64_t sx, int64_t sy, int64_t sz,
+                                  const float *h_w, int64_t t, int64_t nsteps, void *stream)
+{
+    float *buf[4] = {d_p, d_pprev, d_t1, d_t2};
+    for (int i = 0; i < 4; ++i) {
+        if (!buf[i] || !aligned(buf[i], 16))
+            return OOC_E_INVALID;
+        for (int j = 0; j < i; ++j)
+            if (buf[i] == buf[j])
+                return OOC_E_INVALID;
+    }
+    if (!d_kappa || !aligned(d_kappa, 16) || !dims_ok(nx, ny, nz) || nsteps < 0 || t < 0)
+        return OOC_E_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool src = sx >= 0 && h_w != nullptr;
+    // a = p^n, b = p^{n-1}; each pair writes p^{n+1}, p^{n+2} into the two
+    // free buffers (c, d), and the next pair writes into (b, a): outputs
+    // alternate between (t1, t2) and (pprev, p), so an even number of pairs
+    // ends in place and (a, b) is always both fields or both scratch buffers
+    float *a = d_p, *b = d_pprev, *c = d_t1, *d = d_t2;
+    int64_t s = 0;
+    for (; s + 2 <= nsteps; s += 2) {
+        const float w1 = src ? h_w[t + s] : 0.0f, w2 = src ? h_w[t + s + 1] : 0.0f;
+        if (launch_wave25x2(a, b, d_kappa, c, d, nx, ny, nz, src ? sx : -1, sy, sz, w1, w2, st) != cudaSuccess)
+            return OOC_E_CUDA;
+        float *oa = a, *ob = b;
+        a = d;
+        b = c;
+        c = ob;
+        d = oa;
+    }
+    if (s < nsteps) {  // an odd last step, p^{n+1} over p^{n-1} in place
+        const float w = src ? h_w[t + s] : 0.0f;
+        if (launch_wave25(ConstRing{a, nz, 0}, Ring{b, nz, 0}, ConstRing{d_kappa, nz, 0}, nx, ny, nz, 0, nz,
+                          src ? sx : -1, sy, sz, w, st) != cudaSuccess)
+            return OOC_E_CUDA;
+        float *tmp = a;
+        a = b;
+        b = tmp;
+    }
+    // the results are in (a, b): in place, swapped, or in the scratch fields
+    if (a == d_pprev && b == d_p)
+        return cuda_status(launch_swap(d_p, d_pprev, nx * ny * nz, st));
+    const size_t bytes = sizeof(float) * (size_t)(nx * ny * nz);
+    if (a != d_p && cudaMemcpyAsync(d_p, a, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return OOC_E_CUDA;
+    if (b != d_pprev && cudaMemcpyAsync(d_pprev, b, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return OOC_E_CUDA;
+    return OOC_OK;
+}
+
 ooc_status ooc_wave25_steps_f64(double *d_p, double *d_pprev, const double *d_kappa, int64_t nx, int64_t ny,
                                 int64_t nz, int64_t sx, int64_t sy, int64_t sz, const double *h_w, int64_t t,
                                 int64_t nsteps, void *stream)

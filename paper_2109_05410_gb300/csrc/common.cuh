@@ -84,6 +84,11 @@ cudaError_t launch_heat7_f64(const double *in, double *out, int64_t nx, int64_t 
                              cudaStream_t st);
 // FP64 rings (stencil64.cu): heat7 one step on [z0, z1) from `in` into
 // `out`; wave25 one leapfrog step with p_prev overwritten in place.
+// Two wave25 steps per launch on dense fields (wave_fused.cu): p^{n+1}
+// into c_out and p^{n+2} into d_out, all five buffers distinct.
+cudaError_t launch_wave25x2(const float *a, const float *b, const float *kap, float *c_out, float *d_out, int64_t nx,
+                            int64_t ny, int64_t nz, int64_t sx, int64_t sy, int64_t sz, float w1, float w2,
+                            cudaStream_t st);
 cudaError_t launch_heat7_f64_ring(DConstRing in, DRing out, int64_t nx, int64_t ny, int64_t nz, int64_t z0, int64_t z1,
                                   double r, cudaStream_t st);
 cudaError_t launch_wave25_f64(DConstRing p, DRing pprev_out, DConstRing kappa, int64_t nx, int64_t ny, int64_t nz,

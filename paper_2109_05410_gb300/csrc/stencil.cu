@@ -32,6 +32,7 @@
 // p_prev is read only by the thread that writes p' there.
 #include <type_traits>
 
+#include "cp_async.cuh"
 #include "stencil_common.cuh"
 
 namespace ooc {
@@ -440,28 +441,6 @@ OOC_PRAGMA(unroll OOC_HEATX2_UNROLL)
 }
 
 #if !OOC_WAVE_TMA
-// x-neighbour at offset idx in [-4, 7] from the thread's first point, given
-// its own 4 points c and the 4-point groups to its left (l) and right (rr).
-__device__ __forceinline__ float pick(const float (&l)[4], const float (&c)[4], const float (&rr)[4], int idx)
-{
-    return idx < 0 ? l[idx + 4] : (idx < 4 ? c[idx] : rr[idx - 4]);
-}
-
-// cp.async (16-byte global -> shared copies that bypass the registers; a
-// source size of 0 fills zeros) and its group waits.
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, bool valid)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(valid ? 16 : 0)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait()
-{
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 // wave25 staging: the p tile of every plane (8 own rows and 4 halo rows on
 // each side, plus the 4-point groups beyond the own rows' ends) in kWavePS
 // stages, and p_prev / kappa of the own rows in kWaveKS stages.  The copy
