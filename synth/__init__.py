@@ -18,6 +18,7 @@ __all__ = [
     "sine_mode",
     "sine_modes_field",
     "smooth_random_field",
+    "smooth_random_field_torch",
     "layered_velocity",
     "ricker",
     "random_blocks",
@@ -79,6 +80,34 @@ def smooth_random_field(shape, corr_len, seed, nterms=256, dtype=np.float32, ych
         y1 = min(ny, y0 + ychunk)
         B = (Y[y0:y1, None, :] * X[None, :, :]).reshape(-1, J)  # ((y1-y0)*nx, J)
         out[:, y0:y1, :] = (Z @ B.T).reshape(nz, y1 - y0, nx)
+    return out
+
+
+def smooth_random_field_torch(shape, corr_len, seed, nterms=16, device="cuda", zchunk=64):
+    """The recipe of ``smooth_random_field`` evaluated with torch on
+    ``device`` (float64 terms, float32 result), for fields too large for the
+    host-side product (billions of points).  The wavenumbers and phases are
+    the same draws as ``smooth_random_field`` with the same seed and
+    ``nterms``; values agree with it to float64 rounding of the cosines."""
+    import torch
+
+    nz, ny, nx = shape
+    rng = np.random.default_rng(seed)
+    J = nterms
+    k = rng.normal(0.0, 1.0 / corr_len, size=(3, J))
+    ph = rng.uniform(0.0, 2.0 * math.pi, size=(3, J))
+
+    def axis(n, a):
+        i = torch.arange(n, dtype=torch.float64, device=device)
+        return torch.cos(torch.outer(i, torch.from_numpy(k[a]).to(device)) + torch.from_numpy(ph[a]).to(device))
+
+    X, Y = axis(nx, 0), axis(ny, 1)
+    Z = axis(nz, 2) * math.sqrt(8.0 / J)
+    B = (Y[:, None, :] * X[None, :, :]).reshape(-1, J)  # (ny*nx, J)
+    out = torch.empty(shape, dtype=torch.float32, device=device)
+    for z0 in range(0, nz, zchunk):
+        z1 = min(nz, z0 + zchunk)
+        out[z0:z1] = (Z[z0:z1] @ B.T).reshape(z1 - z0, ny, nx).to(torch.float32)
     return out
 
 
