@@ -413,12 +413,16 @@ ooc_status enqueue_steps(ooc_plan *p, int64_t nsteps, ooc_stats *st, int64_t *sl
             // still read; staged fields land in staging buffer g&1, free
             // once slab g-2's decode has run (ev_dec below).
             int64_t need = direct ? g - 2 : -1;
-            if (pass > 0) {
-                // the host units read here were written by slabs i, i+1 of the
-                // previous pass.  The event ring holds the last kEv slabs, so
-                // an older slab is covered by waiting for slab g-3 (the D2H
-                // stream runs in order).
-                int64_t gp = g - p->nslab + (i + 1 < p->nslab ? 1 : 0);
+            if (pass > 0 && sg.in_hi > sg.in_lo) {
+                // the host units read here, [in_lo, in_hi), were written by
+                // the previous pass's slabs up to the one holding plane
+                // in_hi - 1: slab i + 1 when W <= T, further when W > T.  The
+                // event ring holds the last kEv slabs, so an older slab is
+                // covered by waiting for slab g-3 (the D2H stream runs in
+                // order).
+                const int64_t last = (sg.in_hi - 1) / p->T;
+                const int64_t jl = last < p->nslab - 1 ? last : p->nslab - 1;
+                int64_t gp = g - p->nslab + (jl - i);
                 if (gp < g - 3)
                     gp = g - 3;
                 if (gp > need)

@@ -513,6 +513,63 @@ def test_heat7_8cube_two_slabs_against_brute_force(ooc, k):
     assert np.abs(got.astype(np.float64) - u).max() < 1e-6 * max(1.0, np.abs(u).max())
 
 
+# Degenerate plans: grids of one or two 4-plane slabs, k h far beyond the
+# grid (the common region is wider than the grid itself), common regions
+# wider than a slab (a slab's input units then come from several slabs of
+# the previous pass, whose write-backs it must wait for), the smallest grid
+# (one codec block), and calls of zero steps between others.
+@pytest.mark.parametrize("fmt,rate", [("fp32", 16), ("fr4", 16), ("bf16", 16), ("fr4", 8)])
+@pytest.mark.parametrize("shape,T,k,calls", [((4, 4, 4), 4, 8, [0, 3, 9]), ((8, 4, 4), 4, 5, [7, 0]),
+                                             ((4, 8, 12), None, 1, [2, 0, 1]), ((12, 4, 8), 4, 3, [4, 4]),
+                                             ((16, 4, 4), 4, 9, [20])])
+def test_heat7_degenerate_plans(ooc, fmt, rate, shape, T, k, calls):
+    nz, ny, nx = shape
+    u0 = np.random.default_rng(sum(shape) + k).normal(size=shape).astype(np.float32)
+    kw = {"slab_planes": T} if T else {"device_budget_bytes": 1 << 24}
+    plan = ooc.Plan(nx=nx, ny=ny, nz=nz, stencil="heat7", k=k, rw_format=fmt, rw_rate=rate, **kw)
+    try:
+        if T:
+            assert plan.info()["nslab"] == nz // T
+        plan.set_field(0, u0)
+        for n in calls:
+            plan.step(n)
+        got = plan.get_field(0)
+        st = plan.stats()
+    finally:
+        plan.close()
+    ref = incore_heat(ooc, u0, calls, k, fmt, rate)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+    assert st["steps_done"] == sum(calls)
+    assert st["passes"] == len(pass_lengths(calls, k))
+
+
+@pytest.mark.parametrize("fmt,rate,ro_fmt,ro_rate", [("fp32", 16, "fp32", 16), ("fr4", 16, "fr4", 16),
+                                                     ("bf16", 16, "fr4", 12)])
+@pytest.mark.parametrize("shape,T,k,calls", [((8, 4, 4), 4, 10, [13]), ((4, 4, 4), 4, 3, [0, 4, 1]),
+                                             ((12, 8, 4), 4, 2, [5]), ((24, 8, 4), 4, 3, [7]),
+                                             ((32, 4, 8), 8, 5, [11, 4])])
+def test_wave25_degenerate_plans(ooc, fmt, rate, ro_fmt, ro_rate, shape, T, k, calls):
+    nz, ny, nx = shape
+    kappa, p0, pm1, src, w = wave_inputs(shape, sum(calls))
+    plan = ooc.Plan(nx=nx, ny=ny, nz=nz, stencil="wave25", k=k, rw_format=fmt, rw_rate=rate, ro_format=ro_fmt,
+                    ro_rate=ro_rate, slab_planes=T)
+    try:
+        assert plan.info()["nslab"] == nz // T
+        plan.set_field(0, p0)
+        plan.set_field(1, pm1)
+        plan.set_field(2, kappa)
+        plan.set_source(*src, w)
+        for n in calls:
+            plan.step(n)
+        got_p, got_pp = plan.get_field(0), plan.get_field(1)
+    finally:
+        plan.close()
+    ref_p, ref_pp = incore_wave(ooc, p0, pm1, kappa, calls, k, fmt, rate, ro_fmt, ro_rate, src, w)
+    assert np.abs(ref_p).max() > 0
+    assert np.array_equal(got_p.view(np.uint32), ref_p.view(np.uint32))
+    assert np.array_equal(got_pp.view(np.uint32), ref_pp.view(np.uint32))
+
+
 @pytest.mark.parametrize("fmt,rate", [("fp32", 16), ("fr4", 16), ("bf16", 16)])
 def test_graph_replay_matches_direct_launches(ooc, fmt, rate):
     # heat7 calls without profiling are captured as a CUDA graph per
