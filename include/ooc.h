@@ -386,8 +386,11 @@ ooc_status ooc_set_source(ooc_plan *plan, int64_t sx, int64_t sy, int64_t sz, co
  * (the last pass may be shorter).  Returns after the last D2H has landed,
  * or OOC_E_TIMEOUT if that takes longer than wait_timeout_ms.  After a
  * timeout the enqueued passes still run to completion on the plan's
- * streams: synchronise those streams before touching the arenas.  The
- * call's steps are enqueued before the wait, so a timed-out call still
+ * streams.  The plan's later ooc_step, ooc_set_field and ooc_get_field
+ * calls wait for them first (under the same deadline, OOC_E_TIMEOUT
+ * again if they have not finished); a caller who touches the arenas
+ * directly synchronises those streams first.  The call's steps are
+ * enqueued before the wait, so a timed-out call still
  * advances the plan's time (host and device copies alike) and counts its
  * steps, passes and launches in the statistics. */
 ooc_status ooc_step(ooc_plan *plan, int64_t nsteps);

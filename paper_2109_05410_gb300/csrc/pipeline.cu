@@ -111,6 +111,7 @@ struct ooc_plan {
     int64_t graph_nsteps = 0;
     ooc_stats graph_delta{};  // counters one replay adds
     cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr}, ev_done = nullptr;
+    cudaEvent_t ev_tail[3] = {nullptr, nullptr, nullptr};  // drain(): the streams' tails
     std::vector<ProfPair> prof;
     size_t prof_used = 0;
     int64_t prof_pass = 0, prof_slab = 0;  // pass and slab being enqueued
@@ -582,13 +583,28 @@ ooc_status enqueue_steps(ooc_plan *p, int64_t nsteps, ooc_stats *st, int64_t *sl
 
 ooc_status ensure_graph_events(ooc_plan *p)
 {
-    if (p->ev_done)
-        return OOC_OK;
-    if (cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->ev_join[0], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->ev_join[1], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->ev_done, cudaEventDisableTiming) != cudaSuccess)
-        return OOC_E_CUDA;
+    cudaEvent_t *evs[] = {&p->ev_fork,    &p->ev_join[0], &p->ev_join[1], &p->ev_done,
+                          &p->ev_tail[0], &p->ev_tail[1], &p->ev_tail[2]};
+    for (cudaEvent_t *e : evs)
+        if (!*e && cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) {
+            *e = nullptr;
+            return OOC_E_CUDA;
+        }
+    return OOC_OK;
+}
+
+// A call that returned OOC_E_TIMEOUT left its copies and kernels queued.  A
+// later call that reads or writes the host image or the rings starts only
+// once the plan's three streams have drained, under the same deadline as
+// every host wait (OOC_E_TIMEOUT again if they have not).  Streams that are
+// idle, the normal case, cost three event records.
+ooc_status drain(ooc_plan *p)
+{
+    OOC_TRY(ensure_graph_events(p));
+    for (int i = 0; i < 3; ++i)
+        OOC_CUDA(cudaEventRecord(p->ev_tail[i], p->st[i]));
+    for (int i = 0; i < 3; ++i)
+        OOC_TRY(wait_event(p, p->ev_tail[i]));
     return OOC_OK;
 }
 
@@ -864,6 +880,7 @@ ooc_status set_field_impl(ooc_plan *p, int field, const void *host_src)
 {
     if (!p || !p->bound || !host_src || field < 0 || field >= p->nfield)
         return OOC_E_INVALID;
+    OOC_TRY(drain(p));
     const int64_t nz = p->cfg.nz;
     const size_t pb = (size_t)p->plane_elems * p->esize;
     char *img = p->host + p->off_host[field];
@@ -905,6 +922,7 @@ ooc_status get_field_impl(ooc_plan *p, int field, void *host_dst)
 {
     if (!p || !p->bound || !host_dst || field < 0 || field >= p->nfield)
         return OOC_E_INVALID;
+    OOC_TRY(drain(p));
     const int64_t nz = p->cfg.nz;
     const size_t pb = (size_t)p->plane_elems * p->esize;
     char *img = p->host + p->off_host[field];
@@ -979,6 +997,7 @@ ooc_status ooc_step(ooc_plan *p, int64_t nsteps)
     if (nsteps == 0)
         return OOC_OK;
     const auto t_start = std::chrono::steady_clock::now();
+    OOC_TRY(drain(p));
     p->prof_used = 0;
     p->trace.clear();
     // A call's launches depend only on nsteps (the wave's source amplitudes
@@ -1113,7 +1132,8 @@ void ooc_plan_destroy(ooc_plan *p)
         cudaEventDestroy(pp.b);
     }
     drop_graph(p);
-    for (cudaEvent_t e : {p->ev_fork, p->ev_join[0], p->ev_join[1], p->ev_done})
+    for (cudaEvent_t e : {p->ev_fork, p->ev_join[0], p->ev_join[1], p->ev_done, p->ev_tail[0], p->ev_tail[1],
+                          p->ev_tail[2]})
         if (e)
             cudaEventDestroy(e);
     delete p;

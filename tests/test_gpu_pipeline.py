@@ -479,6 +479,39 @@ def test_step_deadline_reports_timeout_and_work_completes(ooc):
     assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
 
 
+@pytest.mark.parametrize("fmt,rate,graph_mode", [("fp32", 16, 0), ("fp32", 16, 1), ("fr4", 16, 1)])
+def test_calls_after_a_timeout_wait_for_its_queued_work(ooc, fmt, rate, graph_mode):
+    # A call that returns OOC_E_TIMEOUT leaves its copies and kernels queued.
+    # The plan's next calls wait for them (under the deadline) before they
+    # touch the host image or the rings, so the caller need not synchronise:
+    # a get_field straight after the timed-out call (a plain host copy of the
+    # image with FP32 storage), then more steps, give the bits of a plan that
+    # waited normally.
+    n = 256
+    u0 = smooth_random_field((n, n, n), 8.0, seed=13)
+    out = []
+    for hurried in (True, False):
+        plan = ooc.Plan(nx=n, ny=n, nz=n, stencil="heat7", k=4, rw_format=fmt, rw_rate=rate, slab_planes=32,
+                        graph_mode=graph_mode)
+        try:
+            plan.set_field(0, u0)
+            if hurried:
+                plan.set_wait_timeout(1)
+                with pytest.raises(ooc.OocError) as err:
+                    plan.step(64)
+                assert err.value.status == 5
+                plan.set_wait_timeout(0)
+            else:
+                plan.step(64)
+            mid = plan.get_field(0)
+            plan.step(8)
+            out.append((mid, plan.get_field(0)))
+        finally:
+            plan.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
 @pytest.mark.parametrize("k", [1, 2])
 def test_heat7_8cube_two_slabs_against_brute_force(ooc, k):
     # The smallest pipeline: 8^3, two slabs of 4 planes, h = 1.  FP32 storage
