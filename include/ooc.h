@@ -267,13 +267,15 @@ ooc_status ooc_wave25_steps_f64(double *d_p, double *d_pprev, const double *d_ka
 ooc_status ooc_heat7_steps_fused(float *d_u, float *d_tmp, int64_t nx, int64_t ny, int64_t nz, double r,
                                  int64_t nsteps, void *stream);
 
-/* Reads and clears the library's device fault word on the current device:
- * *fault = 1 if a kernel launched since the last read gave up one of its
- * bounded waits (a shared-memory copy that did not arrive within about a
- * second) and returned without writing the rest of its planes, else 0.
- * ooc_step checks it itself and returns OOC_E_TIMEOUT; callers of the
- * in-core entry points read it after synchronising their stream.  Kernels
- * never trap or spin without bound. */
+/* Reads and clears the library's device fault words on the current device.
+ * *fault is a bit set, 0 when nothing went wrong: 1 if a kernel launched
+ * since the last read gave up one of its bounded waits (a shared-memory
+ * copy that did not arrive within about a second) and returned without
+ * writing the rest of its planes; 2 if ooc_gather or ooc_scatter_add met an
+ * index outside its field and skipped it.  ooc_step checks the first
+ * itself and returns OOC_E_TIMEOUT; callers of the in-core entry points
+ * read it after synchronising their stream.  Kernels never trap, spin
+ * without bound or access memory through an unchecked index. */
 ooc_status ooc_take_device_fault(int *fault);
 
 /* Largest grid, in points, that ooc_heat7_steps_noalloc accepts: the size of
@@ -306,12 +308,19 @@ ooc_status ooc_heat7_steps_noalloc(float *d_u, int64_t nx, int64_t ny, int64_t n
  *   p^{n+1} = 2 p^n - p^{n-1} + kappa L(p^n) + w[n] delta_src,  tr[n] = p^{n+1}(rec)
  * Adjoint for dJ/dtr = res:  mu^m = 2 mu^{m+1} - mu^{m+2} + L(kappa mu^{m+1})
  * + S^T res[m-1], m = N..1;  dJ/dkappa = sum_n mu^{n+1} L(p^n) (FP64).
- * Receivers are flat indices (int64, device, distinct). */
+ * Receivers are flat indices (int64, device, distinct) in [0, nx ny nz):
+ * both checkpointed calls check them before any kernel uses them and
+ * return OOC_E_INVALID if one lies outside the field. */
 
-/* d_out[i] = d_field[d_idx[i]], i < n (device pointers). */
-ooc_status ooc_gather(const float *d_field, const int64_t *d_idx, int64_t n, float *d_out, void *stream);
-/* d_field[d_idx[i]] += d_val[i]; indices must be distinct. */
-ooc_status ooc_scatter_add(float *d_field, const int64_t *d_idx, int64_t n, const float *d_val, void *stream);
+/* d_out[i] = d_field[d_idx[i]], i < n (device pointers; d_field holds
+ * field_size values).  An index outside [0, field_size) is skipped (d_out[i]
+ * = 0) and sets bit 2 of the device fault word (ooc_take_device_fault). */
+ooc_status ooc_gather(const float *d_field, int64_t field_size, const int64_t *d_idx, int64_t n, float *d_out,
+                      void *stream);
+/* d_field[d_idx[i]] += d_val[i]; indices must be distinct.  An index
+ * outside [0, field_size) is skipped and sets bit 2 of the fault word. */
+ooc_status ooc_scatter_add(float *d_field, int64_t field_size, const int64_t *d_idx, int64_t n, const float *d_val,
+                           void *stream);
 /* One adjoint step on dense fields: d_out = 2 mu - mu_prev + L(kappa * mu);
  * d_out may alias d_mu_prev (then it is updated in place). */
 ooc_status ooc_wave25_adjoint_step(const float *d_mu, const float *d_mu_prev, float *d_out, const float *d_kappa,

@@ -140,9 +140,10 @@ _SIGS = {
     "ooc_plan_destroy": (None, [ctypes.c_void_p]),
     "ooc_heat7_steps_noalloc": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int64] * 3
                                 + [ctypes.c_double, ctypes.c_int64, ctypes.c_void_p]),
-    "ooc_gather": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
-    "ooc_scatter_add": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
-                                       ctypes.c_void_p]),
+    "ooc_gather": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                  ctypes.c_void_p]),
+    "ooc_scatter_add": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
     "ooc_wave25_adjoint_step": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int64] * 3 + [ctypes.c_void_p]),
     "ooc_wave25_grad_accum": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int64] * 3 + [ctypes.c_void_p]),
     "ooc_kappa_from_velocity": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
@@ -191,6 +192,45 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _dev(t, dtype, name, numel=None, ndim=None):
+    """Device pointer of a tensor checked against what the C call reads or
+    writes through it: a CUDA tensor of ``dtype``, contiguous (no strides or
+    broadcast views), with ``ndim`` dimensions and at least ``numel``
+    elements when given.  The library cannot see a buffer's size, so a wrong
+    tensor fails here instead of reaching memory it does not own."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name}: expected a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name}: expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous tensor")
+    if ndim is not None and t.dim() != ndim:
+        raise ValueError(f"{name}: expected {ndim} dimensions, got {t.dim()}")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name}: holds {t.numel()} elements, the call needs {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host(t, name):
+    """Pointer of a contiguous uint8 CPU tensor (the library checks its size
+    and that it is pinned where it must be)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.uint8 or not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous uint8 CPU tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _f32():
+    import torch
+    return torch.float32
+
+
+def _dt(name):
+    import torch
+    return getattr(torch, name)
+
+
 def _stream(stream):
     import torch
     if stream is None:
@@ -203,8 +243,9 @@ def ooc_status_string(s):
 
 
 def ooc_take_device_fault():
-    """1 if a kernel gave up a bounded wait since the last call, else 0
-    (reads and clears the library's device fault word)."""
+    """Bit set of the library's device fault words (read and cleared): 1 if
+    a kernel gave up a bounded wait since the last call, 2 if a gather or
+    scatter skipped an index outside its field; 0 when nothing went wrong."""
     f = ctypes.c_int()
     _check(lib().ooc_take_device_fault(ctypes.byref(f)), "ooc_take_device_fault")
     return f.value
@@ -222,8 +263,8 @@ def ooc_compress(d_in, rate, d_out=None, stream=None):
     nbytes = ooc_compressed_bytes(nx, ny, nz, rate)
     if d_out is None:
         d_out = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=d_in.device)
-    _check(lib().ooc_compress(_ptr(d_in), nx, ny, nz, rate, _ptr(d_out), d_out.numel() * d_out.element_size(),
-                              _stream(stream)), "ooc_compress")
+    _check(lib().ooc_compress(_dev(d_in, _f32(), "d_in", ndim=3), nx, ny, nz, rate, _dev(d_out, _dt("uint8"), "d_out"),
+                              d_out.numel(), _stream(stream)), "ooc_compress")
     return d_out
 
 
@@ -232,8 +273,8 @@ def ooc_decompress(d_in, shape, rate, d_out=None, stream=None):
     nz, ny, nx = shape
     if d_out is None:
         d_out = torch.empty(shape, dtype=torch.float32, device=d_in.device)
-    _check(lib().ooc_decompress(_ptr(d_in), d_in.numel() * d_in.element_size(), nx, ny, nz, rate, _ptr(d_out),
-                                _stream(stream)), "ooc_decompress")
+    _check(lib().ooc_decompress(_dev(d_in, _dt("uint8"), "d_in"), d_in.numel(), nx, ny, nz, rate,
+                                _dev(d_out, _f32(), "d_out", numel=nx * ny * nz), _stream(stream)), "ooc_decompress")
     return d_out
 
 
@@ -246,8 +287,8 @@ def ooc_compress64(d_in, rate, d_out=None, stream=None):
     nbytes = ooc_compressed_bytes(nx, ny, nz, rate)
     if d_out is None:
         d_out = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=d_in.device)
-    _check(lib().ooc_compress64(_ptr(d_in), nx, ny, nz, rate, _ptr(d_out), d_out.numel() * d_out.element_size(),
-                                _stream(stream)), "ooc_compress64")
+    _check(lib().ooc_compress64(_dev(d_in, _dt("float64"), "d_in", ndim=3), nx, ny, nz, rate,
+                                _dev(d_out, _dt("uint8"), "d_out"), d_out.numel(), _stream(stream)), "ooc_compress64")
     return d_out
 
 
@@ -256,8 +297,9 @@ def ooc_decompress64(d_in, shape, rate, d_out=None, stream=None):
     nz, ny, nx = shape
     if d_out is None:
         d_out = torch.empty(shape, dtype=torch.float64, device=d_in.device)
-    _check(lib().ooc_decompress64(_ptr(d_in), d_in.numel() * d_in.element_size(), nx, ny, nz, rate, _ptr(d_out),
-                                  _stream(stream)), "ooc_decompress64")
+    _check(lib().ooc_decompress64(_dev(d_in, _dt("uint8"), "d_in"), d_in.numel(), nx, ny, nz, rate,
+                                  _dev(d_out, _dt("float64"), "d_out", numel=nx * ny * nz), _stream(stream)),
+           "ooc_decompress64")
     return d_out
 
 
@@ -287,8 +329,9 @@ def ooc_compress_var(d_in, mode, param, d_out=None, d_index=None, stream=None):
         d_index = torch.empty(nblk + 1, dtype=torch.int64, device=d_in.device)
     scratch = torch.empty(max(ooc_var_scratch_bytes(nx, ny, nz), 8), dtype=torch.uint8, device=d_in.device)
     used = ctypes.c_size_t(0)
-    _check(lib().ooc_compress_var(_ptr(d_in), nx, ny, nz, int(mode), float(param), _ptr(d_out),
-                                  d_out.numel() * d_out.element_size(), _ptr(d_index), _ptr(scratch),
+    _check(lib().ooc_compress_var(_dev(d_in, _f32(), "d_in", ndim=3), nx, ny, nz, int(mode), float(param),
+                                  _dev(d_out, _dt("uint8"), "d_out"), d_out.numel(),
+                                  _dev(d_index, _dt("int64"), "d_index", numel=nblk + 1), _ptr(scratch),
                                   scratch.numel(), ctypes.byref(used), _stream(stream)), "ooc_compress_var")
     return d_out[:used.value], d_index
 
@@ -298,8 +341,11 @@ def ooc_decompress_var(d_in, d_index, shape, mode, param, d_out=None, stream=Non
     nz, ny, nx = shape
     if d_out is None:
         d_out = torch.empty(shape, dtype=torch.float32, device=d_in.device)
-    _check(lib().ooc_decompress_var(_ptr(d_in), d_in.numel() * d_in.element_size(), _ptr(d_index), nx, ny, nz,
-                                    int(mode), float(param), _ptr(d_out), _stream(stream)), "ooc_decompress_var")
+    nblk = ((nx + 3) // 4) * ((ny + 3) // 4) * ((nz + 3) // 4)
+    _check(lib().ooc_decompress_var(_dev(d_in, _dt("uint8"), "d_in"), d_in.numel(),
+                                    _dev(d_index, _dt("int64"), "d_index", numel=nblk + 1), nx, ny, nz, int(mode),
+                                    float(param), _dev(d_out, _f32(), "d_out", numel=nx * ny * nz), _stream(stream)),
+           "ooc_decompress_var")
     return d_out
 
 
@@ -307,7 +353,8 @@ def ooc_bf16_pack(d_in, d_out=None, stream=None):
     import torch
     if d_out is None:
         d_out = torch.empty(d_in.shape, dtype=torch.int16, device=d_in.device)
-    _check(lib().ooc_bf16_pack(_ptr(d_in), _ptr(d_out), d_in.numel(), _stream(stream)), "ooc_bf16_pack")
+    _check(lib().ooc_bf16_pack(_dev(d_in, _f32(), "d_in"), _dev(d_out, _dt("int16"), "d_out", numel=d_in.numel()),
+                               d_in.numel(), _stream(stream)), "ooc_bf16_pack")
     return d_out
 
 
@@ -315,30 +362,33 @@ def ooc_bf16_unpack(d_in, d_out=None, stream=None):
     import torch
     if d_out is None:
         d_out = torch.empty(d_in.shape, dtype=torch.float32, device=d_in.device)
-    _check(lib().ooc_bf16_unpack(_ptr(d_in), _ptr(d_out), d_in.numel(), _stream(stream)), "ooc_bf16_unpack")
+    _check(lib().ooc_bf16_unpack(_dev(d_in, _dt("int16"), "d_in"), _dev(d_out, _f32(), "d_out", numel=d_in.numel()),
+                                 d_in.numel(), _stream(stream)), "ooc_bf16_unpack")
     return d_out
 
 
 def ooc_heat7_steps(d_u, d_tmp, nsteps, r=1.0 / 6.0, stream=None):
     nz, ny, nx = d_u.shape
-    _check(lib().ooc_heat7_steps(_ptr(d_u), _ptr(d_tmp), nx, ny, nz, float(r), int(nsteps), _stream(stream)),
-           "ooc_heat7_steps")
+    _check(lib().ooc_heat7_steps(_dev(d_u, _f32(), "d_u", ndim=3), _dev(d_tmp, _f32(), "d_tmp", numel=d_u.numel()),
+                                 nx, ny, nz, float(r), int(nsteps), _stream(stream)), "ooc_heat7_steps")
     return d_u
 
 
 def ooc_heat7_steps_f64(d_u, d_tmp, nsteps, r=1.0 / 6.0, stream=None):
     """heat7 in FP64 (float64 CUDA tensors [nz, ny, nx])."""
     nz, ny, nx = d_u.shape
-    _check(lib().ooc_heat7_steps_f64(_ptr(d_u), _ptr(d_tmp), nx, ny, nz, float(r), int(nsteps), _stream(stream)),
-           "ooc_heat7_steps_f64")
+    f64 = _dt("float64")
+    _check(lib().ooc_heat7_steps_f64(_dev(d_u, f64, "d_u", ndim=3), _dev(d_tmp, f64, "d_tmp", numel=d_u.numel()), nx,
+                                     ny, nz, float(r), int(nsteps), _stream(stream)), "ooc_heat7_steps_f64")
     return d_u
 
 
 def ooc_heat7_steps_fused(d_u, d_tmp, nsteps, r=1.0 / 6.0, stream=None):
     """ooc_heat7_steps with each pair of steps in one launch (bit-identical)."""
     nz, ny, nx = d_u.shape
-    _check(lib().ooc_heat7_steps_fused(_ptr(d_u), _ptr(d_tmp), nx, ny, nz, float(r), int(nsteps), _stream(stream)),
-           "ooc_heat7_steps_fused")
+    _check(lib().ooc_heat7_steps_fused(_dev(d_u, _f32(), "d_u", ndim=3),
+                                       _dev(d_tmp, _f32(), "d_tmp", numel=d_u.numel()), nx, ny, nz, float(r),
+                                       int(nsteps), _stream(stream)), "ooc_heat7_steps_fused")
     return d_u
 
 
@@ -346,8 +396,8 @@ def ooc_heat7_steps_noalloc(d_u, nsteps, r=1.0 / 6.0, stream=None):
     """ooc_heat7_steps without a scratch field: the library's fixed scratch
     array (OOC_NOALLOC_MAX_POINTS points) holds the second field."""
     nz, ny, nx = d_u.shape
-    _check(lib().ooc_heat7_steps_noalloc(_ptr(d_u), nx, ny, nz, float(r), int(nsteps), _stream(stream)),
-           "ooc_heat7_steps_noalloc")
+    _check(lib().ooc_heat7_steps_noalloc(_dev(d_u, _f32(), "d_u", ndim=3), nx, ny, nz, float(r), int(nsteps),
+                                         _stream(stream)), "ooc_heat7_steps_noalloc")
     return d_u
 
 
@@ -366,7 +416,9 @@ def ooc_wave25_steps(d_p, d_pprev, d_kappa, nsteps, src=None, w=None, t=0, strea
         if len(w) < t + nsteps:
             raise ValueError("source series shorter than t + nsteps")
         wp = w.ctypes.data_as(ctypes.c_void_p)
-    _check(lib().ooc_wave25_steps(_ptr(d_p), _ptr(d_pprev), _ptr(d_kappa), nx, ny, nz, sx, sy, sz, wp, int(t),
+    n = d_p.numel()
+    _check(lib().ooc_wave25_steps(_dev(d_p, _f32(), "d_p", ndim=3), _dev(d_pprev, _f32(), "d_pprev", numel=n),
+                                  _dev(d_kappa, _f32(), "d_kappa", numel=n), nx, ny, nz, sx, sy, sz, wp, int(t),
                                   int(nsteps), _stream(stream)), "ooc_wave25_steps")
     return d_p, d_pprev
 
@@ -387,8 +439,11 @@ def ooc_wave25_steps_fused(d_p, d_pprev, d_kappa, nsteps, src=None, w=None, t=0,
         if len(w) < t + nsteps:
             raise ValueError("source series shorter than t + nsteps")
         wp = w.ctypes.data_as(ctypes.c_void_p)
-    _check(lib().ooc_wave25_steps_fused(_ptr(d_p), _ptr(d_pprev), _ptr(d_kappa), _ptr(t1), _ptr(t2), nx, ny, nz, sx,
-                                        sy, sz, wp, int(t), int(nsteps), _stream(stream)), "ooc_wave25_steps_fused")
+    n = d_p.numel()
+    _check(lib().ooc_wave25_steps_fused(_dev(d_p, _f32(), "d_p", ndim=3), _dev(d_pprev, _f32(), "d_pprev", numel=n),
+                                        _dev(d_kappa, _f32(), "d_kappa", numel=n), _dev(t1, _f32(), "d_t1", numel=n),
+                                        _dev(t2, _f32(), "d_t2", numel=n), nx, ny, nz, sx, sy, sz, wp, int(t),
+                                        int(nsteps), _stream(stream)), "ooc_wave25_steps_fused")
     return d_p, d_pprev
 
 
@@ -404,7 +459,9 @@ def ooc_wave25_steps_f64(d_p, d_pprev, d_kappa, nsteps, src=None, w=None, t=0, s
         if len(w) < t + nsteps:
             raise ValueError("source series shorter than t + nsteps")
         wp = w.ctypes.data_as(ctypes.c_void_p)
-    _check(lib().ooc_wave25_steps_f64(_ptr(d_p), _ptr(d_pprev), _ptr(d_kappa), nx, ny, nz, sx, sy, sz, wp, int(t),
+    n, f64 = d_p.numel(), _dt("float64")
+    _check(lib().ooc_wave25_steps_f64(_dev(d_p, f64, "d_p", ndim=3), _dev(d_pprev, f64, "d_pprev", numel=n),
+                                      _dev(d_kappa, f64, "d_kappa", numel=n), nx, ny, nz, sx, sy, sz, wp, int(t),
                                       int(nsteps), _stream(stream)), "ooc_wave25_steps_f64")
     return d_p, d_pprev
 
@@ -413,12 +470,16 @@ def ooc_gather(d_field, d_idx, d_out=None, stream=None):
     import torch
     if d_out is None:
         d_out = torch.empty(d_idx.numel(), dtype=torch.float32, device=d_field.device)
-    _check(lib().ooc_gather(_ptr(d_field), _ptr(d_idx), d_idx.numel(), _ptr(d_out), _stream(stream)), "ooc_gather")
+    _check(lib().ooc_gather(_dev(d_field, _f32(), "d_field"), d_field.numel(), _dev(d_idx, _dt("int64"), "d_idx"),
+                            d_idx.numel(), _dev(d_out, _f32(), "d_out", numel=d_idx.numel()), _stream(stream)),
+           "ooc_gather")
     return d_out
 
 
 def ooc_scatter_add(d_field, d_idx, d_val, stream=None):
-    _check(lib().ooc_scatter_add(_ptr(d_field), _ptr(d_idx), d_idx.numel(), _ptr(d_val), _stream(stream)),
+    _check(lib().ooc_scatter_add(_dev(d_field, _f32(), "d_field"), d_field.numel(),
+                                 _dev(d_idx, _dt("int64"), "d_idx"), d_idx.numel(),
+                                 _dev(d_val, _f32(), "d_val", numel=d_idx.numel()), _stream(stream)),
            "ooc_scatter_add")
     return d_field
 
@@ -428,14 +489,18 @@ def ooc_wave25_adjoint_step(d_mu, d_mu_prev, d_kappa, d_out=None, stream=None):
     nz, ny, nx = d_mu.shape
     if d_out is None:
         d_out = d_mu_prev
-    _check(lib().ooc_wave25_adjoint_step(_ptr(d_mu), _ptr(d_mu_prev), _ptr(d_out), _ptr(d_kappa), nx, ny, nz,
-                                         _stream(stream)), "ooc_wave25_adjoint_step")
+    n = d_mu.numel()
+    _check(lib().ooc_wave25_adjoint_step(_dev(d_mu, _f32(), "d_mu", ndim=3), _dev(d_mu_prev, _f32(), "d_mu_prev", numel=n),
+                                         _dev(d_out, _f32(), "d_out", numel=n), _dev(d_kappa, _f32(), "d_kappa", numel=n),
+                                         nx, ny, nz, _stream(stream)), "ooc_wave25_adjoint_step")
     return d_out
 
 
 def ooc_wave25_grad_accum(d_grad, d_mu, d_p, stream=None):
     nz, ny, nx = d_mu.shape
-    _check(lib().ooc_wave25_grad_accum(_ptr(d_grad), _ptr(d_mu), _ptr(d_p), nx, ny, nz, _stream(stream)),
+    n = d_mu.numel()
+    _check(lib().ooc_wave25_grad_accum(_dev(d_grad, _dt("float64"), "d_grad", numel=n), _dev(d_mu, _f32(), "d_mu", ndim=3),
+                                       _dev(d_p, _f32(), "d_p", numel=n), nx, ny, nz, _stream(stream)),
            "ooc_wave25_grad_accum")
     return d_grad
 
@@ -444,8 +509,8 @@ def ooc_kappa_from_velocity(d_v, dt_over_dx, d_kappa=None, stream=None):
     import torch
     if d_kappa is None:
         d_kappa = torch.empty_like(d_v)
-    _check(lib().ooc_kappa_from_velocity(_ptr(d_v), _ptr(d_kappa), d_v.numel(), float(dt_over_dx), _stream(stream)),
-           "ooc_kappa_from_velocity")
+    _check(lib().ooc_kappa_from_velocity(_dev(d_v, _f32(), "d_v"), _dev(d_kappa, _f32(), "d_kappa", numel=d_v.numel()),
+                                         d_v.numel(), float(dt_over_dx), _stream(stream)), "ooc_kappa_from_velocity")
     return d_kappa
 
 
@@ -453,8 +518,10 @@ def ooc_velocity_grad(d_grad_kappa, d_v, dt_over_dx, d_grad_v=None, stream=None)
     import torch
     if d_grad_v is None:
         d_grad_v = torch.empty_like(d_v)
-    _check(lib().ooc_velocity_grad(_ptr(d_grad_kappa), _ptr(d_v), _ptr(d_grad_v), d_v.numel(), float(dt_over_dx),
-                                   _stream(stream)), "ooc_velocity_grad")
+    n = d_v.numel()
+    _check(lib().ooc_velocity_grad(_dev(d_grad_kappa, _dt("float64"), "d_grad_kappa", numel=n), _dev(d_v, _f32(), "d_v"),
+                                   _dev(d_grad_v, _f32(), "d_grad_v", numel=n), n, float(dt_over_dx), _stream(stream)),
+           "ooc_velocity_grad")
     return d_grad_v
 
 
@@ -481,9 +548,12 @@ def ooc_wave25_forward_ckpt(d_kappa, nsteps, d_rec, d_traces, every, rate, h_ckp
     nz, ny, nx = d_kappa.shape
     sx, sy, sz, w_keep, wp = _src_args(src, w, nsteps)
     arr = (ctypes.c_void_p * 2)(*[s.cuda_stream for s in streams])
-    _check(lib().ooc_wave25_forward_ckpt(_ptr(d_kappa), nx, ny, nz, sx, sy, sz, wp, int(nsteps), _ptr(d_rec),
-                                         d_rec.numel(), _ptr(d_traces), int(every), int(rate), _ptr(h_ckpt),
-                                         h_ckpt.numel(), _ptr(d_work), d_work.numel(), arr),
+    nrec = d_rec.numel()
+    _check(lib().ooc_wave25_forward_ckpt(_dev(d_kappa, _f32(), "d_kappa", ndim=3), nx, ny, nz, sx, sy, sz, wp,
+                                         int(nsteps), _dev(d_rec, _dt("int64"), "d_rec"), nrec,
+                                         _dev(d_traces, _f32(), "d_traces", numel=int(nsteps) * nrec), int(every),
+                                         int(rate), _host(h_ckpt, "h_ckpt"), h_ckpt.numel(),
+                                         _dev(d_work, _dt("uint8"), "d_work"), d_work.numel(), arr),
            "ooc_wave25_forward_ckpt")
     return d_traces
 
@@ -493,9 +563,13 @@ def ooc_wave25_backward_ckpt(d_kappa, nsteps, d_rec, d_res, every, rate, h_ckpt,
     nz, ny, nx = d_kappa.shape
     sx, sy, sz, w_keep, wp = _src_args(src, w, nsteps)
     arr = (ctypes.c_void_p * 2)(*[s.cuda_stream for s in streams])
-    _check(lib().ooc_wave25_backward_ckpt(_ptr(d_kappa), nx, ny, nz, sx, sy, sz, wp, int(nsteps), _ptr(d_rec),
-                                          d_rec.numel(), _ptr(d_res), int(every), int(rate), _ptr(h_ckpt),
-                                          h_ckpt.numel(), _ptr(d_grad), _ptr(d_work), d_work.numel(), arr),
+    nrec = d_rec.numel()
+    _check(lib().ooc_wave25_backward_ckpt(_dev(d_kappa, _f32(), "d_kappa", ndim=3), nx, ny, nz, sx, sy, sz, wp,
+                                          int(nsteps), _dev(d_rec, _dt("int64"), "d_rec"), nrec,
+                                          _dev(d_res, _f32(), "d_res", numel=int(nsteps) * nrec), int(every), int(rate),
+                                          _host(h_ckpt, "h_ckpt"), h_ckpt.numel(),
+                                          _dev(d_grad, _dt("float64"), "d_grad", numel=d_kappa.numel()),
+                                          _dev(d_work, _dt("uint8"), "d_work"), d_work.numel(), arr),
            "ooc_wave25_backward_ckpt")
     return d_grad
 

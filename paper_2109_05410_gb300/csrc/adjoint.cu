@@ -34,7 +34,28 @@
 
 using namespace ooc;
 
+namespace ooc {
+// Set by a gather or scatter kernel that skipped an index outside its field;
+// read and cleared by take_index_fault().
+__device__ unsigned g_index_fault = 0u;
+
+cudaError_t take_index_fault(unsigned *fault)
+{
+    unsigned v = 0u;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_index_fault, sizeof(v));
+    if (e == cudaSuccess && v != 0u) {
+        const unsigned zero = 0u;
+        e = cudaMemcpyToSymbol(g_index_fault, &zero, sizeof(zero));
+    }
+    *fault = v;
+    return e;
+}
+}  // namespace ooc
+
 namespace {
+
+// Set by check_indices_kernel (receiver indices of the checkpointed calls).
+__device__ unsigned g_receivers_bad = 0u;
 
 constexpr int kTX = 32, kTY = 8, kSeg = 4 * kTX, kR = 4;
 
@@ -146,31 +167,58 @@ __global__ void __launch_bounds__(kTX *kTY, 2)
     }
 }
 
-__global__ void gather_kernel(const float *__restrict__ f, const int64_t *__restrict__ idx, int64_t n,
+// Gather and scatter skip an index outside the field [0, size) (a gather
+// writes 0 there) and set g_index_fault, so no index reaches memory beyond
+// the field.
+__global__ void gather_kernel(const float *__restrict__ f, int64_t size, const int64_t *__restrict__ idx, int64_t n,
                               float *__restrict__ out)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n)
-        out[i] = f[idx[i]];
+    if (i < n) {
+        const int64_t j = idx[i];
+        if (j >= 0 && j < size) {
+            out[i] = f[j];
+        } else {
+            out[i] = 0.0f;
+            atomicOr(&g_index_fault, 1u);
+        }
+    }
 }
 
 // Receiver indices are distinct, so every point has one writer.
-__global__ void scatter_add_kernel(float *f, const int64_t *__restrict__ idx, int64_t n, const float *__restrict__ v)
+__global__ void scatter_add_kernel(float *f, int64_t size, const int64_t *__restrict__ idx, int64_t n,
+                                   const float *__restrict__ v)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n)
-        f[idx[i]] += v[i];
+    if (i < n) {
+        const int64_t j = idx[i];
+        if (j >= 0 && j < size)
+            f[j] += v[i];
+        else
+            atomicOr(&g_index_fault, 1u);
+    }
 }
 
 // f[idx[i]] += v[i] * kap[idx[i]] (receiver residual injected into w = kappa mu).
-__global__ void scatter_add_scaled_kernel(float *f, const int64_t *__restrict__ idx, int64_t n,
+__global__ void scatter_add_scaled_kernel(float *f, int64_t size, const int64_t *__restrict__ idx, int64_t n,
                                           const float *__restrict__ v, const float *__restrict__ kap)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         const int64_t j = idx[i];
-        f[j] += v[i] * kap[j];
+        if (j >= 0 && j < size)
+            f[j] += v[i] * kap[j];
+        else
+            atomicOr(&g_index_fault, 1u);
     }
+}
+
+// Sets g_receivers_bad when an index lies outside [0, size).
+__global__ void check_indices_kernel(const int64_t *__restrict__ idx, int64_t n, int64_t size)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && (idx[i] < 0 || idx[i] >= size))
+        atomicOr(&g_receivers_bad, 1u);
 }
 
 // g[i] += (double) a[i]; a[i] = 0: a segment's FP32 gradient sum into the
@@ -297,6 +345,32 @@ struct Events {
     }
 };
 
+// The checkpointed calls check their receiver indices once, before any
+// kernel reads or writes through them: OOC_E_INVALID if one lies outside
+// the field.  The wait is bounded like the calls' other waits.
+ooc_status check_receivers(const int64_t *d_rec, int64_t nrec, int64_t size, cudaStream_t st, cudaEvent_t ev)
+{
+    if (nrec == 0)
+        return OOC_OK;
+    const unsigned zero = 0u;
+    if (cudaMemcpyToSymbolAsync(g_receivers_bad, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return OOC_E_CUDA;
+    check_indices_kernel<<<(unsigned)((nrec + 255) / 256), 256, 0, st>>>(d_rec, nrec, size);
+    if (cudaGetLastError() != cudaSuccess || cudaEventRecord(ev, st) != cudaSuccess)
+        return OOC_E_CUDA;
+    const ooc_status w = wait_ev(ev, 600000);
+    if (w != OOC_OK)
+        return w;
+    unsigned bad = 0u;
+    if (cudaMemcpyFromSymbolAsync(&bad, g_receivers_bad, sizeof(bad), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaEventRecord(ev, st) != cudaSuccess)
+        return OOC_E_CUDA;
+    const ooc_status w2 = wait_ev(ev, 600000);
+    if (w2 != OOC_OK)
+        return w2;
+    return bad ? OOC_E_INVALID : OOC_OK;
+}
+
 #define TRY_CUDA(x)                  \
     do {                             \
         if ((x) != cudaSuccess)      \
@@ -307,23 +381,27 @@ struct Events {
 
 extern "C" {
 
-ooc_status ooc_gather(const float *d_field, const int64_t *d_idx, int64_t n, float *d_out, void *stream)
+ooc_status ooc_gather(const float *d_field, int64_t field_size, const int64_t *d_idx, int64_t n, float *d_out,
+                      void *stream)
 {
-    if (n < 0 || (n > 0 && (!d_field || !d_idx || !d_out)))
+    if (n < 0 || field_size < 0 || (n > 0 && (!d_field || !d_idx || !d_out)))
         return OOC_E_INVALID;
     if (n == 0)
         return OOC_OK;
-    gather_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(d_field, d_idx, n, d_out);
+    gather_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(d_field, field_size, d_idx, n,
+                                                                                 d_out);
     return cudaGetLastError() == cudaSuccess ? OOC_OK : OOC_E_CUDA;
 }
 
-ooc_status ooc_scatter_add(float *d_field, const int64_t *d_idx, int64_t n, const float *d_val, void *stream)
+ooc_status ooc_scatter_add(float *d_field, int64_t field_size, const int64_t *d_idx, int64_t n, const float *d_val,
+                           void *stream)
 {
-    if (n < 0 || (n > 0 && (!d_field || !d_idx || !d_val)))
+    if (n < 0 || field_size < 0 || (n > 0 && (!d_field || !d_idx || !d_val)))
         return OOC_E_INVALID;
     if (n == 0)
         return OOC_OK;
-    scatter_add_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(d_field, d_idx, n, d_val);
+    scatter_add_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(d_field, field_size, d_idx, n,
+                                                                                      d_val);
     return cudaGetLastError() == cudaSuccess ? OOC_OK : OOC_E_CUDA;
 }
 
@@ -401,6 +479,11 @@ ooc_status ooc_wave25_forward_ckpt(const float *d_kappa, int64_t nx, int64_t ny,
     const size_t cb = a256(field_bytes(n, rate));
     Events ev;
     TRY_CUDA(ev.make());  // e[0..1]: staging filled, e[2..3]: staging drained
+    {
+        const ooc_status rc = check_receivers(d_rec, nrec, n, sC, ev.e[4]);
+        if (rc != OOC_OK)
+            return rc;
+    }
     TRY_CUDA(cudaMemsetAsync(p, 0, sizeof(float) * n, sC));
     TRY_CUDA(cudaMemsetAsync(pp, 0, sizeof(float) * n, sC));
     const bool src = sx >= 0 && h_w != nullptr;
@@ -431,7 +514,8 @@ ooc_status ooc_wave25_forward_ckpt(const float *d_kappa, int64_t nx, int64_t ny,
         p = pp;
         pp = t;
         if (nrec > 0)
-            TRY_CUDA(ooc_gather(p, d_rec, nrec, d_traces + s * nrec, sC) == OOC_OK ? cudaSuccess : cudaErrorUnknown);
+            TRY_CUDA(ooc_gather(p, n, d_rec, nrec, d_traces + s * nrec, sC) == OOC_OK ? cudaSuccess
+                                                                                     : cudaErrorUnknown);
     }
     TRY_CUDA(cudaEventRecord(ev.e[4], sC));
     TRY_CUDA(cudaEventRecord(ev.e[5], sD));
@@ -462,6 +546,11 @@ ooc_status ooc_wave25_backward_ckpt(const float *d_kappa, int64_t nx, int64_t ny
     auto hist = [&](int64_t j) { return (float *)(w + L.hist0 + (size_t)j * fb); };
     Events ev;
     TRY_CUDA(ev.make());  // e[0..1]: staging loaded (sD), e[2..3]: staging consumed (sC)
+    {
+        const ooc_status rc = check_receivers(d_rec, nrec, n, sC, ev.e[4]);
+        if (rc != OOC_OK)
+            return rc;
+    }
     TRY_CUDA(cudaMemsetAsync(mu1, 0, sizeof(float) * n, sC));
     TRY_CUDA(cudaMemsetAsync(mu2, 0, sizeof(float) * n, sC));
     TRY_CUDA(cudaMemsetAsync(d_grad, 0, sizeof(double) * n, sC));
@@ -510,7 +599,7 @@ ooc_status ooc_wave25_backward_ckpt(const float *d_kappa, int64_t nx, int64_t ny
                                       ConstRing{d_kappa, nz, 0}, nx, ny, nz, 0, nz, -1, -1, -1, 0.0f, sC));
             if (nrec > 0) {  // + kappa S^T res[m-1]
                 scatter_add_scaled_kernel<<<(unsigned)((nrec + 255) / 256), 256, 0, sC>>>(
-                    mu2, d_rec, nrec, d_res + (m - 1) * nrec, d_kappa);
+                    mu2, n, d_rec, nrec, d_res + (m - 1) * nrec, d_kappa);
                 TRY_CUDA(cudaGetLastError());
             }
             // += w^m L(p^{m-1}), in FP32 within the segment

@@ -475,9 +475,9 @@ extern "C" ooc_status ooc_take_device_fault(int *fault)
 {
     if (!fault)
         return OOC_E_INVALID;
-    unsigned v = 0u;
-    if (take_stencil_fault(&v) != cudaSuccess)
+    unsigned v = 0u, vi = 0u;
+    if (take_stencil_fault(&v) != cudaSuccess || take_index_fault(&vi) != cudaSuccess)
         return OOC_E_CUDA;
-    *fault = v != 0u ? 1 : 0;
+    *fault = (v != 0u ? 1 : 0) | (vi != 0u ? 2 : 0);
     return OOC_OK;
 }

@@ -104,6 +104,9 @@ cudaError_t launch_wave25_to(ConstRing p, ConstRing pprev, Ring pnew, ConstRing 
 // Reads and clears the device word that a stencil kernel sets when one of
 // its bounded waits gives up (nonzero: that launch left planes unwritten).
 cudaError_t take_stencil_fault(unsigned *fault);
+// Reads and clears the word set by gather / scatter kernels that skipped an
+// index outside their field.
+cudaError_t take_index_fault(unsigned *fault);
 // plan time on the device: *t += n (one thread)
 cudaError_t launch_add_time(int64_t *t, int64_t n, cudaStream_t st);
 // Codec over the 4-aligned plane range [z0, z1) of a ring; the stream part

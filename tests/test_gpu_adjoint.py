@@ -53,6 +53,59 @@ def test_gather_scatter(ooc):
     assert ooc.ooc_gather(f, idx).cpu().tolist() == [5.0, 17.0, 999.0, 0.0]
     ooc.ooc_scatter_add(f, idx, torch.ones(4, device="cuda"))
     assert f[17].item() == 18.0 and f[1].item() == 1.0
+    torch.cuda.synchronize()
+    assert ooc.ooc_take_device_fault() == 0
+
+
+def test_gather_scatter_skip_indices_outside_the_field(ooc):
+    # Indices outside [0, field size) never reach memory: the gather gives 0
+    # there, the scatter skips them, and the device fault word reports it.
+    # The field is a slice of a larger buffer whose other values must stay.
+    buf = torch.arange(1200, dtype=torch.float32, device="cuda")
+    f = buf[100:1100]
+    idx = torch.tensor([5, -1, 1000, 999, 1 << 40], dtype=torch.int64, device="cuda")
+    assert ooc.ooc_take_device_fault() == 0
+    assert ooc.ooc_gather(f, idx).cpu().tolist() == [105.0, 0.0, 0.0, 1099.0, 0.0]
+    torch.cuda.synchronize()
+    assert ooc.ooc_take_device_fault() == 2
+    ooc.ooc_scatter_add(f, idx, torch.full((5,), 0.5, device="cuda"))
+    torch.cuda.synchronize()
+    assert ooc.ooc_take_device_fault() == 2
+    assert ooc.ooc_take_device_fault() == 0  # read and cleared
+    want = np.arange(1200, dtype=np.float32)
+    want[105] += 0.5
+    want[1099] += 0.5
+    assert np.array_equal(buf.cpu().numpy(), want)
+
+
+def test_checkpointed_calls_refuse_receivers_outside_the_field(ooc):
+    n, N, every, rate = 16, 12, 4, 16
+    shape = (n, n, n)
+    d_kap = torch.full(shape, 0.05, device="cuda")
+    traces = torch.zeros((N, 3), device="cuda")
+    h_ckpt = torch.empty(ooc.ooc_wave25_ckpt_bytes(shape, N, every, rate), dtype=torch.uint8, pin_memory=True)
+    work = torch.empty(ooc.ooc_wave25_adjoint_work_bytes(shape, every, rate), dtype=torch.uint8, device="cuda")
+    streams = [torch.cuda.current_stream(), torch.cuda.Stream()]
+    w = np.ones(N, dtype=np.float32)
+    for bad in (n ** 3, -3):
+        d_rec = torch.tensor([0, bad, 7], dtype=torch.int64, device="cuda")
+        with pytest.raises(ooc.OocError) as err:
+            ooc.ooc_wave25_forward_ckpt(d_kap, N, d_rec, traces, every, rate, h_ckpt, work, streams, src=(8, 8, 8),
+                                        w=w)
+        assert err.value.status == 1
+        g = torch.zeros(shape, dtype=torch.float64, device="cuda")
+        with pytest.raises(ooc.OocError) as err:
+            ooc.ooc_wave25_backward_ckpt(d_kap, N, d_rec, traces, every, rate, h_ckpt, g, work, streams,
+                                         src=(8, 8, 8), w=w)
+        assert err.value.status == 1
+    torch.cuda.synchronize()
+    assert ooc.ooc_take_device_fault() == 0
+    assert not traces.any()
+    # the same call with the receivers in the field runs
+    d_rec = torch.tensor([0, n ** 3 - 1, 7], dtype=torch.int64, device="cuda")
+    ooc.ooc_wave25_forward_ckpt(d_kap, N, d_rec, traces, every, rate, h_ckpt, work, streams, src=(8, 8, 8), w=w)
+    torch.cuda.synchronize()
+    assert ooc.ooc_take_device_fault() == 0
 
 
 def problem(n, nsteps, seed=3, rec_stride=2):
