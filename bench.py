@@ -9,17 +9,22 @@ compressed-vs-uncompressed comparison.  Error is stated against the FP64
 oracle on a sampled central 128^3 sub-box (exact dependency cone).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload heat1024|kernels512|window56|wave1024|precision|precision192|adjoint512|fp64|
-                   window56_fp64]
+                  [--workload heat1024|kernels512|window56|wave1024|wave1024_error|precision|precision192|
+                   adjoint512|fp64|window56_fp64]
 
 Prints one JSON line (rank 0).  The default workload is the headline; the
 others measure the remaining configurations: one launch of each kernel on a
 512^3 field (kernels512), the headline's kernels on one 56-plane 1024^2
-window (window56, the ncu capture case of the headline), the 1024^3 wave with the
-paper's four storage codes (wave1024), the long-horizon precision study
-(precision at 384^3 with an FP64-oracle prefix; precision192 with the oracle
-over all 4320 steps) and the checkpointed adjoint at 512^3 (adjoint512).  N > 1 runs N independent replicas (the
-method works on one GPU; there is no data-path collective).
+window (window56, the ncu capture case of the headline), the 1024^3 wave with
+the paper's four storage codes (wave1024) and its accuracy over 2000 steps
+against an FP64 run (wave1024_error), the long-horizon precision study over
+4320 steps against an FP64 run (precision at 384^3, precision192), the
+checkpointed adjoint at 512^3 (adjoint512) and FP64 fields (fp64,
+window56_fp64).  The FP64 runs these errors are taken against use the
+library's FP64 wave kernel, which the GPU tests hold to the FP64 oracle; the
+CPU oracle itself runs only in the reference arm and the cpu_baseline leg.
+N > 1 runs N independent replicas (the method works on one GPU; there is no
+data-path collective).
 """
 from __future__ import annotations
 
@@ -876,16 +881,51 @@ def run_wave1024(args, world, rank, local):
     return 0
 
 
-def run_precision(args, world, rank, local, n=384, oracle_budget_s=120.0):
+def field_errors(got, ref, nsample_per_plane=100, seed=0, floor_frac=1e-3, zchunk=64):
+    """Errors of a field against a reference, both CUDA tensors [nz, ny, nx]:
+    rel-L2, max-abs and the paper-style mean pointwise relative error on 100
+    sampled points per plane (Section VI-C), leaving out samples with |ref|
+    below floor_frac * max|ref|.  The sample points are drawn from
+    numpy.random.default_rng(seed): for each plane nsample_per_plane rows,
+    then as many columns.  Sums run in FP64 over z-chunks."""
+    import torch
+    nz, ny, nx = ref.shape
+    sq_d = sq_r = 0.0
+    max_abs = max_ref = 0.0
+    for z0 in range(0, nz, zchunk):
+        r = ref[z0:z0 + zchunk].double()
+        d = got[z0:z0 + zchunk].double() - r
+        sq_d += float((d * d).sum())
+        sq_r += float((r * r).sum())
+        max_abs = max(max_abs, float(d.abs().max()))
+        max_ref = max(max_ref, float(r.abs().max()))
+        del r, d
+    rng = np.random.default_rng(seed)
+    ys = rng.integers(0, ny, size=(nz, nsample_per_plane))
+    xs = rng.integers(0, nx, size=(nz, nsample_per_plane))
+    flat = torch.from_numpy(((np.arange(nz)[:, None] * ny + ys) * nx + xs).ravel()).to(ref.device)
+    rs = ref.reshape(-1)[flat].double()
+    vs = got.reshape(-1)[flat].double()
+    keep = rs.abs() >= floor_frac * max_ref
+    mean_rel = float(((vs - rs).abs()[keep] / rs.abs()[keep]).mean()) if bool(keep.any()) else 0.0
+    return {"rel_l2": (sq_d / sq_r) ** 0.5 if sq_r > 0 else sq_d ** 0.5, "max_abs": max_abs,
+            "mean_rel_sampled": mean_rel, "samples": int(rs.numel()), "excluded": int((~keep).sum())}
+
+
+FP64_REFERENCE_NOTE = ("FP64 reference: the same wave run in FP64 arithmetic by the library's FP64 wave25 kernel "
+                       "(ooc_wave25_steps_f64, in-core, FP32 kappa values and source amplitudes), which the GPU "
+                       "tests hold to the FP64 oracle within 1e-13 rel-L2 on this configuration's inputs")
+
+
+def run_precision(args, world, rank, local, n=384):
     """Long-horizon precision study: wave25 at n^3 (384^3, the configuration's
     size; 192^3 with --workload precision192), 4320 steps, k = 10, 6 slabs,
     storage FP32, BF16, FR4 at 8/12/16/24 bits/value (both read-write levels
-    and kappa), FP32 compute.  The formats run side by side, 100 steps at a
-    time.  Every 100 steps: rel-L2, max-abs and the mean pointwise relative
-    error on 100 sampled points per plane against the FP64 oracle, for as
-    long a prefix as the oracle finishes within oracle_budget_s on the host
-    cores (at 192^3 all 4320 steps), and against the FP32-storage run (a
-    self-consistency check) over all steps; Gpts/s per format."""
+    and kappa), FP32 compute.  The formats run side by side with an FP64
+    reference run, 100 steps at a time.  Every 100 steps: rel-L2, max-abs
+    and the mean pointwise relative error on 100 sampled points per plane
+    against the FP64 run over all 4320 steps, and against the FP32-storage
+    run (a self-consistency check); Gpts/s per format."""
     import torch
 
     import paper_2109_05410_gb300 as ooc
@@ -912,20 +952,16 @@ def run_precision(args, world, rank, local, n=384, oracle_budget_s=120.0):
         plan.set_field(2, kappa)
         plan.set_source(*src, w)
         plans[name], tms[name] = plan, 0.0
-    oracle_on = rank == 0
-    if oracle_on:
-        import oracle
-        oracle.build()
-        p = np.zeros((n, n, n))
-        pp = np.zeros((n, n, n))
-        kap64 = kappa.astype(np.float64)
-        w64 = w.astype(np.float64)
-        srcf = (src[2] * n + src[1]) * n + src[0]
-    t_oracle, oracle_steps = 0.0, 0
+    p64 = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
+    pp64 = torch.zeros_like(p64)
+    k64 = torch.from_numpy(kappa.astype(np.float64)).cuda()
+    w64 = w.astype(np.float64)
     errs = {name: [] for name in plans}
     self_errs = {name: [] for name in plans}
     done = 0
     for m in marks:
+        ooc.ooc_wave25_steps_f64(p64, pp64, k64, m - done, src=src, w=w64, t=done)
+        torch.cuda.synchronize()  # the FP64 run is not inside any format's timed calls
         fields = {}
         for name, plan in plans.items():
             e0, e1 = _cuda_events(torch)
@@ -934,39 +970,106 @@ def run_precision(args, world, rank, local, n=384, oracle_budget_s=120.0):
             e1.record(plan.streams[2])
             e1.synchronize()
             tms[name] += e0.elapsed_time(e1)
-            fields[name] = plan.get_field(0, out=np.empty((n, n, n), dtype=np.float32))
-        if oracle_on and t_oracle < oracle_budget_s:
-            t0 = time.perf_counter()
-            p, pp = oracle.wave25_run(p, pp, kap64, m - done, src=srcf, w=w64, t0=done)
-            t_oracle += time.perf_counter() - t0
-            oracle_steps = m
-            for name, f in fields.items():
-                e = oracle.error_metrics(f, p)
-                errs[name].append([m, e["rel_l2"], e["max_abs"], e["mean_rel_sampled"]])
-        ref = fields["fp32"].astype(np.float64)
-        nref = np.linalg.norm(ref)
+            fields[name] = torch.from_numpy(plan.get_field(0, out=np.empty((n, n, n), dtype=np.float32))).cuda()
+        torch.cuda.synchronize()
         for name, f in fields.items():
-            d = f.astype(np.float64) - ref
-            self_errs[name].append([m, float(np.linalg.norm(d) / nref) if nref > 0 else 0.0,
-                                    float(np.abs(d).max())])
+            e = field_errors(f, p64)
+            errs[name].append([m, e["rel_l2"], e["max_abs"], e["mean_rel_sampled"]])
+            se = field_errors(f, fields["fp32"])
+            self_errs[name].append([m, se["rel_l2"], se["max_abs"]])
         del fields
         done = m
     speed = {name: n ** 3 * total / (tms[name] / 1e3) / 1e9 for name in plans}
     for plan in plans.values():
         plan.close()
+    fault = ooc.ooc_take_device_fault()
+    del p64, pp64, k64
+    torch.cuda.empty_cache()
     if rank != 0:
         return 0
     line = {"workload": "precision" if n == 384 else f"precision{n}", "grid": [n, n, n], "steps": total, "k": k,
-            "slab_planes": T, "nslab": -(-n // T),
-            "oracle_prefix_steps": oracle_steps,
-            "oracle_note": (f"FP64 oracle errors every {every} steps over the first {oracle_steps} of {total} steps, "
-                            f"as many as {oracle_budget_s:.0f} s of host time allowed"),
+            "slab_planes": T, "nslab": -(-n // T), "reference": FP64_REFERENCE_NOTE,
+            "errors_note": f"errors_every_100: [step, rel-L2, max-abs, mean relative error on 100 sampled points "
+                           f"per plane] against the FP64 run, every {every} steps over all {total} steps",
             "self_consistency_note": "errors_vs_fp32_storage_every_100: the same pipeline with FP32 storage, "
-                                     "not the FP64 oracle",
+                                     "not the FP64 run",
             "formats": {name: {"Gpts": speed[name], "errors_every_100": errs[name],
                                "errors_vs_fp32_storage_every_100": self_errs[name]} for name in plans},
-            "oracle_seconds": t_oracle, "oracle_threads": oracle.threads()}
+            "device_fault": fault}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_wave1024_error(args, world, rank, local):
+    """The 1024^3 wave configuration's accuracy run (Section VI-C): 2000 steps
+    from rest with the Ricker source, k = 10, 4 GiB device budget; code 1
+    (FP32 storage) and code 4 (read-write levels and kappa at FR4-16) side
+    by side with an FP64 reference run, 100 steps at a time.  Every 100
+    steps: rel-L2, max-abs and the sampled mean relative error of each code
+    against the FP64 run; Gpts/s of each code over the run."""
+    import torch
+
+    import paper_2109_05410_gb300 as ooc
+    from synth import ricker
+    torch.cuda.set_device(local)
+    ooc.build()
+    ooc.lib()
+    n, k, total, every = 1024, 10, 2000, 100
+    kappa, src, dt = wave_inputs(n)
+    w = (ricker(total, dt) * float(kappa[src[2], src[1], src[0]])).astype(np.float32)
+    zero = np.zeros((n, n, n), dtype=np.float32)
+    codes = {"code1_fp32": ("fp32", "fp32"), "code4_rw_ro_fr4-16": ("fr4", "fr4")}
+    plans, tms = {}, {}
+    for name, (rw, ro) in codes.items():
+        plan = ooc.Plan(nx=n, ny=n, nz=n, stencil="wave25", k=k, rw_format=rw, rw_rate=16, ro_format=ro,
+                        ro_rate=16, device_budget_bytes=4 << 30, profile=0)
+        plan.set_field(0, zero)
+        plan.set_field(1, zero)
+        plan.set_field(2, kappa)
+        plan.set_source(*src, w)
+        plans[name], tms[name] = plan, 0.0
+    del zero
+    p64 = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
+    pp64 = torch.zeros_like(p64)
+    k64 = torch.from_numpy(kappa.astype(np.float64)).cuda()
+    w64 = w.astype(np.float64)
+    host = np.empty((n, n, n), dtype=np.float32)
+    errs = {name: [] for name in plans}
+    t_ref = 0.0
+    done = 0
+    for m in range(every, total + 1, every):
+        e0, e1 = _cuda_events(torch)
+        e0.record()
+        ooc.ooc_wave25_steps_f64(p64, pp64, k64, m - done, src=src, w=w64, t=done)
+        e1.record()
+        e1.synchronize()
+        t_ref += e0.elapsed_time(e1)
+        for name, plan in plans.items():
+            e0, e1 = _cuda_events(torch)
+            e0.record(plan.streams[0])
+            plan.step(m - done)
+            e1.record(plan.streams[2])
+            e1.synchronize()
+            tms[name] += e0.elapsed_time(e1)
+            f = torch.from_numpy(plan.get_field(0, out=host)).cuda()
+            e = field_errors(f, p64)
+            errs[name].append([m, e["rel_l2"], e["max_abs"], e["mean_rel_sampled"]])
+            del f
+        done = m
+    for plan in plans.values():
+        plan.close()
+    fault = ooc.ooc_take_device_fault()
+    del p64, pp64, k64
+    torch.cuda.empty_cache()
+    if rank == 0:
+        print(json.dumps({"workload": "wave1024_error", "grid": [n, n, n], "steps": total, "k": k,
+                          "device_budget_bytes": 4 << 30, "reference": FP64_REFERENCE_NOTE,
+                          "fp64_reference_Gpts": n ** 3 * total / (t_ref / 1e3) / 1e9,
+                          "errors_note": f"errors_every_100: [step, rel-L2, max-abs, mean relative error on 100 "
+                                         f"sampled points per plane] against the FP64 run, every {every} steps",
+                          "codes": {name: {"Gpts": n ** 3 * total / (tms[name] / 1e3) / 1e9,
+                                           "errors_every_100": errs[name]} for name in plans},
+                          "device_fault": fault}), flush=True)
     return 0
 
 
@@ -1209,8 +1312,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="heat1024",
-                    choices=["heat1024", "kernels512", "window56", "wave1024", "precision", "precision192",
-                             "adjoint512", "fp64", "window56_fp64"])
+                    choices=["heat1024", "kernels512", "window56", "wave1024", "wave1024_error", "precision",
+                             "precision192", "adjoint512", "fp64", "window56_fp64"])
     args = ap.parse_args()
     world, rank, local = dist_init(args)
     try:
@@ -1219,7 +1322,8 @@ def main():
         runner = {"heat1024": run_gpu, "kernels512": run_kernels512, "window56": run_window56,
                   "wave1024": run_wave1024,
                   "precision": run_precision,
-                  "precision192": lambda a, w, r, l: run_precision(a, w, r, l, n=192, oracle_budget_s=1e9),
+                  "precision192": lambda a, w, r, l: run_precision(a, w, r, l, n=192),
+                  "wave1024_error": run_wave1024_error,
                   "adjoint512": run_adjoint512, "fp64": run_fp64,
                   "window56_fp64": run_window56_fp64}[args.workload]
         return runner(args, world, rank, local)

@@ -127,3 +127,23 @@ def test_ncu_counters_follow_the_kernel_source(tmp_path, monkeypatch):
         assert bench.ncu_counters(kernel) is c
         write(first, srcs[first].replace("namespace ooc {", "namespace ooc { constexpr int kChanged = 1;", 1))
         assert bench.ncu_counters(kernel) is None
+
+
+def test_field_errors_match_the_oracle_metrics():
+    # The bench computes its accuracy figures on the device; on CPU tensors
+    # the same function must give the oracle's metrics (the same sampled
+    # points, the same floor) on a field with values near zero.
+    import numpy as np
+    import torch
+
+    import bench
+    import oracle
+    rng = np.random.default_rng(7)
+    ref = rng.normal(size=(12, 10, 9))
+    ref[3] *= 1e-6  # a plane below the floor
+    got = (ref + 1e-5 * rng.normal(size=ref.shape)).astype(np.float32)
+    want = oracle.error_metrics(got, ref)
+    have = bench.field_errors(torch.from_numpy(got), torch.from_numpy(ref), zchunk=5)
+    for key in ("rel_l2", "max_abs", "mean_rel_sampled"):
+        assert abs(have[key] - want[key]) <= 1e-12 * abs(want[key]), key
+    assert have["samples"] == want["samples"] and have["excluded"] == want["excluded"]

@@ -266,3 +266,50 @@ def test_fp64_wave_graph_replay_with_the_source_table(ooc):
             plan.close()
     assert np.abs(outs[1]).max() > 0
     assert np.array_equal(outs[0].view(np.uint64), outs[1].view(np.uint64))
+
+
+def test_fp64_reference_of_the_precision_configuration(ooc):
+    # The precision and wave1024_error workloads take their errors against an
+    # FP64 run by this kernel: here it runs the 384^3 configuration's inputs
+    # (layered velocity, FP32 kappa, the Ricker source at the centre, from
+    # rest) for 40 steps and meets the FP64 oracle over the whole field.
+    import bench
+    n, nsteps = 384, 40
+    kappa, src, dt = bench.wave_inputs(n)
+    w = (ricker(nsteps, dt) * float(kappa[src[2], src[1], src[0]])).astype(np.float32).astype(np.float64)
+    k64 = kappa.astype(np.float64)
+    p = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
+    pp = torch.zeros_like(p)
+    ooc.ooc_wave25_steps_f64(p, pp, torch.from_numpy(k64).cuda(), nsteps, src=src, w=w)
+    torch.cuda.synchronize()
+    srcf = (src[2] * n + src[1]) * n + src[0]
+    want, _ = oracle.wave25_run(np.zeros((n, n, n)), np.zeros((n, n, n)), k64, nsteps, src=srcf, w=w)
+    m = oracle.error_metrics(p.cpu().numpy(), want)
+    assert m["rel_l2"] < 1e-13, m
+
+
+def test_fp64_reference_of_the_1024_wave_configuration(ooc):
+    # The same at 1024^3 (the wave1024_error workload): after 20 steps from
+    # rest the field is nonzero only within 4 x 20 = 80 cells of the source,
+    # so the oracle on the 208^3 box around it (104 cells out, zero ghosts
+    # beyond) gives every nonzero value exactly; outside the box the GPU
+    # field must be exactly zero.
+    import bench
+    n, nsteps, m = 1024, 20, 104
+    kappa, src, dt = bench.wave_inputs(n)
+    w = (ricker(nsteps, dt) * float(kappa[src[2], src[1], src[0]])).astype(np.float32).astype(np.float64)
+    p = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
+    pp = torch.zeros_like(p)
+    ooc.ooc_wave25_steps_f64(p, pp, torch.from_numpy(kappa.astype(np.float64)).cuda(), nsteps, src=src, w=w)
+    torch.cuda.synchronize()
+    lo = [c - m for c in src]
+    box = (slice(lo[2], lo[2] + 2 * m), slice(lo[1], lo[1] + 2 * m), slice(lo[0], lo[0] + 2 * m))
+    sub_k = kappa[box].astype(np.float64)
+    srcf = (m * 2 * m + m) * 2 * m + m
+    want, _ = oracle.wave25_run(np.zeros(sub_k.shape), np.zeros(sub_k.shape), sub_k, nsteps, src=srcf, w=w)
+    got = p[box].cpu().numpy()
+    assert np.abs(want).max() > 0
+    e = oracle.error_metrics(got, want)
+    assert e["rel_l2"] < 1e-13, e
+    p[box] = 0.0
+    assert int(torch.count_nonzero(p)) == 0
