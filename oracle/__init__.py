@@ -8,8 +8,9 @@ FP64 heat7 and wave25 stencils (C, OpenMP over z), BF16 storage rounding
 pipeline applies at pass boundaries.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
-leg may import this package.  It shares no code with the CUDA library in
-``paper_2109_05410_gb300/csrc`` and never imports the product package.
+leg and reference arm (``--impl reference``) may import this package.  It
+shares no code with the CUDA library in ``paper_2109_05410_gb300/csrc`` and
+never imports the product package.
 
 The C sources are compiled with gcc into ``oracle/_build/liboracle.so`` on
 first use (or by :func:`build`).

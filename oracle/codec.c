@@ -2,7 +2,7 @@
  * oracle/codec.c -- TEST INFRASTRUCTURE ONLY.  Serial CPU reference of the
  * fixed-rate 4x4x4 block codec ("FR4") that stores FP32 slabs at R bits per
  * value.  Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline
- * leg may load it; the product path never does.
+ * leg and reference arm may load it; the product path never does.
  *
  * The paper (Section IV) picks a fixed-rate lossy codec in the cuZFP family
  * because the user fixes the bits kept per value (so "32 bits per double"

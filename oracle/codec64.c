@@ -1,8 +1,8 @@
 /*
  * oracle/codec64.c -- TEST INFRASTRUCTURE ONLY.  Serial CPU reference of
  * FR4D, the fixed-rate 4x4x4 block codec for FP64 fields.  Only tests/,
- * __graft_entry__.smoke() and bench.py's CPU-baseline leg may load it; the
- * product path never does.
+ * __graft_entry__.smoke() and bench.py's CPU-baseline leg and reference arm
+ * may load it; the product path never does.
  *
  * The paper ran its wave fields in double precision and stored them at 32
  * and 24 of every 64 bits (Section VI, codes 2-4); Section IV asks for a

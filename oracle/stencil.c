@@ -2,7 +2,7 @@
  * oracle/stencil.c -- TEST INFRASTRUCTURE ONLY.  Plain FP64 CPU stencils
  * (triple loops, OpenMP over z) that define what the GPU stencil path must
  * compute.  Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline
- * leg may load this.
+ * leg and reference arm may load this.
  *
  * Grids are [z][y][x] (x fastest).  Values outside [0,n) on any axis are
  * zero ghosts (Dirichlet zero), as deep as the stencil reaches.
