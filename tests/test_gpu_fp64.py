@@ -313,3 +313,66 @@ def test_fp64_reference_of_the_1024_wave_configuration(ooc):
     assert e["rel_l2"] < 1e-13, e
     p[box] = 0.0
     assert int(torch.count_nonzero(p)) == 0
+
+
+@pytest.mark.parametrize("fmt,rate", [("fp64", 64), ("fr4", 32)])
+@pytest.mark.parametrize("shape,T,k,calls", [((4, 4, 4), 4, 8, [0, 3, 9]), ((16, 4, 4), 4, 9, [20]),
+                                             ((12, 8, 4), 4, 2, [5, 0, 3])])
+def test_fp64_heat_degenerate_plans(ooc, fmt, rate, shape, T, k, calls):
+    # FP64 plans on one-block grids, k h beyond the grid and common regions
+    # up to 3 slabs wide (inputs from several slabs of the previous pass):
+    # bit-identical to the in-core FP64 path with the same round trips
+    nz, ny, nx = shape
+    u0 = np.random.default_rng(sum(shape) + k).normal(size=shape)
+    plan = ooc.Plan(nx=nx, ny=ny, nz=nz, stencil="heat7", k=k, rw_format=fmt, rw_rate=rate, slab_planes=T,
+                    precision="fp64")
+    try:
+        assert plan.info()["nslab"] == nz // T
+        plan.set_field(0, u0)
+        for n in calls:
+            plan.step(n)
+        got = plan.get_field(0)
+    finally:
+        plan.close()
+    u = roundtrip64(ooc, torch.from_numpy(u0).cuda(), fmt, rate)
+    tmp = torch.empty_like(u)
+    for kp in pass_lengths(calls, k):
+        ooc.ooc_heat7_steps_f64(u, tmp, kp)
+        u = roundtrip64(ooc, u, fmt, rate)
+    torch.cuda.synchronize()
+    assert np.array_equal(got.view(np.uint64), u.cpu().numpy().view(np.uint64))
+
+
+@pytest.mark.parametrize("shape,T,k,calls", [((24, 8, 4), 4, 3, [7]), ((8, 4, 4), 4, 10, [13])])
+def test_fp64_wave_degenerate_plans(ooc, shape, T, k, calls):
+    nz, ny, nx = shape
+    kappa, src, w = wave_case(shape, sum(calls))
+    rng = np.random.default_rng(nz)
+    p0 = 1e-3 * rng.normal(size=shape)
+    pm1 = 0.9 * p0
+    plan = ooc.Plan(nx=nx, ny=ny, nz=nz, stencil="wave25", k=k, rw_format="fr4", rw_rate=32, ro_format="fp64",
+                    ro_rate=64, slab_planes=T, precision="fp64")
+    try:
+        assert plan.info()["nslab"] == nz // T
+        plan.set_field(0, p0)
+        plan.set_field(1, pm1)
+        plan.set_field(2, kappa)
+        plan.set_source(*src, w.astype(np.float32))
+        for n in calls:
+            plan.step(n)
+        got_p, got_pp = plan.get_field(0), plan.get_field(1)
+    finally:
+        plan.close()
+    kap = torch.from_numpy(kappa).cuda()
+    p = roundtrip64(ooc, torch.from_numpy(p0).cuda(), "fr4", 32)
+    pp = roundtrip64(ooc, torch.from_numpy(pm1).cuda(), "fr4", 32)
+    t = 0
+    for kp in pass_lengths(calls, k):
+        ooc.ooc_wave25_steps_f64(p, pp, kap, kp, src=src, w=w, t=t)
+        t += kp
+        p = roundtrip64(ooc, p, "fr4", 32)
+        pp = roundtrip64(ooc, pp, "fr4", 32)
+    torch.cuda.synchronize()
+    assert np.abs(got_p).max() > 0
+    assert np.array_equal(got_p.view(np.uint64), p.cpu().numpy().view(np.uint64))
+    assert np.array_equal(got_pp.view(np.uint64), pp.cpu().numpy().view(np.uint64))
