@@ -6,6 +6,17 @@
 
 #include "tma.cuh"
 
+// the pair's point updates in packed FP32 pairs (heat_pt4x2, the same bits
+// as heat_pt4, which -DOOC_HEAT_F32X2=0 selects)
+#ifndef OOC_HEAT_F32X2
+#define OOC_HEAT_F32X2 1
+#endif
+#if OOC_HEAT_F32X2
+#define OOC_HEATX2T_PT heat_pt4x2
+#else
+#define OOC_HEATX2T_PT heat_pt4
+#endif
+
 namespace ooc {
 
 using namespace sten;
@@ -199,7 +210,7 @@ OOC_PRAGMA(unroll OOC_HEATX2T_UNROLL)
                     xl = srow(sc, L0 + j + 1)[3];
                 if (lane == kTX - 1)
                     xr = srow(sc, L0 + j + 1)[4 * kTX + 4];
-                const float4 o = heat_pt4(cq[j], xl, xr, j == 0 ? upo : cq[j - 1], j == R - 1 ? dno : cq[j + 1],
+                const float4 o = OOC_HEATX2T_PT(cq[j], xl, xr, j == 0 ? upo : cq[j - 1], j == R - 1 ? dno : cq[j + 1],
                                           pq[j], nq[j], r);
                 sv[j] = in[j] ? o : z4;
             }
@@ -247,7 +258,7 @@ OOC_PRAGMA(unroll OOC_HEATX2T_UNROLL)
             for (int j = 0; j < R; ++j) {
                 const float yl = __shfl_up_sync(0xffffffffu, s1[j].w, 1);
                 const float yr = __shfl_down_sync(0xffffffffu, s1[j].x, 1);
-                const float4 o = heat_pt4(s1[j], yl, yr, j == 0 ? upo : s1[j - 1], j == R - 1 ? dno : s1[j + 1],
+                const float4 o = OOC_HEATX2T_PT(s1[j], yl, yr, j == 0 ? upo : s1[j - 1], j == R - 1 ? dno : s1[j + 1],
                                           s2[j], sv[j], r);
                 if (own[j])
                     *reinterpret_cast<float4 *>(op + off[j]) = o;

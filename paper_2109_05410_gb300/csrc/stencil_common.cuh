@@ -3,6 +3,7 @@
 // loading fused heat7 pairs; heat_tma.cu: the TMA-staged fused heat7 pairs).
 #pragma once
 #include "common.cuh"
+#include "f32x2.cuh"
 
 #define OOC_PRAGMA_(x) _Pragma(#x)
 #define OOC_PRAGMA(x) OOC_PRAGMA_(x)
@@ -62,6 +63,25 @@ __device__ __forceinline__ float4 heat_pt4(float4 c, float xl, float xr, float4 
     o.y = heat_pt(c.y, c.x, c.z, up.y, dn.y, zm.y, zp.y, r);
     o.z = heat_pt(c.z, c.y, c.w, up.z, dn.z, zm.z, zp.z, r);
     o.w = heat_pt(c.w, c.z, xr, up.w, dn.w, zm.w, zp.w, r);
+    return o;
+}
+
+// heat_pt4 with points (0, 1) and (2, 3) in packed FP32 pairs (f32x2.cuh):
+// the same operations in the same order, so the same bits, with half the
+// floating-point instructions.
+__device__ __forceinline__ float4 heat_pt4x2(float4 c, float xl, float xr, float4 up, float4 dn, float4 zm, float4 zp,
+                                             float r)
+{
+    const F2 c01 = pk2(c.x, c.y), c23 = pk2(c.z, c.w);
+    const F2 mid = pk2(c.y, c.z);  // right neighbours of (0, 1), left neighbours of (2, 3)
+    const F2 t01 = add2(add2(add2(pk2(xl, c.x), mid), add2(pk2(up.x, up.y), pk2(dn.x, dn.y))),
+                        add2(pk2(zm.x, zm.y), pk2(zp.x, zp.y)));
+    const F2 t23 = add2(add2(add2(mid, pk2(c.w, xr)), add2(pk2(up.z, up.w), pk2(dn.z, dn.w))),
+                        add2(pk2(zm.z, zm.w), pk2(zp.z, zp.w)));
+    const F2 m6 = dup2(-6.0f), r2 = dup2(r);
+    float4 o;
+    unpk2(fma2(r2, fma2(m6, c01, t01), c01), o.x, o.y);
+    unpk2(fma2(r2, fma2(m6, c23, t23), c23), o.z, o.w);
     return o;
 }
 
