@@ -198,11 +198,15 @@ size_t ooc_var_scratch_bytes(int64_t nx, int64_t ny, int64_t nz);
  * (device, out_cap bytes) and d_index (device, nblocks + 1 uint64).
  * d_scratch: ooc_var_scratch_bytes(...) device bytes.  Runs on `stream`
  * and returns when the size is known: *out_bytes (host) = 4 * total words.
- * Two passes: block sizes, a prefix sum into d_index, then the blocks.  If
- * the stream would exceed out_cap, returns OOC_E_INVALID after the first
- * pass without writing d_out (d_index then holds the offsets).  The host
- * waits for the first pass by polling an event against a 10-minute
- * deadline: OOC_E_TIMEOUT past it, with the first pass still enqueued. */
+ * One pass: each CTA codes its blocks, learns its offset from the CTAs
+ * before it (a decoupled look-back over per-tile sums in d_scratch, every
+ * wait bounded) and writes its blocks and their offsets.  If the stream
+ * exceeds out_cap, returns OOC_E_INVALID with *out_bytes the size it
+ * needs; d_index then holds every offset, and d_out only the blocks that
+ * end within out_cap (nothing is written past it).  The host waits for
+ * the pass by polling an event against a 10-minute deadline (OOC_E_TIMEOUT
+ * past it, with the pass still enqueued); a look-back that gave up also
+ * returns OOC_E_TIMEOUT. */
 ooc_status ooc_compress_var(const float *d_in, int64_t nx, int64_t ny, int64_t nz, int mode, double param,
                             void *d_out, size_t out_cap, uint64_t *d_index, void *d_scratch,
                             size_t scratch_bytes, size_t *out_bytes, void *stream);

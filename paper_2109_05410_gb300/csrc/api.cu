@@ -148,7 +148,7 @@ ooc_status ooc_compress(const float *d_in, int64_t nx, int64_t ny, int64_t nz, i
     if (!aligned(d_in, 4))
         return OOC_E_INVALID;
     return cuda_status(
-        launch_fr4_encode_dense(d_in, nx, ny, nz, 2 * rate, OOC_FR4_RATE, 0, 0, (uint32_t *)d_out, nullptr, st));
+        launch_fr4_encode_dense(d_in, nx, ny, nz, 2 * rate, (uint32_t *)d_out, st));
 }
 
 ooc_status ooc_decompress(const void *d_in, size_t in_bytes, int64_t nx, int64_t ny, int64_t nz, int rate,
@@ -230,7 +230,7 @@ size_t ooc_compress_var_bound(int64_t nx, int64_t ny, int64_t nz)
 
 size_t ooc_var_scratch_bytes(int64_t nx, int64_t ny, int64_t nz)
 {
-    return shape_ok(nx, ny, nz) ? scan_scratch_bytes(fr4_blocks(nx, ny, nz)) : 0;
+    return shape_ok(nx, ny, nz) ? var_scratch_bytes(fr4_blocks(nx, ny, nz)) : 0;
 }
 
 ooc_status ooc_compress_var(const float *d_in, int64_t nx, int64_t ny, int64_t nz, int mode, double param,
@@ -245,26 +245,25 @@ ooc_status ooc_compress_var(const float *d_in, int64_t nx, int64_t ny, int64_t n
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t nblk = fr4_blocks(nx, ny, nz);
     *out_bytes = 0;
-    // pass 1: block sizes, then offsets
-    cudaError_t e = launch_fr4_encode_dense(d_in, nx, ny, nz, (int)kVarBlockWords, mode, mparam, 0, nullptr,
-                                            d_index, st);
-    if (e == cudaSuccess)
-        e = launch_exclusive_scan(d_index, nblk, (uint64_t *)d_scratch, st);
-    if (e != cudaSuccess)
+    // one pass: every block's size, offset and words (a block is written
+    // only if it ends within out_cap)
+    if (launch_fr4_encode_var(d_in, nx, ny, nz, mode, mparam, (uint32_t *)d_out, (uint64_t)(out_cap / 4), d_index,
+                              d_scratch, st) != cudaSuccess)
         return OOC_E_CUDA;
-    // the total is read once the first pass has run; the wait is bounded
+    // the total is read once the pass has run; the wait is bounded
     const ooc_status ws = wait_stream(st, kCallWaitMs);
     if (ws != OOC_OK)
         return ws;
+    unsigned fault = 0u;
+    if (take_codec_fault(&fault) != cudaSuccess)
+        return OOC_E_CUDA;
+    if (fault)
+        return OOC_E_TIMEOUT;
     uint64_t total = 0;
     if (cudaMemcpy(&total, d_index + nblk, sizeof(total), cudaMemcpyDeviceToHost) != cudaSuccess)
         return OOC_E_CUDA;
     *out_bytes = (size_t)total * 4;
-    if (*out_bytes > out_cap)
-        return OOC_E_INVALID;
-    // pass 2: the blocks at their offsets
-    return cuda_status(launch_fr4_encode_dense(d_in, nx, ny, nz, (int)kVarBlockWords, mode, mparam, 1,
-                                               (uint32_t *)d_out, d_index, st));
+    return *out_bytes > out_cap ? OOC_E_INVALID : OOC_OK;
 }
 
 ooc_status ooc_decompress_var(const void *d_in, size_t in_bytes, const uint64_t *d_index, int64_t nx, int64_t ny,
@@ -475,9 +474,10 @@ extern "C" ooc_status ooc_take_device_fault(int *fault)
 {
     if (!fault)
         return OOC_E_INVALID;
-    unsigned v = 0u, vi = 0u;
-    if (take_stencil_fault(&v) != cudaSuccess || take_index_fault(&vi) != cudaSuccess)
+    unsigned v = 0u, vc = 0u, vi = 0u;
+    if (take_stencil_fault(&v) != cudaSuccess || take_codec_fault(&vc) != cudaSuccess ||
+        take_index_fault(&vi) != cudaSuccess)
         return OOC_E_CUDA;
-    *fault = (v != 0u ? 1 : 0) | (vi != 0u ? 2 : 0);
+    *fault = (v != 0u || vc != 0u ? 1 : 0) | (vi != 0u ? 2 : 0);
     return OOC_OK;
 }

@@ -31,6 +31,11 @@
 #include "common.cuh"
 
 namespace ooc {
+
+// Set by a kernel whose bounded wait gave up (the variable-size encoder's
+// look-back); read and cleared by take_codec_fault().
+__device__ unsigned g_codec_fault = 0u;
+
 namespace {
 
 constexpr int kPrec = 26;  // block-floating-point precision (bits)
@@ -999,13 +1004,11 @@ __device__ __forceinline__ void gather_clamped(const float *in, int64_t nx, int6
     }
 }
 
-// Fixed rate (mode OOC_FR4_RATE): `words` words per block, the CTA's output
-// staged and written with coalesced stores.  Variable-size modes: phase 0
-// writes each block's word count to index[b]; phase 1 (index now holding
-// offsets) writes block b's words at out + index[b].
+// Fixed rate for any shape: `words` words per block, the CTA's output
+// staged and written with coalesced stores.
 __global__ void __launch_bounds__(kThreads)
     fr4_encode_dense_kernel(const float *__restrict__ in, int64_t nx, int64_t ny, int64_t nz, int64_t nblk, int words,
-                            int mode, int mparam, int phase, uint32_t *__restrict__ out, uint64_t *__restrict__ index)
+                            uint32_t *__restrict__ out)
 {
     extern __shared__ uint32_t smem[];
     __shared__ uint16_t dtab[256];
@@ -1015,27 +1018,12 @@ __global__ void __launch_bounds__(kThreads)
     const int64_t first = (int64_t)blockIdx.x * kThreads;
     const int64_t b = first + threadIdx.x;
     uint32_t *mine = smem + threadIdx.x * stride;
-    int bits = 0;
     if (b < nblk) {
         const int64_t nbx = (nx + 3) >> 2, nby = (ny + 3) >> 2;
         const int64_t bx = b % nbx, t2 = b / nbx, by = t2 % nby, bz = t2 / nby;
         uint32_t v[64];
         gather_clamped(in, nx, ny, nz, bx, by, bz, v);
-        bits = encode_block(v, words, mode, mparam, mine, smem + kThreads * stride + threadIdx.x * kPlaneStride,
-                            dtab);
-    }
-    if (mode != OOC_FR4_RATE) {  // uniform over the grid: no barrier on this path
-        if (b >= nblk)
-            return;
-        const int nw = (bits + 31) >> 5;
-        if (phase == 0) {
-            index[b] = (uint64_t)nw;
-            return;
-        }
-        uint32_t *dst = out + index[b];
-        for (int i = 0; i < nw; ++i)
-            dst[i] = mine[i];
-        return;
+        encode_block(v, words, OOC_FR4_RATE, 0, mine, smem + kThreads * stride + threadIdx.x * kPlaneStride, dtab);
     }
     __syncthreads();
     const int64_t left = nblk - first;
@@ -1095,80 +1083,126 @@ __global__ void __launch_bounds__(kThreads)
             }
 }
 
-// ---- exclusive prefix sum of block sizes into offsets -----------------------------
-constexpr int kScan = 1024;
+// ---- variable-size modes: one pass with a decoupled look-back ---------------------
+// Tile t is the kThreads blocks of the t-th CTA to start: an atomic counter
+// numbers the CTAs as they begin, so every tile a CTA waits on is already
+// running and never waits on a later one.  status[t] holds the tile's state
+// in bits 62-63 and a word count in bits 0-61: kTileAgg its own words,
+// kTilePrefix the words of tiles 0 .. t, kTileFailed a look-back that gave up.
+// Each published value carries everything its reader needs, so relaxed
+// 64-bit loads and stores suffice.
+constexpr uint64_t kTileAgg = 1ull << 62, kTilePrefix = 2ull << 62, kTileFailed = 3ull << 62;
+constexpr uint64_t kTileValue = (1ull << 62) - 1;
+constexpr int kLookbackSpins = 1 << 24;  // about a second of 64 ns sleeps per tile waited on
 
-// Exclusive scan of x over the CTA (1024 threads); *total gets the sum.
-__device__ __forceinline__ uint64_t cta_exclusive_scan(uint64_t x, uint64_t *warp_tot, uint64_t *total)
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const unsigned long long *p)
 {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Block b's words at out + index[b]; index[nblk] = total words.  A block is
+// written only if it ends within out_words.  scratch: the tile counter, then
+// one status word per tile, all zero at launch.
+__global__ void __launch_bounds__(kThreads)
+    fr4_encode_var_kernel(const float *__restrict__ in, int64_t nx, int64_t ny, int64_t nz, int64_t nblk, int mode,
+                          int mparam, uint32_t *__restrict__ out, uint64_t out_words, uint64_t *__restrict__ index,
+                          unsigned long long *scratch)
+{
+    extern __shared__ uint32_t smem[];
+    __shared__ uint16_t dtab[256];
+    __shared__ uint64_t warp_tot[kThreads / 32];
+    __shared__ int64_t s_tile;
+    __shared__ uint64_t s_prefix;
+    __shared__ int s_fail;
+    unsigned long long *status = scratch + 1;
+    if (threadIdx.x == 0) {
+        s_tile = (int64_t)atomicAdd(scratch, 1ull);
+        s_fail = 0;
+    }
+    init_dup_table(dtab);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    constexpr int stride = kVarWords + kSlack + 1;
+    const int64_t b = tile * kThreads + threadIdx.x;
+    uint32_t *mine = smem + threadIdx.x * stride;
+    uint64_t nw = 0;
+    if (b < nblk) {
+        const int64_t nbx = (nx + 3) >> 2, nby = (ny + 3) >> 2;
+        const int64_t bx = b % nbx, t2 = b / nbx, by = t2 % nby, bz = t2 / nby;
+        uint32_t v[64];
+        gather_clamped(in, nx, ny, nz, bx, by, bz, v);
+        const int bits = encode_block(v, kVarWords, mode, mparam, mine,
+                                      smem + kThreads * stride + threadIdx.x * kPlaneStride, dtab);
+        nw = (uint64_t)((bits + 31) >> 5);
+    }
+    // exclusive scan of the word counts over the CTA
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint64_t s = x;
+    uint64_t incl = nw;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const uint64_t t = __shfl_up_sync(0xffffffffu, s, d);
+        const uint64_t t = __shfl_up_sync(0xffffffffu, incl, d);
         if (lane >= d)
-            s += t;
+            incl += t;
     }
     if (lane == 31)
-        warp_tot[warp] = s;
+        warp_tot[warp] = incl;
     __syncthreads();
-    if (warp == 0) {
-        uint64_t w = warp_tot[lane];
+    uint64_t before = incl - nw, total = 0;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint64_t t = __shfl_up_sync(0xffffffffu, w, d);
-            if (lane >= d)
-                w += t;
+    for (int w = 0; w < kThreads / 32; ++w) {
+        if (w < warp)
+            before += warp_tot[w];
+        total += warp_tot[w];
+    }
+    if (threadIdx.x == 0) {
+        uint64_t prefix = 0;
+        if (tile == 0) {
+            st_relaxed_u64(&status[0], kTilePrefix | total);
+        } else {
+            st_relaxed_u64(&status[tile], kTileAgg | total);
+            bool failed = false;
+            for (int64_t j = tile - 1;; --j) {  // tile 0 publishes a prefix, so j stays >= 0
+                uint64_t v = ld_relaxed_u64(&status[j]);
+                for (int spins = 0; (v >> 62) == 0 && spins < kLookbackSpins; ++spins) {
+                    __nanosleep(64);
+                    v = ld_relaxed_u64(&status[j]);
+                }
+                const uint64_t state = v & ~kTileValue;
+                if (state == 0 || state == kTileFailed) {
+                    failed = true;
+                    break;
+                }
+                prefix += v & kTileValue;
+                if (state == kTilePrefix)
+                    break;
+            }
+            if (failed) {
+                st_relaxed_u64(&status[tile], kTileFailed);  // later tiles stop at once
+                atomicOr(&g_codec_fault, 1u);
+                s_fail = 1;
+            } else {
+                st_relaxed_u64(&status[tile], kTilePrefix | (prefix + total));
+            }
         }
-        warp_tot[lane] = w;
+        s_prefix = prefix;
     }
     __syncthreads();
-    const uint64_t before = (warp > 0 ? warp_tot[warp - 1] : 0ull) + s - x;
-    *total = warp_tot[31];
-    __syncthreads();  // warp_tot is reused by the caller's next scan
-    return before;
-}
-
-// v[0..n) -> exclusive prefix within tiles of 1024; tile totals to sums.
-__global__ void __launch_bounds__(kScan) scan_tiles_kernel(uint64_t *v, int64_t n, uint64_t *sums)
-{
-    __shared__ uint64_t warp_tot[32];
-    const int64_t i = (int64_t)blockIdx.x * kScan + threadIdx.x;
-    const uint64_t x = i < n ? v[i] : 0ull;
-    uint64_t total;
-    const uint64_t before = cta_exclusive_scan(x, warp_tot, &total);
-    if (i < n)
-        v[i] = before;
-    if (threadIdx.x == 0)
-        sums[blockIdx.x] = total;
-}
-
-// sums[0..m) -> exclusive prefix (one CTA, chunks of 1024); sums[m] = total.
-__global__ void __launch_bounds__(kScan) scan_sums_kernel(uint64_t *sums, int64_t m)
-{
-    __shared__ uint64_t warp_tot[32];
-    uint64_t carry = 0;
-    for (int64_t base = 0; base < m; base += kScan) {
-        const int64_t i = base + threadIdx.x;
-        const uint64_t x = i < m ? sums[i] : 0ull;
-        uint64_t total;
-        const uint64_t before = cta_exclusive_scan(x, warp_tot, &total);
-        if (i < m)
-            sums[i] = carry + before;
-        carry += total;
-    }
-    if (threadIdx.x == 0)
-        sums[m] = carry;
-}
-
-__global__ void __launch_bounds__(kScan) add_tile_offsets_kernel(uint64_t *v, int64_t n, const uint64_t *sums,
-                                                                 int64_t m)
-{
-    const int64_t i = (int64_t)blockIdx.x * kScan + threadIdx.x;
-    if (i < n)
-        v[i] += sums[blockIdx.x];
-    if (i == 0)
-        v[n] = sums[m];
+    if (s_fail || b >= nblk)
+        return;
+    const uint64_t off = s_prefix + before;
+    index[b] = off;
+    if (b == nblk - 1)
+        index[nblk] = off + nw;
+    if (off + nw <= out_words)
+        for (uint64_t i = 0; i < nw; ++i)
+            out[off + i] = mine[i];
 }
 
 size_t dense_smem_bytes(int words, bool encoder)
@@ -1185,6 +1219,9 @@ cudaError_t ensure_dense_smem_attr()
         return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(fr4_encode_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)dense_smem_bytes(kVarWords, true));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fr4_encode_var_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)dense_smem_bytes(kVarWords, true));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(fr4_decode_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)dense_smem_bytes(kVarWords, false));
@@ -1289,8 +1326,8 @@ cudaError_t launch_fr4d_decode(const uint32_t *in, int64_t nx, int64_t ny, int64
 
 int64_t fr4_blocks(int64_t nx, int64_t ny, int64_t nz) { return ((nx + 3) / 4) * ((ny + 3) / 4) * ((nz + 3) / 4); }
 
-cudaError_t launch_fr4_encode_dense(const float *in, int64_t nx, int64_t ny, int64_t nz, int words, int mode,
-                                    int mparam, int phase, uint32_t *out, uint64_t *index, cudaStream_t st)
+cudaError_t launch_fr4_encode_dense(const float *in, int64_t nx, int64_t ny, int64_t nz, int words, uint32_t *out,
+                                    cudaStream_t st)
 {
     const int64_t nblk = fr4_blocks(nx, ny, nz);
     if (nblk <= 0)
@@ -1301,9 +1338,39 @@ cudaError_t launch_fr4_encode_dense(const float *in, int64_t nx, int64_t ny, int
     if (e != cudaSuccess)
         return e;
     const int64_t grid = (nblk + kThreads - 1) / kThreads;
-    fr4_encode_dense_kernel<<<(unsigned)grid, kThreads, dense_smem_bytes(words, true), st>>>(
-        in, nx, ny, nz, nblk, words, mode, mparam, phase, out, index);
+    fr4_encode_dense_kernel<<<(unsigned)grid, kThreads, dense_smem_bytes(words, true), st>>>(in, nx, ny, nz, nblk,
+                                                                                             words, out);
     return cudaGetLastError();
+}
+
+cudaError_t launch_fr4_encode_var(const float *in, int64_t nx, int64_t ny, int64_t nz, int mode, int mparam,
+                                  uint32_t *out, uint64_t out_words, uint64_t *index, void *scratch, cudaStream_t st)
+{
+    const int64_t nblk = fr4_blocks(nx, ny, nz);
+    if (nblk <= 0)
+        return cudaSuccess;
+    cudaError_t e = ensure_dense_smem_attr();
+    if (e != cudaSuccess)
+        return e;
+    e = cudaMemsetAsync(scratch, 0, var_scratch_bytes(nblk), st);
+    if (e != cudaSuccess)
+        return e;
+    const int64_t grid = (nblk + kThreads - 1) / kThreads;
+    fr4_encode_var_kernel<<<(unsigned)grid, kThreads, dense_smem_bytes(kVarWords, true), st>>>(
+        in, nx, ny, nz, nblk, mode, mparam, out, out_words, index, (unsigned long long *)scratch);
+    return cudaGetLastError();
+}
+
+cudaError_t take_codec_fault(unsigned *fault)
+{
+    unsigned v = 0u;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_codec_fault, sizeof(v));
+    if (e == cudaSuccess && v != 0u) {
+        const unsigned zero = 0u;
+        e = cudaMemcpyToSymbol(g_codec_fault, &zero, sizeof(zero));
+    }
+    *fault = v;
+    return e;
 }
 
 cudaError_t launch_fr4_decode_dense(const uint32_t *in, int64_t in_words, const uint64_t *index, int64_t nx,
@@ -1322,17 +1389,8 @@ cudaError_t launch_fr4_decode_dense(const uint32_t *in, int64_t in_words, const 
     return cudaGetLastError();
 }
 
-size_t scan_scratch_bytes(int64_t n) { return sizeof(uint64_t) * (size_t)((n + kScan - 1) / kScan + 1); }
+// the tile counter and one status word per tile of the variable-size encoder
+size_t var_scratch_bytes(int64_t nblk) { return sizeof(uint64_t) * (size_t)((nblk + kThreads - 1) / kThreads + 1); }
 
-cudaError_t launch_exclusive_scan(uint64_t *v, int64_t n, uint64_t *scratch, cudaStream_t st)
-{
-    if (n <= 0)
-        return cudaSuccess;
-    const int64_t m = (n + kScan - 1) / kScan;
-    scan_tiles_kernel<<<(unsigned)m, kScan, 0, st>>>(v, n, scratch);
-    scan_sums_kernel<<<1, kScan, 0, st>>>(scratch, m);
-    add_tile_offsets_kernel<<<(unsigned)m, kScan, 0, st>>>(v, n, scratch, m);
-    return cudaGetLastError();
-}
 
 }  // namespace ooc

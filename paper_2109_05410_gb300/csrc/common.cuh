@@ -127,15 +127,22 @@ cudaError_t launch_fr4d_decode(const uint32_t *in, int64_t nx, int64_t ny, int64
 // `words` = 130; encode phase 0 writes block word counts to index[b], phase 1
 // writes the blocks at the offsets then in index.
 int64_t fr4_blocks(int64_t nx, int64_t ny, int64_t nz);
-cudaError_t launch_fr4_encode_dense(const float *in, int64_t nx, int64_t ny, int64_t nz, int words, int mode,
-                                    int mparam, int phase, uint32_t *out, uint64_t *index, cudaStream_t st);
+cudaError_t launch_fr4_encode_dense(const float *in, int64_t nx, int64_t ny, int64_t nz, int words, uint32_t *out,
+                                    cudaStream_t st);
+// Variable-size modes in one pass: block b's words at out + index[b]
+// (index[nblk] = total); blocks ending past out_words are not written.
+// scratch: var_scratch_bytes(nblk) device bytes.
+cudaError_t launch_fr4_encode_var(const float *in, int64_t nx, int64_t ny, int64_t nz, int mode, int mparam,
+                                  uint32_t *out, uint64_t out_words, uint64_t *index, void *scratch, cudaStream_t st);
+size_t var_scratch_bytes(int64_t nblk);
+// Reads and clears the word set when the variable-size encoder's bounded
+// look-back gave up.
+cudaError_t take_codec_fault(unsigned *fault);
 cudaError_t launch_fr4_decode_dense(const uint32_t *in, int64_t in_words, const uint64_t *index, int64_t nx,
                                     int64_t ny, int64_t nz, int words, int mode, int mparam, float *out,
                                     cudaStream_t st);
 // Exclusive prefix sum of v[0..n) in place, v[n] = total; scratch of
 // scan_scratch_bytes(n) bytes.
-size_t scan_scratch_bytes(int64_t n);
-cudaError_t launch_exclusive_scan(uint64_t *v, int64_t n, uint64_t *scratch, cudaStream_t st);
 // BF16 storage over plane ranges of a ring.
 cudaError_t launch_bf16_pack_ring(ConstRing in, int64_t nx, int64_t ny, int64_t z0, int64_t z1, uint16_t *out,
                                   cudaStream_t st);

@@ -85,6 +85,30 @@ def test_small_capacity_and_bad_arguments(ooc):
             ooc.ooc_compress_var(f, mode, param)
 
 
+def test_overflow_writes_whole_blocks_within_the_capacity_only(ooc):
+    # A stream larger than the capacity: the call reports the size it needs,
+    # every offset, and the leading blocks that fit; nothing lands past the
+    # capacity (checked on a guard region behind it).
+    f = torch.from_numpy(smooth_random_field((16, 24, 40), 3.0, seed=8)).cuda()
+    full, index = ooc.ooc_compress_var(f, ooc.OOC_FR4_PRECISION, 20)
+    need = full.numel()
+    cap = (need // 2) // 4 * 4
+    buf = torch.full((cap + 4096,), 0xA5, dtype=torch.uint8, device="cuda")
+    idx2 = torch.empty_like(index)
+    with pytest.raises(ooc.OocError) as err:
+        ooc.ooc_compress_var(f, ooc.OOC_FR4_PRECISION, 20, d_out=buf[:cap], d_index=idx2)
+    assert err.value.status == 1
+    assert torch.equal(idx2, index)
+    assert bool((buf[cap:] == 0xA5).all())
+    words = full.view(torch.int32).cpu().numpy()
+    got = buf[:cap].view(torch.int32).cpu().numpy()
+    offs = index.cpu().numpy()
+    fits = offs[1:] * 4 <= cap
+    assert fits.any() and not fits.all()
+    last = int(offs[1:][fits][-1])  # end of the last block that fits
+    assert np.array_equal(got[:last], words[:last])
+
+
 def test_corrupt_index_decodes_without_fault(ooc):
     # offsets are clamped to the stream and blocks to 130 words
     f = torch.from_numpy(smooth_random_field((12, 12, 12), 3.0, seed=6)).cuda()

@@ -45,7 +45,8 @@ def test_compressed_bytes(L):
     assert ooc.ooc_compressed_bytes(1, 1, 1, 8) == 64
     assert ooc.ooc_compressed_bytes(0, 8, 8, 16) == 0
     assert ooc.ooc_compress_var_bound(5, 5, 5) == 8 * 130 * 4
-    assert ooc.ooc_var_scratch_bytes(1024, 1024, 1024) == 8 * (16384 + 1)
+    # the encoder's tile counter and one status word per tile of 128 blocks
+    assert ooc.ooc_var_scratch_bytes(1024, 1024, 1024) == 8 * (256 ** 3 // 128 + 1)
     assert ooc.ooc_compressed_bytes(8, 8, 8, 65) == 0
 
 
