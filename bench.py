@@ -312,6 +312,15 @@ def cpu_oracle_leg(u0):
     v, dt, cores = oracle_sample(384, 8)
     cpu = {"value": v, "unit": "Gpts/s", "cores": cores, "kind": "oracle",
            "sample": f"384^3 smooth field, 8 steps (2 passes of k=4), FP64 heat7 + FR4-16 round trips, {dt:.1f} s"}
+    # the same steps in FP32 on the host cores (the GPU's arithmetic, no
+    # storage round trips): a CPU throughput for the FP32 work itself
+    from synth import smooth_random_field
+    u32 = smooth_random_field((384,) * 3, 32.0, seed=2)
+    t = time.perf_counter()
+    oracle.heat7_run_f32(u32, 8)
+    dt32 = time.perf_counter() - t
+    cpu["fp32_variant"] = {"value": 384 ** 3 * 8 / dt32 / 1e9, "unit": "Gpts/s", "cores": cores,
+                           "sample": f"384^3 smooth field, 8 FP32 heat7 steps in place, {dt32:.2f} s"}
     return exact, cpu
 
 

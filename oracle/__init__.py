@@ -78,6 +78,7 @@ def lib():
                 "fr4d_decode_planes": (i64, [vp, i64, vp]),
                 "oracle_heat7_step": (None, [vp, vp, i64, i64, i64, dbl]),
                 "oracle_heat7_run": (None, [vp, vp, i64, i64, i64, dbl, i64]),
+                "oracle_heat7_run_f32": (None, [vp, vp, i64, i64, i64, ctypes.c_float, i64]),
                 "oracle_laplacian8": (None, [vp, vp, i64, i64, i64]),
                 "oracle_wave25_step": (None, [vp, vp, vp, vp, i64, i64, i64, i64, dbl]),
                 "oracle_wave25_run": (None, [vp, vp, vp, vp, i64, i64, i64, i64, vp, i64, i64]),
@@ -342,6 +343,16 @@ def heat7_run(u, nsteps, r=1.0 / 6.0):
     tmp = np.empty_like(a)
     nz, ny, nx = a.shape
     lib().oracle_heat7_run(_p(a), _p(tmp), nx, ny, nz, r, nsteps)
+    return a
+
+
+def heat7_run_f32(u, nsteps, r=1.0 / 6.0):
+    """The heat steps in FP32 arithmetic (not a reference: the CPU doing the
+    GPU's FP32 work, timed beside the FP64 oracle)."""
+    a = np.array(u, dtype=np.float32, order="C", copy=True)
+    tmp = np.empty_like(a)
+    nz, ny, nx = a.shape
+    lib().oracle_heat7_run_f32(_p(a), _p(tmp), nx, ny, nz, r, nsteps)
     return a
 
 

@@ -89,6 +89,40 @@ void oracle_heat7_run(double *u, double *tmp, int64_t nx, int64_t ny, int64_t nz
     }
 }
 
+/* The same heat steps in FP32 (float inputs, float arithmetic in the
+ * delta form above, zero ghosts): the CPU doing the GPU's FP32 work, for
+ * timing beside the FP64 oracle.  Not a reference: FP32 rounding differs
+ * from the FP64 definition by about 1e-7 per step. */
+static inline float atf(const float *f, int64_t nx, int64_t ny, int64_t nz, int64_t x, int64_t y, int64_t z)
+{
+    if (x < 0 || x >= nx || y < 0 || y >= ny || z < 0 || z >= nz)
+        return 0.0f;
+    return f[(z * ny + y) * nx + x];
+}
+
+void oracle_heat7_run_f32(float *u, float *tmp, int64_t nx, int64_t ny, int64_t nz, float r, int64_t nsteps)
+{
+    for (int64_t s = 0; s < nsteps; s++) {
+        float *in = (s & 1) ? tmp : u, *out = (s & 1) ? u : tmp;
+#pragma omp parallel for schedule(static)
+        for (int64_t z = 0; z < nz; z++)
+            for (int64_t y = 0; y < ny; y++)
+                for (int64_t x = 0; x < nx; x++) {
+                    float c = atf(in, nx, ny, nz, x, y, z);
+                    float sum = atf(in, nx, ny, nz, x - 1, y, z) + atf(in, nx, ny, nz, x + 1, y, z) +
+                                atf(in, nx, ny, nz, x, y - 1, z) + atf(in, nx, ny, nz, x, y + 1, z) +
+                                atf(in, nx, ny, nz, x, y, z - 1) + atf(in, nx, ny, nz, x, y, z + 1);
+                    out[(z * ny + y) * nx + x] = c + r * (sum - 6.0f * c);
+                }
+    }
+    if (nsteps & 1) {
+        int64_t n = nx * ny * nz;
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; i++)
+            u[i] = tmp[i];
+    }
+}
+
 /* nsteps leapfrog steps.  On entry (p, p_prev) = (p^t, p^{t-1}); on return
  * (p^{t+nsteps}, p^{t+nsteps-1}).  Step j (0-based) adds w[t0 + j] at src,
  * where w has at least t0 + nsteps entries (or is NULL). */

@@ -229,3 +229,25 @@ def test_paper_rates_are_fr4_rates_for_float():
         rate = int(round(32 / ratio))
         x = np.random.default_rng(bits).normal(size=shape).astype(np.float32)
         assert oracle.fr4_encode(x, rate).nbytes * ratio == fp32
+
+
+def test_heat7_fp32_variant_is_the_fp32_update():
+    # The FP32 CPU variant (timed beside the FP64 oracle) computes the same
+    # update in float arithmetic: bit for bit the numpy float32 evaluation
+    # with the same association (the oracle is compiled without contraction),
+    # and within FP32 rounding of the FP64 definition.
+    rng = np.random.default_rng(17)
+    u0 = rng.normal(size=(10, 12, 14)).astype(np.float32)
+    r = np.float32(1.0 / 6.0)
+    u = u0.copy()
+    for _ in range(3):
+        p = np.pad(u, 1)  # zero ghosts
+        s = (p[1:-1, 1:-1, :-2] + p[1:-1, 1:-1, 2:]) + p[1:-1, :-2, 1:-1]
+        s = ((s + p[1:-1, 2:, 1:-1]) + p[:-2, 1:-1, 1:-1]) + p[2:, 1:-1, 1:-1]
+        u = (u + r * (s - np.float32(6.0) * u)).astype(np.float32)
+    got = oracle.heat7_run_f32(u0, 3)
+    assert got.dtype == np.float32
+    assert np.array_equal(got.view(np.uint32), u.view(np.uint32))
+    ref = oracle.heat7_run(u0.astype(np.float64), 5)
+    got5 = oracle.heat7_run_f32(u0, 5)
+    assert np.abs(got5 - ref).max() <= 1e-6 * np.abs(ref).max()
