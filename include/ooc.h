@@ -93,9 +93,12 @@ typedef struct {
     int32_t graph_mode;          /* 0 = heat7 calls without profiling are captured once per distinct
                                     nsteps as a CUDA graph and replayed; 1 = always launch directly */
     int32_t debug_checks;        /* 1 = guard words after every region of the device arena, checked on
-                                    the device after each ooc_step / ooc_set_field / ooc_get_field,
-                                    and host checks of every launch's plane window and every copy's
-                                    byte range; a failure returns OOC_E_CORRUPT.  0 = off */
+                                    the device after each ooc_step / ooc_set_field / ooc_get_field
+                                    (a failure returns OOC_E_CORRUPT), and ooc_set_field checks
+                                    that every input value is finite (OOC_E_INVALID otherwise; the
+                                    field's stored contents are then unspecified).  The host checks
+                                    of every launch's plane window and every copy's byte range run
+                                    in every plan (OOC_E_CORRUPT).  0 = off */
     int32_t precision;           /* OOC_PREC_FP32 (0) or OOC_PREC_FP64 */
 } ooc_config;
 

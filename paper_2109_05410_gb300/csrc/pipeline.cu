@@ -24,6 +24,7 @@
 // ordered by events.  FP32 slabs land directly in the ring (no staging);
 // BF16/FR4 slabs go through double-buffered staging and a decode kernel.
 #include <chrono>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -55,6 +56,20 @@ __global__ void check_guards_kernel(const unsigned char *base, GuardList g, int 
         const uint32_t w = reinterpret_cast<const uint32_t *>(base + g.off[i])[threadIdx.x];
         if (w != 0xA5A5A5A5u)
             atomicOr(flag, 1);
+    }
+}
+
+// debug_checks: sets bit 2 of *flag when a value of the n 32-bit words at w
+// is not finite (exponent bits all ones).  FP32 values are every word; FP64
+// values have their exponent in the high word of each pair (stride 2).
+__global__ void check_finite_kernel(const uint32_t *w, int64_t n, int stride, int *flag)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i * stride < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = w[i * stride + stride - 1];
+        const uint32_t e = stride == 1 ? 0x7f800000u : 0x7ff00000u;
+        if ((v & e) == e)
+            atomicOr(flag, 2);
     }
 }
 
@@ -268,11 +283,10 @@ ooc_status arm_guards(ooc_plan *p)
 
 ooc_status check_guards(ooc_plan *p);
 
-// Host-side debug check of an internal invariant.
-inline ooc_status expect(const ooc_plan *p, bool ok)
-{
-    return (!p->cfg.debug_checks || ok) ? OOC_OK : OOC_E_CORRUPT;
-}
+// Host-side check of an internal invariant of the schedule (a window that
+// leaves its ring, a unit outside the host image, a staging overflow): the
+// call returns OOC_E_CORRUPT before anything reaches the GPU.
+inline ooc_status expect(const ooc_plan *, bool ok) { return ok ? OOC_OK : OOC_E_CORRUPT; }
 
 ooc_status prof_begin(ooc_plan *p, cudaStream_t st, int kind, size_t *idx)
 {
@@ -627,7 +641,13 @@ ooc_status check_guards(ooc_plan *p)
     OOC_TRY(wait_event(p, p->ev_done));
     int flag = 0;
     OOC_CUDA(cudaMemcpy(&flag, p->dev + p->off_flag, sizeof(int), cudaMemcpyDeviceToHost));
-    return flag ? OOC_E_CORRUPT : OOC_OK;
+    if (flag & 1)
+        return OOC_E_CORRUPT;
+    if (flag & 2) {  // a non-finite input value (ooc_set_field): reported once
+        OOC_CUDA(cudaMemset(p->dev + p->off_flag, 0, sizeof(int)));
+        return OOC_E_INVALID;
+    }
+    return OOC_OK;
 }
 
 void drop_graph(ooc_plan *p)
@@ -876,6 +896,23 @@ namespace {
 
 // ooc_set_field / ooc_set_field64: host_src holds nx*ny*nz values of the
 // plan's precision.
+// debug_checks on fields stored raw: every value finite (FP32 or FP64)
+bool all_finite(const void *src, int64_t n, int esize)
+{
+    if (esize == 8) {
+        const double *d = (const double *)src;
+        for (int64_t i = 0; i < n; ++i)
+            if (!std::isfinite(d[i]))
+                return false;
+        return true;
+    }
+    const float *f = (const float *)src;
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(f[i]))
+            return false;
+    return true;
+}
+
 ooc_status set_field_impl(ooc_plan *p, int field, const void *host_src)
 {
     if (!p || !p->bound || !host_src || field < 0 || field >= p->nfield)
@@ -885,6 +922,8 @@ ooc_status set_field_impl(ooc_plan *p, int field, const void *host_src)
     const size_t pb = (size_t)p->plane_elems * p->esize;
     char *img = p->host + p->off_host[field];
     if (!staged(p, field)) {
+        if (p->cfg.debug_checks && !all_finite(host_src, p->plane_elems * nz, p->esize))
+            return OOC_E_INVALID;
         std::memcpy(img, host_src, pb * nz);
         return OOC_OK;
     }
@@ -906,6 +945,12 @@ ooc_status set_field_impl(ooc_plan *p, int field, const void *host_src)
         OOC_CUDA(cudaStreamWaitEvent(sC, p->ev_h2d[e], 0));
         if (j >= 2)
             OOC_CUDA(cudaStreamWaitEvent(sC, p->ev_d2h[e2], 0));
+        if (p->cfg.debug_checks) {  // the slab fills ring slots 0 .. z1 - z0 - 1
+            check_finite_kernel<<<152 * 4, 256, 0, sC>>>((const uint32_t *)(p->dev + p->off_ring[b]),
+                                                         (z1 - z0) * (int64_t)(pb / 4), p->esize / 4,
+                                                         (int *)(p->dev + p->off_flag));
+            OOC_CUDA(cudaGetLastError());
+        }
         char *stage = p->dev + p->off_in[b][field];
         OOC_TRY(encode_from(p, field, b, zb, stage, z0, z1, sC));
         OOC_CUDA(cudaEventRecord(p->ev_comp[e], sC));

@@ -769,3 +769,44 @@ def test_debug_guard_overwrite_is_reported(ooc):
     finally:
         torch.cuda.synchronize()
         plan.close()
+
+
+@pytest.mark.parametrize("fmt,rate", [("fr4", 16), ("fp32", 16), ("bf16", 16)])
+def test_debug_checks_refuse_non_finite_input(ooc, fmt, rate):
+    # With debug_checks, a NaN or infinity in ooc_set_field's input returns
+    # OOC_E_INVALID (checked on the device for staged formats, on the host
+    # for FP32 storage); the next finite field is accepted.  Without debug
+    # checks the call does not look.
+    u = np.random.default_rng(5).normal(size=(16, 12, 20)).astype(np.float32)
+    for bad in (np.nan, np.inf):
+        v = u.copy()
+        v[9, 3, 17] = bad
+        plan = ooc.Plan(nx=20, ny=12, nz=16, stencil="heat7", k=2, rw_format=fmt, rw_rate=rate, slab_planes=8,
+                        debug_checks=1)
+        try:
+            with pytest.raises(ooc.OocError) as err:
+                plan.set_field(0, v)
+            assert err.value.status == 1
+            plan.set_field(0, u)
+            plan.step(2)
+        finally:
+            plan.close()
+        quiet = ooc.Plan(nx=20, ny=12, nz=16, stencil="heat7", k=2, rw_format=fmt, rw_rate=rate, slab_planes=8)
+        try:
+            quiet.set_field(0, v)
+        finally:
+            quiet.close()
+    assert ooc.ooc_take_device_fault() == 0
+
+
+def test_fp64_debug_checks_refuse_non_finite_input(ooc):
+    u = np.random.default_rng(6).normal(size=(8, 8, 12))
+    u[2, 5, 7] = -np.inf
+    plan = ooc.Plan(nx=12, ny=8, nz=8, stencil="heat7", k=2, rw_format="fp64", rw_rate=64, slab_planes=4,
+                    precision="fp64", debug_checks=1)
+    try:
+        with pytest.raises(ooc.OocError) as err:
+            plan.set_field(0, u)
+        assert err.value.status == 1
+    finally:
+        plan.close()
