@@ -47,6 +47,29 @@ def test_encode_decode_bit_exact(ooc, kind, rate):
     assert np.array_equal(got_x.view(np.uint32), ref_x.view(np.uint32))
 
 
+@pytest.mark.parametrize("kind,rate", [(k, 16) for k in KINDS] + [("normal", 8), ("normal", 24), ("smooth", 8),
+                                                                    ("smooth", 24)])
+def test_million_blocks_bit_exact(ooc, kind, rate):
+    # 10^6 blocks of each class, streams and decoded values word for word
+    # against the oracle.  Smooth blocks are cut from a smooth field (the
+    # same block order on both sides); the other classes come from the
+    # block generator.
+    n = 1_000_000
+    if kind == "smooth":
+        x = smooth_random_field((40, 1000, 1600), 3.0, seed=rate, nterms=64)
+        assert x.size == 64 * n
+    else:
+        x = random_blocks(kind, n, seed=rate * 7 + len(kind))
+    ref_w = oracle.fr4_encode(x, rate)
+    got_w = gpu_encode(ooc, x, rate)
+    assert got_w.size == n * 2 * rate
+    mism = np.flatnonzero(got_w != ref_w)
+    assert mism.size == 0, f"{mism.size} words differ, first at block {mism[0] // (2 * rate)}"
+    ref_x = oracle.fr4_decode(ref_w, x.shape, rate)
+    got_x = gpu_decode(ooc, ref_w, x.shape, rate)
+    assert np.array_equal(got_x.view(np.uint32), ref_x.view(np.uint32))
+
+
 @pytest.mark.parametrize("shape", [(4, 4, 4), (12, 20, 36), (8, 4, 132), (36, 28, 8)])
 def test_non_cubic_shapes(ooc, shape):
     x = smooth_random_field(shape, 3.0, seed=sum(shape)).astype(np.float32)

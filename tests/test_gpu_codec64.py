@@ -48,6 +48,26 @@ def test_encode_decode_bit_exact(ooc, kind, rate):
     assert np.array_equal(got_x.view(np.uint64), ref_x.view(np.uint64))
 
 
+@pytest.mark.parametrize("kind,rate", [(k, 32) for k in KINDS] + [("normal", 24), ("smooth", 24)])
+def test_million_blocks_bit_exact(ooc, kind, rate):
+    # 10^6 blocks of each class at the paper's 32 (and 24) of 64 bits,
+    # streams and values word for word against the oracle; smooth blocks are
+    # cut from a smooth FP64 field
+    n = 1_000_000
+    if kind == "smooth":
+        x = smooth_random_field((40, 1000, 1600), 3.0, seed=rate, nterms=64, dtype=np.float64)
+    else:
+        x = random_blocks64(kind, n, seed=rate * 5 + len(kind))
+    ref_w = oracle.fr4d_encode(x, rate)
+    got_w = gpu_encode(ooc, x, rate)
+    assert got_w.size == n * 2 * rate
+    mism = np.flatnonzero(got_w != ref_w)
+    assert mism.size == 0, f"{mism.size} words differ, first at block {mism[0] // (2 * rate)}"
+    ref_x = oracle.fr4d_decode(ref_w, x.shape, rate)
+    got_x = gpu_decode(ooc, ref_w, x.shape, rate)
+    assert np.array_equal(got_x.view(np.uint64), ref_x.view(np.uint64))
+
+
 @pytest.mark.parametrize("shape", [(4, 4, 4), (12, 20, 36), (8, 4, 132), (36, 28, 8)])
 def test_fields_of_several_shapes(ooc, shape):
     x = smooth_random_field(shape, 3.0, seed=sum(shape), dtype=np.float64)
