@@ -360,7 +360,7 @@ ooc_status encode_from(ooc_plan *p, int f, int r, int64_t zb, char *dst, int64_t
 
 // Ring holding field f's input level (heat: u -> ring 0; wave: p^t -> 0,
 // p^{t-1} -> 1, kappa -> 2) and its output after a pass of kp steps.
-int input_ring(const ooc_plan *p, int f) { return f; }
+int input_ring(const ooc_plan *, int f) { return f; }
 int output_ring(const ooc_plan *p, int f, int64_t kp)
 {
     if (f == 0)
