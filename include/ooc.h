@@ -90,8 +90,10 @@ typedef struct {
                                       intermediate level kept on chip; 1 = one step per launch; 0 =
                                       default = 2 when k >= 2, else 1.  Results are bit-identical.
                                       wave25: 0 or 1. */
-    int32_t graph_mode;          /* 0 = heat7 calls without profiling are captured once per distinct
-                                    nsteps as a CUDA graph and replayed; 1 = always launch directly */
+    int32_t graph_mode;          /* 0 = calls without profiling are captured once per distinct nsteps
+                                    as a CUDA graph and replayed (heat7 always; wave25 when its
+                                    source series fits the device table of 16384 amplitudes, or
+                                    it has no source); 1 = always launch directly */
     int32_t debug_checks;        /* 1 = guard words after every region of the device arena, checked on
                                     the device after each ooc_step / ooc_set_field / ooc_get_field
                                     (a failure returns OOC_E_CORRUPT), and ooc_set_field checks
