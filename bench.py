@@ -335,6 +335,7 @@ def wave1024_summary(torch, ooc, nsteps=100, reps=2):
     w = (ricker(nsteps * (reps + 1), dt) * float(kappa[src[2], src[1], src[0]])).astype(np.float32)
     zero = np.zeros((n, n, n), dtype=np.float32)
     out = {}
+    fields = {}
     for name, (rw, ro) in (("code1_fp32", ("fp32", "fp32")), ("code4_rw_ro_fr4-16", ("fr4", "fr4"))):
         plan = ooc.Plan(nx=n, ny=n, nz=n, stencil="wave25", k=k, rw_format=rw, rw_rate=16, ro_format=ro, ro_rate=16,
                         device_budget_bytes=4 << 30)
@@ -346,13 +347,28 @@ def wave1024_summary(torch, ooc, nsteps=100, reps=2):
             plan.step(nsteps)
             ms = timed_steps(torch, plan, nsteps, reps)
             out[name] = n ** 3 * nsteps / (statistics.mean(ms) / 1e3) / 1e9
+            fields[name] = plan.get_field(0)
         finally:
             plan.close()
         del plan
         torch.cuda.empty_cache()
     out["speedup_code4_vs_code1"] = out["code4_rw_ro_fr4-16"] / out["code1_fp32"]
+    # both codes' p after the same steps against an FP64 run of them (the
+    # library's FP64 wave kernel, held to the FP64 oracle by the GPU tests)
+    total = nsteps * (reps + 1)
+    p64 = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
+    pp64 = torch.zeros_like(p64)
+    ooc.ooc_wave25_steps_f64(p64, pp64, torch.from_numpy(kappa.astype(np.float64)).cuda(), total, src=src,
+                             w=w.astype(np.float64))
+    torch.cuda.synchronize()
+    del pp64
+    for name, f in fields.items():
+        out[f"{name}_rel_l2_vs_fp64"] = field_errors(torch.from_numpy(f).cuda(), p64)["rel_l2"]
+    del fields, p64
+    torch.cuda.empty_cache()
     out["what"] = (f"wave25 1024^3, 4 GiB budget, k = {k}, {reps} timed calls of {nsteps} steps after one untimed; "
-                   "bench.py --workload wave1024 has the full study")
+                   f"errors of p after all {total} steps against an FP64 run; "
+                   "bench.py --workload wave1024 and wave1024_error have the full study")
     return out
 
 
