@@ -65,6 +65,36 @@ def test_heat7_fused_pairs_bit_identical(ooc, shape, nsteps):
     assert np.array_equal(a.cpu().numpy().view(np.uint32), b.cpu().numpy().view(np.uint32))
 
 
+@pytest.mark.parametrize("scale", ["subnormal", "mixed", "large"])
+def test_heat7_fused_pairs_bit_identical_on_special_values(ooc, scale):
+    # The fused pairs compute their point updates in packed FP32 pairs, the
+    # single steps in scalar FP32; neither flushes subnormals, and both round
+    # each operation to nearest even.  Fields of subnormals (with +-0 and
+    # signs mixed), of values spread over the whole exponent range, and of
+    # values near the top of the range (sums of six stay finite) give the
+    # same bits.
+    g = np.random.default_rng({"subnormal": 1, "mixed": 2, "large": 3}[scale])
+    shape = (20, 36, 260)
+    if scale == "subnormal":
+        u0 = (g.standard_normal(shape) * 1e-40).astype(np.float32)
+        u0[g.random(shape) < 0.1] = 0.0
+        u0[g.random(shape) < 0.05] = -0.0
+    elif scale == "mixed":
+        u0 = (g.standard_normal(shape) * 10.0 ** g.integers(-44, 38, size=shape)).astype(np.float32)
+    else:
+        u0 = (g.uniform(-1.0, 1.0, shape) * 5e37).astype(np.float32)
+    assert np.all(np.isfinite(u0))
+    a = torch.from_numpy(u0).cuda()
+    b = a.clone()
+    ooc.ooc_heat7_steps(a, torch.empty_like(a), 4)
+    ooc.ooc_heat7_steps_fused(b, torch.empty_like(b), 4)
+    torch.cuda.synchronize()
+    got_a, got_b = a.cpu().numpy(), b.cpu().numpy()
+    if scale == "subnormal":
+        assert np.any((got_a != 0) & (np.abs(got_a) < np.finfo(np.float32).tiny))  # subnormals survive
+    assert np.array_equal(got_a.view(np.uint32), got_b.view(np.uint32))
+
+
 def test_heat7_fused_matches_fp64(ooc):
     u0, _ = sine_modes_field((64, 72, 136), seed=2)
     d = torch.from_numpy(u0).cuda()
