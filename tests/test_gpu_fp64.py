@@ -376,3 +376,94 @@ def test_fp64_wave_degenerate_plans(ooc, shape, T, k, calls):
     assert np.abs(got_p).max() > 0
     assert np.array_equal(got_p.view(np.uint64), p.cpu().numpy().view(np.uint64))
     assert np.array_equal(got_pp.view(np.uint64), pp.cpu().numpy().view(np.uint64))
+
+
+def test_full_size_fp64_heat_configuration(ooc):
+    # The fp64 workload's heat configuration at its size: 1024^3 FP64, 2 GiB
+    # device budget, k = 4, FR4D at 32 of 64 bits, one call of 32 steps.
+    # Bit-identical over the whole field to the in-core FP64 kernel with the
+    # same round trips (compared on the device), and on the central 128^3
+    # sub-box (exact dependency cone) within FR4D-32's storage error of the
+    # FP64 oracle run without storage.
+    n, k, nsteps, rate = 1024, 4, 32, 32
+    u0 = smooth_random_field((n, n, n), 32.0, seed=2, dtype=np.float64)
+    plan = ooc.Plan(nx=n, ny=n, nz=n, stencil="heat7", k=k, rw_format="fr4", rw_rate=rate,
+                    device_budget_bytes=2 << 30, precision="fp64")
+    try:
+        assert plan.device_bytes <= 2 << 30 and plan.info()["nslab"] > 1
+        plan.set_field(0, u0)
+        plan.step(nsteps)
+        got = plan.get_field(0)
+    finally:
+        plan.close()
+    u = roundtrip64(ooc, torch.from_numpy(u0).cuda(), "fr4", rate)
+    tmp = torch.empty_like(u)
+    for kp in pass_lengths([nsteps], k):
+        ooc.ooc_heat7_steps_f64(u, tmp, kp)
+        u = roundtrip64(ooc, u, "fr4", rate)
+    del tmp
+    g = torch.from_numpy(got).cuda()
+    assert torch.equal(g.view(torch.int64), u.view(torch.int64))
+    del g, u
+    torch.cuda.empty_cache()
+    c0, c1 = n // 2 - 64, n // 2 + 64
+    sub = u0[c0 - nsteps:c1 + nsteps, c0 - nsteps:c1 + nsteps, c0 - nsteps:c1 + nsteps]
+    exact = oracle.heat7_run(sub, nsteps)[nsteps:-nsteps, nsteps:-nsteps, nsteps:-nsteps]
+    m = oracle.error_metrics(got[c0:c1, c0:c1, c0:c1], exact)
+    assert m["rel_l2"] < 1e-7, m
+
+
+def test_full_size_fp64_wave_configuration(ooc):
+    # The fp64 workload's wave configuration at its size: 1024^3 FP64, 8 GiB
+    # budget, k = 10, code 4 (both levels and kappa FR4D-32), from rest with
+    # the source, 20 steps.  Bit-identical over the whole field to the
+    # in-core FP64 kernel with the same round trips; and the central 32^3
+    # box against the FP64 oracle run without storage on a 208^3 sub-box
+    # (20 steps move information 80 cells, the field is zero beyond that
+    # from the source, so the sub-box's zero ghosts are exact).
+    from synth import layered_velocity
+    n, k, nsteps, rate, m = 1024, 10, 20, 32, 104
+    v = layered_velocity((n, n, n), seed=3)
+    dt = 0.4 * 10.0 / float(v.max())
+    kappa = (np.asarray(v, dtype=np.float64) * (dt / 10.0)) ** 2
+    del v
+    src = (n // 2, n // 2, n // 2)
+    w = (ricker(nsteps, dt) * float(kappa[src[2], src[1], src[0]])).astype(np.float32)
+    zero = np.zeros((n, n, n), dtype=np.float64)
+    plan = ooc.Plan(nx=n, ny=n, nz=n, stencil="wave25", k=k, rw_format="fr4", rw_rate=rate, ro_format="fr4",
+                    ro_rate=rate, device_budget_bytes=8 << 30, precision="fp64")
+    try:
+        assert plan.device_bytes <= 8 << 30 and plan.info()["nslab"] > 1
+        plan.set_field(0, zero)
+        plan.set_field(1, zero)
+        plan.set_field(2, kappa)
+        plan.set_source(*src, w)
+        plan.step(nsteps)
+        got = plan.get_field(0)
+    finally:
+        plan.close()
+    del zero
+    kap = roundtrip64(ooc, torch.from_numpy(kappa).cuda(), "fr4", rate)
+    p = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
+    pp = torch.zeros_like(p)
+    w64 = w.astype(np.float64)
+    t = 0
+    for kp in pass_lengths([nsteps], k):
+        ooc.ooc_wave25_steps_f64(p, pp, kap, kp, src=src, w=w64, t=t)
+        t += kp
+        p = roundtrip64(ooc, p, "fr4", rate)
+        pp = roundtrip64(ooc, pp, "fr4", rate)
+    del kap, pp
+    g = torch.from_numpy(got).cuda()
+    assert torch.equal(g.view(torch.int64), p.view(torch.int64))
+    del g, p
+    torch.cuda.empty_cache()
+    lo = [c - m for c in src]
+    box = (slice(lo[2], lo[2] + 2 * m), slice(lo[1], lo[1] + 2 * m), slice(lo[0], lo[0] + 2 * m))
+    srcf = (m * 2 * m + m) * 2 * m + m
+    exact, _ = oracle.wave25_run(np.zeros((2 * m,) * 3), np.zeros((2 * m,) * 3), kappa[box], nsteps, src=srcf,
+                                 w=w64)
+    cen = (slice(m - 16, m + 16),) * 3
+    e = oracle.error_metrics(got[box][cen], exact[cen])
+    assert np.abs(exact[cen]).max() > 0
+    assert e["rel_l2"] < 1e-6, e
