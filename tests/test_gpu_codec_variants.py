@@ -118,3 +118,22 @@ def test_corrupt_index_decodes_without_fault(ooc):
     out = ooc.ooc_decompress_var(stream, bad, (12, 12, 12), ooc.OOC_FR4_PRECISION, 16)
     torch.cuda.synchronize()
     assert out.shape == (12, 12, 12)
+
+
+@pytest.mark.parametrize("mode,param", [(1, 16), (2, 1e-4)])
+def test_variable_modes_full_size(ooc, mode, param):
+    # The 512^3 field the kernel workload times (2 M blocks, 16 K tiles of
+    # the one-pass encoder's look-back): the whole stream and index word for
+    # word against the oracle, and the decoded field.
+    n = 512
+    f = smooth_random_field((n, n, n), 32.0, seed=2)
+    d = torch.from_numpy(f).cuda()
+    stream, index = ooc.ooc_compress_var(d, mode, param)
+    torch.cuda.synchronize()
+    words_ref, index_ref = oracle.fr4_encode_var(f, mode, param)
+    assert np.array_equal(index.cpu().numpy().astype(np.uint64), index_ref)
+    assert np.array_equal(stream.cpu().numpy().view(np.uint32), words_ref)
+    got = ooc.ooc_decompress_var(stream, index, f.shape, mode, param).cpu().numpy()
+    ref = oracle.fr4_decode_var(words_ref, index_ref, f.shape, mode, param)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+    assert ooc.ooc_take_device_fault() == 0
