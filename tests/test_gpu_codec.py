@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
-from synth import random_blocks, smooth_random_field, sine_modes_field
+from synth import random_blocks, smooth_random_field
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu

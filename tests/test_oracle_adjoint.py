@@ -3,7 +3,6 @@
 differences of the misfit in random directions, and a per-entry brute force
 gradient on 8^3."""
 import numpy as np
-import pytest
 
 import oracle
 from synth import ricker
