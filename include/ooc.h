@@ -27,6 +27,11 @@
  *     GPU that loads it, outside any plan's budget.
  *   - Every function returns an ooc_status and never aborts the process.
  *   - Streams are cudaStream_t passed as void* (0 = legacy default stream).
+ *   - Threads: different plans, and in-core calls on distinct buffers, may
+ *     run at the same time from different host threads; the library's
+ *     process-wide state (launch constants, the tensor-map cache) is set up
+ *     once, thread-safely.  Calls on one plan must not overlap.  The device
+ *     fault words (ooc_take_device_fault) are per process.
  */
 #ifndef OOC_H
 #define OOC_H

@@ -970,17 +970,16 @@ size_t smem_bytes64(int rate, bool encoder)
 
 cudaError_t ensure_smem_attr64()
 {
-    static bool done = false;
-    if (done)
-        return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(fr4d_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_bytes64(64, true));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fr4d_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_bytes64(64, false));
-    if (e == cudaSuccess)
-        done = true;
-    return e;
+    // set once per process (thread-safe); the attribute is per function
+    static const cudaError_t once = [] {
+        cudaError_t e = cudaFuncSetAttribute(fr4d_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem_bytes64(64, true));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(fr4d_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_bytes64(64, false));
+        return e;
+    }();
+    return once;
 }
 
 // ---- dense fields of any shape, fixed rate and variable-size modes -------------
@@ -1214,20 +1213,19 @@ size_t dense_smem_bytes(int words, bool encoder)
 
 cudaError_t ensure_dense_smem_attr()
 {
-    static bool done = false;
-    if (done)
-        return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(fr4_encode_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)dense_smem_bytes(kVarWords, true));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fr4_encode_var_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)dense_smem_bytes(kVarWords, true));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fr4_decode_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)dense_smem_bytes(kVarWords, false));
-    if (e == cudaSuccess)
-        done = true;
-    return e;
+    // set once per process (thread-safe); the attribute is per function
+    static const cudaError_t once = [] {
+        cudaError_t e = cudaFuncSetAttribute(fr4_encode_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)dense_smem_bytes(kVarWords, true));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(fr4_encode_var_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)dense_smem_bytes(kVarWords, true));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(fr4_decode_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)dense_smem_bytes(kVarWords, false));
+        return e;
+    }();
+    return once;
 }
 
 // Shared memory per CTA (encoder): each thread's compressed words plus
@@ -1243,20 +1241,19 @@ size_t smem_bytes(int rate, bool encoder)
 
 cudaError_t ensure_smem_attr()
 {
-    static bool done = false;  // per process; the attribute is per function
-    if (done)
-        return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(fr4_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_bytes(64, true));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fr4_decode_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_bytes(64, false));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fr4_decode_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_bytes(64, false));
-    if (e == cudaSuccess)
-        done = true;
-    return e;
+    // set once per process (thread-safe); the attribute is per function
+    static const cudaError_t once = [] {
+        cudaError_t e = cudaFuncSetAttribute(fr4_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem_bytes(64, true));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(fr4_decode_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_bytes(64, false));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(fr4_decode_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_bytes(64, false));
+        return e;
+    }();
+    return once;
 }
 
 }  // namespace

@@ -367,15 +367,16 @@ cudaError_t launch_heat7x2(ConstRing in, Ring out, int64_t nx, int64_t ny, int64
         return cudaSuccess;
     constexpr int NW = kX2tNW;
     constexpr int TYO = X2t::tyo;
-    static int res = 0;
     const size_t smem = heat7x2t_smem_bytes();
-    if (res == 0) {
-        const cudaError_t e = cudaFuncSetAttribute(heat7x2t_kernel<kX2tNS, kX2tR, kX2tNW>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess)
-            return e;
-        res = resident((const void *)heat7x2t_kernel<kX2tNS, kX2tR, kX2tNW>, kTX * NW, smem);
-    }
+    // set once (thread-safe); 0 if the attribute could not be set
+    static const int res = [smem]() -> int {
+        if (cudaFuncSetAttribute(heat7x2t_kernel<kX2tNS, kX2tR, kX2tNW>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return 0;
+        return resident((const void *)heat7x2t_kernel<kX2tNS, kX2tR, kX2tNW>, kTX * NW, smem);
+    }();
+    if (res <= 0)
+        return cudaErrorInvalidValue;
     const int64_t gx = (nx + kSeg - 9) / (kSeg - 8), gy = (ny + TYO - 1) / TYO;
     const int64_t chunk = choose_chunk(gx * gy, z1 - z0, 8, 5, res);
     if (in.nslot != out.nslot || in.zbase != out.zbase || in.nslot > (1ll << 30) || in.base == out.base ||

@@ -721,9 +721,7 @@ cudaError_t launch_heat7(ConstRing in, Ring out, int64_t nx, int64_t ny, int64_t
 {
     if (z1 <= z0)
         return cudaSuccess;
-    static int res = 0;
-    if (res == 0)
-        res = resident((const void *)heat7_kernel, kTX * kHeatTY);
+    static const int res = resident((const void *)heat7_kernel, kTX * kHeatTY);  // once, thread-safe
     const int64_t gx = (nx + kSeg - 1) / kSeg, gy = (ny + kHeatTY - 1) / kHeatTY;
     const int64_t chunk = choose_chunk(gx * gy, z1 - z0, 8, 3, res);
     const int64_t gz = (z1 - z0 + chunk - 1) / chunk;
@@ -746,14 +744,10 @@ cudaError_t launch_heat7x2_regs(ConstRing in, Ring out, int64_t nx, int64_t ny, 
 #if OOC_HEATX2_ROWS != 1
     constexpr int NW = kHeatX2NW;
     constexpr int TYO = 2 * NW - 2;
-    static int res = 0;
-    if (res == 0)
-        res = resident((const void *)heat7x2r_kernel<NW>, kTX * NW);
+    static const int res = resident((const void *)heat7x2r_kernel<NW>, kTX * NW);  // once, thread-safe
 #else
     constexpr int TYO = kHeatX2TY;
-    static int res = 0;
-    if (res == 0)
-        res = resident((const void *)heat7x2_kernel<TYO>, kTX * (TYO + 2));
+    static const int res = resident((const void *)heat7x2_kernel<TYO>, kTX * (TYO + 2));  // once, thread-safe
 #endif
     const int64_t gx = (nx + kSeg - 9) / (kSeg - 8), gy = (ny + TYO - 1) / TYO;
     const int64_t chunk = choose_chunk(gx * gy, z1 - z0, 8, 5, res);
@@ -784,13 +778,15 @@ cudaError_t launch_wave25_to(ConstRing p, ConstRing pprev, Ring pnew, ConstRing 
 {
     if (z1 <= z0)
         return cudaSuccess;
-    static int res = 0;
-    if (res == 0) {
+    // set once (thread-safe); 0 if the attribute could not be set
+    static const int res = []() -> int {
         if (cudaFuncSetAttribute(wave25_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(WaveSmem)) != cudaSuccess)
-            return cudaErrorInvalidValue;
-        res = resident((const void *)wave25_kernel<0>, kTX * kWaveTY, sizeof(WaveSmem));
-    }
+            return 0;
+        return resident((const void *)wave25_kernel<0>, kTX * kWaveTY, sizeof(WaveSmem));
+    }();
+    if (res <= 0)
+        return cudaErrorInvalidValue;
     const int64_t gx = (nx + kSeg - 1) / kSeg, gy = (ny + kWaveTY - 1) / kWaveTY;
     const int64_t chunk = choose_chunk(gx * gy, z1 - z0, 16, 9, res);
     const int64_t gz = (z1 - z0 + chunk - 1) / chunk;
@@ -806,13 +802,15 @@ cudaError_t launch_wave25_to(ConstRing p, ConstRing pprev, Ring pnew, ConstRing 
 cudaError_t launch_wave25_grad(const float *p, const float *mu, double *g, int64_t nx, int64_t ny, int64_t nz,
                                cudaStream_t st)
 {
-    static int res = 0;
-    if (res == 0) {
+    // set once (thread-safe); 0 if the attribute could not be set
+    static const int res = []() -> int {
         if (cudaFuncSetAttribute(wave25_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(WaveSmem)) != cudaSuccess)
-            return cudaErrorInvalidValue;
-        res = resident((const void *)wave25_kernel<1>, kTX * kWaveTY, sizeof(WaveSmem));
-    }
+            return 0;
+        return resident((const void *)wave25_kernel<1>, kTX * kWaveTY, sizeof(WaveSmem));
+    }();
+    if (res <= 0)
+        return cudaErrorInvalidValue;
     const int64_t gx = (nx + kSeg - 1) / kSeg, gy = (ny + kWaveTY - 1) / kWaveTY;
     const int64_t chunk = choose_chunk(gx * gy, nz, 16, 9, res);
     const int64_t gz = (nz + chunk - 1) / chunk;
@@ -827,13 +825,15 @@ cudaError_t launch_wave25_grad(const float *p, const float *mu, double *g, int64
 cudaError_t launch_wave25_grad32(const float *p, const float *mu, float *gacc, int64_t nx, int64_t ny, int64_t nz,
                                  cudaStream_t st)
 {
-    static int res = 0;
-    if (res == 0) {
+    // set once (thread-safe); 0 if the attribute could not be set
+    static const int res = []() -> int {
         if (cudaFuncSetAttribute(wave25_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(WaveSmem)) != cudaSuccess)
-            return cudaErrorInvalidValue;
-        res = resident((const void *)wave25_kernel<2>, kTX * kWaveTY, sizeof(WaveSmem));
-    }
+            return 0;
+        return resident((const void *)wave25_kernel<2>, kTX * kWaveTY, sizeof(WaveSmem));
+    }();
+    if (res <= 0)
+        return cudaErrorInvalidValue;
     const int64_t gx = (nx + kSeg - 1) / kSeg, gy = (ny + kWaveTY - 1) / kWaveTY;
     const int64_t chunk = choose_chunk(gx * gy, nz, 16, 9, res);
     const int64_t gz = (nz + chunk - 1) / chunk;

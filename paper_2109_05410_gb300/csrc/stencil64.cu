@@ -255,9 +255,7 @@ cudaError_t launch_heat7_f64_ring(DConstRing in, DRing out, int64_t nx, int64_t 
 {
     if (z1 <= z0)
         return cudaSuccess;
-    static int res = 0;
-    if (res == 0)
-        res = resident((const void *)heat7_f64_kernel, kTX * kTY64);
+    static const int res = resident((const void *)heat7_f64_kernel, kTX * kTY64);  // once, thread-safe
     const int64_t gx = (nx + kSeg64 - 1) / kSeg64, gy = (ny + kTY64 - 1) / kTY64;
     const int64_t chunk = choose_chunk(gx * gy, z1 - z0, 8, 2, res);
     const int64_t gz = (z1 - z0 + chunk - 1) / chunk;
@@ -281,9 +279,7 @@ cudaError_t launch_wave25_f64(DConstRing p, DRing pprev_out, DConstRing kappa, i
 {
     if (z1 <= z0)
         return cudaSuccess;
-    static int res = 0;
-    if (res == 0)
-        res = resident((const void *)wave25_f64_kernel, kTX * kWTY64);
+    static const int res = resident((const void *)wave25_f64_kernel, kTX * kWTY64);  // once, thread-safe
     const int64_t gx = (nx + kSeg64 - 1) / kSeg64, gy = (ny + kWTY64 - 1) / kWTY64;
     const int64_t chunk = choose_chunk(gx * gy, z1 - z0, 16, 9, res);
     const int64_t gz = (z1 - z0 + chunk - 1) / chunk;

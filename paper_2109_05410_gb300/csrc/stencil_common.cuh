@@ -108,14 +108,12 @@ inline int64_t choose_chunk(int64_t ntiles, int64_t height, int64_t min_chunk, i
 
 inline int resident(const void *fn, int threads, size_t dyn_smem = 0)
 {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
+    static const int sms = [] {  // once, thread-safe
+        int dev = 0, n = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0)
-            sms = 152;
-    }
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        return n > 0 ? n : 152;
+    }();
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, dyn_smem) != cudaSuccess || per_sm <= 0)
         per_sm = 1;

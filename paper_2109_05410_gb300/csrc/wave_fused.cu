@@ -267,13 +267,15 @@ cudaError_t launch_wave25x2(const float *a, const float *b, const float *kap, fl
                             int64_t ny, int64_t nz, int64_t sx, int64_t sy, int64_t sz, float w1, float w2,
                             cudaStream_t st)
 {
-    static int res = 0;
-    if (res == 0) {
+    // set once (thread-safe); 0 if the attribute could not be set
+    static const int res = []() -> int {
         if (cudaFuncSetAttribute(wave25x2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(FusedSmem)) != cudaSuccess)
-            return cudaErrorInvalidValue;
-        res = resident((const void *)wave25x2_kernel, kTX * kFW, sizeof(FusedSmem));
-    }
+            return 0;
+        return resident((const void *)wave25x2_kernel, kTX * kFW, sizeof(FusedSmem));
+    }();
+    if (res <= 0)
+        return cudaErrorInvalidValue;
     const int64_t gx = (nx + kFSeg - 1) / kFSeg, gy = (ny + kFO - 1) / kFO;
     const int64_t chunk = choose_chunk(gx * gy, nz, 24, 17, res);
     const int64_t gz = (nz + chunk - 1) / chunk;

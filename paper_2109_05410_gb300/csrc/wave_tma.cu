@@ -274,15 +274,16 @@ cudaError_t launch_wave25t(const float *p, const float *pprev, float *pout, cons
 {
     if (z1 <= z0)
         return cudaSuccess;
-    static int res = 0;
     const size_t smem = wave_tma_smem_bytes();
-    if (res == 0) {
-        const cudaError_t e = cudaFuncSetAttribute(wave25t_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)smem);
-        if (e != cudaSuccess)
-            return e;
-        res = resident((const void *)wave25t_kernel<MODE>, kTX * kWTY, smem);
-    }
+    // set once (thread-safe); 0 if the attribute could not be set
+    static const int res = [smem]() -> int {
+        if (cudaFuncSetAttribute(wave25t_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem) != cudaSuccess)
+            return 0;
+        return resident((const void *)wave25t_kernel<MODE>, kTX * kWTY, smem);
+    }();
+    if (res <= 0)
+        return cudaErrorInvalidValue;
     const int64_t gx = (nx + kSeg - 1) / kSeg, gy = (ny + kWTY - 1) / kWTY;
     const int64_t chunk = choose_chunk(gx * gy, z1 - z0, 16, 9, res);
     const int64_t gz = (z1 - z0 + chunk - 1) / chunk;

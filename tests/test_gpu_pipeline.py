@@ -810,3 +810,58 @@ def test_fp64_debug_checks_refuse_non_finite_input(ooc):
         assert err.value.status == 1
     finally:
         plan.close()
+
+
+def test_plans_run_concurrently_from_two_host_threads(ooc):
+    # Two plans (a heat7 FR4-16 plan and a wave code-4 plan) stepped at the
+    # same time from two host threads, each on its own streams: each gives
+    # the bits of the same plan run alone.  The library's process-wide state
+    # (launch constants, the tensor-map cache, fault words) is initialised
+    # once, thread-safely.
+    import threading
+    n = 96
+    u0 = smooth_random_field((n, n, n), 8.0, seed=31)
+    kappa, p0, pm1, src, w = wave_inputs((n, n, n), 40)
+
+    def heat():
+        plan = ooc.Plan(nx=n, ny=n, nz=n, stencil="heat7", k=4, rw_format="fr4", rw_rate=16, slab_planes=24)
+        try:
+            plan.set_field(0, u0)
+            for _ in range(4):
+                plan.step(8)
+            return plan.get_field(0)
+        finally:
+            plan.close()
+
+    def wave():
+        plan = ooc.Plan(nx=n, ny=n, nz=n, stencil="wave25", k=5, rw_format="fr4", rw_rate=16, ro_format="fr4",
+                        ro_rate=16, slab_planes=24)
+        try:
+            plan.set_field(0, p0)
+            plan.set_field(1, pm1)
+            plan.set_field(2, kappa)
+            plan.set_source(*src, w)
+            for _ in range(4):
+                plan.step(10)
+            return plan.get_field(0)
+        finally:
+            plan.close()
+
+    alone = [heat(), wave()]
+    results, errors = [None, None], []
+
+    def run(i, fn):
+        try:
+            results[i] = fn()
+        except Exception as exc:  # reported below
+            errors.append(exc)
+
+    threads = [threading.Thread(target=run, args=(0, heat)), threading.Thread(target=run, args=(1, wave))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=600)
+    assert not errors, errors
+    for got, want in zip(results, alone):
+        assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+    assert ooc.ooc_take_device_fault() == 0
