@@ -284,8 +284,9 @@ ooc_status ooc_heat7_steps_fused(float *d_u, float *d_tmp, int64_t nx, int64_t n
 /* Reads and clears the library's device fault words on the current device.
  * *fault is a bit set, 0 when nothing went wrong: 1 if a kernel launched
  * since the last read gave up one of its bounded waits (a shared-memory
- * copy that did not arrive within about a second) and returned without
- * writing the rest of its planes; 2 if ooc_gather or ooc_scatter_add met an
+ * copy, or the variable-size encoder's look-back at an earlier tile, that
+ * did not complete within about a second) and returned without writing the
+ * rest of its output; 2 if ooc_gather or ooc_scatter_add met an
  * index outside its field and skipped it.  ooc_step checks the first
  * itself and returns OOC_E_TIMEOUT; callers of the in-core entry points
  * read it after synchronising their stream.  Kernels never trap, spin
