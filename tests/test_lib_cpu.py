@@ -95,6 +95,16 @@ def test_plan_validation(L):
     assert plan_create(L, make_cfg(spl=1, stencil=ooc.OOC_WAVE25, slab_planes=32, k=2))[0] == 0
 
 
+def test_plan_side_limits(L):
+    # Each side may be up to 2^20 points (a multiple of 4); one block more
+    # is refused.  The largest side's plan fits a one-plane-thick slab.
+    big = 1 << 20
+    assert plan_create(L, make_cfg(n=(4, 4, big), k=1, slab_planes=4))[0] == 0
+    assert plan_create(L, make_cfg(n=(big, 4, 4), k=1, slab_planes=4))[0] == 0
+    for n in ((4, 4, big + 4), (4, big + 4, 4), (big + 4, 4, 4)):
+        assert plan_create(L, make_cfg(n=n, k=1, slab_planes=4))[0] == 1
+
+
 def test_fused_pairs_reserve_bands(L):
     # Fused heat7 pairs keep, per pair of the pass and slab parity, the 2h
     # top planes of the intermediate level for the next slab.
