@@ -97,7 +97,7 @@ def test_plan_validation(L):
 
 def test_plan_side_limits(L):
     # Each side may be up to 2^20 points (a multiple of 4); one block more
-    # is refused.  The largest side's plan fits a one-plane-thick slab.
+    # is refused (plans with slabs of 4 planes).
     big = 1 << 20
     assert plan_create(L, make_cfg(n=(4, 4, big), k=1, slab_planes=4))[0] == 0
     assert plan_create(L, make_cfg(n=(big, 4, 4), k=1, slab_planes=4))[0] == 0
